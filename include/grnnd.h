@@ -1,0 +1,234 @@
+/*
+ * grnnd.h — C ABI of the GB300 (sm_103a) GRNND graph-construction library.
+ *
+ * GRNND (arXiv 2510.02774) builds a sparse proximity graph by Relative
+ * NN-Descent: random initial pools (Alg 3), then rounds of disordered
+ * neighbour propagation (Alg 4 with the pair rule of Eq 2) over fixed-capacity
+ * double-buffered pools (Sec 3.5), with reverse-edge sampling between outer
+ * iterations (Sec 3.6).  The graph is queried with a candidate-list search
+ * (Sec 2.1, Sec 4.2).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns GRNND_OK (0) or a negative grnnd_status; calls never
+ *     abort.  On failure grnnd_last_error() returns a thread-local message and
+ *     output handles are set to NULL.
+ *   - "device" pointers are CUDA device (or managed) memory on the current
+ *     device; "host or device" pointers are classified with
+ *     cudaPointerGetAttributes and copied as needed.
+ *   - Point matrices are row-major float32, one row per point.  Step-level
+ *     calls take a leading dimension `ld` (floats per row): ld >= d, ld % 4 == 0,
+ *     and the base address 16-byte aligned (rows are moved with bulk copies).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Step-level calls are asynchronous on that stream; grnnd_build*,
+ *     grnnd_search and grnnd_graph_copy are synchronous on return.
+ *   - Pool layout (step-level calls): a pool is n rows of R slots of uint64
+ *     keys plus an int32 degree per row.  A key packs one entry as
+ *         key = (ordered_bits(dist) << 32) | (id << 1) | old
+ *     where ordered_bits maps float32 to uint32 monotonically (non-negative x:
+ *     bits | 0x80000000; negative x: ~bits), so key order is (dist, id) order.
+ *     `old` = 1 marks an entry that survived its own vertex's previous prune.
+ *     Row v holds deg[v] keys in ascending order followed by empty slots
+ *     (0xFFFFFFFFFFFFFFFF).  Ids must be < 2^31.
+ *   - Distances: GRNND_L2SQ = squared Euclidean distance (the square of Alg 5's
+ *     result; every decision is the same), GRNND_IP = 1 - <x, y>.  In the FP32
+ *     form every recorded distance is the canonical FP32 value: one fused
+ *     multiply-add per dimension in ascending dimension order, so the same
+ *     pair always gets the same bits wherever it is computed.
+ */
+#ifndef GRNND_H
+#define GRNND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GRNND_API __attribute__((visibility("default")))
+#else
+#define GRNND_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRNND_OK = 0,
+    GRNND_EINVAL = -1,   /* invalid argument; nothing was launched */
+    GRNND_ENOMEM = -2,   /* device allocation or HBM budget exceeded before any launch */
+    GRNND_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    GRNND_ETIMEOUT = -4, /* a device-side wait gave up after its iteration limit */
+    GRNND_EBUSY = -5     /* the object is in use by another call */
+} grnnd_status;
+
+typedef enum { GRNND_L2SQ = 0, GRNND_IP = 1 } grnnd_metric;
+
+/* Arithmetic of the pair-distance tiles (dist_tile).  FP32: direct differences
+ * on CUDA cores (the canonical form).  BF16: Gram tiles of a bfloat16 copy on
+ * the tensor cores with FP32 accumulation; decisions within the stated error
+ * bound are re-decided in FP32. */
+typedef enum { GRNND_FP32 = 0, GRNND_BF16 = 1 } grnnd_precision;
+
+/* Visit order of a pool's pairs: disordered (Sec 3.3, the paper's method),
+ * ascending (dist, id) (Alg 2's serial order), or descending (Sec 4.3 ablation). */
+typedef enum { GRNND_ORDER_RANDOM = 0, GRNND_ORDER_ASC = 1, GRNND_ORDER_DESC = 2 } grnnd_order;
+
+typedef struct grnnd_graph grnnd_graph; /* opaque, library-owned */
+
+/* Parameters of a build (Table 1: S, R, T1, T2, rho). */
+typedef struct grnnd_params {
+    int32_t S;            /* initial random neighbours per vertex, 1 <= S <= min(R, n-1) */
+    int32_t R;            /* pool capacity = maximum out-degree, 2 <= R <= 64 */
+    int32_t T1;           /* outer iterations, >= 1 */
+    int32_t T2;           /* inner iterations (rounds) per outer iteration, >= 1 */
+    float rho;            /* reverse-edge sampling ratio in [0, 1] (Sec 3.6); default 0.6 */
+    uint64_t seed;        /* seed of the counter-based hash behind every random choice */
+    int32_t metric;       /* grnnd_metric */
+    int32_t precision;    /* grnnd_precision */
+    int32_t order;        /* grnnd_order */
+    int32_t final_prune;  /* 1: return the survivors of one more prune pass; 0: the last pool */
+    void *stream;         /* cudaStream_t for all work of the build; NULL = legacy default */
+    uint64_t hbm_budget;  /* bytes the build may allocate; 0 = no limit */
+} grnnd_params;
+
+/* Fills *p with defaults: S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, L2SQ, FP32,
+ * random order, final_prune=1, stream=NULL, no budget. */
+GRNND_API void grnnd_params_default(grnnd_params *p);
+
+/* Builds a graph over n points of dimension d (Alg 3).  `points` is host or
+ * device memory, n rows of d contiguous floats; every value must be finite.
+ * Validation: n >= 2, d >= 1, 1 <= S <= min(R, n-1), 2 <= R <= 64, T1, T2 >= 1.
+ * On success *graph_out owns a device copy of the points and the graph; free it
+ * with grnnd_free.  Runs on the legacy default stream. */
+GRNND_API int grnnd_build(const float *points, int64_t n, int32_t d, int32_t metric, int32_t S,
+                int32_t R, int32_t T1, int32_t T2, uint64_t seed, grnnd_graph **graph_out);
+
+/* Same as grnnd_build with every parameter of grnnd_params. */
+GRNND_API int grnnd_build_ex(const float *points, int64_t n, int32_t d, const grnnd_params *p,
+                   grnnd_graph **graph_out);
+
+/* Candidate-list search (Sec 4.2): best-first expansion from the entry point
+ * (the point nearest the dataset mean) with a candidate list of `beam`
+ * entries; stops when every listed candidate is expanded and writes the k
+ * nearest found ids per query, ascending by (dist, id), -1 padded.
+ * `queries` (nq x d floats) and `ids_out` (nq x k int32) are host or device.
+ * 1 <= k <= beam <= 256. */
+GRNND_API int grnnd_search(const grnnd_graph *g, const float *queries, int64_t nq, int32_t k,
+                 int32_t beam, int32_t *ids_out);
+
+/* Sizes of a graph: n, d, R (row capacity) and the search entry id.  Any
+ * output pointer may be NULL. */
+GRNND_API int grnnd_graph_info(const grnnd_graph *g, int64_t *n, int32_t *d, int32_t *R,
+                     int32_t *entry);
+
+/* Device pointers into the graph (valid until grnnd_free): ids n x R int32
+ * (-1 padded), dists n x R float32 (+inf padded), deg n int32.  Row v lists
+ * its deg[v] neighbours ascending by (dist, id). */
+GRNND_API int grnnd_graph_view(const grnnd_graph *g, const int32_t **ids, const float **dists,
+                     const int32_t **deg);
+
+/* Copies the graph into caller buffers (host or device; any may be NULL). */
+GRNND_API int grnnd_graph_copy(const grnnd_graph *g, int32_t *ids, float *dists, int32_t *deg);
+
+/* Counters of the last build of g: [0] rounds run, [1] vertices processed with
+ * new entries, [2] candidate rows gathered, [3] pair distances evaluated,
+ * [4] pairs fired, [5] proposals merged.  `out` is host memory of `count`
+ * int64 slots; returns the number written. */
+GRNND_API int grnnd_graph_stats(const grnnd_graph *g, int64_t *out, int32_t count);
+
+GRNND_API void grnnd_free(grnnd_graph *g);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+GRNND_API const char *grnnd_last_error(void);
+
+/* ------------------------------------------------------------------------- */
+/* Step-level entry points on caller-owned device buffers                     */
+/* ------------------------------------------------------------------------- */
+
+/* rnd_init (Alg 3, INITIAL_NEIGHBORS): for each vertex v, the first S distinct
+ * ids u != v drawn as r = h(seed,0,0,v,j) mod (n-1), u = r + (r >= v), for
+ * j = 0, 1, ...; their canonical FP32 distances; the row sorted by key, all
+ * entries new.  points: device, n x ld.  keys: device n x R (written in full).
+ * deg: device n (written).  h is five chained SplitMix64 steps:
+ * h = f(f(f(f(f(seed) ^ t1) ^ t2) ^ v) ^ x). */
+GRNND_API int grnnd_pool_init(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                    int32_t S, int32_t R, uint64_t seed, uint64_t *keys, int32_t *deg,
+                    void *stream);
+
+/* Bytes of device workspace that grnnd_join_round and grnnd_reverse_sample
+ * need for n vertices with capacity R. */
+GRNND_API size_t grnnd_workspace_size(int64_t n, int32_t R);
+
+/* One round of Alg 4: pool_in -> pool_out, i.e. rnd_join (gather + dist_tile +
+ * rng_prune + proposal emission) followed by rev_merge (proposal bucketing and
+ * per-target top-R selection).  For each vertex v with m = deg_in[v] entries:
+ * the entries are visited in order pi (order key h(seed, t1, t2, v, id), ties
+ * by id; or ascending / descending key); pairs (pi_a, pi_b), b = 1..m-1,
+ * a = 0..b-1, are evaluated unless either side is already bottom or both are
+ * old; a pair fires when d(a,b) < max(d(v,a), d(v,b)) (Eq 2), making the entry
+ * with the larger (dist, id) bottom and proposing it to the other one with
+ * distance d(a,b); every survivor is proposed back to v as old.  pool_out[u] =
+ * the R smallest keys among the distinct ids proposed to u (a duplicate keeps
+ * its smallest distance and is old if any copy is old).  Buffers are device
+ * memory; keys_out/deg_out must not alias the inputs (Sec 3.5 double buffer:
+ * the caller swaps the two pools afterwards, which is pool_swap).
+ * stats (optional, device int64[8], accumulated): [0] vertices with new
+ * entries, [1] rows gathered, [2] pair distances, [3] pairs fired,
+ * [4] proposals, [5] new entries in pool_out. */
+GRNND_API int grnnd_join_round(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                     int32_t R, const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
+                     int32_t t1, int32_t t2, int32_t order, uint64_t *keys_out, int32_t *deg_out,
+                     void *workspace, size_t workspace_bytes, int64_t *stats, void *stream);
+
+/* Reverse-edge sampling (Sec 3.6): for each v with k = deg_in[v], the first
+ * floor((double)rho * k) entries n of its row propose (v, d(v,n), new) to n;
+ * pool_out[u] = merge of pool_in[u] with the proposals to u (same rule as the
+ * round).  0 <= rho <= 1. */
+GRNND_API int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t *keys_in,
+                         const int32_t *deg_in, uint64_t *keys_out, int32_t *deg_out,
+                         void *workspace, size_t workspace_bytes, int64_t *stats, void *stream);
+
+/* Final prune-only pass: the prune of a round with order key t1 (t2 = 0),
+ * keeping only each vertex's survivors, in key order; no redirects.
+ * keys_out: device n x R (written in full), deg_out: device n. */
+GRNND_API int grnnd_final_prune(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                      int32_t R, const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
+                      int32_t t1, int32_t order, uint64_t *keys_out, int32_t *deg_out,
+                      void *stream);
+
+/* Canonical FP32 distances of np point pairs: out[i] = d(points[pairs[2i]],
+ * points[pairs[2i+1]]) exactly as the pool kernels compute it.  pairs: device
+ * int32 (np x 2), out: device float32 (np). */
+GRNND_API int grnnd_pair_dist(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                    const int32_t *pairs, int64_t np, float *out, void *stream);
+
+/* Search entry (reading C13 of the design notes): the id of the point nearest
+ * the dataset mean, ties to the smaller id, computed in FP64.  entry_out:
+ * device int32[1].  workspace: device, >= grnnd_entry_workspace_size(n, d). */
+GRNND_API size_t grnnd_entry_workspace_size(int64_t n, int32_t d);
+GRNND_API int grnnd_entry_point(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                      int32_t *entry_out, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Candidate-list search on a caller-provided graph: gids device n x R int32
+ * (-1 padded), gdeg device n; queries device nq x ldq; ids_out device nq x k
+ * (-1 padded), dists_out device nq x k (may be NULL).  entry: a vertex id. */
+GRNND_API int grnnd_search_graph(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                       const int32_t *gids, const int32_t *gdeg, int32_t R, int32_t entry,
+                       const float *queries, int64_t nq, int32_t ldq, int32_t k, int32_t beam,
+                       int32_t *ids_out, float *dists_out, void *stream);
+
+/* Exact k nearest neighbours by (canonical FP32 dist, id) — the ground truth
+ * of Recall@k (Sec 2.1).  Device buffers; 1 <= k <= 32. */
+GRNND_API int grnnd_brute_knn(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                    const float *queries, int64_t nq, int32_t ldq, int32_t k, int32_t *ids_out,
+                    float *dists_out, void *stream);
+
+/* Converts pool keys to (ids, dists): ids n x R int32 (-1 for empty),
+ * dists n x R float32 (+inf for empty).  Device buffers. */
+GRNND_API int grnnd_keys_to_graph(int64_t n, int32_t R, const uint64_t *keys, int32_t *ids, float *dists,
+                        void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRNND_H */

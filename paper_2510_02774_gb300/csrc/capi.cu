@@ -1,0 +1,460 @@
+// Host driver and C ABI of the GRNND library (declarations in include/grnnd.h).
+//
+// grnnd_build_ex runs Alg 3 on one GPU: rnd_init, then T1 outer iterations of T2 rounds
+// (rnd_join + rev_merge into the other pool buffer, then a pointer swap: Sec 3.5), with
+// reverse-edge sampling (Sec 3.6) after every outer iteration but the last, then the
+// optional final prune, the export to (ids, dists) rows and the search entry.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "grnnd.h"
+#include "internal.h"
+
+struct grnnd_graph {
+  int64_t n = 0;
+  int32_t d = 0, ld = 0, R = 0, metric = 0, entry = 0;
+  float* points = nullptr;   // n x ld, zero padded
+  int32_t* ids = nullptr;    // n x R
+  float* dists = nullptr;    // n x R
+  int32_t* deg = nullptr;    // n
+  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define GR_CU(call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError();                                                                   \
+      return fail(GRNND_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                       \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int32_t round4(int32_t d) { return (d + 3) & ~3; }
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Owned device allocation released on scope exit.
+struct DevMem {
+  void* p = nullptr;
+  ~DevMem() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+  void* release() {
+    void* q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+int check_step_points(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric) {
+  if (!points) return fail(GRNND_EINVAL, "points is NULL");
+  if (n < 1 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n out of range");
+  if (d < 1 || ld < d || (ld & 3) != 0) return fail(GRNND_EINVAL, "need d >= 1, ld >= d, ld % 4 == 0");
+  if (((uintptr_t)points & 15u) != 0) return fail(GRNND_EINVAL, "points must be 16-byte aligned");
+  if (metric != GRNND_L2SQ && metric != GRNND_IP) return fail(GRNND_EINVAL, "unknown metric");
+  return GRNND_OK;
+}
+
+int check_R(int32_t R) {
+  if (R < 2 || R > 64) return fail(GRNND_EINVAL, "R must be in [2, 64]");
+  return GRNND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grnnd_last_error(void) { return g_err.c_str(); }
+
+void grnnd_params_default(grnnd_params* p) {
+  if (!p) return;
+  p->S = 16;
+  p->R = 32;
+  p->T1 = 4;
+  p->T2 = 8;
+  p->rho = 0.6f;
+  p->seed = 0;
+  p->metric = GRNND_L2SQ;
+  p->precision = GRNND_FP32;
+  p->order = GRNND_ORDER_RANDOM;
+  p->final_prune = 1;
+  p->stream = nullptr;
+  p->hbm_budget = 0;
+}
+
+size_t grnnd_workspace_size(int64_t n, int32_t R) {
+  if (n < 1 || R < 1) return 0;
+  return grnnd::workspace_bytes(n, R);
+}
+
+size_t grnnd_entry_workspace_size(int64_t n, int32_t d) {
+  if (n < 1 || d < 1) return 0;
+  return grnnd::entry_workspace_bytes(n, d);
+}
+
+int grnnd_pool_init(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                    int32_t S, int32_t R, uint64_t seed, uint64_t* keys, int32_t* deg,
+                    void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if ((rc = check_R(R))) return rc;
+  if (n < 2 || S < 1 || S > R || (int64_t)S > n - 1)
+    return fail(GRNND_EINVAL, "need n >= 2 and 1 <= S <= min(R, n-1)");
+  if (!keys || !deg) return fail(GRNND_EINVAL, "keys/deg is NULL");
+  GR_CU(grnnd::launch_pool_init(points, n, d, ld, metric, S, R, seed, keys, deg,
+                                (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                     int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
+                     int32_t t1, int32_t t2, int32_t order, uint64_t* keys_out, int32_t* deg_out,
+                     void* workspace, size_t workspace_bytes, int64_t* stats, void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if ((rc = check_R(R))) return rc;
+  if (!keys_in || !deg_in || !keys_out || !deg_out) return fail(GRNND_EINVAL, "pool buffer is NULL");
+  if (keys_in == keys_out || deg_in == deg_out)
+    return fail(GRNND_EINVAL, "output pool must not alias the input pool");
+  if (order < 0 || order > 2) return fail(GRNND_EINVAL, "unknown order");
+  grnnd::Workspace ws;
+  if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
+    return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
+  GR_CU(grnnd::launch_join(points, n, d, ld, metric, R, keys_in, deg_in, seed, t1, t2, order, 0,
+                           ws, nullptr, nullptr, stats, st));
+  GR_CU(grnnd::launch_merge(ws, R, keys_out, deg_out, stats, st));
+  if (stats) GR_CU(cudaMemcpyAsync(stats + 5, ws.round_new, 8, cudaMemcpyDeviceToDevice, st));
+  return GRNND_OK;
+}
+
+int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t* keys_in,
+                         const int32_t* deg_in, uint64_t* keys_out, int32_t* deg_out,
+                         void* workspace, size_t workspace_bytes, int64_t* stats, void* stream) {
+  int rc = check_R(R);
+  if (rc) return rc;
+  if (n < 1) return fail(GRNND_EINVAL, "n out of range");
+  if (!(rho >= 0.0f && rho <= 1.0f)) return fail(GRNND_EINVAL, "rho must be in [0, 1]");
+  if (!keys_in || !deg_in || !keys_out || !deg_out) return fail(GRNND_EINVAL, "pool buffer is NULL");
+  if (keys_in == keys_out || deg_in == deg_out)
+    return fail(GRNND_EINVAL, "output pool must not alias the input pool");
+  grnnd::Workspace ws;
+  if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
+    return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
+  GR_CU(grnnd::launch_reverse_propose(n, R, rho, keys_in, deg_in, ws, st));
+  GR_CU(grnnd::launch_merge(ws, 2 * R, keys_out, deg_out, stats, st));
+  return GRNND_OK;
+}
+
+int grnnd_final_prune(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                      int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
+                      int32_t t1, int32_t order, uint64_t* keys_out, int32_t* deg_out,
+                      void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if ((rc = check_R(R))) return rc;
+  if (!keys_in || !deg_in || !keys_out || !deg_out) return fail(GRNND_EINVAL, "pool buffer is NULL");
+  if (order < 0 || order > 2) return fail(GRNND_EINVAL, "unknown order");
+  grnnd::Workspace ws;  // the final pass emits no proposals
+  GR_CU(grnnd::launch_join(points, n, d, ld, metric, R, keys_in, deg_in, seed, t1, 0, order, 1, ws,
+                           keys_out, deg_out, nullptr, (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+int grnnd_pair_dist(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                    const int32_t* pairs, int64_t np, float* out, void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if (np < 0 || (np > 0 && (!pairs || !out))) return fail(GRNND_EINVAL, "bad pair list");
+  GR_CU(grnnd::launch_pair_dist(points, d, ld, metric, pairs, np, out, (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+int grnnd_entry_point(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                      int32_t* entry_out, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if (!entry_out || !workspace || workspace_bytes < grnnd::entry_workspace_bytes(n, d))
+    return fail(GRNND_EINVAL, "entry_out/workspace missing or too small");
+  GR_CU(grnnd::launch_entry(points, n, d, ld, metric, entry_out, workspace, workspace_bytes,
+                            (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+int grnnd_search_graph(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                       const int32_t* gids, const int32_t* gdeg, int32_t R, int32_t entry,
+                       const float* queries, int64_t nq, int32_t ldq, int32_t k, int32_t beam,
+                       int32_t* ids_out, float* dists_out, void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if (!gids || !gdeg || R < 1 || entry < 0 || entry >= n) return fail(GRNND_EINVAL, "bad graph");
+  if (nq < 0 || (nq > 0 && (!queries || !ids_out)) || ldq < d)
+    return fail(GRNND_EINVAL, "bad queries/ids_out");
+  if (k < 1 || beam < k || beam > 256) return fail(GRNND_EINVAL, "need 1 <= k <= beam <= 256");
+  if (d > 1024) return fail(GRNND_EINVAL, "search supports d <= 1024");
+  GR_CU(grnnd::launch_search(points, n, d, ld, metric, gids, gdeg, R, entry, queries, nq, ldq, k,
+                             beam, ids_out, dists_out, (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+int grnnd_brute_knn(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                    const float* queries, int64_t nq, int32_t ldq, int32_t k, int32_t* ids_out,
+                    float* dists_out, void* stream) {
+  int rc = check_step_points(points, n, d, ld, metric);
+  if (rc) return rc;
+  if (nq < 0 || (nq > 0 && (!queries || !ids_out)) || ldq < d)
+    return fail(GRNND_EINVAL, "bad queries/ids_out");
+  if (k < 1 || k > 32 || k > n) return fail(GRNND_EINVAL, "need 1 <= k <= min(32, n)");
+  GR_CU(grnnd::launch_brute_knn(points, n, d, ld, metric, queries, nq, ldq, k, ids_out, dists_out,
+                                (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+int grnnd_keys_to_graph(int64_t n, int32_t R, const uint64_t* keys, int32_t* ids, float* dists,
+                        void* stream) {
+  if (n < 1 || R < 1 || !keys) return fail(GRNND_EINVAL, "bad arguments");
+  GR_CU(grnnd::launch_keys_to_graph(n, R, keys, ids, dists, nullptr, (cudaStream_t)stream));
+  return GRNND_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Whole build
+// ---------------------------------------------------------------------------------------
+
+int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
+                   grnnd_graph** graph_out) {
+  if (graph_out) *graph_out = nullptr;
+  if (!graph_out) return fail(GRNND_EINVAL, "graph_out is NULL");
+  if (!p) return fail(GRNND_EINVAL, "params is NULL");
+  if (!points) return fail(GRNND_EINVAL, "points is NULL");
+  if (n < 2 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n must be in [2, 2^31 - 2]");
+  if (d < 1) return fail(GRNND_EINVAL, "d must be >= 1");
+  int rc = check_R(p->R);
+  if (rc) return rc;
+  if (p->S < 1 || p->S > p->R || (int64_t)p->S > n - 1)
+    return fail(GRNND_EINVAL, "need 1 <= S <= min(R, n-1)");
+  if (p->T1 < 1 || p->T2 < 1) return fail(GRNND_EINVAL, "T1 and T2 must be >= 1");
+  if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return fail(GRNND_EINVAL, "rho must be in [0, 1]");
+  if (p->metric != GRNND_L2SQ && p->metric != GRNND_IP) return fail(GRNND_EINVAL, "unknown metric");
+  if (p->order < 0 || p->order > 2) return fail(GRNND_EINVAL, "unknown order");
+  if (p->precision != GRNND_FP32) return fail(GRNND_EINVAL, "only GRNND_FP32 is available in this build");
+  const int32_t R = p->R, ld = round4(d);
+  cudaStream_t st = (cudaStream_t)p->stream;
+
+  const size_t pts_b = al256((size_t)n * ld * 4);
+  const size_t pool_b = al256((size_t)n * R * 8), deg_b = al256((size_t)n * 4);
+  const size_t ws_b = grnnd::workspace_bytes(n, R);
+  const size_t ent_b = grnnd::entry_workspace_bytes(n, d);
+  const size_t graph_b = al256((size_t)n * R * 4) * 2 + deg_b;
+  const size_t stats_b = 256;
+  const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b;
+  if (p->hbm_budget && pts_b + graph_b + scratch_b > p->hbm_budget)
+    return fail(GRNND_ENOMEM, "build needs " + std::to_string(pts_b + graph_b + scratch_b) +
+                                  " bytes, above hbm_budget " + std::to_string(p->hbm_budget));
+
+  DevMem mpts, mgraph, mscratch;
+  GR_CU(mpts.alloc(pts_b));
+  GR_CU(mgraph.alloc(graph_b));
+  GR_CU(mscratch.alloc(scratch_b));
+  float* X = static_cast<float*>(mpts.p);
+  char* gp = static_cast<char*>(mgraph.p);
+  int32_t* gids = reinterpret_cast<int32_t*>(gp);
+  float* gd = reinterpret_cast<float*>(gp + al256((size_t)n * R * 4));
+  int32_t* gdeg = reinterpret_cast<int32_t*>(gp + 2 * al256((size_t)n * R * 4));
+  char* sp = static_cast<char*>(mscratch.p);
+  uint64_t* poolA = reinterpret_cast<uint64_t*>(sp);
+  uint64_t* poolB = reinterpret_cast<uint64_t*>(sp + pool_b);
+  int32_t* degA = reinterpret_cast<int32_t*>(sp + 2 * pool_b);
+  int32_t* degB = reinterpret_cast<int32_t*>(sp + 2 * pool_b + deg_b);
+  int64_t* stats = reinterpret_cast<int64_t*>(sp + 2 * pool_b + 2 * deg_b);
+  void* wsp = sp + 2 * pool_b + 2 * deg_b + stats_b;
+  const size_t wsp_b = std::max(ws_b, ent_b);
+
+  // points -> padded device rows
+  const cudaMemcpyKind kind = is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (ld != d) GR_CU(cudaMemsetAsync(X, 0, (size_t)n * ld * 4, st));
+  GR_CU(cudaMemcpy2DAsync(X, (size_t)ld * 4, points, (size_t)d * 4, (size_t)d * 4, (size_t)n, kind, st));
+  GR_CU(cudaMemsetAsync(stats, 0, stats_b, st));
+  grnnd::Workspace ws;
+  if (!grnnd::carve_workspace(wsp, wsp_b, n, R, &ws)) return fail(GRNND_EINVAL, "internal workspace");
+  GR_CU(cudaMemsetAsync(ws.err, 0, 4, st));
+  GR_CU(grnnd::launch_check_finite(X, n, d, ld, ws.err, st));
+  int32_t h_flag = 0;
+  GR_CU(cudaMemcpyAsync(&h_flag, ws.err, 4, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaStreamSynchronize(st));
+  if (h_flag) return fail(GRNND_EINVAL, "points contain a non-finite value");
+
+  GR_CU(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st));
+  int64_t rounds = 0;
+  for (int32_t t1 = 1; t1 <= p->T1; ++t1) {
+    for (int32_t t2 = 1; t2 <= p->T2; ++t2) {
+      GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
+      GR_CU(grnnd::launch_join(X, n, d, ld, p->metric, R, poolA, degA, p->seed, t1, t2, p->order, 0,
+                               ws, nullptr, nullptr, stats, st));
+      GR_CU(grnnd::launch_merge(ws, R, poolB, degB, stats, st));
+      std::swap(poolA, poolB);  // pool_swap: the written pool is read next round
+      std::swap(degA, degB);
+      ++rounds;
+      int64_t fresh = 0;
+      GR_CU(cudaMemcpyAsync(&fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
+      GR_CU(cudaStreamSynchronize(st));
+      if (fresh == 0) break;  // no new entry anywhere: the remaining rounds are identities
+    }
+    if (t1 != p->T1) {
+      GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
+      GR_CU(grnnd::launch_reverse_propose(n, R, p->rho, poolA, degA, ws, st));
+      GR_CU(grnnd::launch_merge(ws, 2 * R, poolB, degB, nullptr, st));
+      std::swap(poolA, poolB);
+      std::swap(degA, degB);
+    }
+  }
+  uint64_t* gkeys = poolA;
+  int32_t* gdg = degA;
+  if (p->final_prune) {
+    GR_CU(grnnd::launch_join(X, n, d, ld, p->metric, R, poolA, degA, p->seed, p->T1 + 1, 0, p->order,
+                             1, ws, poolB, degB, nullptr, st));
+    gkeys = poolB;
+    gdg = degB;
+  }
+  GR_CU(grnnd::launch_keys_to_graph(n, R, gkeys, gids, gd, nullptr, st));
+  GR_CU(cudaMemcpyAsync(gdeg, gdg, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+  int32_t h_err = 0;
+  GR_CU(cudaMemcpyAsync(&h_err, ws.err, 4, cudaMemcpyDeviceToHost, st));
+  // the entry workspace reuses the (now idle) round workspace
+  int32_t* d_entry = reinterpret_cast<int32_t*>(stats + 16);
+  GR_CU(grnnd::launch_entry(X, n, d, ld, p->metric, d_entry, wsp, wsp_b, st));
+  int32_t h_entry = 0;
+  int64_t h_stats[8];
+  GR_CU(cudaMemcpyAsync(&h_entry, d_entry, 4, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaMemcpyAsync(h_stats, stats, 64, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaStreamSynchronize(st));
+  if (h_err) return fail(GRNND_ETIMEOUT, "a device-side wait reached its iteration limit");
+
+  grnnd_graph* g = new grnnd_graph();
+  g->n = n;
+  g->d = d;
+  g->ld = ld;
+  g->R = R;
+  g->metric = p->metric;
+  g->entry = h_entry;
+  g->points = static_cast<float*>(mpts.release());
+  char* gbase = static_cast<char*>(mgraph.release());
+  g->ids = reinterpret_cast<int32_t*>(gbase);
+  g->dists = reinterpret_cast<float*>(gbase + al256((size_t)n * R * 4));
+  g->deg = reinterpret_cast<int32_t*>(gbase + 2 * al256((size_t)n * R * 4));
+  g->stats[0] = rounds;
+  g->stats[1] = h_stats[0];
+  g->stats[2] = h_stats[1];
+  g->stats[3] = h_stats[2];
+  g->stats[4] = h_stats[3];
+  g->stats[5] = h_stats[6];
+  *graph_out = g;
+  return GRNND_OK;
+}
+
+int grnnd_build(const float* points, int64_t n, int32_t d, int32_t metric, int32_t S, int32_t R,
+                int32_t T1, int32_t T2, uint64_t seed, grnnd_graph** graph_out) {
+  grnnd_params p;
+  grnnd_params_default(&p);
+  p.metric = metric;
+  p.S = S;
+  p.R = R;
+  p.T1 = T1;
+  p.T2 = T2;
+  p.seed = seed;
+  return grnnd_build_ex(points, n, d, &p, graph_out);
+}
+
+int grnnd_search(const grnnd_graph* g, const float* queries, int64_t nq, int32_t k, int32_t beam,
+                 int32_t* ids_out) {
+  if (!g) return fail(GRNND_EINVAL, "graph is NULL");
+  if (nq < 0 || (nq > 0 && (!queries || !ids_out))) return fail(GRNND_EINVAL, "bad queries/ids_out");
+  if (k < 1 || beam < k || beam > 256) return fail(GRNND_EINVAL, "need 1 <= k <= beam <= 256");
+  if (g->d > 1024) return fail(GRNND_EINVAL, "search supports d <= 1024");
+  if (nq == 0) return GRNND_OK;
+  const int32_t ldq = g->ld;
+  DevMem mq, mo;
+  GR_CU(mq.alloc((size_t)nq * ldq * 4));
+  const bool out_dev = is_device_ptr(ids_out);
+  int32_t* dids = ids_out;
+  if (!out_dev) {
+    GR_CU(mo.alloc((size_t)nq * k * 4));
+    dids = static_cast<int32_t*>(mo.p);
+  }
+  float* dq = static_cast<float*>(mq.p);
+  const cudaMemcpyKind kind = is_device_ptr(queries) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (ldq != g->d) GR_CU(cudaMemset(dq, 0, (size_t)nq * ldq * 4));
+  GR_CU(cudaMemcpy2D(dq, (size_t)ldq * 4, queries, (size_t)g->d * 4, (size_t)g->d * 4, (size_t)nq, kind));
+  GR_CU(grnnd::launch_search(g->points, g->n, g->d, g->ld, g->metric, g->ids, g->deg, g->R, g->entry,
+                             dq, nq, ldq, k, beam, dids, nullptr, 0));
+  if (!out_dev) GR_CU(cudaMemcpy(ids_out, dids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost));
+  GR_CU(cudaDeviceSynchronize());
+  return GRNND_OK;
+}
+
+int grnnd_graph_info(const grnnd_graph* g, int64_t* n, int32_t* d, int32_t* R, int32_t* entry) {
+  if (!g) return fail(GRNND_EINVAL, "graph is NULL");
+  if (n) *n = g->n;
+  if (d) *d = g->d;
+  if (R) *R = g->R;
+  if (entry) *entry = g->entry;
+  return GRNND_OK;
+}
+
+int grnnd_graph_view(const grnnd_graph* g, const int32_t** ids, const float** dists,
+                     const int32_t** deg) {
+  if (!g) return fail(GRNND_EINVAL, "graph is NULL");
+  if (ids) *ids = g->ids;
+  if (dists) *dists = g->dists;
+  if (deg) *deg = g->deg;
+  return GRNND_OK;
+}
+
+int grnnd_graph_copy(const grnnd_graph* g, int32_t* ids, float* dists, int32_t* deg) {
+  if (!g) return fail(GRNND_EINVAL, "graph is NULL");
+  const size_t nr = (size_t)g->n * g->R;
+  if (ids) GR_CU(cudaMemcpy(ids, g->ids, nr * 4, cudaMemcpyDefault));
+  if (dists) GR_CU(cudaMemcpy(dists, g->dists, nr * 4, cudaMemcpyDefault));
+  if (deg) GR_CU(cudaMemcpy(deg, g->deg, (size_t)g->n * 4, cudaMemcpyDefault));
+  return GRNND_OK;
+}
+
+int grnnd_graph_stats(const grnnd_graph* g, int64_t* out, int32_t count) {
+  if (!g || !out || count < 0) return fail(GRNND_EINVAL, "bad arguments");
+  const int32_t c = std::min<int32_t>(count, 6);
+  for (int32_t i = 0; i < c; ++i) out[i] = g->stats[i];
+  return c;
+}
+
+void grnnd_free(grnnd_graph* g) {
+  if (!g) return;
+  cudaFree(g->points);
+  cudaFree(g->ids);  // ids, dists and deg share one allocation
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Device helpers shared by the GRNND kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grnnd {
+
+constexpr uint64_t kEmpty = ~0ull;
+constexpr int kMaxR = 64;  // pool capacity handled by the 64-bit prune masks
+
+// Counter-based hash of the design notes (reading C9): five chained SplitMix64
+// steps, each the published gamma increment followed by the 30/27/31 finaliser.
+__host__ __device__ __forceinline__ uint64_t splitmix_step(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t counter_hash(uint64_t seed, uint64_t t1, uint64_t t2,
+                                                          uint64_t v, uint64_t x) {
+  uint64_t h = splitmix_step(seed);
+  h = splitmix_step(h ^ t1);
+  h = splitmix_step(h ^ t2);
+  h = splitmix_step(h ^ v);
+  return splitmix_step(h ^ x);
+}
+
+// ---- pool keys: (ordered float bits << 32) | (id << 1) | old -------------------------
+__device__ __forceinline__ uint32_t ordered_bits(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+__device__ __forceinline__ uint64_t make_key(float dist, uint32_t id, uint32_t old) {
+  return ((uint64_t)ordered_bits(dist) << 32) | ((uint64_t)id << 1) | (uint64_t)old;
+}
+__device__ __forceinline__ uint32_t key_id(uint64_t k) { return (uint32_t)(k >> 1) & 0x7fffffffu; }
+__device__ __forceinline__ float key_dist(uint64_t k) { return from_ordered((uint32_t)(k >> 32)); }
+__device__ __forceinline__ uint32_t key_old(uint64_t k) { return (uint32_t)k & 1u; }
+
+// ---- canonical FP32 distance: one rounded op per dimension, ascending order ----------
+// L2SQ: t = a - b (rounded), acc = fma(t, t, acc).  IP: acc = fma(a, b, acc), d = 1 - acc.
+template <int METRIC>
+__device__ __forceinline__ float dist_step(float acc, float a, float b) {
+  if (METRIC == 0) {
+    float t = __fsub_rn(a, b);
+    return __fmaf_rn(t, t, acc);
+  }
+  return __fmaf_rn(a, b, acc);
+}
+template <int METRIC>
+__device__ __forceinline__ float dist_finish(float acc) {
+  return METRIC == 0 ? acc : __fsub_rn(1.0f, acc);
+}
+template <int METRIC>
+__device__ __forceinline__ float dist_step4(float acc, float4 a, float4 b) {
+  acc = dist_step<METRIC>(acc, a.x, b.x);
+  acc = dist_step<METRIC>(acc, a.y, b.y);
+  acc = dist_step<METRIC>(acc, a.z, b.z);
+  return dist_step<METRIC>(acc, a.w, b.w);
+}
+
+// Canonical distance of two rows in global memory (16-byte aligned rows).
+template <int METRIC>
+__device__ __forceinline__ float row_dist(const float* __restrict__ a, const float* __restrict__ b,
+                                          int d) {
+  float acc = 0.0f;
+  int k = 0;
+  for (; k + 4 <= d; k += 4) {
+    float4 x = __ldg(reinterpret_cast<const float4*>(a + k));
+    float4 y = __ldg(reinterpret_cast<const float4*>(b + k));
+    acc = dist_step4<METRIC>(acc, x, y);
+  }
+  for (; k < d; ++k) acc = dist_step<METRIC>(acc, __ldg(a + k), __ldg(b + k));
+  return dist_finish<METRIC>(acc);
+}
+
+// ---- warp bitonic sort of 32*E uint64 values, element index e = j*32 + lane ----------
+template <int E>
+__device__ __forceinline__ void warp_sort_u64(uint64_t (&x)[E]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+    for (int s = k >> 1; s > 0; s >>= 1) {
+      if (s >= 32) {
+        const int js = s >> 5;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          if ((j & js) == 0) {
+            const int j2 = j | js;
+            const bool up = (((j << 5) | lane) & k) == 0;
+            uint64_t a = x[j], b = x[j2];
+            bool sw = up ? (a > b) : (a < b);
+            x[j] = sw ? b : a;
+            x[j2] = sw ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int e = (j << 5) | lane;
+          const bool up = (e & k) == 0;
+          const bool lower = (e & s) == 0;
+          uint64_t o = __shfl_xor_sync(0xffffffffu, x[j], s);
+          uint64_t mn = x[j] < o ? x[j] : o;
+          uint64_t mx = x[j] < o ? o : x[j];
+          x[j] = (lower == up) ? mn : mx;
+        }
+      }
+    }
+  }
+}
+
+// ---- bounded mbarrier wait (every wait has an iteration limit) ----------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(a),
+      "r"(bytes)
+      : "memory");
+}
+// Returns true when the phase with the given parity completed, false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// Bulk copy global -> shared (no tensor map); completion counted on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes,
+                                         uint64_t* bar) {
+  uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+      "l"(gmem_src), "r"(bytes), "r"(b)
+      : "memory");
+}
+
+// Status word written by kernels whose bounded waits gave up.
+constexpr int kErrTimeout = 1;
+
+}  // namespace grnnd

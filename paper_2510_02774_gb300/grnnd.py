@@ -1,0 +1,375 @@
+"""Thin Python binding of the GRNND C ABI (include/grnnd.h).
+
+Argument marshalling only: every step of the build and the search runs in the
+CUDA kernels of ``libgrnnd.so``.  PyTorch supplies device memory and the
+current stream.  When the library is missing the calls raise; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libgrnnd.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "grnnd.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
+L2SQ, IP = 0, 1
+FP32, BF16 = 0, 1
+ORDER_RANDOM, ORDER_ASC, ORDER_DESC = 0, 1, 2
+EMPTY = 0xFFFFFFFFFFFFFFFF
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GrnndError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"grnnd status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int32), ("R", ctypes.c_int32), ("T1", ctypes.c_int32), ("T2", ctypes.c_int32),
+                ("rho", ctypes.c_float), ("seed", ctypes.c_uint64), ("metric", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("order", ctypes.c_int32), ("final_prune", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_uint64)]
+
+
+_SIGS = {
+    # name: (restype, argtypes)
+    "grnnd_params_default": (None, [ctypes.POINTER(Params)]),
+    "grnnd_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "grnnd_build_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Params),
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "grnnd_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p]),
+    "grnnd_graph_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "grnnd_graph_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "grnnd_graph_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_graph_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "grnnd_free": (None, [ctypes.c_void_p]),
+    "grnnd_last_error": (ctypes.c_char_p, []),
+    "grnnd_pool_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "grnnd_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
+    "grnnd_join_round": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_reverse_sample": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_final_prune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_pair_dist": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_entry_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
+    "grnnd_entry_point": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "grnnd_search_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_brute_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_keys_to_graph": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib(path: str | None = None):
+    """Loads libgrnnd.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -m paper_2510_02774_gb300.build`")
+        L = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != OK:
+        msg = lib().grnnd_last_error()
+        raise GrnndError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------------------
+# torch helpers (device memory and streams only)
+# ---------------------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def device_points(X, device="cuda"):
+    """Copies points (numpy or torch, n x d float32) into a device tensor of shape
+    (n, ld) with ld = d rounded up to 4 and zero padding.  Returns (tensor, d)."""
+    torch = _torch()
+    Xt = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float32)) if isinstance(X, np.ndarray) else X
+    n, d = Xt.shape
+    ld = (d + 3) & ~3
+    out = torch.zeros((n, ld), dtype=torch.float32, device=device)
+    out[:, :d] = Xt.to(device=device, dtype=torch.float32)
+    return out, d
+
+
+def workspace(n: int, R: int, device="cuda"):
+    torch = _torch()
+    nb = int(lib().grnnd_workspace_size(n, R))
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------------------------------
+# Whole build and search
+# ---------------------------------------------------------------------------------------
+
+@dataclass
+class Graph:
+    handle: ctypes.c_void_p
+    n: int
+    d: int
+    R: int
+    entry: int
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().grnnd_free(h)
+            except Exception:
+                pass
+            self.handle = ctypes.c_void_p(0)
+
+    def to_numpy(self):
+        """(ids n x R int32 -1 padded, dists n x R float32, deg n int32) on the host."""
+        ids = np.empty((self.n, self.R), np.int32)
+        dists = np.empty((self.n, self.R), np.float32)
+        deg = np.empty(self.n, np.int32)
+        _check(lib().grnnd_graph_copy(self.handle, ids.ctypes.data_as(ctypes.c_void_p),
+                                      dists.ctypes.data_as(ctypes.c_void_p), deg.ctypes.data_as(ctypes.c_void_p)))
+        return ids, dists, deg
+
+    def stats(self):
+        out = np.zeros(6, np.int64)
+        lib().grnnd_graph_stats(self.handle, out.ctypes.data_as(ctypes.c_void_p), 6)
+        keys = ["rounds", "vertices_with_new", "rows_gathered", "pair_distances", "pairs_fired", "proposals_merged"]
+        return dict(zip(keys, out.tolist()))
+
+    def search(self, queries, k: int = 10, beam: int = 64):
+        """Candidate-list search; queries numpy (host) or torch (host or device)."""
+        return search(self, queries, k, beam)
+
+
+def params(S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,
+           final_prune=True, stream=None, hbm_budget=0) -> Params:
+    p = Params()
+    lib().grnnd_params_default(ctypes.byref(p))
+    p.S, p.R, p.T1, p.T2, p.rho, p.seed = S, R, T1, T2, rho, seed
+    p.metric, p.precision, p.order, p.final_prune = metric, precision, order, int(bool(final_prune))
+    p.stream = stream
+    p.hbm_budget = hbm_budget
+    return p
+
+
+def build(points, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,
+          final_prune=True, stream=None, hbm_budget=0) -> Graph:
+    """grnnd_build_ex on numpy (host) or torch (host or device) points of shape (n, d).
+    With torch CUDA points the build runs on the current torch stream."""
+    if isinstance(points, np.ndarray):
+        pts = np.ascontiguousarray(points, dtype=np.float32)
+        ptr = pts.ctypes.data_as(ctypes.c_void_p)
+        st = None
+    else:
+        pts = points.contiguous()
+        ptr = ctypes.c_void_p(pts.data_ptr())
+        st = _stream_ptr(stream).value if pts.is_cuda else None
+    n, d = pts.shape
+    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, hbm_budget)
+    h = ctypes.c_void_p()
+    _check(lib().grnnd_build_ex(ptr, n, d, ctypes.byref(p), ctypes.byref(h)))
+    n_, d_, R_, e_ = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().grnnd_graph_info(h, ctypes.byref(n_), ctypes.byref(d_), ctypes.byref(R_), ctypes.byref(e_)))
+    return Graph(h, n_.value, d_.value, R_.value, e_.value)
+
+
+def search(graph: Graph, queries, k: int = 10, beam: int = 64):
+    if isinstance(queries, np.ndarray):
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        out = np.empty((q.shape[0], k), np.int32)
+        _check(lib().grnnd_search(graph.handle, q.ctypes.data_as(ctypes.c_void_p), q.shape[0], k, beam,
+                                  out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+    torch = _torch()
+    q = queries.contiguous().to(torch.float32)
+    out = torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device)
+    _check(lib().grnnd_search(graph.handle, _ptr(q), q.shape[0], k, beam, _ptr(out)))
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Step-level calls on torch device tensors (X is (n, ld) float32 from device_points)
+# ---------------------------------------------------------------------------------------
+
+def pool_init(X, d: int, S: int, R: int, seed: int, metric: int = L2SQ, stream=None):
+    torch = _torch()
+    n, ld = X.shape
+    keys = torch.empty((n, R), dtype=torch.int64, device=X.device)
+    deg = torch.empty(n, dtype=torch.int32, device=X.device)
+    _check(lib().grnnd_pool_init(_ptr(X), n, d, ld, metric, S, R, seed, _ptr(keys), _ptr(deg), _stream_ptr(stream)))
+    return keys, deg
+
+
+def join_round(X, d: int, keys, deg, seed: int, t1: int, t2: int, order: int = ORDER_RANDOM, metric: int = L2SQ,
+               ws=None, stats=None, stream=None):
+    torch = _torch()
+    n, ld = X.shape
+    R = keys.shape[1]
+    ws = workspace(n, R, X.device) if ws is None else ws
+    k2 = torch.empty_like(keys)
+    d2 = torch.empty_like(deg)
+    _check(lib().grnnd_join_round(_ptr(X), n, d, ld, metric, R, _ptr(keys), _ptr(deg), seed, t1, t2, order,
+                                  _ptr(k2), _ptr(d2), _ptr(ws), ws.numel(), _ptr(stats), _stream_ptr(stream)))
+    return k2, d2
+
+
+def reverse_sample(keys, deg, rho: float, ws=None, stats=None, stream=None):
+    torch = _torch()
+    n, R = keys.shape
+    ws = workspace(n, R, keys.device) if ws is None else ws
+    k2 = torch.empty_like(keys)
+    d2 = torch.empty_like(deg)
+    _check(lib().grnnd_reverse_sample(n, R, ctypes.c_float(rho), _ptr(keys), _ptr(deg), _ptr(k2), _ptr(d2), _ptr(ws),
+                                      ws.numel(), _ptr(stats), _stream_ptr(stream)))
+    return k2, d2
+
+
+def final_prune(X, d: int, keys, deg, seed: int, t1: int, order: int = ORDER_RANDOM, metric: int = L2SQ, stream=None):
+    torch = _torch()
+    n, ld = X.shape
+    R = keys.shape[1]
+    k2 = torch.empty_like(keys)
+    d2 = torch.empty_like(deg)
+    _check(lib().grnnd_final_prune(_ptr(X), n, d, ld, metric, R, _ptr(keys), _ptr(deg), seed, t1, order, _ptr(k2),
+                                   _ptr(d2), _stream_ptr(stream)))
+    return k2, d2
+
+
+def pair_dist(X, d: int, pairs, metric: int = L2SQ, stream=None):
+    torch = _torch()
+    n, ld = X.shape
+    pairs = pairs.to(device=X.device, dtype=torch.int32).contiguous()
+    out = torch.empty(pairs.shape[0], dtype=torch.float32, device=X.device)
+    _check(lib().grnnd_pair_dist(_ptr(X), n, d, ld, metric, _ptr(pairs), pairs.shape[0], _ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def entry_point(X, d: int, metric: int = L2SQ, stream=None) -> int:
+    torch = _torch()
+    n, ld = X.shape
+    ws = torch.empty(int(lib().grnnd_entry_workspace_size(n, d)), dtype=torch.uint8, device=X.device)
+    e = torch.empty(1, dtype=torch.int32, device=X.device)
+    _check(lib().grnnd_entry_point(_ptr(X), n, d, ld, metric, _ptr(e), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return int(e.item())
+
+
+def search_graph(X, d: int, gids, gdeg, entry: int, Q, k: int, beam: int, metric: int = L2SQ, stream=None):
+    torch = _torch()
+    n, ld = X.shape
+    R = gids.shape[1]
+    nq, ldq = Q.shape
+    ids = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+    dd = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    _check(lib().grnnd_search_graph(_ptr(X), n, d, ld, metric, _ptr(gids), _ptr(gdeg), R, entry, _ptr(Q), nq, ldq, k,
+                                    beam, _ptr(ids), _ptr(dd), _stream_ptr(stream)))
+    return ids, dd
+
+
+def brute_knn(X, d: int, Q, k: int, metric: int = L2SQ, stream=None):
+    torch = _torch()
+    n, ld = X.shape
+    nq, ldq = Q.shape
+    ids = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+    dd = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    _check(lib().grnnd_brute_knn(_ptr(X), n, d, ld, metric, _ptr(Q), nq, ldq, k, _ptr(ids), _ptr(dd),
+                                 _stream_ptr(stream)))
+    return ids, dd
+
+
+def keys_to_graph(keys):
+    torch = _torch()
+    n, R = keys.shape
+    ids = torch.empty((n, R), dtype=torch.int32, device=keys.device)
+    dd = torch.empty((n, R), dtype=torch.float32, device=keys.device)
+    _check(lib().grnnd_keys_to_graph(n, R, _ptr(keys), _ptr(ids), _ptr(dd), _stream_ptr()))
+    return ids, dd
+
+
+# ---------------------------------------------------------------------------------------
+# Host-side decoding of pool keys (for comparisons in tests and reports)
+# ---------------------------------------------------------------------------------------
+
+def decode_keys(keys) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """keys (n, R) int64/uint64 -> (ids int32 -1 for empty, dist float32, old uint8)."""
+    k = np.asarray(keys).view(np.uint64) if np.asarray(keys).dtype != np.uint64 else np.asarray(keys)
+    empty = k == np.uint64(EMPTY)
+    ob = (k >> np.uint64(32)).astype(np.uint32)
+    neg = (ob & np.uint32(0x80000000)) == 0
+    bits = np.where(neg, ~ob, ob & np.uint32(0x7FFFFFFF)).astype(np.uint32)
+    dist = bits.view(np.float32)
+    ids = ((k >> np.uint64(1)) & np.uint64(0x7FFFFFFF)).astype(np.int32)
+    old = (k & np.uint64(1)).astype(np.uint8)
+    ids[empty] = -1
+    dist = np.where(empty, np.float32(np.inf), dist).astype(np.float32)
+    old[empty] = 0
+    return ids, dist, old
+
+
+def encode_keys(ids, dist, old) -> np.ndarray:
+    """Inverse of decode_keys: (ids, float32 dist, old) -> uint64 keys (EMPTY where id < 0)."""
+    ids = np.asarray(ids, np.int64)
+    d32 = np.asarray(dist, np.float32)
+    bits = d32.view(np.uint32)
+    ob = np.where((bits & np.uint32(0x80000000)) != 0, ~bits, bits | np.uint32(0x80000000)).astype(np.uint64)
+    k = (ob << np.uint64(32)) | (ids.astype(np.uint64) << np.uint64(1)) | np.asarray(old, np.uint64)
+    return np.where(ids < 0, np.uint64(EMPTY), k).astype(np.uint64)
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/grnnd.h."""
+    import re
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"GRNND_API\s+[\w\s\*]*?\b(grnnd_\w+)\s*\(", txt)))

@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads, exports every declared entry point, and rejects
+bad arguments before touching the GPU (no compute calls: runs without a GPU)."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2510_02774_gb300 import build as B
+from paper_2510_02774_gb300 import grnnd as G
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return G.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    declared = G.header_functions()
+    assert len(declared) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", G.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    missing = [f for f in declared if f not in exported]
+    assert not missing, missing
+    assert set(declared) == set(G._SIGS), "binding and header disagree"
+    for f in declared:
+        assert hasattr(L, f)
+
+
+def test_defaults(L):
+    p = G.Params()
+    L.grnnd_params_default(ctypes.byref(p))
+    assert (p.S, p.R, p.T1, p.T2, p.final_prune, p.metric, p.precision, p.order) == (16, 32, 4, 8, 1, 0, 0, 0)
+    assert abs(p.rho - 0.6) < 1e-7
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(S=8, R=4), "S"),          # S > R
+    (dict(S=2, R=65), "R"),         # R above the 64-slot masks
+    (dict(S=2, R=1), "R"),
+    (dict(S=2, R=4, T1=0), "T1"),
+    (dict(S=2, R=4, rho=1.5), "rho"),
+    (dict(S=2, R=4, metric=7), "metric"),
+    (dict(S=2, R=4, order=9), "order"),
+])
+def test_build_rejects_bad_params_before_any_launch(L, kw, frag):
+    X = np.zeros((10, 3), np.float32)
+    with pytest.raises(G.GrnndError) as e:
+        G.build(X, **kw)
+    assert e.value.status == G.EINVAL
+    assert frag in str(e.value)
+
+
+def test_build_rejects_too_few_points(L):
+    with pytest.raises(G.GrnndError) as e:
+        G.build(np.zeros((1, 4), np.float32), S=1, R=2)
+    assert e.value.status == G.EINVAL
+    with pytest.raises(G.GrnndError) as e:   # S > n - 1
+        G.build(np.zeros((4, 4), np.float32), S=4, R=8)
+    assert e.value.status == G.EINVAL
+
+
+def test_step_calls_validate_layout(L):
+    null = ctypes.c_void_p(0)
+    bad = ctypes.c_void_p(16 * 1000 + 4)  # not 16-byte aligned
+    rc = L.grnnd_pool_init(bad, 10, 3, 4, 0, 2, 4, 0, null, null, null)
+    assert rc == G.EINVAL and b"aligned" in L.grnnd_last_error()
+    rc = L.grnnd_pool_init(ctypes.c_void_p(1 << 20), 10, 5, 5, 0, 2, 4, 0, null, null, null)
+    assert rc == G.EINVAL and b"ld" in L.grnnd_last_error()
+    rc = L.grnnd_search(null, null, 1, 1, 1, null)
+    assert rc == G.EINVAL
+
+
+def test_workspace_size_scales(L):
+    a = L.grnnd_workspace_size(1000, 32)
+    b = L.grnnd_workspace_size(2000, 32)
+    assert a > 1000 * 2 * 32 * 20 and b > a
+
+
+def test_key_codec_orders_like_dist_then_id():
+    ids = np.array([[3, 1, 2, -1]], np.int32)
+    d = np.array([[0.5, 0.5, -2.0, 0.0]], np.float32)
+    k = G.encode_keys(ids, d, np.array([[1, 0, 0, 0]]))
+    i2, d2, o2 = G.decode_keys(k)
+    assert (i2 == ids).all() and (o2 == [[1, 0, 0, 0]]).all()
+    assert d2[0, :3].tolist() == [0.5, 0.5, -2.0]
+    order = np.argsort(k[0, :3])
+    assert order.tolist() == [2, 1, 0]  # (-2, 2) < (0.5, 1) < (0.5, 3)

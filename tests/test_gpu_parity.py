@@ -1,0 +1,312 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar: on integer-valued inputs every FP32 distance is exact, so pools, graphs,
+entry points, search results and k-NN lists must be bit-identical to the
+oracle's (ties broken by id on both sides).  On continuous inputs one join
+step must give identical neighbour-id sets except where the oracle flags a
+comparison within the FP32 error bound, and every FP32 distance must be within
+1e-5 relative of FP64.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_02774_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd
+    grnnd.lib()
+    return grnnd
+
+
+def to_keys(G, pool):
+    return torch.from_numpy(G.encode_keys(pool.ids, pool.dist.astype(np.float32), pool.old).view(np.int64)).cuda()
+
+
+def from_gpu(G, keys, deg):
+    ids, dist, old = G.decode_keys(keys.cpu().numpy().view(np.uint64))
+    return ids, dist, old, deg.cpu().numpy()
+
+
+def assert_pool_equal(G, keys, deg, pool):
+    ids, dist, old, dg = from_gpu(G, keys, deg)
+    assert (dg == pool.deg).all(), np.nonzero(dg != pool.deg)[0][:10]
+    bad = np.nonzero((ids != pool.ids).any(1))[0]
+    assert len(bad) == 0, (bad[:5], ids[bad[0]], pool.ids[bad[0]])
+    assert (old == pool.old).all()
+    m = pool.ids >= 0
+    assert (dist[m] == pool.dist[m].astype(np.float32)).all()
+
+
+def oracle_state(orc, X, S, R, seed, rounds, metric=0, order=0):
+    p, _ = orc.init(X, S, R, seed, metric=metric)
+    for r in range(rounds):
+        p, _, _ = orc.round_(X, p, seed, 1, r + 1, order=order, metric=metric)
+    return p
+
+
+# ---------------------------------------------------------------------------------------
+# distances
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [1, 5, 33, 128, 200])
+@pytest.mark.parametrize("metric", [0, 1])
+def test_pair_dist_exact_on_integers(G, orc, d, metric):
+    X = synth.small_integers(400, d, -8, 8, seed=d)
+    Xd, _ = G.device_points(X)
+    g = np.random.default_rng(1)
+    pairs = g.integers(0, 400, size=(3000, 2)).astype(np.int32)
+    got = G.pair_dist(Xd, d, torch.from_numpy(pairs), metric).cpu().numpy()
+    want = np.array([orc.dist(X[a], X[b], metric) for a, b in pairs])
+    assert (got.astype(np.float64) == want).all()
+
+
+def test_pair_dist_fp32_within_1e5_of_fp64(G, orc):
+    X = synth.gaussian_mixture(2000, 128, 20, 10.0, 1.0, seed=0)
+    Xd, _ = G.device_points(X)
+    pairs = np.random.default_rng(2).integers(0, 2000, size=(4000, 2)).astype(np.int32)
+    pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+    got = G.pair_dist(Xd, 128, torch.from_numpy(pairs)).cpu().numpy().astype(np.float64)
+    want = np.array([orc.dist(X[a], X[b]) for a, b in pairs])
+    assert np.max(np.abs(got - want) / want) <= 1e-5
+
+
+# ---------------------------------------------------------------------------------------
+# rnd_init
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d,S,R", [(3000, 33, 16, 32), (700, 8, 64, 64), (2, 3, 1, 2), (65, 5, 64, 64)])
+def test_pool_init_matches_oracle(G, orc, n, d, S, R):
+    X = synth.small_integers(n, d, -8, 8, seed=n + d)
+    Xd, _ = G.device_points(X)
+    keys, deg = G.pool_init(Xd, d, S, R, seed=123)
+    pool, _ = orc.init(X, S, R, 123)
+    assert_pool_equal(G, keys, deg, pool)
+
+
+# ---------------------------------------------------------------------------------------
+# one round: rnd_join + rev_merge
+# ---------------------------------------------------------------------------------------
+
+CASES = [
+    # n, d, S, R, order, metric, rounds of history
+    (2000, 33, 16, 32, 0, 0, 0),
+    (2000, 33, 16, 32, 0, 0, 3),
+    (1500, 4, 8, 8, 0, 0, 2),        # many coincident points: ties everywhere
+    (1500, 200, 32, 64, 0, 0, 1),    # two dimension chunks, full-width masks
+    (1500, 16, 64, 64, 0, 0, 0),     # every pool starts full: 2016 pairs per vertex
+    (1200, 12, 16, 32, 1, 0, 2),     # ascending order (Alg 2)
+    (1200, 12, 16, 32, 2, 0, 2),     # descending order
+    (1200, 12, 16, 32, 0, 1, 2),     # inner product
+]
+
+
+@pytest.mark.parametrize("n,d,S,R,order,metric,hist", CASES)
+def test_join_round_matches_oracle(G, orc, n, d, S, R, order, metric, hist):
+    X = synth.small_integers(n, d, -3 if d <= 4 else -8, 3 if d <= 4 else 8, seed=7 * d + R)
+    Xd, _ = G.device_points(X)
+    seed = 99
+    p = oracle_state(orc, X, S, R, seed, hist, metric, order)
+    keys, deg = to_keys(G, p), torch.from_numpy(p.deg).cuda()
+    for t2 in (hist + 1, hist + 2):
+        want, _, st = orc.round_(X, p, seed, 1, t2, order=order, metric=metric)
+        stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+        keys, deg = G.join_round(Xd, d, keys, deg, seed, 1, t2, order, metric, stats=stats)
+        assert_pool_equal(G, keys, deg, want)
+        s = stats.cpu().numpy()
+        assert s[3] == st[1]          # pairs fired
+        assert s[4] == st[2]          # proposals
+        assert s[5] == int(((want.old == 0) & (want.ids >= 0)).sum())
+        p = want
+
+
+def test_join_round_skips_old_pairs_exactly(G, orc):
+    # the device always skips old x old pairs; the oracle evaluates them: same pools
+    X = synth.small_integers(1500, 10, -8, 8, seed=5)
+    Xd, _ = G.device_points(X)
+    p = oracle_state(orc, X, 16, 32, 3, 4)
+    assert p.old.sum() > 0
+    want, _, st_full = orc.round_(X, p, 3, 1, 5, skip_old=False)
+    _, _, st_skip = orc.round_(X, p, 3, 1, 5, skip_old=True)
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    keys, deg = G.join_round(Xd, 10, to_keys(G, p), torch.from_numpy(p.deg).cuda(), 3, 1, 5, stats=stats)
+    assert_pool_equal(G, keys, deg, want)
+    k = ((p.old == 0) & (p.ids >= 0)).sum(1).astype(np.int64)
+    m = p.deg.astype(np.int64)
+    assert stats[2].item() == int((k * (m - 1) - k * (k - 1) // 2).sum())  # pairs with a new side
+    assert st_skip[0] < st_full[0]
+
+
+def test_join_round_gaussian_config1(G, orc):
+    """10k x 32 mixture: one step from the same state gives the oracle's id sets except
+    on vertices the oracle flags as FP32-ambiguous (and the targets they reach)."""
+    X = synth.gaussian_mixture(10000, 32, 20, 10.0, 1.0, seed=0)
+    Xd, _ = G.device_points(X)
+    tol = 2 * (32 + 2) * 2.0**-24 * 2
+    p = oracle_state(orc, X, 16, 32, 0, 2)
+    want, flags, _ = orc.round_(X, p, 0, 1, 3, tol=tol)
+    keys, deg = G.join_round(Xd, 32, to_keys(G, p), torch.from_numpy(p.deg).cuda(), 0, 1, 3)
+    ids, dist, old, dg = from_gpu(G, keys, deg)
+    unsure = np.zeros(len(X), bool)
+    for v in np.nonzero(flags & 1)[0]:
+        unsure[v] = True
+        unsure[p.ids[v, :p.deg[v]]] = True
+    unsure |= (flags & 2) != 0
+    assert (flags != 0).mean() < 0.005      # FP32-ambiguous decisions are rare
+    assert unsure.mean() < 0.05             # ... and reach few targets
+    same = [set(ids[u, :dg[u]]) == set(want.ids[u, :want.deg[u]]) for u in range(len(X)) if not unsure[u]]
+    assert all(same)
+    m = (ids >= 0) & ~unsure[:, None] & (ids == want.ids)
+    rel = np.abs(dist[m].astype(np.float64) - want.dist[m]) / np.maximum(want.dist[m], 1e-30)
+    assert rel.max() <= 1e-5
+
+
+# ---------------------------------------------------------------------------------------
+# reverse sampling, final prune
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho", [0.0, 0.6, 1.0])
+def test_reverse_sample_matches_oracle(G, orc, rho):
+    X = synth.small_integers(3000, 9, -8, 8, seed=11)
+    p = oracle_state(orc, X, 16, 32, 5, 6)
+    want, _ = orc.reverse(p, rho)
+    keys, deg = G.reverse_sample(to_keys(G, p), torch.from_numpy(p.deg).cuda(), rho)
+    assert_pool_equal(G, keys, deg, want)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_final_prune_matches_oracle(G, orc, order):
+    X = synth.small_integers(2500, 20, -8, 8, seed=13)
+    Xd, _ = G.device_points(X)
+    p = oracle_state(orc, X, 16, 32, 8, 2)
+    gids, gd, gdeg, _ = orc.final_prune(X, p, 8, 9, order=order)
+    keys, deg = G.final_prune(Xd, 20, to_keys(G, p), torch.from_numpy(p.deg).cuda(), 8, 9, order)
+    ids, dist, _, dg = from_gpu(G, keys, deg)
+    assert (dg == gdeg).all() and (ids == gids).all()
+    m = gids >= 0
+    assert (dist[m] == gd[m].astype(np.float32)).all()
+
+
+# ---------------------------------------------------------------------------------------
+# whole build through grnnd_build_ex
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d,S,R,T1,T2,metric,order,final", [
+    (3000, 16, 8, 16, 3, 4, 0, 0, True),
+    (2000, 7, 12, 32, 2, 5, 0, 0, False),
+    (1500, 24, 16, 32, 2, 3, 1, 0, True),
+    (1500, 24, 16, 32, 2, 3, 0, 1, True),
+])
+def test_build_matches_oracle(G, orc, n, d, S, R, T1, T2, metric, order, final):
+    X = synth.small_integers(n, d, -8, 8, seed=n + d)
+    g = G.build(X, S=S, R=R, T1=T1, T2=T2, rho=0.6, seed=17, metric=metric, order=order, final_prune=final)
+    ids, dist, deg = g.to_numpy()
+    wids, wd, wdeg, _ = orc.build_graph(X, S, R, T1, T2, 0.6, 17, metric=metric, order=order, final_prune=final)
+    assert (deg == wdeg).all()
+    assert (ids == wids).all()
+    m = wids >= 0
+    assert (dist[m] == wd[m].astype(np.float32)).all()
+    assert g.entry == orc.entry(X, metric)
+    st = g.stats()
+    assert st["rounds"] >= 1 and st["pair_distances"] > 0
+
+
+def test_build_device_input_equals_host_input(G):
+    X = synth.gaussian_mixture(4000, 20, 8, 5.0, 1.0, seed=4)
+    a = G.build(X, S=8, R=16, T1=2, T2=3, seed=1).to_numpy()
+    b = G.build(torch.from_numpy(X).cuda(), S=8, R=16, T1=2, T2=3, seed=1).to_numpy()
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def test_build_is_deterministic(G):
+    X = synth.gaussian_mixture(5000, 32, 10, 10.0, 1.0, seed=9)
+    a = G.build(X, S=16, R=32, T1=2, T2=4, seed=3).to_numpy()
+    b = G.build(X, S=16, R=32, T1=2, T2=4, seed=3).to_numpy()
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def test_build_degenerate_inputs(G, orc):
+    # every point identical: all distances 0, every decision settled by ids
+    X = np.ones((300, 6), np.float32)
+    g = G.build(X, S=8, R=16, T1=2, T2=2, seed=2)
+    ids, dist, deg = g.to_numpy()
+    wids, _, wdeg, _ = orc.build_graph(X, 8, 16, 2, 2, 0.6, 2)
+    assert (ids == wids).all() and (deg == wdeg).all()
+    # the smallest problem: two points
+    g2 = G.build(np.array([[0.0], [1.0]], np.float32), S=1, R=2, T1=1, T2=1)
+    i2, d2, dg2 = g2.to_numpy()
+    assert dg2.tolist() == [1, 1] and i2[0, 0] == 1 and i2[1, 0] == 0 and d2[0, 0] == 1.0
+
+
+def test_build_rejects_non_finite(G):
+    X = np.zeros((50, 4), np.float32)
+    X[7, 2] = np.nan
+    with pytest.raises(G.GrnndError) as e:
+        G.build(X, S=4, R=8)
+    assert e.value.status == G.EINVAL
+
+
+def test_hbm_budget_is_checked_before_allocation(G):
+    X = np.zeros((1000, 8), np.float32)
+    with pytest.raises(G.GrnndError) as e:
+        G.build(X, S=4, R=8, hbm_budget=1000)
+    assert e.value.status == G.ENOMEM
+
+
+# ---------------------------------------------------------------------------------------
+# entry, search, k-NN
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_entry_point_matches_oracle(G, orc, metric):
+    X = synth.small_integers(5000, 13, -8, 8, seed=3)
+    Xd, _ = G.device_points(X)
+    assert G.entry_point(Xd, 13, metric) == orc.entry(X, metric)
+
+
+@pytest.mark.parametrize("beam", [10, 32, 64, 200])
+def test_search_matches_oracle(G, orc, beam):
+    X, Q = synth.small_integers(3000, 12, -8, 8, seed=21, nq=120)
+    gids, gd, gdeg, _ = orc.build_graph(X, 8, 16, 2, 3, 0.6, 4)
+    e = orc.entry(X)
+    want, wdist, _ = orc.search(gids, gdeg, X, Q, 10, beam, e)
+    Xd, _ = G.device_points(X)
+    Qd, _ = G.device_points(Q)
+    ids, dd = G.search_graph(Xd, 12, torch.from_numpy(gids).cuda(), torch.from_numpy(gdeg).cuda(), e, Qd, 10, beam)
+    assert (ids.cpu().numpy() == want).all()
+    assert (dd.cpu().numpy().astype(np.float64) == wdist).all()
+
+
+def test_search_api_matches_step_search(G):
+    X, Q = synth.gaussian_mixture(6000, 24, 10, 5.0, 1.0, seed=2, nq=200)
+    g = G.build(X, S=12, R=24, T1=2, T2=4, seed=5)
+    a = g.search(Q, 10, 48)
+    ids, _, deg = g.to_numpy()
+    Xd, _ = G.device_points(X)
+    Qd, _ = G.device_points(Q)
+    b, _ = G.search_graph(Xd, 24, torch.from_numpy(ids).cuda(), torch.from_numpy(deg).cuda(), g.entry, Qd, 10, 48)
+    assert (a == b.cpu().numpy()).all()
+    c = g.search(torch.from_numpy(Q).cuda(), 10, 48)
+    assert (c.cpu().numpy() == a).all()
+
+
+@pytest.mark.parametrize("n,d,k", [(3000, 33, 10), (777, 3, 32), (100, 130, 1)])
+def test_brute_knn_matches_oracle(G, orc, n, d, k):
+    X, Q = synth.small_integers(n, d, -4, 4, seed=n, nq=70)
+    want, wd = orc.brute_knn(X, Q, k)
+    Xd, _ = G.device_points(X)
+    Qd, _ = G.device_points(Q)
+    ids, dd = G.brute_knn(Xd, d, Qd, k)
+    assert (ids.cpu().numpy() == want).all()
+    assert (dd.cpu().numpy().astype(np.float64) == wd).all()
