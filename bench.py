@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""GRNND build benchmark on one GB300 (or N independent replicas under torchrun).
+
+A step is one whole build (Alg 3: rnd_init, T1 x T2 rounds of rnd_join + rev_merge,
+reverse sampling, final prune, export, search entry) of the SIFT-shaped synthetic
+workload: n = 1,000,000 points of d = 128, S = 32, R = 64, T1 = 4, T2 = 15, rho = 0.6,
+seeded, integer values in [0, 255].  `value` = points/s with the points resident in
+HBM; `e2e` = the same through grnnd_build with pinned host input and the graph read
+back to pinned host memory.  Recall@10 at beam 64 over 10,000 held-out queries is
+measured after the timed region.
+
+`--impl reference` times the FP64 CPU oracle (the correctness reference) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build points/s at recall@10>=0.95 (BF16 vs FP32, 1 GB300); p50/p99 build latency"
+WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 1000-cluster mixture, "
+                         "integers in [0,255]; S=32, R=64, T1=4, T2=15, rho=0.6; 10,000 queries, k=10, beam 64",
+                n=1_000_000, d=128, S=32, R=64, T1=4, T2=15, rho=0.6, nq=10_000, k=10, beam=64)
+# ncu DRAM bytes per rnd_join launch for the current kernel source (see profiles/);
+# reported only while the kernel source is unchanged since the capture.
+TRAFFIC = {"kernel": "rnd_join", "bytes_per_launch": None, "source_sha256": None}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (default: the full workload)")
+    ap.add_argument("--nq", type=int, default=WORKLOAD["nq"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.index = ids[local_rank] if local_rank < len(ids) and ids[local_rank].strip().isdigit() else str(local_rank)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", self.index, "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None,
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------
+
+def oracle_build_rate(X, n_sample: int):
+    from oracle import oracle as O
+    O.build()
+    Xs = X[:n_sample]
+    w = WORKLOAD
+    t = time.perf_counter()
+    O.build_graph(Xs, w["S"], w["R"], w["T1"], w["T2"], w["rho"], 0)
+    dt = time.perf_counter() - t
+    return n_sample / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2510_02774_gb300 import synth
+    X = synth.sift_like(args.n, 0, seed=args.seed)
+    n_s = 5000
+    for _ in range(args.warmup):
+        oracle_build_rate(X, n_s)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_build_rate(X, n_s)
+        times.append(dt)
+    tot = sum(times)
+    value = n_s * args.steps / tot
+    sample = (f"oracle build of the first {n_s} points of the same {args.n}-point dataset per step "
+              f"(S=32, R=64, T1=4, T2=15), single thread, FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**{k: v for k, v in WORKLOAD.items()}, "n": args.n, "sample_points": n_s},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+
+KERNELS_PER_GROUP = {"scan": 3, "entry": 4}
+
+
+def _source_sha():
+    with open(os.path.join(ROOT, "paper_2510_02774_gb300", "csrc", "pool_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def main():
+    args = _args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2510_02774_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2510_02774_gb300 import grnnd, synth
+    grnnd.lib()
+
+    w = WORKLOAD
+    n, d = args.n, w["d"]
+    X, Q = synth.sift_like(n, args.nq, seed=args.seed + rank)   # each replica builds its own dataset
+    Xd = torch.from_numpy(X).cuda()
+    kw = dict(S=w["S"], R=w["R"], T1=w["T1"], T2=w["T2"], rho=w["rho"], seed=args.seed)
+    stream = torch.cuda.current_stream()
+
+    def one_build():
+        return grnnd.build(Xd, **kw)
+
+    for _ in range(args.warmup):
+        g = one_build()
+        del g
+    torch.cuda.synchronize()
+
+    # ---- timed region: K builds with the points resident in HBM ----------------------
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    grnnd.profile_begin()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        g = one_build()
+        ev[i][1].record(stream)
+        stats.append(g.stats())
+        if i + 1 < args.steps:
+            del g
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kern = grnnd.profile_end()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    total_ms = e0.elapsed_time(e1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = n * world * args.steps / (total_ms / 1e3)
+
+    # ---- recall@10 at beam 64 on the last graph (not timed) --------------------------
+    recall = None
+    if not args.no_recall and args.nq > 0:
+        Xp, _ = grnnd.device_points(X)
+        Qp, _ = grnnd.device_points(Q)
+        gt, _ = grnnd.brute_knn(Xp, d, Qp, w["k"])
+        found = g.search(torch.from_numpy(Q).cuda(), w["k"], w["beam"])
+        gt_np, f_np = gt.cpu().numpy(), found.cpu().numpy()
+        recall = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w["k"] for a, b in zip(f_np, gt_np)]))
+        del Xp, Qp
+    del g
+
+    # ---- e2e: public API with pinned host input and the graph read back ----------------
+    e2e_steps = args.e2e_steps or args.steps
+    Xh = torch.from_numpy(X).pin_memory()
+    ids_h = torch.empty((n, w["R"]), dtype=torch.int32).pin_memory()
+    deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    import ctypes
+    L = grnnd.lib()
+
+    def e2e_step():
+        p = grnnd.params(**kw)
+        h = ctypes.c_void_p()
+        grnnd._check(L.grnnd_build_ex(ctypes.c_void_p(Xh.data_ptr()), n, d, ctypes.byref(p), ctypes.byref(h)))
+        grnnd._check(L.grnnd_graph_copy(h, ctypes.c_void_p(ids_h.data_ptr()), None, ctypes.c_void_p(deg_h.data_ptr())))
+        L.grnnd_free(h)
+
+    e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+    e2e_value = n * world * e2e_steps / float(t_e.item())
+
+    # ---- roofline of the dominant kernel ------------------------------------------------
+    dom = max(kern.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    agg = {k: sum(s[k] for s in stats) for k in stats[0]}
+    rounds = agg["rounds"]
+    if dom_name == "rnd_join":
+        algo = agg["rows_gathered"] * d * 4 + rounds * n * 4 + agg["proposals"] * (8 + 12 + 4)
+    elif dom_name in ("select", "scatter"):
+        algo = agg["proposals_merged"] * (8 + 8) + dom_launches / args.steps * args.steps * n * w["R"] * 8
+    else:
+        algo = None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    roof = None
+    if algo is not None:
+        achieved = algo / (dom_ms / 1e3) / 1e9
+        traffic = None
+        if TRAFFIC["kernel"] == dom_name and TRAFFIC["source_sha256"] == _source_sha():
+            traffic = TRAFFIC["bytes_per_launch"]
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": algo / dom_launches,
+                "avg_launch_ms": dom_ms / dom_launches, "launches": dom_launches}
+    launches = sum(v[0] * KERNELS_PER_GROUP.get(k, 1) for k, v in kern.items())
+
+    # ---- CPU baseline (oracle) on a bounded sample --------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = min(20000, n)
+        rate, dt = oracle_build_rate(X, n_s)
+        cpu = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n_s} points of the same dataset, same S/R/T1/T2/rho, FP64 single thread, {dt:.1f} s"}
+
+    if rank == 0:
+        q = sorted(step_ms)
+        p99 = q[min(len(q) - 1, int(round(0.99 * (len(q) - 1))))]
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {**{k: v for k, v in WORKLOAD.items()}, "n": n, "nq": args.nq, "precision": "fp32",
+                           "l2": "inputs larger than L2 (512 MB of points per replica)",
+                           "parallelism": f"{world} independent replica(s)"},
+                "p50_ms": statistics.median(step_ms), "p99_ms": p99, "recall@10": recall, "beam": w["beam"],
+                "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n * d * 4,
+                        "d2h_bytes_per_step": n * w["R"] * 4 + n * 4},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "kernels_ms": {k: round(v[1], 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])},
+                "build_stats": {k: v / args.steps for k, v in agg.items()}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

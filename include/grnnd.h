@@ -129,16 +129,31 @@ GRNND_API int grnnd_graph_view(const grnnd_graph *g, const int32_t **ids, const 
 /* Copies the graph into caller buffers (host or device; any may be NULL). */
 GRNND_API int grnnd_graph_copy(const grnnd_graph *g, int32_t *ids, float *dists, int32_t *deg);
 
-/* Counters of the last build of g: [0] rounds run, [1] vertices processed with
- * new entries, [2] candidate rows gathered, [3] pair distances evaluated,
- * [4] pairs fired, [5] proposals merged.  `out` is host memory of `count`
- * int64 slots; returns the number written. */
+/* Counters of the build of g: [0] rounds run, [1] vertex prunes with a new
+ * entry, [2] candidate rows gathered, [3] pair distances evaluated, [4] pairs
+ * fired, [5] proposals emitted by the rounds, [6] proposals merged (rounds and
+ * reverse sampling).  `out` is host memory of `count` int64 slots; returns the
+ * number written (at most 7). */
 GRNND_API int grnnd_graph_stats(const grnnd_graph *g, int64_t *out, int32_t count);
 
 GRNND_API void grnnd_free(grnnd_graph *g);
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
 GRNND_API const char *grnnd_last_error(void);
+
+/* Per-kernel timing (tracing).  Between grnnd_profile_begin and
+ * grnnd_profile_end every kernel that the calling thread launches through this
+ * library is bracketed by two CUDA events recorded on its launching stream.
+ * grnnd_profile_end synchronises those events and writes one entry per kernel
+ * name (launch count and summed event time in ms) into `out` (host memory,
+ * max_entries slots); *n_entries receives the number of distinct names. */
+typedef struct grnnd_kernel_time {
+    char name[32];
+    int64_t launches;
+    double ms;
+} grnnd_kernel_time;
+GRNND_API int grnnd_profile_begin(void);
+GRNND_API int grnnd_profile_end(grnnd_kernel_time *out, int32_t max_entries, int32_t *n_entries);
 
 /* ------------------------------------------------------------------------- */
 /* Step-level entry points on caller-owned device buffers                     */

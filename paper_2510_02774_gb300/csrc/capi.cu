@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "grnnd.h"
 #include "internal.h"
@@ -81,11 +82,90 @@ int check_R(int32_t R) {
   return GRNND_OK;
 }
 
+// ---- per-kernel event profiler (thread-local) ------------------------------------------
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  const char* open_name = nullptr;
+  cudaEvent_t open_ev = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+thread_local Profiler g_prof;
+
 }  // namespace
+
+namespace grnnd {
+void prof_start(const char* name, cudaStream_t st) {
+  if (!g_prof.on) return;
+  g_prof.open_name = name;
+  g_prof.open_ev = g_prof.get();
+  cudaEventRecord(g_prof.open_ev, st);
+}
+void prof_stop(cudaStream_t st) {
+  if (!g_prof.on || !g_prof.open_ev) return;
+  cudaEvent_t b = g_prof.get();
+  cudaEventRecord(b, st);
+  g_prof.recs.push_back({g_prof.open_name, g_prof.open_ev, b});
+  g_prof.open_ev = nullptr;
+}
+}  // namespace grnnd
 
 extern "C" {
 
 const char* grnnd_last_error(void) { return g_err.c_str(); }
+
+int grnnd_profile_begin(void) {
+  for (auto& r : g_prof.recs) {
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+  g_prof.on = true;
+  return GRNND_OK;
+}
+
+int grnnd_profile_end(grnnd_kernel_time* out, int32_t max_entries, int32_t* n_entries) {
+  g_prof.on = false;
+  std::vector<grnnd_kernel_time> acc;
+  for (auto& r : g_prof.recs) {
+    float ms = 0.0f;
+    GR_CU(cudaEventSynchronize(r.b));
+    GR_CU(cudaEventElapsedTime(&ms, r.a, r.b));
+    size_t i = 0;
+    while (i < acc.size() && std::strcmp(acc[i].name, r.name) != 0) ++i;
+    if (i == acc.size()) {
+      grnnd_kernel_time t;
+      std::memset(&t, 0, sizeof(t));
+      std::strncpy(t.name, r.name, sizeof(t.name) - 1);
+      acc.push_back(t);
+    }
+    acc[i].launches += 1;
+    acc[i].ms += ms;
+  }
+  for (auto& r : g_prof.recs) {
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+  if (n_entries) *n_entries = (int32_t)acc.size();
+  if (out)
+    for (int32_t i = 0; i < max_entries && i < (int32_t)acc.size(); ++i) out[i] = acc[i];
+  return GRNND_OK;
+}
 
 void grnnd_params_default(grnnd_params* p) {
   if (!p) return;
@@ -371,7 +451,8 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   g->stats[2] = h_stats[1];
   g->stats[3] = h_stats[2];
   g->stats[4] = h_stats[3];
-  g->stats[5] = h_stats[6];
+  g->stats[5] = h_stats[4];
+  g->stats[6] = h_stats[6];
   *graph_out = g;
   return GRNND_OK;
 }
@@ -445,7 +526,7 @@ int grnnd_graph_copy(const grnnd_graph* g, int32_t* ids, float* dists, int32_t* 
 
 int grnnd_graph_stats(const grnnd_graph* g, int64_t* out, int32_t count) {
   if (!g || !out || count < 0) return fail(GRNND_EINVAL, "bad arguments");
-  const int32_t c = std::min<int32_t>(count, 6);
+  const int32_t c = std::min<int32_t>(count, 7);
   for (int32_t i = 0; i < c; ++i) out[i] = g->stats[i];
   return c;
 }

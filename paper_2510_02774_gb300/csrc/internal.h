@@ -65,4 +65,14 @@ cudaError_t launch_brute_knn(const float* X, int64_t n, int d, int ld, int metri
 
 int sm_count();
 
+// Per-kernel event profiler of the calling thread (no-ops unless enabled).
+void prof_start(const char* name, cudaStream_t st);
+void prof_stop(cudaStream_t st);
+
+struct ProfScope {
+  cudaStream_t st;
+  ProfScope(const char* name, cudaStream_t s) : st(s) { prof_start(name, s); }
+  ~ProfScope() { prof_stop(st); }
+};
+
 }  // namespace grnnd

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
                              uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>(ceil_div(n, 8), (int64_t)sm_count() * 16);
+  ProfScope ps("rnd_init", st);
   if (metric == 0)
     rnd_init_kernel<0><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg);
   else
@@ -410,6 +411,7 @@ cudaError_t launch_join(const float* X, int64_t n, int d, int ld, int metric, in
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JT, smem);
   if (per_sm < 1) per_sm = 1;
   const int64_t blocks = std::min<int64_t>(n, (int64_t)sm_count() * per_sm);
+  ProfScope ps(mode == 0 ? "rnd_join" : "final_prune", st);
   kern<<<(unsigned)blocks, JT, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -450,6 +452,7 @@ __global__ void reverse_propose_kernel(int64_t n, int R, float rho,
 cudaError_t launch_reverse_propose(int64_t n, int R, float rho, const uint64_t* keys,
                                    const int32_t* deg, const Workspace& ws, cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
+  ProfScope ps("reverse_propose", st);
   reverse_propose_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, R, rho, keys, deg, ws.prop_tgt,
                                                           ws.prop_key, ws.count);
   return cudaGetLastError();
@@ -681,17 +684,26 @@ cudaError_t launch_merge(const Workspace& ws, int stride, uint64_t* keys_out, in
                          int64_t* stats, cudaStream_t st) {
   const int64_t n = ws.n;
   const int64_t nb = ceil_div(n, SCAN_TILE);
-  scan_reduce_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(ws.count, n, ws.bsum);
-  scan_blocks_kernel<<<1, 1024, 0, st>>>(ws.bsum, nb, ws.off + n);
-  scan_apply_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(ws.count, n, ws.bsum, ws.off);
+  {
+    ProfScope ps("scan", st);
+    scan_reduce_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(ws.count, n, ws.bsum);
+    scan_blocks_kernel<<<1, 1024, 0, st>>>(ws.bsum, nb, ws.off + n);
+    scan_apply_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(ws.count, n, ws.bsum, ws.off);
+  }
   const int64_t nslots = n * stride;
   const int64_t sblocks = std::min<int64_t>(ceil_div(nslots, 256), (int64_t)sm_count() * 32);
-  scatter_kernel<<<(unsigned)sblocks, 256, 0, st>>>(ws.prop_tgt, ws.prop_key, nslots, ws.off,
-                                                   ws.count, ws.bucket);
+  {
+    ProfScope ps("scatter", st);
+    scatter_kernel<<<(unsigned)sblocks, 256, 0, st>>>(ws.prop_tgt, ws.prop_key, nslots, ws.off,
+                                                     ws.count, ws.bucket);
+  }
   cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
   const int64_t blocks = std::min<int64_t>(ceil_div(n, 8), (int64_t)sm_count() * 16);
-  select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws.bucket, ws.off, n, ws.R, keys_out, deg_out,
-                                                 ws.round_new, stats);
+  {
+    ProfScope ps("select", st);
+    select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws.bucket, ws.off, n, ws.R, keys_out, deg_out,
+                                                   ws.round_new, stats);
+  }
   return cudaGetLastError();
 }
 
@@ -714,6 +726,7 @@ cudaError_t launch_keys_to_graph(int64_t n, int R, const uint64_t* keys, int32_t
   (void)deg;
   const int64_t total = n * R;
   const int64_t blocks = std::min<int64_t>(ceil_div(total, 256), (int64_t)sm_count() * 32);
+  ProfScope ps("export", st);
   keys_to_graph_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(total, R, keys, ids,
                                                                              dists);
   return cudaGetLastError();

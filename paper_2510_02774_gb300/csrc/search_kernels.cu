@@ -53,6 +53,7 @@ __global__ void check_finite_kernel(const float* __restrict__ X, int64_t n, int 
 cudaError_t launch_check_finite(const float* X, int64_t n, int d, int ld, int32_t* flag,
                                 cudaStream_t st) {
   const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n * d, 256), (int64_t)sm_count() * 8);
+  ProfScope ps("check_finite", st);
   check_finite_kernel<<<std::max(blocks, 1u), 256, 0, st>>>(X, n, d, ld, flag);
   return cudaGetLastError();
 }
@@ -164,6 +165,7 @@ cudaError_t launch_entry(const float* X, int64_t n, int d, int ld, int metric, i
   int32_t* bi = reinterpret_cast<int32_t*>(p);
   const int64_t rpb = ceil_div(n, kEntryBlocks);
   const int nb = (int)ceil_div(n, rpb);
+  ProfScope ps("entry", st);
   colsum_kernel<<<nb, 256, 0, st>>>(X, n, d, ld, rpb, partial);
   mean_kernel<<<(unsigned)ceil_div(d, 256), 256, 0, st>>>(partial, nb, d, n, mu);
   const int nb2 = (int)std::min<int64_t>(kEntryBlocks, ceil_div(n, 256));
@@ -304,6 +306,7 @@ cudaError_t launch_search(const float* X, int64_t n, int d, int ld, int metric,
   if (nq == 0) return cudaSuccess;
   if (d > kMaxD || beam > kMaxBeam) return cudaErrorInvalidValue;
   const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nq, SW), (int64_t)sm_count() * 8);
+  ProfScope ps("search", st);
   if (metric == 0)
     search_kernel<0><<<blocks, SW * 32, 0, st>>>(X, n, d, ld, gids, gdeg, R, entry, Q, nq, ldq, k,
                                                  beam, ids_out, dists_out);
@@ -410,6 +413,7 @@ cudaError_t launch_brute_knn(const float* X, int64_t n, int d, int ld, int metri
   if (nq == 0) return cudaSuccess;
   if (k < 1 || k > KMAX) return cudaErrorInvalidValue;
   const unsigned blocks = (unsigned)ceil_div(nq, BQ);
+  ProfScope ps("brute_knn", st);
   if (metric == 0)
     brute_knn_kernel<0><<<blocks, 256, 0, st>>>(X, n, d, ld, Q, nq, ldq, k, ids_out, dists_out);
   else

@@ -41,7 +41,13 @@ class Params(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_uint64)]
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
 _SIGS = {
+    "grnnd_profile_begin": (ctypes.c_int, []),
+    "grnnd_profile_end": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     # name: (restype, argtypes)
     "grnnd_params_default": (None, [ctypes.POINTER(Params)]),
     "grnnd_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -119,6 +125,19 @@ def _check(rc: int):
 # torch helpers (device memory and streams only)
 # ---------------------------------------------------------------------------------------
 
+def profile_begin():
+    """Starts per-kernel CUDA-event timing of this thread's library launches."""
+    _check(lib().grnnd_profile_begin())
+
+
+def profile_end() -> dict:
+    """Stops timing; returns {kernel name: (launches, total ms)}."""
+    buf = (KernelTime * 64)()
+    n = ctypes.c_int32()
+    _check(lib().grnnd_profile_end(buf, 64, ctypes.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(min(n.value, 64))}
+
+
 def _torch():
     import torch
     return torch
@@ -183,9 +202,10 @@ class Graph:
         return ids, dists, deg
 
     def stats(self):
-        out = np.zeros(6, np.int64)
-        lib().grnnd_graph_stats(self.handle, out.ctypes.data_as(ctypes.c_void_p), 6)
-        keys = ["rounds", "vertices_with_new", "rows_gathered", "pair_distances", "pairs_fired", "proposals_merged"]
+        out = np.zeros(7, np.int64)
+        lib().grnnd_graph_stats(self.handle, out.ctypes.data_as(ctypes.c_void_p), 7)
+        keys = ["rounds", "vertices_with_new", "rows_gathered", "pair_distances", "pairs_fired", "proposals",
+                "proposals_merged"]
         return dict(zip(keys, out.tolist()))
 
     def search(self, queries, k: int = 10, beam: int = 64):
