@@ -242,6 +242,22 @@ GRNND_API int grnnd_brute_knn(const float *points, int64_t n, int32_t d, int32_t
 GRNND_API int grnnd_keys_to_graph(int64_t n, int32_t R, const uint64_t *keys, int32_t *ids, float *dists,
                         void *stream);
 
+/* Search entry without device allocation.  The paper has no counterpart: this
+ * is a library service for callers that may not allocate device memory when
+ * they need the entry point (an application that owns all GPU memory through
+ * its own arena, a latency-critical loop that must not pay cudaMalloc's
+ * implicit synchronisation, a plugin given buffers but no allocator).  Same
+ * result as grnnd_entry_point; the scratch is one fixed device array of
+ * 4,208,640 bytes inside the library (held on every GPU that loads it until
+ * exit), so 1 <= d <= 1024 (larger d returns GRNND_EINVAL).  No cudaMalloc or
+ * cudaFree is called.  The first call on a device looks up the array's address
+ * with that device current; make it before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the GPU race, so order them on
+ * one stream.  points: device n x ld (16-byte aligned, ld % 4 == 0);
+ * entry_out: device int32[1]. */
+GRNND_API int grnnd_entry_point_noalloc(const float *points, int64_t n, int32_t d, int32_t ld,
+                                        int32_t metric, int32_t *entry_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,8 @@ thread_local Profiler g_prof;
 }  // namespace
 
 namespace grnnd {
+void set_last_error(const std::string& msg) { g_err = msg; }
+
 void prof_start(const char* name, cudaStream_t st) {
   if (!g_prof.on) return;
   g_prof.open_name = name;

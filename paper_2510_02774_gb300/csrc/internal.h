@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace grnnd {
@@ -64,6 +65,9 @@ cudaError_t launch_brute_knn(const float* X, int64_t n, int d, int ld, int metri
                              cudaStream_t st);
 
 int sm_count();
+
+// Sets the thread-local message returned by grnnd_last_error.
+void set_last_error(const std::string& msg);
 
 // Per-kernel event profiler of the calling thread (no-ops unless enabled).
 void prof_start(const char* name, cudaStream_t st);

@@ -84,6 +84,8 @@ _SIGS = {
     "grnnd_entry_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
     "grnnd_entry_point": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "grnnd_entry_point_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_search_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
@@ -322,6 +324,16 @@ def entry_point(X, d: int, metric: int = L2SQ, stream=None) -> int:
     ws = torch.empty(int(lib().grnnd_entry_workspace_size(n, d)), dtype=torch.uint8, device=X.device)
     e = torch.empty(1, dtype=torch.int32, device=X.device)
     _check(lib().grnnd_entry_point(_ptr(X), n, d, ld, metric, _ptr(e), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return int(e.item())
+
+
+def entry_point_noalloc(X, d: int, metric: int = L2SQ, out=None, stream=None) -> int:
+    """Search entry computed with the library's fixed device scratch (no allocation by
+    the library; `out` may be a caller-provided device int32 tensor of one element)."""
+    torch = _torch()
+    n, ld = X.shape
+    e = torch.empty(1, dtype=torch.int32, device=X.device) if out is None else out
+    _check(lib().grnnd_entry_point_noalloc(_ptr(X), n, d, ld, metric, _ptr(e), _stream_ptr(stream)))
     return int(e.item())
 
 
