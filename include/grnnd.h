@@ -131,9 +131,10 @@ GRNND_API int grnnd_graph_copy(const grnnd_graph *g, int32_t *ids, float *dists,
 
 /* Counters of the build of g: [0] rounds run, [1] vertex prunes with a new
  * entry, [2] candidate rows gathered, [3] pair distances evaluated, [4] pairs
- * fired, [5] proposals emitted by the rounds, [6] proposals merged (rounds and
- * reverse sampling).  `out` is host memory of `count` int64 slots; returns the
- * number written (at most 7). */
+ * fired, [5] proposals of the rounds (every pool entry once per round), [6]
+ * redirects and reverse proposals merged, [7] BF16 decisions re-taken in FP32.
+ * `out` is host memory of `count` int64 slots; returns the number written (at
+ * most 8). */
 GRNND_API int grnnd_graph_stats(const grnnd_graph *g, int64_t *out, int32_t count);
 
 GRNND_API void grnnd_free(grnnd_graph *g);
@@ -188,7 +189,8 @@ GRNND_API size_t grnnd_workspace_size(int64_t n, int32_t R);
  * the caller swaps the two pools afterwards, which is pool_swap).
  * stats (optional, device int64[8], accumulated): [0] vertices with new
  * entries, [1] rows gathered, [2] pair distances, [3] pairs fired,
- * [4] proposals, [5] new entries in pool_out. */
+ * [4] proposals (every pool entry, proposed explicitly or kept in place),
+ * [5] new entries in pool_out, [6] redirects merged. */
 GRNND_API int grnnd_join_round(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
                      int32_t R, const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
                      int32_t t1, int32_t t2, int32_t order, uint64_t *keys_out, int32_t *deg_out,
@@ -204,11 +206,12 @@ GRNND_API int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64
 
 /* Final prune-only pass: the prune of a round with order key t1 (t2 = 0),
  * keeping only each vertex's survivors, in key order; no redirects.
- * keys_out: device n x R (written in full), deg_out: device n. */
+ * keys_out: device n x R (written in full, must not alias keys_in), deg_out:
+ * device n; workspace as for grnnd_join_round. */
 GRNND_API int grnnd_final_prune(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
                       int32_t R, const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
                       int32_t t1, int32_t order, uint64_t *keys_out, int32_t *deg_out,
-                      void *stream);
+                      void *workspace, size_t workspace_bytes, void *stream);
 
 /* Canonical FP32 distances of np point pairs: out[i] = d(points[pairs[2i]],
  * points[pairs[2i+1]]) exactly as the pool kernels compute it.  pairs: device

@@ -224,10 +224,13 @@ int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int3
   if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
     return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
-  GR_CU(grnnd::launch_join(points, n, d, ld, metric, R, keys_in, deg_in, seed, t1, t2, order, 0,
-                           ws, nullptr, nullptr, stats, st));
-  GR_CU(grnnd::launch_merge(ws, R, keys_out, deg_out, stats, st));
+  grnnd::PointsSet P;
+  P.X = points;
+  P.ld = ld;
+  P.d = d;
+  P.metric = metric;
+  GR_CU(grnnd::launch_round(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out, deg_out,
+                            stats, st));
   if (stats) GR_CU(cudaMemcpyAsync(stats + 5, ws.round_new, 8, cudaMemcpyDeviceToDevice, st));
   return GRNND_OK;
 }
@@ -245,25 +248,32 @@ int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t* keys_i
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
     return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
-  cudaStream_t st = (cudaStream_t)stream;
-  GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
-  GR_CU(grnnd::launch_reverse_propose(n, R, rho, keys_in, deg_in, ws, st));
-  GR_CU(grnnd::launch_merge(ws, 2 * R, keys_out, deg_out, stats, st));
+  GR_CU(grnnd::launch_reverse(n, R, rho, keys_in, deg_in, ws, keys_out, deg_out, stats,
+                              (cudaStream_t)stream));
   return GRNND_OK;
 }
 
 int grnnd_final_prune(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
                       int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
                       int32_t t1, int32_t order, uint64_t* keys_out, int32_t* deg_out,
-                      void* stream) {
+                      void* workspace, size_t workspace_bytes, void* stream) {
   int rc = check_step_points(points, n, d, ld, metric);
   if (rc) return rc;
   if ((rc = check_R(R))) return rc;
   if (!keys_in || !deg_in || !keys_out || !deg_out) return fail(GRNND_EINVAL, "pool buffer is NULL");
+  if (keys_in == keys_out || deg_in == deg_out)
+    return fail(GRNND_EINVAL, "output pool must not alias the input pool");
   if (order < 0 || order > 2) return fail(GRNND_EINVAL, "unknown order");
-  grnnd::Workspace ws;  // the final pass emits no proposals
-  GR_CU(grnnd::launch_join(points, n, d, ld, metric, R, keys_in, deg_in, seed, t1, 0, order, 1, ws,
-                           keys_out, deg_out, nullptr, (cudaStream_t)stream));
+  grnnd::Workspace ws;
+  if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
+    return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
+  grnnd::PointsSet P;
+  P.X = points;
+  P.ld = ld;
+  P.d = d;
+  P.metric = metric;
+  GR_CU(grnnd::launch_final(P, n, R, keys_in, deg_in, seed, t1, order, ws, keys_out, deg_out,
+                            (cudaStream_t)stream));
   return GRNND_OK;
 }
 
@@ -343,17 +353,21 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return fail(GRNND_EINVAL, "rho must be in [0, 1]");
   if (p->metric != GRNND_L2SQ && p->metric != GRNND_IP) return fail(GRNND_EINVAL, "unknown metric");
   if (p->order < 0 || p->order > 2) return fail(GRNND_EINVAL, "unknown order");
-  if (p->precision != GRNND_FP32) return fail(GRNND_EINVAL, "only GRNND_FP32 is available in this build");
+  if (p->precision != GRNND_FP32 && p->precision != GRNND_BF16)
+    return fail(GRNND_EINVAL, "unknown precision");
   const int32_t R = p->R, ld = round4(d);
+  const bool bf16 = p->precision == GRNND_BF16;
+  const int32_t ldb = (d + 15) & ~15;
   cudaStream_t st = (cudaStream_t)p->stream;
 
   const size_t pts_b = al256((size_t)n * ld * 4);
+  const size_t q_b = bf16 ? al256((size_t)n * ldb * 2) + al256((size_t)n * 8) + 256 : 0;
   const size_t pool_b = al256((size_t)n * R * 8), deg_b = al256((size_t)n * 4);
   const size_t ws_b = grnnd::workspace_bytes(n, R);
   const size_t ent_b = grnnd::entry_workspace_bytes(n, d);
   const size_t graph_b = al256((size_t)n * R * 4) * 2 + deg_b;
   const size_t stats_b = 256;
-  const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b;
+  const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b + q_b;
   if (p->hbm_budget && pts_b + graph_b + scratch_b > p->hbm_budget)
     return fail(GRNND_ENOMEM, "build needs " + std::to_string(pts_b + graph_b + scratch_b) +
                                   " bytes, above hbm_budget " + std::to_string(p->hbm_budget));
@@ -375,6 +389,7 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   int64_t* stats = reinterpret_cast<int64_t*>(sp + 2 * pool_b + 2 * deg_b);
   void* wsp = sp + 2 * pool_b + 2 * deg_b + stats_b;
   const size_t wsp_b = std::max(ws_b, ent_b);
+  char* qp = sp + 2 * pool_b + 2 * deg_b + stats_b + al256(wsp_b);
 
   // points -> padded device rows
   const cudaMemcpyKind kind = is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -390,14 +405,27 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   GR_CU(cudaStreamSynchronize(st));
   if (h_flag) return fail(GRNND_EINVAL, "points contain a non-finite value");
 
+  grnnd::PointsSet P;
+  P.X = X;
+  P.ld = ld;
+  P.d = d;
+  P.metric = p->metric;
+  if (bf16) {
+    P.precision = 1;
+    P.Xb = qp;
+    P.ldb = ldb;
+    P.aux = reinterpret_cast<const float2*>(qp + al256((size_t)n * ldb * 2));
+    P.qflags = reinterpret_cast<const unsigned*>(qp + al256((size_t)n * ldb * 2) + al256((size_t)n * 8));
+    GR_CU(grnnd::launch_quantize(X, n, d, ld, qp, ldb, const_cast<float2*>(P.aux),
+                                 const_cast<unsigned*>(P.qflags), st));
+  }
+
   GR_CU(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st));
   int64_t rounds = 0;
   for (int32_t t1 = 1; t1 <= p->T1; ++t1) {
     for (int32_t t2 = 1; t2 <= p->T2; ++t2) {
-      GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
-      GR_CU(grnnd::launch_join(X, n, d, ld, p->metric, R, poolA, degA, p->seed, t1, t2, p->order, 0,
-                               ws, nullptr, nullptr, stats, st));
-      GR_CU(grnnd::launch_merge(ws, R, poolB, degB, stats, st));
+      GR_CU(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolB, degB,
+                                stats, st));
       std::swap(poolA, poolB);  // pool_swap: the written pool is read next round
       std::swap(degA, degB);
       ++rounds;
@@ -407,9 +435,7 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
       if (fresh == 0) break;  // no new entry anywhere: the remaining rounds are identities
     }
     if (t1 != p->T1) {
-      GR_CU(cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st));
-      GR_CU(grnnd::launch_reverse_propose(n, R, p->rho, poolA, degA, ws, st));
-      GR_CU(grnnd::launch_merge(ws, 2 * R, poolB, degB, nullptr, st));
+      GR_CU(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolB, degB, nullptr, st));
       std::swap(poolA, poolB);
       std::swap(degA, degB);
     }
@@ -417,8 +443,7 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   uint64_t* gkeys = poolA;
   int32_t* gdg = degA;
   if (p->final_prune) {
-    GR_CU(grnnd::launch_join(X, n, d, ld, p->metric, R, poolA, degA, p->seed, p->T1 + 1, 0, p->order,
-                             1, ws, poolB, degB, nullptr, st));
+    GR_CU(grnnd::launch_final(P, n, R, poolA, degA, p->seed, p->T1 + 1, p->order, ws, poolB, degB, st));
     gkeys = poolB;
     gdg = degB;
   }
@@ -455,6 +480,7 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   g->stats[4] = h_stats[3];
   g->stats[5] = h_stats[4];
   g->stats[6] = h_stats[6];
+  g->stats[7] = h_stats[7];
   *graph_out = g;
   return GRNND_OK;
 }
@@ -528,7 +554,7 @@ int grnnd_graph_copy(const grnnd_graph* g, int32_t* ids, float* dists, int32_t* 
 
 int grnnd_graph_stats(const grnnd_graph* g, int64_t* out, int32_t count) {
   if (!g || !out || count < 0) return fail(GRNND_EINVAL, "bad arguments");
-  const int32_t c = std::min<int32_t>(count, 7);
+  const int32_t c = std::min<int32_t>(count, 8);
   for (int32_t i = 0; i < c; ++i) out[i] = g->stats[i];
   return c;
 }

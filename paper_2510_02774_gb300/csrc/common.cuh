@@ -42,8 +42,11 @@ __device__ __forceinline__ uint32_t key_id(uint64_t k) { return (uint32_t)(k >> 
 __device__ __forceinline__ float key_dist(uint64_t k) { return from_ordered((uint32_t)(k >> 32)); }
 __device__ __forceinline__ uint32_t key_old(uint64_t k) { return (uint32_t)k & 1u; }
 
-// ---- canonical FP32 distance: one rounded op per dimension, ascending order ----------
-// L2SQ: t = a - b (rounded), acc = fma(t, t, acc).  IP: acc = fma(a, b, acc), d = 1 - acc.
+// ---- canonical FP32 distance -------------------------------------------------------------
+// Four partial sums, s_j over the dimensions k = j (mod 4) in ascending k, each step one
+// rounded op: L2SQ t = a - b, s_j = fma(t, t, s_j); IP s_j = fma(a, b, s_j).  The result
+// is (s_0 + s_1) + (s_2 + s_3) (IP: 1 - that).  Every kernel that records a distance uses
+// exactly this evaluation, so a pair gets the same bits wherever it is computed.
 template <int METRIC>
 __device__ __forceinline__ float dist_step(float acc, float a, float b) {
   if (METRIC == 0) {
@@ -53,30 +56,50 @@ __device__ __forceinline__ float dist_step(float acc, float a, float b) {
   return __fmaf_rn(a, b, acc);
 }
 template <int METRIC>
+__device__ __forceinline__ void dist_step4(float4& acc, float4 a, float4 b) {
+  acc.x = dist_step<METRIC>(acc.x, a.x, b.x);
+  acc.y = dist_step<METRIC>(acc.y, a.y, b.y);
+  acc.z = dist_step<METRIC>(acc.z, a.z, b.z);
+  acc.w = dist_step<METRIC>(acc.w, a.w, b.w);
+}
+template <int METRIC>
+__device__ __forceinline__ float dist_finish4(float4 acc) {
+  const float s = __fadd_rn(__fadd_rn(acc.x, acc.y), __fadd_rn(acc.z, acc.w));
+  return METRIC == 0 ? s : __fsub_rn(1.0f, s);
+}
+// Single-accumulator finish for the query-side kernels (their order is free).
+template <int METRIC>
 __device__ __forceinline__ float dist_finish(float acc) {
   return METRIC == 0 ? acc : __fsub_rn(1.0f, acc);
 }
-template <int METRIC>
-__device__ __forceinline__ float dist_step4(float acc, float4 a, float4 b) {
-  acc = dist_step<METRIC>(acc, a.x, b.x);
-  acc = dist_step<METRIC>(acc, a.y, b.y);
-  acc = dist_step<METRIC>(acc, a.z, b.z);
-  return dist_step<METRIC>(acc, a.w, b.w);
+// Keeps the first `keep` (0..3) components of v and zeroes the others.
+__device__ __forceinline__ float4 mask4(float4 v, int keep) {
+  if (keep < 4) v.w = 0.0f;
+  if (keep < 3) v.z = 0.0f;
+  if (keep < 2) v.y = 0.0f;
+  if (keep < 1) v.x = 0.0f;
+  return v;
 }
 
-// Canonical distance of two rows in global memory (16-byte aligned rows).
+// Canonical distance of two rows in global memory (16-byte aligned rows, d dims).
 template <int METRIC>
 __device__ __forceinline__ float row_dist(const float* __restrict__ a, const float* __restrict__ b,
                                           int d) {
-  float acc = 0.0f;
+  float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   int k = 0;
-  for (; k + 4 <= d; k += 4) {
-    float4 x = __ldg(reinterpret_cast<const float4*>(a + k));
-    float4 y = __ldg(reinterpret_cast<const float4*>(b + k));
-    acc = dist_step4<METRIC>(acc, x, y);
+  for (; k + 4 <= d; k += 4)
+    dist_step4<METRIC>(acc, __ldg(reinterpret_cast<const float4*>(a + k)),
+                       __ldg(reinterpret_cast<const float4*>(b + k)));
+  if (k < d) {
+    const int r = d - k;
+    float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f), y = x;
+    x.x = __ldg(a + k);
+    y.x = __ldg(b + k);
+    if (r > 1) { x.y = __ldg(a + k + 1); y.y = __ldg(b + k + 1); }
+    if (r > 2) { x.z = __ldg(a + k + 2); y.z = __ldg(b + k + 2); }
+    dist_step4<METRIC>(acc, x, y);
   }
-  for (; k < d; ++k) acc = dist_step<METRIC>(acc, __ldg(a + k), __ldg(b + k));
-  return dist_finish<METRIC>(acc);
+  return dist_finish4<METRIC>(acc);
 }
 
 // ---- warp bitonic sort of 32*E uint64 values, element index e = j*32 + lane ----------

@@ -8,19 +8,34 @@
 
 namespace grnnd {
 
-// Device workspace of one round / reverse step for n vertices of capacity R.
-// Proposal slots: 2R per vertex (a round uses R, reverse sampling 2R).
+// Device workspace of one round, final pass or reverse step for n vertices of capacity R.
 struct Workspace {
   int64_t n = 0;
   int R = 0;
-  int32_t* prop_tgt = nullptr;   // n*2R target vertex or -1
-  uint64_t* prop_key = nullptr;  // n*2R pool key of the proposal
-  uint64_t* bucket = nullptr;    // n*2R keys bucketed by target
-  int32_t* count = nullptr;      // n proposals per target (zero between steps)
-  int64_t* off = nullptr;        // n+1 exclusive prefix of count
-  int64_t* bsum = nullptr;       // scan block sums
-  int32_t* err = nullptr;        // device status word (bounded waits)
-  int64_t* round_new = nullptr;  // new entries written by the last merge
+  int32_t* red_tgt = nullptr;              // n*R redirect / reverse-proposal targets
+  uint64_t* red_key = nullptr;             // n*R their keys
+  uint64_t* bucket = nullptr;              // n*R keys bucketed by target
+  int32_t* count = nullptr;                // n proposals per target (zeroed per step)
+  int64_t* off = nullptr;                  // n+1 exclusive prefix of count
+  int64_t* bsum = nullptr;                 // scan block sums
+  int32_t* list = nullptr;                 // n vertices with a new entry
+  uint8_t* active = nullptr;               // n flags: the vertex is in the list
+  int32_t* list_n = nullptr;               // length of the list
+  unsigned long long* red_n = nullptr;     // number of redirects / reverse proposals
+  int32_t* err = nullptr;                  // device status word (bounded waits)
+  int64_t* round_new = nullptr;            // new entries written by the last merge
+};
+
+// The points as the pool kernels read them.  precision 0: FP32 rows only; 1: also a
+// BF16 copy (ldb = d rounded up to 16), per-row (norm^2, residual) and dataset flags.
+struct PointsSet {
+  const float* X = nullptr;
+  int ld = 0;
+  const void* Xb = nullptr;
+  int ldb = 0;
+  const float2* aux = nullptr;
+  const unsigned* qflags = nullptr;
+  int d = 0, metric = 0, precision = 0;
 };
 
 size_t workspace_bytes(int64_t n, int R);
@@ -29,18 +44,24 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws);
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
                              uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st);
 
-// mode 0: emit proposals of a round into ws; mode 1: final prune into out_keys/out_deg.
-cudaError_t launch_join(const float* X, int64_t n, int d, int ld, int metric, int R,
-                        const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed, int t1,
-                        int t2, int order, int mode, const Workspace& ws, uint64_t* out_keys,
-                        int32_t* out_deg, int64_t* stats, cudaStream_t st);
+cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xb, int ldb,
+                            float2* aux, unsigned* qflags, cudaStream_t st);
 
-cudaError_t launch_reverse_propose(int64_t n, int R, float rho, const uint64_t* keys,
-                                   const int32_t* deg, const Workspace& ws, cudaStream_t st);
+// One round of Alg 4: prep + rnd_join + scan + scatter + select (keys_out != keys_in).
+cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
+                         const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,
+                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int64_t* stats,
+                         cudaStream_t st);
 
-// scan + scatter + per-target select of the proposals in ws (stride slots per vertex).
-cudaError_t launch_merge(const Workspace& ws, int stride, uint64_t* keys_out, int32_t* deg_out,
-                         int64_t* stats, cudaStream_t st);
+// Final prune-only pass: survivors only, no redirects.
+cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
+                         const int32_t* deg_in, uint64_t seed, int t1, int order,
+                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st);
+
+// Reverse-edge sampling + merge.
+cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
+                           const int32_t* deg_in, const Workspace& ws, uint64_t* keys_out,
+                           int32_t* deg_out, int64_t* stats, cudaStream_t st);
 
 cudaError_t launch_keys_to_graph(int64_t n, int R, const uint64_t* keys, int32_t* ids,
                                  float* dists, int32_t* deg, cudaStream_t st);

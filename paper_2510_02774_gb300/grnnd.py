@@ -78,7 +78,8 @@ _SIGS = {
                                             ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_final_prune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
-                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]),
     "grnnd_pair_dist": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_entry_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
@@ -204,10 +205,10 @@ class Graph:
         return ids, dists, deg
 
     def stats(self):
-        out = np.zeros(7, np.int64)
-        lib().grnnd_graph_stats(self.handle, out.ctypes.data_as(ctypes.c_void_p), 7)
+        out = np.zeros(8, np.int64)
+        lib().grnnd_graph_stats(self.handle, out.ctypes.data_as(ctypes.c_void_p), 8)
         keys = ["rounds", "vertices_with_new", "rows_gathered", "pair_distances", "pairs_fired", "proposals",
-                "proposals_merged"]
+                "merged", "rechecks"]
         return dict(zip(keys, out.tolist()))
 
     def search(self, queries, k: int = 10, beam: int = 64):
@@ -298,14 +299,16 @@ def reverse_sample(keys, deg, rho: float, ws=None, stats=None, stream=None):
     return k2, d2
 
 
-def final_prune(X, d: int, keys, deg, seed: int, t1: int, order: int = ORDER_RANDOM, metric: int = L2SQ, stream=None):
+def final_prune(X, d: int, keys, deg, seed: int, t1: int, order: int = ORDER_RANDOM, metric: int = L2SQ, ws=None,
+                stream=None):
     torch = _torch()
     n, ld = X.shape
     R = keys.shape[1]
+    ws = workspace(n, R, X.device) if ws is None else ws
     k2 = torch.empty_like(keys)
     d2 = torch.empty_like(deg)
     _check(lib().grnnd_final_prune(_ptr(X), n, d, ld, metric, R, _ptr(keys), _ptr(deg), seed, t1, order, _ptr(k2),
-                                   _ptr(d2), _stream_ptr(stream)))
+                                   _ptr(d2), _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return k2, d2
 
 

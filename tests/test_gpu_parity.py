@@ -310,3 +310,75 @@ def test_brute_knn_matches_oracle(G, orc, n, d, k):
     ids, dd = G.brute_knn(Xd, d, Qd, k)
     assert (ids.cpu().numpy() == want).all()
     assert (dd.cpu().numpy().astype(np.float64) == wd).all()
+
+
+# ---------------------------------------------------------------------------------------
+# BF16 form: tensor-core Gram tiles with an error bound and FP32 re-decisions
+# ---------------------------------------------------------------------------------------
+
+def _bf16(X):
+    """Round-to-nearest-even float32 -> bfloat16, returned as float32."""
+    b = np.ascontiguousarray(X, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _bf16_bound(D, ni, nj, ei, ej, d):
+    """The per-pair bound that the BF16 form states (include/grnnd.h): arithmetic,
+    quantisation and FP32 reference-rounding terms, u = 2^-23."""
+    u = 2.0 ** -23
+    g = d * u / (1 - d * u)
+    si, sj = np.sqrt(ni), np.sqrt(nj)
+    ar = (g + 2 * u) * (si + sj) ** 2
+    e = ei + ej
+    qz = e * (2 * np.sqrt(max(D, 0) + ar) + e)
+    return (ar + qz + (d + 3) * u * (max(D, 0) + ar + qz)) * 1.0001
+
+
+@pytest.mark.parametrize("n,d,S,R,metric", [(3000, 16, 8, 16, 0), (2500, 128, 32, 64, 0), (1800, 40, 16, 32, 1),
+                                            (1500, 200, 16, 32, 0)])
+def test_bf16_build_is_exact_on_integer_data(G, orc, n, d, S, R, metric):
+    # integers with d * max|x|^2 < 2^24: every BF16 product and FP32 partial sum is exact,
+    # so the BF16 form must return the FP32 form's graph bit for bit (and the oracle's).
+    X = synth.small_integers(n, d, -8, 8, seed=d + n)
+    a = G.build(X, S=S, R=R, T1=2, T2=4, seed=3, metric=metric, precision=G.FP32).to_numpy()
+    gb = G.build(X, S=S, R=R, T1=2, T2=4, seed=3, metric=metric, precision=G.BF16)
+    b = gb.to_numpy()
+    for x, y in zip(a, b):
+        assert (x == y).all()
+    assert gb.stats()["rechecks"] == 0
+    wids, _, wdeg, _ = orc.build_graph(X, S, R, 2, 4, 0.6, 3, metric=metric)
+    assert (b[0] == wids).all() and (b[2] == wdeg).all()
+
+
+def test_bf16_build_sift_shaped_matches_fp32(G):
+    X = synth.sift_like(20000, 0, seed=1)
+    a = G.build(X, S=32, R=64, T1=2, T2=5, seed=1, precision=G.FP32).to_numpy()
+    b = G.build(X, S=32, R=64, T1=2, T2=5, seed=1, precision=G.BF16).to_numpy()
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def test_bf16_build_continuous_data(G, orc):
+    """Gaussian data: BF16 is not exact, so decisions near the bound are re-taken in FP32.
+    The graph must satisfy every invariant, its recorded distances must be within the
+    stated bound of FP64, and its recall must match the FP32 form's closely."""
+    X, Q = synth.gaussian_mixture(6000, 48, 12, 6.0, 1.0, seed=5, nq=300)
+    ga = G.build(X, S=16, R=32, T1=3, T2=6, seed=2, precision=G.FP32)
+    gb = G.build(X, S=16, R=32, T1=3, T2=6, seed=2, precision=G.BF16)
+    ids, dist, deg = gb.to_numpy()
+    assert gb.stats()["rechecks"] > 0
+    xb = _bf16(X).astype(np.float64)
+    nrm = (xb ** 2).sum(1)
+    res = np.sqrt(((X.astype(np.float64) - xb) ** 2).sum(1))
+    for v in range(0, len(X), 7):
+        row = ids[v, :deg[v]]
+        assert v not in row and len(set(row.tolist())) == len(row) and (row >= 0).all()
+        for j, u in enumerate(row[:8]):
+            ref = orc.dist(X[v], X[u])
+            bound = _bf16_bound(ref, nrm[v], nrm[u], res[v], res[u], X.shape[1])
+            assert abs(dist[v, j] - ref) <= bound
+    gt, _ = orc.brute_knn(X, Q, 10)
+    ra = orc.recall_at_k(ga.search(Q, 10, 32), gt)
+    rb = orc.recall_at_k(gb.search(Q, 10, 32), gt)
+    assert rb >= ra - 0.01 and rb > 0.9
