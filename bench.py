@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16 (the last one is the headline)")
     return ap.parse_args()
 
 
@@ -161,6 +162,11 @@ def run_reference(args, rank, world):
 KERNELS_PER_GROUP = {"scan": 3, "entry": 4}
 
 
+def _pct(xs, p):
+    q = sorted(xs)
+    return q[min(len(q) - 1, int(round(p * (len(q) - 1))))]
+
+
 def _source_sha():
     with open(os.path.join(ROOT, "paper_2510_02774_gb300", "csrc", "pool_kernels.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
@@ -199,56 +205,69 @@ def main():
     kw = dict(S=w["S"], R=w["R"], T1=w["T1"], T2=w["T2"], rho=w["rho"], seed=args.seed)
     stream = torch.cuda.current_stream()
 
-    def one_build():
-        return grnnd.build(Xd, **kw)
-
-    for _ in range(args.warmup):
-        g = one_build()
-        del g
-    torch.cuda.synchronize()
-
-    # ---- timed region: K builds with the points resident in HBM ----------------------
-    clocks = Clocks(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    grnnd.profile_begin()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
-    e0.record(stream)
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        g = one_build()
-        ev[i][1].record(stream)
-        stats.append(g.stats())
-        if i + 1 < args.steps:
+    def timed_form(precision: int):
+        """W untimed builds, then K timed builds bracketed by barrier + synchronize; CUDA
+        events on the build stream; per-kernel events and clocks sampled meanwhile."""
+        for _ in range(args.warmup):
+            g = grnnd.build(Xd, precision=precision, **kw)
             del g
-    e1.record(stream)
-    torch.cuda.synchronize()
-    kern = grnnd.profile_end()
-    clk = clocks.stop()
-    if dist:
-        dist.barrier()
-    total_ms = e0.elapsed_time(e1)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        grnnd.profile_begin()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        g = None
+        e0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            g = grnnd.build(Xd, precision=precision, **kw)
+            ev[i][1].record(stream)
+            stats.append(g.stats())
+            if i + 1 < args.steps:
+                del g
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kern = grnnd.profile_end()
+        clk = clocks.stop()
+        if dist:
+            dist.barrier()
+        total = e0.elapsed_time(e1)
+        t_max = torch.tensor([total], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        return dict(total_ms=float(t_max.item()), step_ms=[a.elapsed_time(b) for a, b in ev], stats=stats,
+                    kern=kern, clocks=clk, graph=g)
+
+    forms = {}
+    names = [f.strip() for f in args.forms.split(",") if f.strip()]
+    for name in names:
+        forms[name] = timed_form({"fp32": grnnd.FP32, "bf16": grnnd.BF16}[name])
+    head_name = names[-1]
+    head = forms[head_name]
+    total_ms, step_ms, stats, kern, clk, g = (head["total_ms"], head["step_ms"], head["stats"], head["kern"],
+                                             head["clocks"], head["graph"])
     value = n * world * args.steps / (total_ms / 1e3)
 
-    # ---- recall@10 at beam 64 on the last graph (not timed) --------------------------
-    recall = None
+    # ---- recall@10 at beam 64 on the last graph of each form (not timed) --------------
+    recall = {}
     if not args.no_recall and args.nq > 0:
         Xp, _ = grnnd.device_points(X)
         Qp, _ = grnnd.device_points(Q)
         gt, _ = grnnd.brute_knn(Xp, d, Qp, w["k"])
-        found = g.search(torch.from_numpy(Q).cuda(), w["k"], w["beam"])
-        gt_np, f_np = gt.cpu().numpy(), found.cpu().numpy()
-        recall = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w["k"] for a, b in zip(f_np, gt_np)]))
+        gt_np = gt.cpu().numpy()
+        Qt = torch.from_numpy(Q).cuda()
+        for name, f in forms.items():
+            found = f["graph"].search(Qt, w["k"], w["beam"]).cpu().numpy()
+            recall[name] = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w["k"]
+                                          for a, b in zip(found, gt_np)]))
         del Xp, Qp
+    for f in forms.values():
+        f["graph"] = None
     del g
 
     # ---- e2e: public API with pinned host input and the graph read back ----------------
@@ -260,7 +279,7 @@ def main():
     L = grnnd.lib()
 
     def e2e_step():
-        p = grnnd.params(**kw)
+        p = grnnd.params(precision={"fp32": grnnd.FP32, "bf16": grnnd.BF16}[head_name], **kw)
         h = ctypes.c_void_p()
         grnnd._check(L.grnnd_build_ex(ctypes.c_void_p(Xh.data_ptr()), n, d, ctypes.byref(p), ctypes.byref(h)))
         grnnd._check(L.grnnd_graph_copy(h, ctypes.c_void_p(ids_h.data_ptr()), None, ctypes.c_void_p(deg_h.data_ptr())))
@@ -286,9 +305,11 @@ def main():
     agg = {k: sum(s[k] for s in stats) for k in stats[0]}
     rounds = agg["rounds"]
     if dom_name == "rnd_join":
-        algo = agg["rows_gathered"] * d * 4 + rounds * n * 4 + agg["proposals"] * (8 + 12 + 4)
-    elif dom_name in ("select", "scatter"):
-        algo = agg["proposals_merged"] * (8 + 8) + dom_launches / args.steps * args.steps * n * w["R"] * 8
+        # BF16 rows (2 B per dimension); pool keys read; survivors written; redirects out
+        algo = (agg["rows_gathered"] * d * 2 + rounds * n * 4 + agg["proposals"] * 8
+                + agg["pairs_fired"] * (12 + 4))
+    elif dom_name == "select":
+        algo = agg["merged"] * 8 + agg["proposals"] * 8 * 2
     else:
         algo = None
     peaks = {}
@@ -319,15 +340,26 @@ def main():
                "sample": f"first {n_s} points of the same dataset, same S/R/T1/T2/rho, FP64 single thread, {dt:.1f} s"}
 
     if rank == 0:
-        q = sorted(step_ms)
-        p99 = q[min(len(q) - 1, int(round(0.99 * (len(q) - 1))))]
+        p99 = _pct(step_ms, 0.99)
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {**{k: v for k, v in WORKLOAD.items()}, "n": n, "nq": args.nq, "precision": "fp32",
+                "scaling": "weak", "vs_baseline": None, "dtype": head_name.replace("fp", "f"), "data": "synthetic",
+                "config": {**{k: v for k, v in WORKLOAD.items()}, "n": n, "nq": args.nq,
+                           "precision": ("bf16 dist_tile (tensor cores, FP32 accumulate, FP32 re-decision)"
+                                         if head_name == "bf16" else "fp32 dist_tile (CUDA cores)"),
                            "l2": "inputs larger than L2 (512 MB of points per replica)",
                            "parallelism": f"{world} independent replica(s)"},
-                "p50_ms": statistics.median(step_ms), "p99_ms": p99, "recall@10": recall, "beam": w["beam"],
+                "p50_ms": statistics.median(step_ms), "p99_ms": p99, "recall@10": recall.get(head_name),
+                "beam": w["beam"],
+                "forms": {k: {"value": n * world * args.steps / (f["total_ms"] / 1e3),
+                              "ms_per_step": f["total_ms"] / args.steps,
+                              "p50_ms": statistics.median(f["step_ms"]), "p99_ms": _pct(f["step_ms"], 0.99),
+                              "recall@10": recall.get(k),
+                              "kernels_ms": {kk: round(vv[1], 3) for kk, vv in
+                                             sorted(f["kern"].items(), key=lambda kv: -kv[1][1])}}
+                          for k, f in forms.items()},
+                "bf16_speedup_vs_fp32": (forms["fp32"]["total_ms"] / forms["bf16"]["total_ms"]
+                                         if "fp32" in forms and "bf16" in forms else None),
                 "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n * d * 4,
                         "d2h_bytes_per_step": n * w["R"] * 4 + n * 4},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,

@@ -185,8 +185,10 @@ GRNND_API size_t grnnd_workspace_size(int64_t n, int32_t R);
  * distance d(a,b); every survivor is proposed back to v as old.  pool_out[u] =
  * the R smallest keys among the distinct ids proposed to u (a duplicate keeps
  * its smallest distance and is old if any copy is old).  Buffers are device
- * memory; keys_out/deg_out must not alias the inputs (Sec 3.5 double buffer:
- * the caller swaps the two pools afterwards, which is pool_swap).
+ * memory.  keys_out/deg_out either are separate buffers (Sec 3.5 double
+ * buffer: the caller swaps the two pools afterwards, which is pool_swap) or
+ * alias keys_in/deg_in exactly (in-place update: each vertex rewrites its own
+ * row and only rows that receive proposals are merged).
  * stats (optional, device int64[8], accumulated): [0] vertices with new
  * entries, [1] rows gathered, [2] pair distances, [3] pairs fired,
  * [4] proposals (every pool entry, proposed explicitly or kept in place),
@@ -199,7 +201,7 @@ GRNND_API int grnnd_join_round(const float *points, int64_t n, int32_t d, int32_
 /* Reverse-edge sampling (Sec 3.6): for each v with k = deg_in[v], the first
  * floor((double)rho * k) entries n of its row propose (v, d(v,n), new) to n;
  * pool_out[u] = merge of pool_in[u] with the proposals to u (same rule as the
- * round).  0 <= rho <= 1. */
+ * round).  0 <= rho <= 1.  The output may alias the input (in place). */
 GRNND_API int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t *keys_in,
                          const int32_t *deg_in, uint64_t *keys_out, int32_t *deg_out,
                          void *workspace, size_t workspace_bytes, int64_t *stats, void *stream);

@@ -217,8 +217,8 @@ int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int3
   if (rc) return rc;
   if ((rc = check_R(R))) return rc;
   if (!keys_in || !deg_in || !keys_out || !deg_out) return fail(GRNND_EINVAL, "pool buffer is NULL");
-  if (keys_in == keys_out || deg_in == deg_out)
-    return fail(GRNND_EINVAL, "output pool must not alias the input pool");
+  if ((keys_in == keys_out) != (deg_in == deg_out))
+    return fail(GRNND_EINVAL, "keys and degrees must both be in place or both separate");
   if (order < 0 || order > 2) return fail(GRNND_EINVAL, "unknown order");
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
@@ -243,8 +243,8 @@ int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t* keys_i
   if (n < 1) return fail(GRNND_EINVAL, "n out of range");
   if (!(rho >= 0.0f && rho <= 1.0f)) return fail(GRNND_EINVAL, "rho must be in [0, 1]");
   if (!keys_in || !deg_in || !keys_out || !deg_out) return fail(GRNND_EINVAL, "pool buffer is NULL");
-  if (keys_in == keys_out || deg_in == deg_out)
-    return fail(GRNND_EINVAL, "output pool must not alias the input pool");
+  if ((keys_in == keys_out) != (deg_in == deg_out))
+    return fail(GRNND_EINVAL, "keys and degrees must both be in place or both separate");
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
     return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
@@ -424,10 +424,10 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   int64_t rounds = 0;
   for (int32_t t1 = 1; t1 <= p->T1; ++t1) {
     for (int32_t t2 = 1; t2 <= p->T2; ++t2) {
-      GR_CU(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolB, degB,
+      // the round updates the pool in place: survivors are rewritten in their own row and
+      // only rows that receive proposals are merged (the role of Sec 3.5's second buffer)
+      GR_CU(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
                                 stats, st));
-      std::swap(poolA, poolB);  // pool_swap: the written pool is read next round
-      std::swap(degA, degB);
       ++rounds;
       int64_t fresh = 0;
       GR_CU(cudaMemcpyAsync(&fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
@@ -435,9 +435,7 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
       if (fresh == 0) break;  // no new entry anywhere: the remaining rounds are identities
     }
     if (t1 != p->T1) {
-      GR_CU(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolB, degB, nullptr, st));
-      std::swap(poolA, poolB);
-      std::swap(degA, degB);
+      GR_CU(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolA, degA, nullptr, st));
     }
   }
   uint64_t* gkeys = poolA;

@@ -12,7 +12,7 @@ namespace grnnd {
 struct Workspace {
   int64_t n = 0;
   int R = 0;
-  int32_t* red_tgt = nullptr;              // n*R redirect / reverse-proposal targets
+  int32_t* red_tgt = nullptr;              // redirect / reverse-proposal targets (-1: unused)
   uint64_t* red_key = nullptr;             // n*R their keys
   uint64_t* bucket = nullptr;              // n*R keys bucketed by target
   int32_t* count = nullptr;                // n proposals per target (zeroed per step)
@@ -20,6 +20,8 @@ struct Workspace {
   int64_t* bsum = nullptr;                 // scan block sums
   int32_t* list = nullptr;                 // n vertices with a new entry
   uint8_t* active = nullptr;               // n flags: the vertex is in the list
+  uint64_t* rec = nullptr;                 // n work records of rec_w words, in list order
+  int rec_w = 0;
   int32_t* list_n = nullptr;               // length of the list
   unsigned long long* red_n = nullptr;     // number of redirects / reverse proposals
   int32_t* err = nullptr;                  // device status word (bounded waits)

@@ -20,6 +20,7 @@ namespace grnnd {
 namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr int64_t kMaxJoinGrid = 2048;  // CTAs of the join at most (sizes the redirect slack)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -162,12 +163,17 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 }
 
 // =====================================================================================
-// prep: active flag and list of the vertices whose pool holds a new entry; counts the
-// entries of every pool (each one is proposed once, explicitly or in place).
+// prep: active flag and list of the vertices whose pool holds a new entry, and for each
+// of them a contiguous work record (in list order) that the join prefetches in bulk:
+//   word 0: v    word 1: m    words 2 .. 2+R: the pool keys    (BF16 form, aux != null)
+//   words 2+R .. 2+2R: per-entry (norm^2, residual) of the quantized row, word 2+2R: the
+//   same for v.  Also counts the entries of every pool (each one is proposed once,
+//   explicitly or in place).
 // =====================================================================================
 __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
                             int64_t n, int R, uint8_t* __restrict__ active,
-                            int32_t* __restrict__ list, int32_t* __restrict__ list_n,
+                            int32_t* __restrict__ list_n, int small_max,
+                            uint64_t* __restrict__ rec, int rec_w, const float2* __restrict__ aux,
                             int64_t* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
   long long props = 0;
@@ -175,17 +181,49 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t v = base + lane;
     bool act = false;
+    int m = 0;
     if (v < n) {
-      const int m = deg[v];
+      m = deg[v];
       props += m;
       for (int j = 0; j < m && !act; ++j) act = !(keys[v * R + j] & 1ull);
       active[v] = act ? 1 : 0;
     }
-    const unsigned b = __ballot_sync(0xffffffffu, act);
-    int off = 0;
-    if (lane == 0 && b) off = atomicAdd(list_n, __popc(b));
-    off = __shfl_sync(0xffffffffu, off, 0);
-    if (act) list[off + __popc(b & lanemask_lt())] = (int32_t)v;
+    // small pools (warp kernel) take record positions from 0 up, larger ones from n - 1 down
+    const unsigned bs = __ballot_sync(0xffffffffu, act && m <= small_max);
+    const unsigned bl = __ballot_sync(0xffffffffu, act && m > small_max);
+    int offs = 0, offl = 0;
+    if (lane == 0 && bs) offs = atomicAdd(&list_n[0], __popc(bs));
+    if (lane == 0 && bl) offl = atomicAdd(&list_n[1], __popc(bl));
+    offs = __shfl_sync(0xffffffffu, offs, 0);
+    offl = __shfl_sync(0xffffffffu, offl, 0);
+    // the warp writes the records of its active vertices, one after the other
+    unsigned left = bs | bl;
+    while (left) {
+      const int l = __ffs(left) - 1;
+      left &= left - 1;
+      const int64_t u = base + l;
+      const int mu = __shfl_sync(0xffffffffu, m, l);
+      const unsigned below_l = (1u << l) - 1u;
+      const int64_t slotpos = ((bs >> l) & 1u) ? (int64_t)(offs + __popc(bs & below_l))
+                                               : n - 1 - (int64_t)(offl + __popc(bl & below_l));
+      uint64_t* r = rec + slotpos * rec_w;
+      if (lane == 0) {
+        r[0] = (uint64_t)u;
+        r[1] = (uint64_t)mu;
+      }
+      for (int j = lane; j < R; j += 32) {
+        const uint64_t k = keys[u * R + j];
+        r[2 + j] = k;
+        if (aux) {
+          const float2 q = j < mu ? aux[key_id(k)] : make_float2(0.0f, 0.0f);
+          r[2 + R + j] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
+        }
+      }
+      if (aux && lane == 0) {
+        const float2 q = aux[u];
+        r[2 + 2 * R] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
+      }
+    }
   }
   if (stats) {
 #pragma unroll
@@ -195,83 +233,115 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
 }
 
 // =====================================================================================
-// rnd_join.  One CTA works through the active list, one vertex at a time, with a
-// two-stage pipeline: while a vertex is computed, the rows of the next one are already
-// on their way into the other shared-memory stage (one bulk copy per row by the TMA
-// engine, completion on an mbarrier).  Per vertex v with m pool entries, k of them new:
+// rnd_join, batched.  A CTA walks a contiguous range of the active list.  It takes the
+// vertices in batches (at most BV vertices, BR pool entries, BP pairs or BT mma tiles)
+// and runs every phase for the whole batch at once, so that each latency (global loads,
+// the gather round trip, barriers, the slot reservation) is paid once per batch:
 //
-//  1. visit order pi = rank of (h(seed,t1,t2,v,id), id) (or ascending / descending key);
-//  2. rows staged new-first, so the pairs with a new side -- the only ones that can fire
-//     (design reading C10) -- are rows i < k, j > i: a dense list of k(m-1) - k(k-1)/2;
-//  3. dist_tile, FP32 form: one thread per pair, the canonical four-accumulator FP32
-//     distance over dimension chunks of DC; BF16 form: Gram tiles on the tensor cores
-//     (mma.sync m16n8k16, FP32 accumulate), D = (|x_i|^2 - g) + (|x_j|^2 - g), with a
-//     per-pair error bound; a decision inside the bound is re-taken with canonical FP32
-//     distances read from the FP32 rows;
-//  4. rng_prune: fire bits F[b] = {a < b : d(a,b) < max(d(v,a), d(v,b))} in pi order; the
-//     sequential pair scan of Alg 4 is resolved column by column with 64-bit masks: in
-//     column b the live firing a's below the first a that makes b the far side become
-//     bottom, and b becomes bottom if such an a exists;
-//  5. survivors are written in key order into the output pool (old); each bottom entry
-//     becomes one redirect (its absorber, distance d(close, far), new) in a compact list.
+//  0. set-up, one warp per vertex: pool keys, visit order pi = rank of
+//     (h(seed,t1,t2,v,id), id) (or ascending / descending key), rows laid out new-first
+//     so that the pairs with a new side -- the only ones that can fire (design reading
+//     C10) -- are local rows i < k, j > i: k(m-1) - k(k-1)/2 pairs per vertex;
+//  1. gather: one bulk copy (TMA engine) per row and dimension chunk into a shared row
+//     arena, all completing on one mbarrier; the next batch's rows are in flight while
+//     the current batch computes (two stages);
+//  2. dist_tile, FP32 form: one thread per pair, the canonical four-accumulator FP32
+//     distance over dimension chunks (partial sums in registers); BF16 form: Gram tiles
+//     on the tensor cores (mma.sync m16n8k16, FP32 accumulate), D = (|x_i|^2 - g) +
+//     (|x_j|^2 - g), with a per-pair error bound; a decision inside the bound is re-taken
+//     with canonical FP32 distances read from the FP32 rows;
+//  3. rng_prune: fire bits F[b] = {a < b : d(a,b) < max(d(v,a), d(v,b))} in pi order,
+//     then one thread per vertex replays the sequential pair scan of Alg 4 on the bits:
+//     in column b, the live firing a's are taken in order; each one that is farther than
+//     b becomes bottom (absorbed by b) until one that is closer makes b bottom;
+//  4. emit: survivors in key order into the output pool (old); each bottom entry is one
+//     redirect (absorber, d(close, far), new) in a compact list.
 // =====================================================================================
 namespace {
 
 constexpr int JT = 256;                        // threads per join CTA
 constexpr int JW = JT / 32;                    // warps per join CTA
-constexpr int MAXP = kMaxR * (kMaxR - 1) / 2;  // 2016 pairs at most
-constexpr int PPT = (MAXP + JT - 1) / JT;      // pairs per thread in the FP32 tile
-constexpr int MAXTILE = 32;                    // 16 x 8 output tiles of a 64-row vertex
-constexpr int TPW = MAXTILE / JW;              // tiles per warp in the BF16 tile
+constexpr int BV = 16;                         // vertices per batch at most
+constexpr int BR = 208;                        // pool entries (rows) per batch at most
+constexpr int BRA = BR + 16;                   // allocated rows: partial mma tiles read past the end
+constexpr int BP = 2048;                       // pairs per batch at most
+constexpr int SPW = 12;                        // FP32 tile: row segments per warp
+constexpr int BSEG = 288;                      // row segments per batch at most
+constexpr int BT = 64;                         // mma output tiles per batch at most
+constexpr int TPW = BT / JW;                   // mma tiles per warp
+constexpr int RECW_MAX = 2 + 2 * kMaxR + 2;    // work-record words (R = 64, BF16 form)
+constexpr int RED_CHUNK = 1024;                // redirect slots reserved per CTA at a time
+
+// A row segment is up to 32 consecutive pairs (i, j0..j0+31) of one new row i: one warp
+// takes a segment, one lane a partner j.
+template <int PREC>
+__host__ __device__ constexpr int seg_budget() { return PREC == 0 ? JW * SPW : BSEG; }
 
 template <int PREC>
 struct Prec;
 template <>
 struct Prec<0> {
   using T = float;
-  static constexpr int DC = 128;        // dimensions per staged chunk
-  static constexpr int RS = DC + 4;     // row stride: rows fall on different banks
-  static constexpr int VEC = 4;         // elements per 16 bytes
+  static constexpr int DC = 32;     // dimensions per staged chunk
+  static constexpr int RS = DC + 4; // 144-byte rows: 16-byte loads of 8 rows hit distinct banks
+  static constexpr int VEC = 4;     // copy granule in elements (16 bytes)
 };
 template <>
 struct Prec<1> {
   using T = __nv_bfloat16;
-  static constexpr int DC = 128;
-  static constexpr int RS = DC + 8;     // 272-byte rows: ldmatrix rows hit distinct banks
-  static constexpr int VEC = 16;        // copy granule: whole k16 steps (32 bytes)
+  static constexpr int DC = 64;
+  static constexpr int RS = DC + 8; // 144-byte rows: ldmatrix rows hit distinct banks
+  static constexpr int VEC = 16;    // whole k16 steps (32 bytes)
 };
 
-struct __align__(16) Meta {
-  uint64_t pkey[kMaxR];      // key by pi position
-  uint64_t skey[kMaxR];      // key by storage slot
-  uint64_t hk[kMaxR];        // order key by storage slot
-  uint64_t bfar[kMaxR];      // bits a < b with key(a) < key(b)
-  int32_t pid[kMaxR];        // id by pi position
-  int32_t rowoff[kMaxR + 1]; // first pair index of new row i
-  float rnrm[kMaxR];         // BF16 form: norm^2 of the quantized row, by row
-  float rdq[kMaxR];          // BF16 form: quantization residual norm, by row
-  int16_t pos_of_slot[kMaxR];
-  int16_t row_of_pos[kMaxR];
-  int16_t pos_of_row[kMaxR];
-  uint8_t tiles[MAXTILE];    // BF16 form: (I << 4) | J of the output tiles with a pair
-  uint64_t newm;
-  int64_t v;
-  float vnrm, vdq;
-  int m, k, npairs, nchunks, ntiles;
+struct __align__(16) Batch {
+  // indexed by batch row (rowbase of the vertex + local row)
+  int32_t rid[BRA];         // point id of the row
+  int32_t roff[BR];         // batch pair index of the first pair of a new row
+  float rnrm[BR];           // BF16 form: norm^2 of the quantized row
+  float rdq[BR];            // BF16 form: quantization residual norm
+  uint8_t rpos[BR];         // pi position of the row
+  uint8_t rvb[BR];          // vertex (in the batch) of the row
+  // indexed by rowbase of the vertex + pi position
+  uint64_t pkey[BR];
+  int32_t pid[BR];
+  uint8_t prow[BR];         // local row of the pi position
+  uint8_t pslot[BR];        // storage slot of the pi position
+  uint16_t seg[BSEG];       // (batch row of the new row << 8) | first partner
+  // per vertex
+  int64_t v[BV];
+  int32_t m[BV], k[BV], np[BV];
+  int32_t rowbase[BV + 1], pairbase[BV + 1], tilebase[BV + 1], segbase[BV + 1];
+  float vnrm[BV], vdq[BV];
+  uint16_t tiles[BT];       // (vb << 8) | (I << 4) | J
+  int nb, nent, ncopy, npairs, ntiles, nseg, nchunks;
 };
 
 template <int PREC>
 struct __align__(16) JoinSmem {
-  typename Prec<PREC>::T rows[2][kMaxR][Prec<PREC>::RS];
-  Meta meta[2];
-  float pd[MAXP];           // pair distances in pair-list order
-  uint64_t fire[kMaxR];
-  int32_t killer[kMaxR];
+  typename Prec<PREC>::T rows[2][BRA][Prec<PREC>::RS];
+  Batch bt[2];
+  float pd[BP];             // pair distances in batch pair order
+  uint64_t fire[BR];        // fire bits by rowbase + pi position
+  uint64_t closer[BR];      // fire bits whose lower pi position is also the closer entry
+  uint64_t colkill[BR];     // entries made bottom in column b (absorbed by b)
+  uint8_t colf[BR];         // absorber of b when b itself became bottom, else 0xFF
+  uint64_t fcol[BV];        // columns with a fire bit, per vertex
+  uint64_t alive[BV];
+  uint64_t smask[BV];       // survivors by storage slot
+  unsigned long long deadbase[BV];
+  // batch formation
+  uint64_t window[BV * RECW_MAX];  // work records of the next candidates (bulk prefetch)
+  int64_t cv[BV];
+  int32_t cm[BV], ck[BV], cnp[BV], cnt_[BV], cns[BV];
+  unsigned long long red_next, red_end;  // this CTA's reserved redirect slots
   uint64_t bar[2];
-  uint64_t alive;
-  uint64_t mask2;
-  unsigned long long red_base;
+  uint64_t wbar;
 };
+
+// two CTAs per SM: 233472 bytes of shared memory minus 1 KB reserved per CTA
+static_assert(sizeof(JoinSmem<0>) <= 115 * 1024 && sizeof(JoinSmem<1>) <= 115 * 1024,
+              "join shared memory must allow two CTAs per SM");
 
 struct PointsDev {
   const float* X;
@@ -289,8 +359,9 @@ struct JoinArgs {
   int R;
   const uint64_t* keys_in;
   const int32_t* deg_in;
-  const int32_t* list;
   const int32_t* list_n;
+  const uint64_t* rec;   // work records in list order
+  int rec_w;             // words per record
   uint64_t seed;
   int t1, t2, order;
   uint64_t* keys_out;  // survivors (in place for the round, final graph for the last pass)
@@ -304,97 +375,248 @@ struct JoinArgs {
   int32_t* err;
 };
 
-// ---- per-vertex set-up (all threads) --------------------------------------------------------
-template <int PREC>
-__device__ void join_setup(Meta& M, int64_t v, const JoinArgs& a) {
-  const int tid = threadIdx.x;
-  const int R = a.R;
-  const int m = a.deg_in[v];
-  const uint64_t kk = (tid < m) ? a.keys_in[v * R + tid] : kEmpty;
-  if (tid < m) {
-    const uint32_t id = key_id(kk);
-    M.skey[tid] = kk;
-    M.hk[tid] = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2,
-                                                (uint64_t)v, (uint64_t)id)
-                : (a.order == 1) ? (uint64_t)tid
-                                 : (uint64_t)(m - 1 - tid);
-  }
-  __syncthreads();
-  if (tid < m) {
-    const uint64_t h = M.hk[tid];
-    const uint32_t id = key_id(kk);
-    int p = 0;
-    for (int j = 0; j < m; ++j) {
-      const uint64_t hj = M.hk[j];
-      p += (hj < h) || (hj == h && key_id(M.skey[j]) < id);
-    }
-    M.pos_of_slot[tid] = (int16_t)p;
-    M.pkey[p] = kk;
-    M.pid[p] = (int32_t)id;
-  }
-  __syncthreads();
-  if (tid < 64) {
-    const bool nw = tid < m && !key_old(M.pkey[tid]);
-    const unsigned b = __ballot_sync(0xffffffffu, nw);
-    if ((tid & 31) == 0) reinterpret_cast<uint32_t*>(&M.newm)[tid >> 5] = b;
-  }
-  __syncthreads();
-  const uint64_t newm = M.newm;
-  const int k = __popcll(newm);
-  const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
-  const int npairs = k * (m - 1) - k * (k - 1) / 2;
-  if (tid < m) {
-    const uint64_t lo = bits_below(tid);
-    const int row = ((newm >> tid) & 1ull) ? __popcll(newm & lo) : k + __popcll(~newm & valid & lo);
-    M.row_of_pos[tid] = (int16_t)row;
-    M.pos_of_row[row] = (int16_t)tid;
-    const uint64_t kb = M.pkey[tid] >> 1;
-    uint64_t bf = 0;
-    for (int q = 0; q < tid; ++q) bf |= ((M.pkey[q] >> 1) < kb ? 1ull : 0ull) << q;
-    M.bfar[tid] = bf;
-    if (PREC == 1) {
-      const float2 x = a.P.aux[M.pid[tid]];
-      M.rnrm[row] = x.x;
-      M.rdq[row] = x.y;
-    }
-  }
-  if (tid <= k) M.rowoff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
-  if (tid == 0) {
-    M.v = v;
-    M.m = m;
-    M.k = k;
-    M.npairs = npairs;
-    M.nchunks = npairs > 0 ? (a.P.d + Prec<PREC>::DC - 1) / Prec<PREC>::DC : 0;
-    if (PREC == 1) {
-      const float2 x = a.P.aux[v];
-      M.vnrm = x.x;
-      M.vdq = x.y;
-      int nt = 0;
-      const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-      for (int I = 0; I < KI; ++I)
-        for (int J = 0; J < NJ; ++J)
-          if (J * 8 + 7 > I * 16) M.tiles[nt++] = (uint8_t)((I << 4) | J);
-      M.ntiles = nt;
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ int tiles_of(int m, int k) {
+  int nt = 0;
+  const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+  for (int I = 0; I < KI; ++I)
+    for (int J = 0; J < NJ; ++J) nt += (J * 8 + 7 > I * 16) ? 1 : 0;
+  return nt;
 }
 
-// ---- bulk copies of one chunk of a vertex's rows (thread 0) ----------------------------------
+// ---- batch formation and per-vertex set-up (all threads) --------------------------------
+// Candidates are the next BV list entries of the CTA's range; warp w loads candidates w
+// and w + JW and keeps their keys in registers for the set-up.  Returns the number of
+// list entries consumed (0 when the range is exhausted).
 template <int PREC>
-__device__ __forceinline__ void join_issue(JoinSmem<PREC>& s, const Meta& M, int chunk, int buf,
+__device__ __forceinline__ void join_prefetch(JoinSmem<PREC>& s, int64_t pos, int64_t end, const JoinArgs& a) {
+  const int64_t cnt = min((int64_t)BV, end - pos);
+  if (cnt <= 0) return;
+  const uint32_t bytes = (uint32_t)(cnt * a.rec_w * 8);
+  mbar_expect_tx(&s.wbar, bytes);
+  bulk_g2s(s.window, a.rec + pos * a.rec_w, bytes, &s.wbar);
+}
+
+template <int PREC>
+__device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t end,
+                               uint32_t& wph, const JoinArgs& a) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int R = a.R, W = a.rec_w;
+  if (pos >= end) return 0;
+  const bool ok = mbar_wait(&s.wbar, wph, kWaitLimit);
+  wph ^= 1u;
+  if (__syncthreads_or(!ok)) {  // the records never arrived: report and stop the CTA
+    if (tid == 0) atomicExch(a.err, kErrTimeout);
+    if (!ok) mbar_wait(&s.wbar, wph ^ 1u, kWaitLimit);
+    return -1;
+  }
+  uint64_t kx[2][2];
+  float2 ax[2][2];
+  int64_t vx[2];
+  int mx[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = warp + h * JW;
+    const int64_t p = pos + c;
+    vx[h] = -1;
+    mx[h] = 0;
+    kx[h][0] = kx[h][1] = kEmpty;
+    if (p < end) {
+      const uint64_t* r = s.window + c * W;
+      const int64_t v = (int64_t)r[0];
+      const int m = (int)r[1];
+      vx[h] = v;
+      mx[h] = m;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int e = j * 32 + lane;
+        if (e < m) kx[h][j] = r[2 + e];
+        if (PREC == 1 && e < m) {
+          const uint64_t q = r[2 + R + e];
+          ax[h][j] = make_float2(__uint_as_float((uint32_t)q), __uint_as_float((uint32_t)(q >> 32)));
+        }
+      }
+      const int k = __popc(__ballot_sync(0xffffffffu, lane < m && !key_old(kx[h][0]))) +
+                    __popc(__ballot_sync(0xffffffffu, lane + 32 < m && !key_old(kx[h][1])));
+      if (lane == 0) {
+        s.cv[c] = v;
+        s.cm[c] = m;
+        s.ck[c] = k;
+        s.cnp[c] = k * (m - 1) - k * (k - 1) / 2;
+        s.cnt_[c] = (PREC == 1) ? tiles_of(m, k) : 0;
+        s.cns[c] = min(k, m - 1) + min(k, max(0, m - 33));
+        if (PREC == 1) {
+          const uint64_t q = r[2 + 2 * R];
+          B.vnrm[c] = __uint_as_float((uint32_t)q);  // read only when c is taken
+          B.vdq[c] = __uint_as_float((uint32_t)(q >> 32));
+        }
+      }
+    } else if (lane == 0) {
+      s.cv[c] = -1;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {  // take the longest prefix of candidates that fits every budget
+    const bool have = lane < BV && s.cv[lane] >= 0;
+    int m = have ? s.cm[lane] : 0, np = have ? s.cnp[lane] : 0, nt = have ? s.cnt_[lane] : 0;
+    int ns = have ? s.cns[lane] : 0;
+    int cp = (have && np > 0) ? m : 0;
+    int im = m, inp = np, inti = nt, icp = cp, ins = ns;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a1 = __shfl_up_sync(0xffffffffu, im, o), a2 = __shfl_up_sync(0xffffffffu, inp, o);
+      const int a3 = __shfl_up_sync(0xffffffffu, inti, o), a4 = __shfl_up_sync(0xffffffffu, icp, o);
+      const int a5 = __shfl_up_sync(0xffffffffu, ins, o);
+      if (lane >= o) {
+        im += a1;
+        inp += a2;
+        inti += a3;
+        icp += a4;
+        ins += a5;
+      }
+    }
+    const bool fits = have && (lane == 0 || (im <= BR && inp <= BP && inti <= BT && ins <= seg_budget<PREC>()));
+    const int nb = __popc(__ballot_sync(0xffffffffu, fits));  // the fitting lanes form a prefix
+    if (lane < nb) {
+      B.v[lane] = s.cv[lane];
+      B.m[lane] = m;
+      B.k[lane] = s.ck[lane];
+      B.np[lane] = np;
+      B.rowbase[lane + 1] = im;
+      B.pairbase[lane + 1] = inp;
+      B.tilebase[lane + 1] = inti;
+      B.segbase[lane + 1] = ins;
+    }
+    if (lane == 0) {
+      B.rowbase[0] = B.pairbase[0] = B.tilebase[0] = B.segbase[0] = 0;
+      B.nb = nb;
+    }
+    if (nb > 0 && lane == nb - 1) {
+      B.nent = im;
+      B.ncopy = icp;
+      B.npairs = inp;
+      B.ntiles = inti;
+      B.nseg = ins;
+      B.nchunks = inp > 0 ? (a.P.d + Prec<PREC>::DC - 1) / Prec<PREC>::DC : 0;
+    }
+    if (nb == 0 && lane == 0) {
+      B.nent = B.ncopy = B.npairs = B.ntiles = B.nseg = B.nchunks = 0;
+    }
+  }
+  __syncthreads();
+  const int nb = B.nb;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int vb = warp + h * JW;
+    if (vb >= nb) continue;
+    const int64_t v = vx[h];
+    const int m = mx[h], k = B.k[vb], rb = B.rowbase[vb];
+    uint64_t hk[2];
+    uint32_t id[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int e = j * 32 + lane;
+      id[j] = key_id(kx[h][j]);
+      hk[j] = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v,
+                                              (uint64_t)id[j])
+              : (a.order == 1) ? (uint64_t)e
+                               : (uint64_t)(m - 1 - e);
+    }
+    int p[2] = {0, 0};
+    for (int f = 0; f < m; ++f) {
+      const uint64_t hf = __shfl_sync(0xffffffffu, (f < 32) ? hk[0] : hk[1], f & 31);
+      const uint32_t idf = __shfl_sync(0xffffffffu, (f < 32) ? id[0] : id[1], f & 31);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) p[j] += (hf < hk[j]) || (hf == hk[j] && idf < id[j]);
+    }
+    // new entries by pi position
+    uint32_t nlo = 0, nhi = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int e = j * 32 + lane;
+      if (e < m && !key_old(kx[h][j])) {
+        if (p[j] < 32) nlo |= 1u << p[j];
+        else nhi |= 1u << (p[j] - 32);
+      }
+    }
+    nlo = __reduce_or_sync(0xffffffffu, nlo);
+    nhi = __reduce_or_sync(0xffffffffu, nhi);
+    const uint64_t newm = ((uint64_t)nhi << 32) | nlo;
+    const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int e = j * 32 + lane;
+      if (e >= m) continue;
+      const int pp = p[j];
+      const uint64_t lo = bits_below(pp);
+      const int row = ((newm >> pp) & 1ull) ? __popcll(newm & lo) : k + __popcll(~newm & valid & lo);
+      B.rid[rb + row] = (int32_t)id[j];
+      B.rpos[rb + row] = (uint8_t)pp;
+      B.rvb[rb + row] = (uint8_t)vb;
+      if (row < k) B.roff[rb + row] = B.pairbase[vb] + row * (m - 1) - row * (row - 1) / 2;
+      B.pkey[rb + pp] = kx[h][j];
+      B.pid[rb + pp] = (int32_t)id[j];
+      B.prow[rb + pp] = (uint8_t)row;
+      B.pslot[rb + pp] = (uint8_t)e;
+      if (PREC == 1) {
+        B.rnrm[rb + row] = ax[h][j].x;
+        B.rdq[rb + row] = ax[h][j].y;
+      }
+    }
+    {  // row segments of the new rows i = lane, lane + 32: one if it has a pair, two past 32
+      int cnt[2], ex[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int i = j * 32 + lane, len = m - 1 - i;
+        cnt[j] = i < k ? (len >= 1) + (len > 32) : 0;
+      }
+      int inc0 = cnt[0], inc1 = cnt[1];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, inc0, o), y1 = __shfl_up_sync(0xffffffffu, inc1, o);
+        if (lane >= o) {
+          inc0 += y0;
+          inc1 += y1;
+        }
+      }
+      ex[0] = inc0 - cnt[0];
+      ex[1] = __shfl_sync(0xffffffffu, inc0, 31) + inc1 - cnt[1];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int i = j * 32 + lane;
+        const int sb = B.segbase[vb] + ex[j];
+        if (cnt[j] > 0) B.seg[sb] = (uint16_t)(((rb + i) << 8) | (i + 1));
+        if (cnt[j] > 1) B.seg[sb + 1] = (uint16_t)(((rb + i) << 8) | (i + 33));
+      }
+    }
+    if (PREC == 1) {  // this vertex's mma tiles, lane (I, J) = (lane / 8, lane % 8)
+      const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+      const int I = lane >> 3, J = lane & 7;
+      const bool ok = I < KI && J < NJ && J * 8 + 7 > I * 16;
+      const unsigned bm = __ballot_sync(0xffffffffu, ok);
+      if (ok) B.tiles[B.tilebase[vb] + __popc(bm & lanemask_lt())] = (uint16_t)((vb << 8) | (I << 4) | J);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) join_prefetch<PREC>(s, pos + nb, end, a);  // the next batch's candidates
+  return nb;
+}
+
+// ---- bulk copies of one dimension chunk of a batch's rows (all threads) ------------------
+template <int PREC>
+__device__ __forceinline__ void join_issue(JoinSmem<PREC>& s, const Batch& B, int chunk, int buf,
                                            const JoinArgs& a) {
   using C = Prec<PREC>;
   const int c0 = chunk * C::DC;
   const int clen = min(C::DC, a.P.d - c0);
   const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
   const uint32_t bytes = (uint32_t)(cpy * sizeof(typename C::T));
-  mbar_expect_tx(&s.bar[buf], (uint32_t)M.m * bytes);
-  for (int p = 0; p < M.m; ++p) {
+  if (threadIdx.x == 0) mbar_expect_tx(&s.bar[buf], (uint32_t)B.ncopy * bytes);
+  for (int r = threadIdx.x; r < B.nent; r += JT) {
+    if (B.np[B.rvb[r]] == 0) continue;
     const typename C::T* src =
-        (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)M.pid[p] * a.P.ld + c0)
-                    : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)M.pid[p] * a.P.ldb + c0);
-    bulk_g2s(&s.rows[buf][M.row_of_pos[p]][0], src, bytes, &s.bar[buf]);
+        (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)B.rid[r] * a.P.ld + c0)
+                    : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)B.rid[r] * a.P.ldb + c0);
+    bulk_g2s(&s.rows[buf][r][0], src, bytes, &s.bar[buf]);
   }
 }
 
@@ -451,103 +673,124 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
   JoinSmem<PREC>& s = *reinterpret_cast<JoinSmem<PREC>*>(smem_raw);
   using C = Prec<PREC>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int list_n = *a.list_n;
-  int64_t idx = blockIdx.x;
-  if (idx >= list_n) return;
+  // the pools of more than 32 entries: records at positions [n - cnt, n)
+  const int64_t cnt = a.list_n[1];
+  const int64_t per = (cnt + gridDim.x - 1) / gridDim.x;
+  int64_t pos = a.n - cnt + (int64_t)blockIdx.x * per;
+  const int64_t end = min(a.n, pos + per);
+  if (pos >= end) return;
   if (tid == 0) {
     mbar_init(&s.bar[0], 1);
     mbar_init(&s.bar[1], 1);
+    mbar_init(&s.wbar, 1);
     fence_mbar_init();
+    s.red_next = s.red_end = 0;
   }
-  if (tid < 64) {
-    s.fire[tid] = 0;
-    s.killer[tid] = -1;
+  for (int t = tid; t < BR; t += JT) {
+    s.fire[t] = 0;
+    s.closer[t] = 0;
   }
+  if (tid < BV) s.fcol[tid] = 0;
   __syncthreads();
   bool exact = false;
   if (PREC == 1) {
     const unsigned fl = a.P.qflags[0];
-    const float mx = __uint_as_float(a.P.qflags[1]);
-    exact = (fl == 0u) && ((double)a.P.d * (double)mx * (double)mx < 16777216.0);
+    const float mxa = __uint_as_float(a.P.qflags[1]);
+    exact = (fl == 0u) && ((double)a.P.d * (double)mxa * (double)mxa < 16777216.0);
   }
   const int R = a.R;
   uint32_t ph[2] = {0u, 0u};
   long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
 
-  join_setup<PREC>(s.meta[0], a.list[idx], a);
-  if (tid == 0 && s.meta[0].nchunks > 0) join_issue<PREC>(s, s.meta[0], 0, 0, a);
-  int mcur = 0, ccur = 0, bcur = 0;
+  uint32_t wph = 0;
+  if (tid == 0) join_prefetch<PREC>(s, pos, end, a);
+  {
+    const int nb0 = join_form_batch<PREC>(s, s.bt[0], pos, end, wph, a);
+    if (nb0 < 0) return;
+    pos += nb0;
+  }
+  if (s.bt[0].nchunks > 0) join_issue<PREC>(s, s.bt[0], 0, 0, a);
+  int bcur = 0, ccur = 0, sbuf = 0;
 
-  float4 facc[PREC == 0 ? PPT : 1];
+  float4 facc[PREC == 0 ? SPW : 1];
   float cacc[PREC == 1 ? TPW : 1][4];
 
   for (;;) {
-    Meta& M = s.meta[mcur];
-    // ---- next stage: the next chunk of this vertex, or the next vertex ----------------
-    int mnext = mcur, cnext = ccur + 1;
+    Batch& B = s.bt[bcur];
+    // ---- next stage: the next chunk of this batch, or the next batch ----------------------
+    int bnext = bcur, cnext = ccur + 1;
     bool have_next = true;
-    if (cnext >= M.nchunks) {
-      const int64_t nidx = idx + gridDim.x;
-      if (nidx < list_n) {
-        mnext = mcur ^ 1;
+    if (cnext >= B.nchunks) {
+      if (pos < end) {
+        bnext = bcur ^ 1;
         cnext = 0;
-        join_setup<PREC>(s.meta[mnext], a.list[nidx], a);
+        const int nbn = join_form_batch<PREC>(s, s.bt[bnext], pos, end, wph, a);
+        if (nbn < 0) {  // let the current stage's copies land before leaving
+          if (B.nchunks > 0) mbar_wait(&s.bar[sbuf], ph[sbuf], kWaitLimit);
+          return;
+        }
+        pos += nbn;
       } else {
         have_next = false;
       }
     }
-    if (have_next && tid == 0 && s.meta[mnext].nchunks > 0)
-      join_issue<PREC>(s, s.meta[mnext], cnext, bcur ^ 1, a);
+    if (have_next && s.bt[bnext].nchunks > 0) join_issue<PREC>(s, s.bt[bnext], cnext, sbuf ^ 1, a);
 
-    // ---- current stage: accumulate one chunk of the tile --------------------------------
-    if (M.nchunks > 0) {
-      const bool ok = mbar_wait(&s.bar[bcur], ph[bcur], kWaitLimit);
-      ph[bcur] ^= 1u;
+    // ---- current stage: one dimension chunk of every tile of the batch ------------------
+    if (B.nchunks > 0) {
+      const bool ok = mbar_wait(&s.bar[sbuf], ph[sbuf], kWaitLimit);
+      ph[sbuf] ^= 1u;
       if (__syncthreads_or(!ok)) {
         // a bounded wait gave up: report, let in-flight copies land, and stop.
         if (tid == 0) atomicExch(a.err, kErrTimeout);
-        if (!ok) mbar_wait(&s.bar[bcur], ph[bcur] ^ 1u, kWaitLimit);
-        if (have_next && s.meta[mnext].nchunks > 0) mbar_wait(&s.bar[bcur ^ 1], ph[bcur ^ 1], kWaitLimit);
+        if (!ok) mbar_wait(&s.bar[sbuf], ph[sbuf] ^ 1u, kWaitLimit);
+        if (have_next && s.bt[bnext].nchunks > 0) mbar_wait(&s.bar[sbuf ^ 1], ph[sbuf ^ 1], kWaitLimit);
         return;
       }
       const int c0 = ccur * C::DC;
       const int clen = min(C::DC, a.P.d - c0);
-      const bool last = (ccur + 1 == M.nchunks);
+      const bool last = (ccur + 1 == B.nchunks);
       if (PREC == 0) {
-        const float* rows = reinterpret_cast<const float*>(&s.rows[bcur][0][0]);
+        const float* rows = reinterpret_cast<const float*>(&s.rows[sbuf][0][0]);
         const int full4 = clen & ~3, rem = clen & 3;
-        int i = 0;
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-          const int q = tid + r * JT;
-          if (q < M.npairs) {
-            while (M.rowoff[i + 1] <= q) ++i;
-            const int j = i + 1 + (q - M.rowoff[i]);
-            const float* ra = rows + i * C::RS;
-            const float* rb = rows + j * C::RS;
-            if (ccur == 0) facc[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            float4 acc = facc[r];
-            for (int t = 0; t < full4; t += 4)
-              dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + t),
-                                 *reinterpret_cast<const float4*>(rb + t));
-            if (rem)
-              dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
-                                 mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
-            facc[r] = acc;
-            if (last) s.pd[q] = dist_finish4<METRIC>(acc);
+        for (int t = 0; t < SPW; ++t) {
+          const int sidx = warp + t * JW;
+          if (sidx < B.nseg) {
+            const int code = B.seg[sidx];
+            const int row = code >> 8, j = (code & 255) + lane;
+            const int vb = B.rvb[row], rb = B.rowbase[vb];
+            if (j < B.m[vb]) {
+              const float* ra = rows + row * C::RS;
+              const float* rbp = rows + (rb + j) * C::RS;
+              if (ccur == 0) facc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              float4 acc = facc[t];
+              for (int u = 0; u < full4; u += 4)
+                dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
+                                   *reinterpret_cast<const float4*>(rbp + u));
+              if (rem)
+                dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
+                                   mask4(*reinterpret_cast<const float4*>(rbp + full4), rem));
+              facc[t] = acc;
+              if (last) s.pd[B.roff[row] + (j - (row - rb) - 1)] = dist_finish4<METRIC>(acc);
+            }
           }
         }
       } else {
-        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[bcur][0][0]);
+        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[sbuf][0][0]);
         const int ksteps = (clen + 15) >> 4;
 #pragma unroll
         for (int t = 0; t < TPW; ++t) {
           const int ti = warp + t * JW;
-          if (ti < M.ntiles) {
-            const int I = M.tiles[ti] >> 4, J = M.tiles[ti] & 15;
+          if (ti < B.ntiles) {
+            const int code = B.tiles[ti];
+            const int vb = code >> 8, I = (code >> 4) & 15, J = code & 15;
+            const int rb = B.rowbase[vb];
             if (ccur == 0) cacc[t][0] = cacc[t][1] = cacc[t][2] = cacc[t][3] = 0.0f;
-            const __nv_bfloat16* pa = rows + (I * 16 + (lane & 15)) * C::RS + ((lane >> 4) << 3);
-            const __nv_bfloat16* pb = rows + (J * 8 + (lane & 7)) * C::RS + (((lane >> 3) & 1) << 3);
+            const int ra = min(rb + I * 16 + (lane & 15), BRA - 1);
+            const int rbb = min(rb + J * 8 + (lane & 7), BRA - 1);
+            const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
+            const __nv_bfloat16* pb = rows + rbb * C::RS + (((lane >> 3) & 1) << 3);
             for (int ks = 0; ks < ksteps; ++ks) {
               uint32_t fa[4], fb[2];
               ldmatrix_x4(fa, pa + ks * 16);
@@ -556,18 +799,19 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
             }
             if (last) {
               const int g = lane >> 2, tg = lane & 3;
+              const int m = B.m[vb], k = B.k[vb];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int i = I * 16 + g + ((e >> 1) << 3);
                 const int j = J * 8 + 2 * tg + (e & 1);
-                if (i < M.k && j > i && j < M.m) {
+                if (i < k && j > i && j < m) {
                   const float gij = cacc[t][e];
                   float Dt;
                   if (METRIC == 0)
-                    Dt = __fadd_rn(__fsub_rn(M.rnrm[i], gij), __fsub_rn(M.rnrm[j], gij));
+                    Dt = __fadd_rn(__fsub_rn(B.rnrm[rb + i], gij), __fsub_rn(B.rnrm[rb + j], gij));
                   else
                     Dt = __fsub_rn(1.0f, gij);
-                  s.pd[M.rowoff[i] + (j - i - 1)] = Dt;
+                  s.pd[B.roff[rb + i] + (j - i - 1)] = Dt;
                 }
               }
             }
@@ -577,115 +821,182 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
     }
     __syncthreads();
 
-    // ---- last chunk done: prune and emit ---------------------------------------------
-    if (ccur + 1 >= M.nchunks) {
-      const int m = M.m;
-      const int64_t v = M.v;
-      const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
-      {
-        int i = 0;
-        for (int q = tid; q < M.npairs; q += JT) {
-          while (M.rowoff[i + 1] <= q) ++i;
-          const int j = i + 1 + (q - M.rowoff[i]);
-          const int pa = M.pos_of_row[i], pb = M.pos_of_row[j];
+    // ---- last chunk done: prune and emit the whole batch --------------------------------
+    if (ccur + 1 >= B.nchunks) {
+      const int nb = B.nb;
+      // fire bits, one warp per row segment
+      for (int sidx = warp; sidx < B.nseg; sidx += JW) {
+        const int code = B.seg[sidx];
+        const int row = code >> 8, j = (code & 255) + lane;
+        const int vb = B.rvb[row], rb = B.rowbase[vb];
+        const int i = row - rb;
+        if (j < B.m[vb]) {
+          const int q = B.roff[row] + (j - i - 1);
+          const int pa = B.rpos[rb + i], pb = B.rpos[rb + j];
           const int lo = min(pa, pb), hi = max(pa, pb);
           const float dab = s.pd[q];
-          const float dva = key_dist(M.pkey[pa]), dvb = key_dist(M.pkey[pb]);
+          const float dva = key_dist(B.pkey[rb + pa]), dvb = key_dist(B.pkey[rb + pb]);
           const float mx = fmaxf(dva, dvb);
           bool fire = dab < mx;
           if (PREC == 1 && !exact) {
-            const float tol = bf16_bound<METRIC>(dab, M.rnrm[i], M.rnrm[j], M.rdq[i], M.rdq[j], a.P.d) +
-                              fmaxf(bf16_bound<METRIC>(dva, M.vnrm, M.rnrm[i], M.vdq, M.rdq[i], a.P.d),
-                                    bf16_bound<METRIC>(dvb, M.vnrm, M.rnrm[j], M.vdq, M.rdq[j], a.P.d));
+            const float tol =
+                bf16_bound<METRIC>(dab, B.rnrm[rb + i], B.rnrm[rb + j], B.rdq[rb + i], B.rdq[rb + j], a.P.d) +
+                fmaxf(bf16_bound<METRIC>(dva, B.vnrm[vb], B.rnrm[rb + i], B.vdq[vb], B.rdq[rb + i], a.P.d),
+                      bf16_bound<METRIC>(dvb, B.vnrm[vb], B.rnrm[rb + j], B.vdq[vb], B.rdq[rb + j], a.P.d));
             if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-              const float* xv = a.P.X + v * a.P.ld;
-              const float* xa = a.P.X + (int64_t)M.pid[pa] * a.P.ld;
-              const float* xb = a.P.X + (int64_t)M.pid[pb] * a.P.ld;
+              const float* xv = a.P.X + B.v[vb] * a.P.ld;
+              const float* xa = a.P.X + (int64_t)B.pid[rb + pa] * a.P.ld;
+              const float* xb = a.P.X + (int64_t)B.pid[rb + pb] * a.P.ld;
               const float d_ab = row_dist<METRIC>(xa, xb, a.P.d);
-              const float d_va = row_dist<METRIC>(xv, xa, a.P.d);
-              const float d_vb = row_dist<METRIC>(xv, xb, a.P.d);
-              fire = d_ab < fmaxf(d_va, d_vb);
+              fire = d_ab < fmaxf(row_dist<METRIC>(xv, xa, a.P.d), row_dist<METRIC>(xv, xb, a.P.d));
               s.pd[q] = d_ab;
               ++st_check;
             }
           }
-          if (fire) atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        uint64_t alive = valid;
-        for (int b = 1; b < m; ++b) {
-          const uint64_t cand = s.fire[b] & alive;
-          if (!cand) continue;
-          const uint64_t x = cand & M.bfar[b];
-          uint64_t kill = cand;
-          if (x) {
-            const int f = __ffsll((long long)x) - 1;
-            kill = cand & bits_below(f);
-            alive &= ~(1ull << b);
-            s.killer[b] = f;
-          }
-          alive &= ~kill;
-          while (kill) {
-            const int q = __ffsll((long long)kill) - 1;
-            s.killer[q] = b;
-            kill &= kill - 1;
+          if (fire) {
+            atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[rb + hi]), 1ull << lo);
+            atomicOr(reinterpret_cast<unsigned long long*>(&s.fcol[vb]), 1ull << hi);
+            if ((B.pkey[rb + lo] >> 1) < (B.pkey[rb + hi] >> 1))
+              atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[rb + hi]), 1ull << lo);
           }
         }
-        s.alive = alive;
-        const int ndead = m - __popcll(alive);
-        if (a.emit_redirects && ndead > 0) s.red_base = atomicAdd(a.red_n, (unsigned long long)ndead);
-        if (M.npairs > 0) {
-          st_vert += 1;
-          st_rows += m;
-          st_pairs += M.npairs;
+      }
+      __syncthreads();
+      if (warp == 0) {  // one chain per vertex, in parallel
+        int ndead = 0;
+        if (lane < nb) {
+          const int m = B.m[lane], rb = B.rowbase[lane];
+          uint64_t alive = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+          uint64_t cols = s.fcol[lane];
+          // only columns with a fire bit can change anything; in column b the live firing
+          // partners are taken in pi order: farther ones are absorbed by b until the first
+          // closer one, which makes b the far side
+          while (cols) {
+            const int b = __ffsll((long long)cols) - 1;
+            cols &= cols - 1;
+            const uint64_t cand = s.fire[rb + b] & alive;
+            uint64_t kill = cand;
+            uint8_t f = 0xFF;
+            const uint64_t x = cand & s.closer[rb + b];
+            if (x) {
+              f = (uint8_t)(__ffsll((long long)x) - 1);
+              kill = cand & bits_below(f);
+              alive &= ~(1ull << b);
+            }
+            alive &= ~kill;
+            s.colkill[rb + b] = kill;
+            s.colf[rb + b] = f;
+          }
+          s.alive[lane] = alive;
+          s.smask[lane] = 0;
+          ndead = m - __popcll(alive);
+          if (B.np[lane] > 0) {
+            st_vert += 1;
+            st_rows += m;
+            st_pairs += B.np[lane];
+          }
+          st_fired += ndead;
         }
-        st_fired += ndead;
+        if (a.emit_redirects) {  // one reservation per batch
+          int incl = ndead;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          unsigned long long base = s.red_next;
+          if (base + (unsigned long long)total > s.red_end) {
+            // chunk exhausted: mark its unused tail, reserve a fresh chunk
+            for (unsigned long long i = base + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+            unsigned long long nbase = 0;
+            if (lane == 0) nbase = atomicAdd(a.red_n, (unsigned long long)RED_CHUNK);
+            base = __shfl_sync(0xffffffffu, nbase, 0);
+            if (lane == 0) s.red_end = base + RED_CHUNK;
+          }
+          if (lane == 0) s.red_next = base + (unsigned long long)total;
+          if (lane < nb) s.deadbase[lane] = base + (unsigned long long)(incl - ndead);
+        }
       }
       __syncthreads();
-      const uint64_t alive = s.alive;
-      // survivors, in key order, into the output pool
-      if (tid < 64) {
-        const bool al = tid < m && ((alive >> M.pos_of_slot[tid]) & 1ull);
-        const unsigned b = __ballot_sync(0xffffffffu, al);
-        if ((tid & 31) == 0) reinterpret_cast<uint32_t*>(&s.mask2)[tid >> 5] = b;
-      }
-      if (a.emit_redirects && tid < m && !((alive >> tid) & 1ull)) {
-        const int cpos = s.killer[tid];
-        const int ri = M.row_of_pos[cpos], rj = M.row_of_pos[tid];
-        const int i = min(ri, rj), j = max(ri, rj);
-        const float dd = s.pd[M.rowoff[i] + (j - i - 1)];
-        const int32_t tgt = M.pid[cpos];
-        const unsigned long long slot = s.red_base + (unsigned long long)__popcll(~alive & valid & bits_below(tid));
-        a.red_tgt[slot] = tgt;
-        a.red_key[slot] = make_key(dd, (uint32_t)M.pid[tid], 0u);
-        atomicAdd(&a.count[tgt], 1);
+      // emit, one thread per pool entry of the batch (indexed by rowbase + pi position)
+      const int t = tid;
+      int ev = -1, ep = 0;
+      uint64_t ealive = 0;
+      if (t < B.nent) {
+        ev = B.rvb[t];  // entries and rows share the batch index range
+        ep = t - B.rowbase[ev];
+        ealive = s.alive[ev];
+        if ((ealive >> ep) & 1ull)
+          atomicOr(reinterpret_cast<unsigned long long*>(&s.smask[ev]), 1ull << B.pslot[t]);
       }
       __syncthreads();
-      const uint64_t sm = s.mask2;
-      const int cnt = __popcll(sm);
-      if (tid < m && ((sm >> tid) & 1ull))
-        a.keys_out[v * R + __popcll(sm & bits_below(tid))] = M.skey[tid] | 1ull;
-      if (tid >= cnt && tid < R) a.keys_out[v * R + tid] = kEmpty;
-      if (tid == 0) a.deg_out[v] = cnt;
-      if (tid < 64) {
-        s.fire[tid] = 0;
-        s.killer[tid] = -1;
+      if (ev >= 0) {
+        const int rb = B.rowbase[ev];
+        const int64_t v = B.v[ev];
+        if ((ealive >> ep) & 1ull) {
+          const int slot = B.pslot[t];
+          a.keys_out[v * R + __popcll(s.smask[ev] & bits_below(slot))] = B.pkey[t] | 1ull;
+        } else if (a.emit_redirects) {
+          const int m = B.m[ev];
+          const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+          const uint64_t cols = s.fcol[ev];
+          int cpos = ((cols >> ep) & 1ull) ? s.colf[t] : 0xFF;
+          if (cpos == 0xFF) {  // absorbed by a later column b: the one whose kill mask holds it
+            uint64_t later = cols & ~bits_below(ep + 1);
+            while (later) {
+              const int b = __ffsll((long long)later) - 1;
+              later &= later - 1;
+              if ((s.colkill[rb + b] >> ep) & 1ull) {
+                cpos = b;
+                break;
+              }
+            }
+          }
+          const int ri = B.prow[rb + cpos], rj = B.prow[t];
+          const int i = min(ri, rj), j = max(ri, rj);
+          const float dd = s.pd[B.roff[rb + i] + (j - i - 1)];
+          const int32_t tgt = B.pid[rb + cpos];
+          const unsigned long long slot = s.deadbase[ev] + (unsigned long long)__popcll(~ealive & valid & bits_below(ep));
+          a.red_tgt[slot] = tgt;
+          a.red_key[slot] = make_key(dd, (uint32_t)B.pid[t], 0u);
+          atomicAdd(&a.count[tgt], 1);
+        }
       }
+      for (int u = tid; u < nb * R; u += JT) {
+        const int vb = u / R, jj = u - vb * R;
+        if (jj >= __popcll(s.alive[vb])) a.keys_out[B.v[vb] * R + jj] = kEmpty;
+      }
+      if (tid < nb) a.deg_out[B.v[tid]] = __popcll(s.alive[tid]);
+      for (int q = tid; q < B.nent; q += JT) {
+        s.fire[q] = 0;
+        s.closer[q] = 0;
+      }
+      if (tid < nb) s.fcol[tid] = 0;
       __syncthreads();
-      idx += gridDim.x;
     }
     if (!have_next) break;
-    mcur = mnext;
+    bcur = bnext;
     ccur = cnext;
-    bcur ^= 1;
+    sbuf ^= 1;
   }
-  if (tid == 0 && a.stats) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)st_vert);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
+  __syncthreads();
+  if (a.emit_redirects)
+    for (unsigned long long i = s.red_next + tid; i < s.red_end; i += JT) a.red_tgt[i] = -1;
+  if (a.stats && warp == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      st_vert += __shfl_xor_sync(0xffffffffu, st_vert, o);
+      st_rows += __shfl_xor_sync(0xffffffffu, st_rows, o);
+      st_pairs += __shfl_xor_sync(0xffffffffu, st_pairs, o);
+      st_fired += __shfl_xor_sync(0xffffffffu, st_fired, o);
+    }
+    if (lane == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)st_vert);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
+    }
   }
   if (a.stats && PREC == 1) {
 #pragma unroll
@@ -707,9 +1018,399 @@ cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name) 
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JT, smem);
   if (per_sm < 1) per_sm = 1;
-  const int64_t blocks = std::min<int64_t>(std::max<int64_t>(a.n, 1), (int64_t)sm_count() * per_sm);
+  const int64_t blocks = std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(a.n, 1), (int64_t)sm_count() * per_sm),
+                                            kMaxJoinGrid);
   ProfScope ps(name, st);
   kern<<<(unsigned)blocks, JT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// =====================================================================================
+// rnd_join for pools of at most 32 entries: one warp per vertex, end to end, with no
+// block-wide barrier (the common case: every pool of the first round, most later ones).
+//
+//   order    warp bitonic sort of (h(seed,t1,t2,v,id), id) (or the key order) -> pi
+//   gather   one bulk copy per row (lane p: the row of pi position p), new rows first,
+//            completing on the warp's own mbarrier; BF16 rows arrive in chunks of 64
+//            dimensions through two stages, FP32 rows (d <= 128) whole
+//   tile     BF16: up to 6 mma.sync m16n8k16 tiles, FP32 accumulators kept across chunks,
+//            the fire decision taken from the accumulators; FP32: one lane per pair, the
+//            canonical four-accumulator distance
+//   prune    every lane replays the mask chain (the data are broadcast), so each lane
+//            learns whether its entry survives and, if not, its absorber
+//   emit     survivors in key order in place; redirects into per-warp slot chunks
+// =====================================================================================
+namespace {
+
+constexpr int WW = 4;    // warps per CTA
+constexpr int WM = 32;   // pool entries per warp-handled vertex at most
+constexpr int WRED = 256;  // redirect slots a warp reserves at a time
+
+template <int PREC>
+struct WPrec;
+template <>
+struct WPrec<0> {
+  using T = float;
+  static constexpr int DC = 128;  // whole rows (the path is used for d <= 128)
+  static constexpr int RS = DC + 4;
+  static constexpr int VEC = 4;
+  static constexpr int ST = 1;    // stages
+};
+template <>
+struct WPrec<1> {
+  using T = __nv_bfloat16;
+  static constexpr int DC = 64;
+  static constexpr int RS = DC + 8;
+  static constexpr int VEC = 16;
+  static constexpr int ST = 2;
+};
+
+template <int PREC>
+struct __align__(16) WarpSlot {
+  typename WPrec<PREC>::T rows[WPrec<PREC>::ST][WM][WPrec<PREC>::RS];
+  float pd[WM * (WM - 1) / 2];
+  uint64_t pkey[WM];         // by pi position
+  int32_t pid[WM];
+  uint32_t fire[WM], closer[WM];
+  float rnrm[WM], rdq[WM];   // BF16 form, by row
+  int32_t roff[WM];          // local pair index of the first pair of new row i
+  uint8_t rpos[WM], prow[WM];
+  uint64_t bar[WPrec<PREC>::ST];
+  unsigned long long red_next, red_end;
+};
+
+__device__ __forceinline__ uint32_t lanes_below32(int p) { return p == 0 ? 0u : (0xffffffffu >> (32 - p)); }
+
+template <int METRIC, int PREC>
+__global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using C = WPrec<PREC>;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpSlot<PREC>& s = reinterpret_cast<WarpSlot<PREC>*>(smem_raw)[wid];
+  const int64_t cnt = a.list_n[0];
+  const int64_t gw = (int64_t)blockIdx.x * WW + wid, GW = (int64_t)gridDim.x * WW;
+  if (gw >= cnt) return;
+  const int R = a.R, W = a.rec_w, d = a.P.d;
+  if (lane == 0) {
+    for (int t = 0; t < C::ST; ++t) mbar_init(&s.bar[t], 1);
+    fence_mbar_init();
+    s.red_next = s.red_end = 0;
+  }
+  __syncwarp();
+  bool exact = false;
+  if (PREC == 1) {
+    const unsigned fl = a.P.qflags[0];
+    const float mxa = __uint_as_float(a.P.qflags[1]);
+    exact = (fl == 0u) && ((double)d * (double)mxa * (double)mxa < 16777216.0);
+  }
+  uint32_t ph[2] = {0u, 0u};
+  int stage = 0;
+  long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
+
+  // prefetch of the first record (registers; consumed one iteration later)
+  const uint64_t* r0 = a.rec + gw * W;
+  int64_t nv = (int64_t)r0[0];
+  int nm = (int)r0[1];
+  uint64_t nkey = lane < R ? r0[2 + lane] : kEmpty;
+  uint64_t naux = (PREC == 1 && lane < R) ? r0[2 + R + lane] : 0ull;
+  uint64_t nvaux = PREC == 1 ? r0[2 + 2 * R] : 0ull;
+
+  for (int64_t p = gw; p < cnt; p += GW) {
+    const int64_t v = nv;
+    const int m = nm;
+    const uint64_t keyl = lane < m ? nkey : kEmpty;
+    const uint64_t auxl = naux;
+    const uint64_t vaux = nvaux;
+    if (p + GW < cnt) {  // next record
+      const uint64_t* rn = a.rec + (p + GW) * W;
+      nv = (int64_t)rn[0];
+      nm = (int)rn[1];
+      nkey = lane < R ? rn[2 + lane] : kEmpty;
+      if (PREC == 1) {
+        naux = lane < R ? rn[2 + R + lane] : 0ull;
+        nvaux = rn[2 + 2 * R];
+      }
+    }
+    // ---- visit order: bitonic sort of (h, id, slot) over the 32 lanes ----------------------
+    const uint32_t idl = key_id(keyl);
+    uint64_t h = ~0ull;
+    uint32_t hid = 0xffffffffu, hs = (uint32_t)lane;
+    if (lane < m)
+      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v, (uint64_t)idl)
+          : (a.order == 1) ? (uint64_t)lane
+                           : (uint64_t)(m - 1 - lane);
+    if (lane < m) hid = idl;
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        const uint64_t oh = __shfl_xor_sync(0xffffffffu, h, jj);
+        const uint32_t oid = __shfl_xor_sync(0xffffffffu, hid, jj);
+        const uint32_t os = __shfl_xor_sync(0xffffffffu, hs, jj);
+        const bool up = (lane & kk) == 0, lower = (lane & jj) == 0;
+        const bool other_less = (oh < h) || (oh == h && oid < hid);
+        const bool take = (lower == up) ? other_less : !other_less;
+        if (take) {
+          h = oh;
+          hid = oid;
+          hs = os;
+        }
+      }
+    }
+    // lane p now holds pi position p: its storage slot hs
+    const int slot = (int)hs;
+    const uint64_t key = __shfl_sync(0xffffffffu, keyl, slot & 31);
+    const uint64_t aux = __shfl_sync(0xffffffffu, auxl, slot & 31);
+    const bool valid_p = lane < m;
+    const uint32_t validm = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
+    const uint32_t newm = __ballot_sync(0xffffffffu, valid_p && !key_old(key));
+    const int k = __popc(newm);
+    const int np = k * (m - 1) - k * (k - 1) / 2;
+    const uint32_t below = lanes_below32(lane);
+    const int row = ((newm >> lane) & 1u) ? __popc(newm & below) : k + __popc(~newm & validm & below);
+    const int32_t id = (int32_t)key_id(key);
+    if (valid_p) {
+      s.pkey[lane] = key;
+      s.pid[lane] = id;
+      s.prow[lane] = (uint8_t)row;
+      s.rpos[row] = (uint8_t)lane;
+      s.fire[lane] = 0u;
+      s.closer[lane] = 0u;
+      if (row < k) s.roff[row] = row * (m - 1) - row * (row - 1) / 2;
+      if (PREC == 1) {
+        s.rnrm[row] = __uint_as_float((uint32_t)aux);
+        s.rdq[row] = __uint_as_float((uint32_t)(aux >> 32));
+      }
+    }
+    __syncwarp();
+
+    // ---- gather + tile ---------------------------------------------------------------
+    const int nch = np > 0 ? (d + C::DC - 1) / C::DC : 0;
+    auto issue = [&](int c, int st) {
+      const int c0 = c * C::DC;
+      const int clen = min(C::DC, d - c0);
+      const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(typename C::T));
+      if (lane == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
+      __syncwarp();
+      if (valid_p) {
+        const typename C::T* src =
+            (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)id * a.P.ld + c0)
+                        : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)id * a.P.ldb + c0);
+        bulk_g2s(&s.rows[st][row][0], src, bytes, &s.bar[st]);
+      }
+    };
+    bool ok = true;
+    float cacc[6][4];
+    if (nch > 0) issue(0, stage);
+    for (int c = 0; c < nch; ++c) {
+      const int st = stage;
+      if (C::ST > 1 && c + 1 < nch) issue(c + 1, stage ^ 1);
+      ok = mbar_wait(&s.bar[st], ph[st], kWaitLimit);
+      ph[st] ^= 1u;
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const int clen = min(C::DC, d - c * C::DC);
+      if (PREC == 1) {
+        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[st][0][0]);
+        const int ksteps = (clen + 15) >> 4;
+        const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+          // tiles (I, J): (0,0..3), (1,2), (1,3)
+          const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
+          if (I < KI && J < NJ) {
+            if (c == 0) cacc[t][0] = cacc[t][1] = cacc[t][2] = cacc[t][3] = 0.0f;
+            const int ra = min(I * 16 + (lane & 15), WM - 1);
+            const int rb = J * 8 + (lane & 7);
+            const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
+            const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
+            for (int ks = 0; ks < ksteps; ++ks) {
+              uint32_t fa[4], fb[2];
+              ldmatrix_x4(fa, pa + ks * 16);
+              ldmatrix_x2(fb, pb + ks * 16);
+              mma_bf16(cacc[t], fa, fb);
+            }
+          }
+        }
+      } else {
+        const float* rows = reinterpret_cast<const float*>(&s.rows[st][0][0]);
+        const int full4 = clen & ~3, rem = clen & 3;
+        for (int q = lane; q < np; q += 32) {
+          int i = 0;  // the new row owning pair q (rows of a vertex: at most 32)
+#pragma unroll
+          for (int w = 16; w > 0; w >>= 1)
+            if (i + w < k && s.roff[i + w] <= q) i += w;
+          const int j = i + 1 + (q - s.roff[i]);
+          const float* ra = rows + i * C::RS;
+          const float* rb = rows + j * C::RS;
+          float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          for (int u = 0; u < full4; u += 4)
+            dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
+                               *reinterpret_cast<const float4*>(rb + u));
+          if (rem)
+            dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
+                               mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
+          const float dab = dist_finish4<METRIC>(acc);
+          s.pd[q] = dab;
+          const int pa = s.rpos[i], pb = s.rpos[j];
+          const int lo = min(pa, pb), hi = max(pa, pb);
+          if (dab < fmaxf(key_dist(s.pkey[pa]), key_dist(s.pkey[pb]))) {
+            atomicOr(&s.fire[hi], 1u << lo);
+            if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1)) atomicOr(&s.closer[hi], 1u << lo);
+          }
+        }
+      }
+      __syncwarp();
+      stage ^= (C::ST > 1) ? 1 : 0;
+    }
+    if (!__all_sync(0xffffffffu, ok)) {  // a bounded wait gave up: report and stop the warp
+      if (lane == 0) atomicExch(a.err, kErrTimeout);
+      for (int t = 0; t < C::ST; ++t) mbar_wait(&s.bar[t], ph[t], kWaitLimit);
+      return;
+    }
+    if (PREC == 1 && nch > 0) {  // D from the accumulators and the fire decision
+      const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+      const int g = lane >> 2, tg = lane & 3;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
+        if (I < KI && J < NJ) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = I * 16 + g + ((e >> 1) << 3);
+            const int j = J * 8 + 2 * tg + (e & 1);
+            if (i < k && j > i && j < m) {
+              const float gij = cacc[t][e];
+              float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(s.rnrm[i], gij), __fsub_rn(s.rnrm[j], gij))
+                                        : __fsub_rn(1.0f, gij);
+              const int pa = s.rpos[i], pb = s.rpos[j];
+              const int lo = min(pa, pb), hi = max(pa, pb);
+              const float dva = key_dist(s.pkey[pa]), dvb = key_dist(s.pkey[pb]);
+              const float mx = fmaxf(dva, dvb);
+              bool fire = dab < mx;
+              if (!exact) {
+                const float vn = __uint_as_float((uint32_t)vaux), vq = __uint_as_float((uint32_t)(vaux >> 32));
+                const float tol = bf16_bound<METRIC>(dab, s.rnrm[i], s.rnrm[j], s.rdq[i], s.rdq[j], d) +
+                                  fmaxf(bf16_bound<METRIC>(dva, vn, s.rnrm[i], vq, s.rdq[i], d),
+                                        bf16_bound<METRIC>(dvb, vn, s.rnrm[j], vq, s.rdq[j], d));
+                if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
+                  const float* xv = a.P.X + v * a.P.ld;
+                  const float* xa = a.P.X + (int64_t)s.pid[pa] * a.P.ld;
+                  const float* xb = a.P.X + (int64_t)s.pid[pb] * a.P.ld;
+                  dab = row_dist<METRIC>(xa, xb, d);
+                  fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
+                  ++st_check;
+                }
+              }
+              s.pd[s.roff[i] + (j - i - 1)] = dab;
+              if (fire) {
+                atomicOr(&s.fire[hi], 1u << lo);
+                if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1)) atomicOr(&s.closer[hi], 1u << lo);
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+
+    // ---- prune: every lane replays the chain over the columns that have fire bits ------
+    uint32_t alive = validm;
+    int mykill = -1;
+    {
+      uint32_t cols = __ballot_sync(0xffffffffu, valid_p && s.fire[lane] != 0u);
+      while (cols) {
+        const int b = __ffs(cols) - 1;
+        cols &= cols - 1;
+        const uint32_t cand = s.fire[b] & alive;
+        const uint32_t x = cand & s.closer[b];
+        uint32_t kill = cand;
+        if (x) {
+          const int f = __ffs(x) - 1;
+          kill = cand & lanes_below32(f);
+          alive &= ~(1u << b);
+          if (lane == b) mykill = f;
+        }
+        alive &= ~kill;
+        if ((kill >> lane) & 1u) mykill = b;
+      }
+    }
+    // ---- emit ----------------------------------------------------------------------------
+    const bool surv = valid_p && ((alive >> lane) & 1u);
+    const uint32_t smask = __reduce_or_sync(0xffffffffu, surv ? (1u << slot) : 0u);
+    const int nkeep = __popc(alive & validm);
+    if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
+    for (int t = nkeep + lane; t < R; t += 32) a.keys_out[v * R + t] = kEmpty;
+    if (lane == 0) a.deg_out[v] = nkeep;
+    const int ndead = m - nkeep;
+    if (a.emit_redirects && ndead > 0) {
+      unsigned long long base = s.red_next;
+      if (base + (unsigned long long)ndead > s.red_end) {
+        for (unsigned long long i = base + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+        unsigned long long nb2 = 0;
+        if (lane == 0) nb2 = atomicAdd(a.red_n, (unsigned long long)WRED);
+        base = __shfl_sync(0xffffffffu, nb2, 0);
+        if (lane == 0) s.red_end = base + WRED;
+      }
+      __syncwarp();
+      if (lane == 0) s.red_next = base + (unsigned long long)ndead;
+      if (valid_p && !surv) {
+        const int ri = s.prow[mykill], rj = row;
+        const int i = min(ri, rj), j = max(ri, rj);
+        const float dd = s.pd[s.roff[i] + (j - i - 1)];
+        const int32_t tgt = s.pid[mykill];
+        const unsigned long long sl = base + (unsigned long long)__popc(~alive & validm & below);
+        a.red_tgt[sl] = tgt;
+        a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
+        atomicAdd(&a.count[tgt], 1);
+      }
+    }
+    if (lane == 0) {
+      if (np > 0) {
+        st_vert += 1;
+        st_rows += m;
+        st_pairs += np;
+      }
+      st_fired += ndead;
+    }
+    __syncwarp();
+  }
+  if (a.emit_redirects)
+    for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+  if (a.stats) {
+    if (lane == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)st_vert);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
+    }
+    if (PREC == 1) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) st_check += __shfl_xor_sync(0xffffffffu, st_check, o);
+      if (lane == 0 && st_check)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[7]), (unsigned long long)st_check);
+    }
+  }
+}
+
+template <int METRIC, int PREC>
+cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* name) {
+  const size_t smem = sizeof(WarpSlot<PREC>) * WW;
+  static bool attr_set = false;
+  auto kern = rnd_join_warp_kernel<METRIC, PREC>;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WW * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
+  ProfScope ps(name, st);
+  kern<<<(unsigned)blocks, WW * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -831,6 +1532,7 @@ __global__ void scatter_kernel(const int32_t* __restrict__ tgt, const uint64_t* 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t = tgt[i];
+    if (t < 0) continue;  // unused tail of a reserved chunk
     const int pos = atomicSub(&count[t], 1) - 1;
     bucket[off[t] + pos] = pk[i];
   }
@@ -877,6 +1579,47 @@ __device__ __forceinline__ void select_pass(uint64_t (&x)[E], uint64_t* buf) {
   warp_sort_u64<E>(x);
 }
 
+// Inserts key b into a sorted, duplicate-free list (x0 holds elements 0..31 by lane, x1
+// elements 32..63) that keeps the R smallest keys: a copy of an id already listed keeps
+// the smaller key and the old bit of either copy.
+__device__ __forceinline__ void list_insert(uint64_t& x0, uint64_t& x1, uint64_t b, int R) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t idb = key_id(b);
+  const unsigned d0 = __ballot_sync(0xffffffffu, x0 != kEmpty && key_id(x0) == idb);
+  const unsigned d1 = __ballot_sync(0xffffffffu, x1 != kEmpty && key_id(x1) == idb);
+  if (d0 | d1) {
+    const int e = d0 ? __ffs(d0) - 1 : 32 + __ffs(d1) - 1;
+    const uint64_t xe = __shfl_sync(0xffffffffu, e < 32 ? x0 : x1, e & 31);
+    if ((b >> 1) >= (xe >> 1)) {  // the listed copy is not farther: keep it
+      if (b & 1ull) {
+        if (lane == e) x0 |= 1ull;
+        if (lane + 32 == e) x1 |= 1ull;
+      }
+      return;
+    }
+    b |= xe & 1ull;  // the nearer copy replaces the listed one: remove element e first
+    const uint64_t x1first = __shfl_sync(0xffffffffu, x1, 0);
+    uint64_t n0 = __shfl_down_sync(0xffffffffu, x0, 1);
+    uint64_t n1 = __shfl_down_sync(0xffffffffu, x1, 1);
+    if (lane == 31) {
+      n0 = x1first;
+      n1 = kEmpty;
+    }
+    if (lane >= e) x0 = n0;
+    if (lane + 32 >= e) x1 = n1;
+  }
+  const int pos = __popc(__ballot_sync(0xffffffffu, x0 < b)) + __popc(__ballot_sync(0xffffffffu, x1 < b));
+  if (pos >= R) return;
+  const uint64_t x0last = __shfl_sync(0xffffffffu, x0, 31);
+  uint64_t u0 = __shfl_up_sync(0xffffffffu, x0, 1);
+  uint64_t u1 = __shfl_up_sync(0xffffffffu, x1, 1);
+  if (lane == 0) u1 = x0last;
+  x0 = lane > pos ? u0 : (lane == pos ? b : x0);
+  x1 = lane + 32 > pos ? u1 : (lane + 32 == pos ? b : x1);
+  if (lane >= R) x0 = kEmpty;
+  if (lane + 32 >= R) x1 = kEmpty;
+}
+
 struct SelectArgs {
   int64_t n;
   int R;
@@ -897,21 +1640,28 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
   uint64_t* buf = bufs[warp];
   const int R = a.R;
   long long n_new = 0, n_in = 0;
+  // in place (keys_out == keys_in): every row already holds the target's base pool
+  const bool in_place = a.keys_out == a.keys_in;
   for (int64_t u = (int64_t)blockIdx.x * 8 + warp; u < a.n; u += (int64_t)gridDim.x * 8) {
-    const bool kept = a.active && a.active[u];
-    const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
-    const int na = kept ? a.deg_out[u] : a.deg_in[u];
     int64_t b0 = 0, c = 0;
     if (a.bucket) {
       b0 = a.off[u];
       c = a.off[u + 1] - b0;
     }
+    const bool kept = in_place || (a.active && a.active[u]);
+    if (c == 0 && kept) continue;  // nothing proposed: the pool in place is final
+    const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
+    const int na = kept ? a.deg_out[u] : a.deg_in[u];
     n_in += c;
     uint64_t out0, out1;
     if (c == 0) {
-      if (kept) continue;  // the kept survivors are already in place (all old)
       out0 = lane < na ? base[lane] : kEmpty;
       out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+    } else if (c <= 32) {  // a few proposals: insert them one by one into the sorted row
+      out0 = lane < na ? base[lane] : kEmpty;
+      out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+      const uint64_t bl = lane < c ? a.bucket[b0 + lane] : kEmpty;
+      for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
     } else {
       uint64_t x[4];
       x[0] = lane < na ? base[lane] : kEmpty;
@@ -970,11 +1720,14 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
 }
 
 cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Workspace& ws,
-                     int64_t* stats, cudaStream_t st) {
+                     const PointsSet& P, int64_t* stats, cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>(ceil_div(ws.n, 256), (int64_t)sm_count() * 8);
   ProfScope ps("prep", st);
-  prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list,
-                                                ws.list_n, stats);
+  // FP32 rows of more than 128 dimensions do not fit the warp kernel's single stage
+  const int small_max = (P.precision == 0 && P.d > 128) ? 0 : 32;
+  prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n,
+                                                small_max, ws.rec, ws.rec_w,
+                                                P.precision == 1 ? P.aux : nullptr, stats);
   return cudaGetLastError();
 }
 
@@ -994,8 +1747,9 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   a.R = R;
   a.keys_in = keys_in;
   a.deg_in = deg_in;
-  a.list = ws.list;
   a.list_n = ws.list_n;
+  a.rec = ws.rec;
+  a.rec_w = ws.rec_w;
   a.seed = seed;
   a.t1 = t1;
   a.t2 = t2;
@@ -1014,6 +1768,14 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
 
 cudaError_t dispatch_join(const PointsSet& P, const JoinArgs& a, cudaStream_t st, const char* name) {
   if (P.precision == 1 && (!P.Xb || !P.aux || !P.qflags)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  // pools of up to 32 entries: one warp per vertex; larger pools: batched CTAs
+  const char* wname = (name[0] == 'r') ? "rnd_join_warp" : "final_prune_warp";
+  if (P.metric == 0)
+    e = P.precision == 1 ? launch_join_warp_t<0, 1>(a, st, wname) : launch_join_warp_t<0, 0>(a, st, wname);
+  else
+    e = P.precision == 1 ? launch_join_warp_t<1, 1>(a, st, wname) : launch_join_warp_t<1, 0>(a, st, wname);
+  if (e != cudaSuccess) return e;
   if (P.metric == 0)
     return P.precision == 1 ? launch_join_t<0, 1>(a, st, name) : launch_join_t<0, 0>(a, st, name);
   return P.precision == 1 ? launch_join_t<1, 1>(a, st, name) : launch_join_t<1, 0>(a, st, name);
@@ -1028,7 +1790,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;  // list_n and red_n
-  if ((e = run_prep(keys_in, deg_in, ws, stats, st)) != cudaSuccess) return e;
+  if ((e = run_prep(keys_in, deg_in, ws, P, stats, st)) != cudaSuccess) return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out,
                                     deg_out, 1, stats);
   if ((e = dispatch_join(P, a, st, "rnd_join")) != cudaSuccess) return e;
@@ -1052,7 +1814,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;
-  if ((e = run_prep(keys_in, deg_in, ws, nullptr, st)) != cudaSuccess) return e;
+  if ((e = run_prep(keys_in, deg_in, ws, P, nullptr, st)) != cudaSuccess) return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, 0, order, ws, keys_out,
                                     deg_out, 0, nullptr);
   if ((e = dispatch_join(P, a, st, "final_prune")) != cudaSuccess) return e;
@@ -1172,18 +1934,23 @@ namespace {
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }
 
+namespace {
+inline int rec_words(int R) { return (2 + 2 * R + 1 + 1) & ~1; }
+inline size_t red_slots(int64_t n, int R) { return (size_t)n * R + (size_t)kMaxJoinGrid * RED_CHUNK; }
+}  // namespace
+
 size_t workspace_bytes(int64_t n, int R) {
-  const size_t slots = (size_t)n * R;
+  const size_t slots = red_slots(n, R);
   const size_t nb = (size_t)ceil_div(n, SCAN_TILE) + 1;
-  return al256(slots * 4) + al256(slots * 8) + al256(slots * 8) + al256((size_t)n * 4) +
+  return al256(slots * 4) + al256(slots * 8) + al256((size_t)n * R * 8) + al256((size_t)n * 4) +
          al256(((size_t)n + 1) * 8) + al256(nb * 8) + al256((size_t)n * 4) + al256((size_t)n) +
-         al256(16) + al256(4) + al256(8);
+         al256((size_t)n * rec_words(R) * 8) + al256(16) + al256(4) + al256(8);
 }
 
 bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) {
   if (!base || bytes < workspace_bytes(n, R)) return false;
   if (((uintptr_t)base & 255u) != 0) return false;
-  const size_t slots = (size_t)n * R;
+  const size_t slots = red_slots(n, R);
   const size_t nb = (size_t)ceil_div(n, SCAN_TILE) + 1;
   char* p = static_cast<char*>(base);
   ws->n = n;
@@ -1193,7 +1960,7 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   ws->red_key = reinterpret_cast<uint64_t*>(p);
   p += al256(slots * 8);
   ws->bucket = reinterpret_cast<uint64_t*>(p);
-  p += al256(slots * 8);
+  p += al256((size_t)n * R * 8);
   ws->count = reinterpret_cast<int32_t*>(p);
   p += al256((size_t)n * 4);
   ws->off = reinterpret_cast<int64_t*>(p);
@@ -1204,6 +1971,9 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   p += al256((size_t)n * 4);
   ws->active = reinterpret_cast<uint8_t*>(p);
   p += al256((size_t)n);
+  ws->rec = reinterpret_cast<uint64_t*>(p);
+  ws->rec_w = rec_words(R);
+  p += al256((size_t)n * rec_words(R) * 8);
   ws->list_n = reinterpret_cast<int32_t*>(p);  // [0] list length, then the redirect count
   ws->red_n = reinterpret_cast<unsigned long long*>(p + 8);
   p += al256(16);

@@ -276,24 +276,25 @@ def pool_init(X, d: int, S: int, R: int, seed: int, metric: int = L2SQ, stream=N
 
 
 def join_round(X, d: int, keys, deg, seed: int, t1: int, t2: int, order: int = ORDER_RANDOM, metric: int = L2SQ,
-               ws=None, stats=None, stream=None):
+               ws=None, stats=None, stream=None, inplace: bool = False):
+    """One round; with inplace=True the pool tensors are updated and returned."""
     torch = _torch()
     n, ld = X.shape
     R = keys.shape[1]
     ws = workspace(n, R, X.device) if ws is None else ws
-    k2 = torch.empty_like(keys)
-    d2 = torch.empty_like(deg)
+    k2 = keys if inplace else torch.empty_like(keys)
+    d2 = deg if inplace else torch.empty_like(deg)
     _check(lib().grnnd_join_round(_ptr(X), n, d, ld, metric, R, _ptr(keys), _ptr(deg), seed, t1, t2, order,
                                   _ptr(k2), _ptr(d2), _ptr(ws), ws.numel(), _ptr(stats), _stream_ptr(stream)))
     return k2, d2
 
 
-def reverse_sample(keys, deg, rho: float, ws=None, stats=None, stream=None):
+def reverse_sample(keys, deg, rho: float, ws=None, stats=None, stream=None, inplace: bool = False):
     torch = _torch()
     n, R = keys.shape
     ws = workspace(n, R, keys.device) if ws is None else ws
-    k2 = torch.empty_like(keys)
-    d2 = torch.empty_like(deg)
+    k2 = keys if inplace else torch.empty_like(keys)
+    d2 = deg if inplace else torch.empty_like(deg)
     _check(lib().grnnd_reverse_sample(n, R, ctypes.c_float(rho), _ptr(keys), _ptr(deg), _ptr(k2), _ptr(d2), _ptr(ws),
                                       ws.numel(), _ptr(stats), _stream_ptr(stream)))
     return k2, d2

@@ -382,3 +382,24 @@ def test_bf16_build_continuous_data(G, orc):
     ra = orc.recall_at_k(ga.search(Q, 10, 32), gt)
     rb = orc.recall_at_k(gb.search(Q, 10, 32), gt)
     assert rb >= ra - 0.01 and rb > 0.9
+
+
+# ---------------------------------------------------------------------------------------
+# in-place pool updates (the build's own mode)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d,S,R,hist", [(2500, 20, 16, 32, 0), (2000, 9, 32, 64, 2), (1500, 150, 48, 64, 1)])
+def test_join_round_in_place_matches_oracle(G, orc, n, d, S, R, hist):
+    X = synth.small_integers(n, d, -8, 8, seed=n + d)
+    Xd, _ = G.device_points(X)
+    p = oracle_state(orc, X, S, R, 41, hist)
+    keys, deg = to_keys(G, p), torch.from_numpy(p.deg).cuda()
+    ws = G.workspace(n, R)
+    for t2 in (hist + 1, hist + 2, hist + 3):
+        want, _, _ = orc.round_(X, p, 41, 1, t2)
+        keys, deg = G.join_round(Xd, d, keys, deg, 41, 1, t2, ws=ws, inplace=True)
+        assert_pool_equal(G, keys, deg, want)
+        p = want
+    want, _ = orc.reverse(p, 0.6)
+    keys, deg = G.reverse_sample(keys, deg, 0.6, ws=ws, inplace=True)
+    assert_pool_equal(G, keys, deg, want)
