@@ -206,6 +206,18 @@ GRNND_API int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64
                          const int32_t *deg_in, uint64_t *keys_out, int32_t *deg_out,
                          void *workspace, size_t workspace_bytes, int64_t *stats, void *stream);
 
+/* Status of the last step (grnnd_join_round, grnnd_reverse_sample or
+ * grnnd_final_prune) that used this workspace, for the same n and R.  Each step
+ * clears the workspace's status word when it starts; a device-side wait of the
+ * step that reaches its iteration limit sets it, and the rest of that step then
+ * does nothing: its output pool is incomplete (rows of vertices that were not
+ * reached keep their input when the step runs in place, and are unspecified
+ * otherwise).  Synchronises `stream`.  Returns GRNND_OK, GRNND_ETIMEOUT, or
+ * GRNND_EINVAL / GRNND_ECUDA.  The paper has no counterpart: it is the error
+ * channel of the bounded waits. */
+GRNND_API int grnnd_workspace_status(const void *workspace, size_t workspace_bytes, int64_t n,
+                                     int32_t R, void *stream);
+
 /* Final prune-only pass: the prune of a round with order key t1 (t2 = 0),
  * keeping only each vertex's survivors, in key order; no redirects.
  * keys_out: device n x R (written in full, must not alias keys_in), deg_out:

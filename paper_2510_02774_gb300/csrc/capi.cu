@@ -235,6 +235,22 @@ int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int3
   return GRNND_OK;
 }
 
+int grnnd_workspace_status(const void* workspace, size_t workspace_bytes, int64_t n, int32_t R,
+                           void* stream) {
+  if (n < 1 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n out of range");
+  int rc = check_R(R);
+  if (rc) return rc;
+  grnnd::Workspace ws;
+  if (!grnnd::carve_workspace(const_cast<void*>(workspace), workspace_bytes, n, R, &ws))
+    return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t h = 0;
+  GR_CU(cudaMemcpyAsync(&h, ws.err, 4, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaStreamSynchronize(st));
+  if (h) return fail(GRNND_ETIMEOUT, "a device-side wait of the last step reached its iteration limit");
+  return GRNND_OK;
+}
+
 int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t* keys_out, int32_t* deg_out,
                          void* workspace, size_t workspace_bytes, int64_t* stats, void* stream) {
@@ -430,8 +446,11 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
                                 stats, st));
       ++rounds;
       int64_t fresh = 0;
+      int32_t rerr = 0;
       GR_CU(cudaMemcpyAsync(&fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
+      GR_CU(cudaMemcpyAsync(&rerr, ws.err, 4, cudaMemcpyDeviceToHost, st));
       GR_CU(cudaStreamSynchronize(st));
+      if (rerr) return fail(GRNND_ETIMEOUT, "a device-side wait of a round reached its iteration limit");
       if (fresh == 0) break;  // no new entry anywhere: the remaining rounds are identities
     }
     if (t1 != p->T1) {

@@ -329,12 +329,14 @@ struct __align__(16) JoinSmem {
   uint64_t fcol[BV];        // columns with a fire bit, per vertex
   uint64_t alive[BV];
   uint64_t smask[BV];       // survivors by storage slot
-  unsigned long long deadbase[BV];
+  int32_t deadrank[BV];     // rank of a vertex's first redirect within the batch
   // batch formation
   uint64_t window[BV * RECW_MAX];  // work records of the next candidates (bulk prefetch)
   int64_t cv[BV];
   int32_t cm[BV], ck[BV], cnp[BV], cnt_[BV], cns[BV];
   unsigned long long red_next, red_end;  // this CTA's reserved redirect slots
+  unsigned long long red_b0, red_b1;     // the batch's redirects: avail at red_b0, the rest at red_b1
+  int32_t red_avail;
   uint64_t bar[2];
   uint64_t wbar;
 };
@@ -678,7 +680,7 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
   const int64_t per = (cnt + gridDim.x - 1) / gridDim.x;
   int64_t pos = a.n - cnt + (int64_t)blockIdx.x * per;
   const int64_t end = min(a.n, pos + per);
-  if (pos >= end) return;
+  if (pos >= end || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
   if (tid == 0) {
     mbar_init(&s.bar[0], 1);
     mbar_init(&s.bar[1], 1);
@@ -905,17 +907,26 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
             if (lane >= o) incl += y;
           }
           const int total = __shfl_sync(0xffffffffu, incl, 31);
-          unsigned long long base = s.red_next;
-          if (base + (unsigned long long)total > s.red_end) {
-            // chunk exhausted: mark its unused tail, reserve a fresh chunk
-            for (unsigned long long i = base + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+          // fill the current chunk to its end, then continue in a fresh one (a batch has at
+          // most BV * 63 <= RED_CHUNK redirects), so only each CTA's last chunk has a tail
+          const unsigned long long base = s.red_next, end = s.red_end;
+          unsigned long long b1 = base, next = base + (unsigned long long)total;
+          int avail = total;
+          if (next > end) {
+            avail = (int)(end - base);
             unsigned long long nbase = 0;
             if (lane == 0) nbase = atomicAdd(a.red_n, (unsigned long long)RED_CHUNK);
-            base = __shfl_sync(0xffffffffu, nbase, 0);
-            if (lane == 0) s.red_end = base + RED_CHUNK;
+            b1 = __shfl_sync(0xffffffffu, nbase, 0);
+            next = b1 + (unsigned long long)(total - avail);
+            if (lane == 0) s.red_end = b1 + RED_CHUNK;
           }
-          if (lane == 0) s.red_next = base + (unsigned long long)total;
-          if (lane < nb) s.deadbase[lane] = base + (unsigned long long)(incl - ndead);
+          if (lane == 0) {
+            s.red_next = next;
+            s.red_b0 = base;
+            s.red_b1 = b1;
+            s.red_avail = avail;
+          }
+          if (lane < nb) s.deadrank[lane] = incl - ndead;
         }
       }
       __syncthreads();
@@ -957,7 +968,9 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
           const int i = min(ri, rj), j = max(ri, rj);
           const float dd = s.pd[B.roff[rb + i] + (j - i - 1)];
           const int32_t tgt = B.pid[rb + cpos];
-          const unsigned long long slot = s.deadbase[ev] + (unsigned long long)__popcll(~ealive & valid & bits_below(ep));
+          const int g = s.deadrank[ev] + __popcll(~ealive & valid & bits_below(ep));
+          const unsigned long long slot =
+              g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
           a.red_tgt[slot] = tgt;
           a.red_key[slot] = make_key(dd, (uint32_t)B.pid[t], 0u);
           atomicAdd(&a.count[tgt], 1);
@@ -1091,7 +1104,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   WarpSlot<PREC>& s = reinterpret_cast<WarpSlot<PREC>*>(smem_raw)[wid];
   const int64_t cnt = a.list_n[0];
   const int64_t gw = (int64_t)blockIdx.x * WW + wid, GW = (int64_t)gridDim.x * WW;
-  if (gw >= cnt) return;
+  if (gw >= cnt || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
   const int R = a.R, W = a.rec_w, d = a.P.d;
   if (lane == 0) {
     for (int t = 0; t < C::ST; ++t) mbar_init(&s.bar[t], 1);
@@ -1105,7 +1118,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const float mxa = __uint_as_float(a.P.qflags[1]);
     exact = (fl == 0u) && ((double)d * (double)mxa * (double)mxa < 16777216.0);
   }
-  uint32_t ph[2] = {0u, 0u};
+  uint32_t phb = 0u, infl = 0u;  // mbarrier phase bit and copies-in-flight bit per stage
   int stage = 0;
   long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
 
@@ -1194,6 +1207,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
       const uint32_t bytes = (uint32_t)(cpy * sizeof(typename C::T));
       if (lane == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
+      infl |= 1u << st;
       __syncwarp();
       if (valid_p) {
         const typename C::T* src =
@@ -1208,9 +1222,10 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     for (int c = 0; c < nch; ++c) {
       const int st = stage;
       if (C::ST > 1 && c + 1 < nch) issue(c + 1, stage ^ 1);
-      ok = mbar_wait(&s.bar[st], ph[st], kWaitLimit);
-      ph[st] ^= 1u;
+      ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
       if (!__all_sync(0xffffffffu, ok)) break;
+      phb ^= 1u << st;
+      infl &= ~(1u << st);
       const int clen = min(C::DC, d - c * C::DC);
       if (PREC == 1) {
         const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[st][0][0]);
@@ -1267,7 +1282,10 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     }
     if (!__all_sync(0xffffffffu, ok)) {  // a bounded wait gave up: report and stop the warp
       if (lane == 0) atomicExch(a.err, kErrTimeout);
-      for (int t = 0; t < C::ST; ++t) mbar_wait(&s.bar[t], ph[t], kWaitLimit);
+      for (int t = 0; t < C::ST; ++t)  // let this warp's copies in flight land
+        if ((infl >> t) & 1u) mbar_wait(&s.bar[t], (phb >> t) & 1u, kWaitLimit);
+      if (a.emit_redirects)
+        for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
       return;
     }
     if (PREC == 1 && nch > 0) {  // D from the accumulators and the fire decision
@@ -1346,22 +1364,27 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     if (lane == 0) a.deg_out[v] = nkeep;
     const int ndead = m - nkeep;
     if (a.emit_redirects && ndead > 0) {
-      unsigned long long base = s.red_next;
-      if (base + (unsigned long long)ndead > s.red_end) {
-        for (unsigned long long i = base + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+      // fill the warp's chunk to its end, then continue in a fresh one (ndead < WRED)
+      const unsigned long long base = s.red_next, end = s.red_end;
+      unsigned long long b1 = base, next = base + (unsigned long long)ndead;
+      int avail = ndead;
+      if (next > end) {
+        avail = (int)(end - base);
         unsigned long long nb2 = 0;
         if (lane == 0) nb2 = atomicAdd(a.red_n, (unsigned long long)WRED);
-        base = __shfl_sync(0xffffffffu, nb2, 0);
-        if (lane == 0) s.red_end = base + WRED;
+        b1 = __shfl_sync(0xffffffffu, nb2, 0);
+        next = b1 + (unsigned long long)(ndead - avail);
+        if (lane == 0) s.red_end = b1 + WRED;
       }
       __syncwarp();
-      if (lane == 0) s.red_next = base + (unsigned long long)ndead;
+      if (lane == 0) s.red_next = next;
       if (valid_p && !surv) {
         const int ri = s.prow[mykill], rj = row;
         const int i = min(ri, rj), j = max(ri, rj);
         const float dd = s.pd[s.roff[i] + (j - i - 1)];
         const int32_t tgt = s.pid[mykill];
-        const unsigned long long sl = base + (unsigned long long)__popc(~alive & validm & below);
+        const int g = __popc(~alive & validm & below);
+        const unsigned long long sl = g < avail ? base + (unsigned long long)g : b1 + (unsigned long long)(g - avail);
         a.red_tgt[sl] = tgt;
         a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
         atomicAdd(&a.count[tgt], 1);
@@ -1411,6 +1434,419 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
   const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
   ProfScope ps(name, st);
   kern<<<(unsigned)blocks, WW * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// =====================================================================================
+// rnd_join for pools of 33..64 entries: a team of two warps (one 64-thread CTA) per
+// vertex; thread t owns pool entry t.  Same steps as the warp kernel, with the visit
+// order from a shared-memory rank, the BF16 tiles split between the two warps and the
+// FP32 pairs between the 64 threads.
+// =====================================================================================
+namespace {
+
+constexpr int TM = 64;     // pool entries per team
+constexpr int TRED = 512;  // redirect slots a team reserves at a time
+
+template <int PREC>
+struct TPrec;
+template <>
+struct TPrec<0> {
+  using T = float;
+  static constexpr int DC = 128;  // whole rows (used for d <= 128)
+  static constexpr int RS = DC + 4;
+  static constexpr int VEC = 4;
+  static constexpr int ST = 1;
+};
+template <>
+struct TPrec<1> {
+  using T = __nv_bfloat16;
+  static constexpr int DC = 64;
+  static constexpr int RS = DC + 8;
+  static constexpr int VEC = 16;
+  static constexpr int ST = 2;
+};
+
+template <int PREC>
+struct __align__(16) TeamSmem {
+  typename TPrec<PREC>::T rows[TPrec<PREC>::ST][TM][TPrec<PREC>::RS];
+  float pd[TM * (TM - 1) / 2];
+  uint64_t hk[TM];           // order key by storage slot
+  uint32_t hid[TM];
+  uint64_t pkey[TM];         // by pi position
+  int32_t pid[TM];
+  uint64_t fire[TM], closer[TM];
+  float rnrm[TM], rdq[TM];   // BF16 form, by row
+  int32_t roff[TM + 1];
+  uint8_t rpos[TM], prow[TM];
+  uint64_t newm, smask;
+  uint64_t bar[TPrec<PREC>::ST];
+  unsigned long long red_next, red_end, red_b0, red_b1;
+  int32_t red_avail;
+};
+
+constexpr int kTeamTiles = 20;  // (I, J) with I < 4, J < 8 and J * 8 + 7 > I * 16
+
+__device__ __forceinline__ void team_tile(int t, int& I, int& J) {
+  // row block I covers new rows 16I..16I+15; column blocks J with 8J + 7 > 16I
+  if (t < 8) { I = 0; J = t; }
+  else if (t < 14) { I = 1; J = t - 6; }
+  else if (t < 18) { I = 2; J = t - 10; }
+  else { I = 3; J = t - 12; }
+}
+
+template <int METRIC, int PREC>
+__global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using C = TPrec<PREC>;
+  TeamSmem<PREC>& s = *reinterpret_cast<TeamSmem<PREC>*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t cnt = a.list_n[1];
+  const int64_t first = a.n - cnt;  // the team list sits at the top of the record array
+  int64_t p = first + blockIdx.x;
+  if (p >= a.n || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
+  const int R = a.R, W = a.rec_w, d = a.P.d;
+  if (tid == 0) {
+    for (int t = 0; t < C::ST; ++t) mbar_init(&s.bar[t], 1);
+    fence_mbar_init();
+    s.red_next = s.red_end = 0;
+  }
+  __syncthreads();
+  bool exact = false;
+  if (PREC == 1) {
+    const unsigned fl = a.P.qflags[0];
+    const float mxa = __uint_as_float(a.P.qflags[1]);
+    exact = (fl == 0u) && ((double)d * (double)mxa * (double)mxa < 16777216.0);
+  }
+  uint32_t phb = 0u, infl = 0u;  // mbarrier phase bit and copies-in-flight bit per stage
+  int stage = 0;
+  long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
+
+  const uint64_t* r0 = a.rec + p * W;
+  int64_t nv = (int64_t)r0[0];
+  int nm = (int)r0[1];
+  uint64_t nkey = tid < R ? r0[2 + tid] : kEmpty;
+  uint64_t naux = (PREC == 1 && tid < R) ? r0[2 + R + tid] : 0ull;
+  uint64_t nvaux = PREC == 1 ? r0[2 + 2 * R] : 0ull;
+
+  for (; p < a.n; p += gridDim.x) {
+    const int64_t v = nv;
+    const int m = nm;
+    const uint64_t keyl = tid < m ? nkey : kEmpty;
+    const uint64_t auxl = naux;
+    const uint64_t vaux = nvaux;
+    if (p + gridDim.x < a.n) {
+      const uint64_t* rn = a.rec + (p + gridDim.x) * W;
+      nv = (int64_t)rn[0];
+      nm = (int)rn[1];
+      nkey = tid < R ? rn[2 + tid] : kEmpty;
+      if (PREC == 1) {
+        naux = tid < R ? rn[2 + R + tid] : 0ull;
+        nvaux = rn[2 + 2 * R];
+      }
+    }
+    // ---- visit order: rank of (h, id) among the m entries --------------------------------
+    const uint32_t idl = key_id(keyl);
+    const bool has = tid < m;
+    uint64_t h = ~0ull;
+    if (has)
+      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v, (uint64_t)idl)
+          : (a.order == 1) ? (uint64_t)tid
+                           : (uint64_t)(m - 1 - tid);
+    s.hk[tid] = h;
+    s.hid[tid] = has ? idl : 0xffffffffu;
+    __syncthreads();
+    int pi = 0;
+    if (has)
+      for (int f = 0; f < m; ++f) {
+        const uint64_t hf = s.hk[f];
+        pi += (hf < h) || (hf == h && s.hid[f] < idl);
+      }
+    const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+    if (tid == 0) s.newm = 0;
+    __syncthreads();
+    if (has && !key_old(keyl)) atomicOr(reinterpret_cast<unsigned long long*>(&s.newm), 1ull << pi);
+    __syncthreads();
+    const uint64_t newm = s.newm;
+    const int k = __popcll(newm);
+    const int np = k * (m - 1) - k * (k - 1) / 2;
+    int row = 0;
+    if (has) {
+      const uint64_t lo = bits_below(pi);
+      row = ((newm >> pi) & 1ull) ? __popcll(newm & lo) : k + __popcll(~newm & valid & lo);
+      s.pkey[pi] = keyl;
+      s.pid[pi] = (int32_t)idl;
+      s.prow[pi] = (uint8_t)row;
+      s.rpos[row] = (uint8_t)pi;
+      s.fire[pi] = 0ull;
+      s.closer[pi] = 0ull;
+      if (PREC == 1) {
+        s.rnrm[row] = __uint_as_float((uint32_t)auxl);
+        s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
+      }
+    }
+    if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
+    __syncthreads();
+
+    // ---- gather + tile -------------------------------------------------------------------
+    const int nch = np > 0 ? (d + C::DC - 1) / C::DC : 0;
+    auto issue = [&](int c, int st) {
+      const int c0 = c * C::DC;
+      const int clen = min(C::DC, d - c0);
+      const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(typename C::T));
+      if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
+      infl |= 1u << st;
+      __syncthreads();
+      if (has) {
+        const typename C::T* src =
+            (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
+                        : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)idl * a.P.ldb + c0);
+        bulk_g2s(&s.rows[st][row][0], src, bytes, &s.bar[st]);
+      }
+    };
+    float cacc[kTeamTiles / 2][4];
+    bool fail = false;
+    if (nch > 0) issue(0, stage);
+    for (int c = 0; c < nch; ++c) {
+      const int st = stage;
+      if (C::ST > 1 && c + 1 < nch) issue(c + 1, stage ^ 1);
+      const bool ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
+      if (__syncthreads_or(!ok)) {  // uniform over the team
+        fail = true;
+        break;
+      }
+      phb ^= 1u << st;
+      infl &= ~(1u << st);
+      const int clen = min(C::DC, d - c * C::DC);
+      if (PREC == 1) {
+        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[st][0][0]);
+        const int ksteps = (clen + 15) >> 4;
+        const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+#pragma unroll
+        for (int u = 0; u < kTeamTiles / 2; ++u) {
+          int I, J;
+          team_tile(2 * u + warp, I, J);
+          if (I < KI && J < NJ) {
+            if (c == 0) cacc[u][0] = cacc[u][1] = cacc[u][2] = cacc[u][3] = 0.0f;
+            const int ra = min(I * 16 + (lane & 15), TM - 1);
+            const int rb = J * 8 + (lane & 7);
+            const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
+            const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
+            for (int ks = 0; ks < ksteps; ++ks) {
+              uint32_t fa[4], fb[2];
+              ldmatrix_x4(fa, pa + ks * 16);
+              ldmatrix_x2(fb, pb + ks * 16);
+              mma_bf16(cacc[u], fa, fb);
+            }
+          }
+        }
+      } else {
+        const float* rows = reinterpret_cast<const float*>(&s.rows[st][0][0]);
+        const int full4 = clen & ~3, rem = clen & 3;
+        for (int q = tid; q < np; q += TM) {
+          int i = 0;  // the new row owning pair q
+#pragma unroll
+          for (int w = 32; w > 0; w >>= 1)
+            if (i + w < k && s.roff[i + w] <= q) i += w;
+          const int j = i + 1 + (q - s.roff[i]);
+          const float* ra = rows + i * C::RS;
+          const float* rb = rows + j * C::RS;
+          float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          for (int u = 0; u < full4; u += 4)
+            dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
+                               *reinterpret_cast<const float4*>(rb + u));
+          if (rem)
+            dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
+                               mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
+          const float dab = dist_finish4<METRIC>(acc);
+          s.pd[q] = dab;
+          const int pa = s.rpos[i], pb = s.rpos[j];
+          const int lo = min(pa, pb), hi = max(pa, pb);
+          if (dab < fmaxf(key_dist(s.pkey[pa]), key_dist(s.pkey[pb]))) {
+            atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
+            if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
+              atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
+          }
+        }
+      }
+      __syncthreads();
+      stage ^= (C::ST > 1) ? 1 : 0;
+    }
+    if (fail) {  // a bounded wait gave up: report, let the copies in flight land, stop
+      if (tid == 0) atomicExch(a.err, kErrTimeout);
+      for (int t = 0; t < C::ST; ++t)
+        if ((infl >> t) & 1u) mbar_wait(&s.bar[t], (phb >> t) & 1u, kWaitLimit);
+      if (a.emit_redirects)
+        for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
+      return;
+    }
+    if (PREC == 1 && nch > 0) {  // accumulators to shared memory, then one thread per pair
+      const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+      const int g = lane >> 2, tg = lane & 3;
+#pragma unroll
+      for (int u = 0; u < kTeamTiles / 2; ++u) {
+        int I, J;
+        team_tile(2 * u + warp, I, J);
+        if (I < KI && J < NJ) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = I * 16 + g + ((e >> 1) << 3);
+            const int j = J * 8 + 2 * tg + (e & 1);
+            if (i < k && j > i && j < m) s.pd[s.roff[i] + (j - i - 1)] = cacc[u][e];
+          }
+        }
+      }
+      __syncthreads();
+      const float vn = __uint_as_float((uint32_t)vaux), vq = __uint_as_float((uint32_t)(vaux >> 32));
+      for (int q = tid; q < np; q += TM) {
+        int i = 0;
+#pragma unroll
+        for (int w = 32; w > 0; w >>= 1)
+          if (i + w < k && s.roff[i + w] <= q) i += w;
+        const int j = i + 1 + (q - s.roff[i]);
+        const float gij = s.pd[q];
+        float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(s.rnrm[i], gij), __fsub_rn(s.rnrm[j], gij))
+                                  : __fsub_rn(1.0f, gij);
+        const int pa = s.rpos[i], pb = s.rpos[j];
+        const int lo = min(pa, pb), hi = max(pa, pb);
+        const float dva = key_dist(s.pkey[pa]), dvb = key_dist(s.pkey[pb]);
+        const float mx = fmaxf(dva, dvb);
+        bool fire = dab < mx;
+        if (!exact) {
+          const float tol = bf16_bound<METRIC>(dab, s.rnrm[i], s.rnrm[j], s.rdq[i], s.rdq[j], d) +
+                            fmaxf(bf16_bound<METRIC>(dva, vn, s.rnrm[i], vq, s.rdq[i], d),
+                                  bf16_bound<METRIC>(dvb, vn, s.rnrm[j], vq, s.rdq[j], d));
+          if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
+            const float* xv = a.P.X + v * a.P.ld;
+            const float* xa = a.P.X + (int64_t)s.pid[pa] * a.P.ld;
+            const float* xb = a.P.X + (int64_t)s.pid[pb] * a.P.ld;
+            dab = row_dist<METRIC>(xa, xb, d);
+            fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
+            ++st_check;
+          }
+        }
+        s.pd[q] = dab;
+        if (fire) {
+          atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
+          if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
+            atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- prune: every thread replays the chain over the columns with fire bits -----------
+    uint64_t alive = valid;
+    int mykill = -1;
+    {
+      const unsigned c0 = __ballot_sync(0xffffffffu, has && s.fire[tid] != 0ull);
+      if (lane == 0) reinterpret_cast<uint32_t*>(&s.smask)[warp] = c0;
+      __syncthreads();
+      uint64_t cols = s.smask;
+      while (cols) {
+        const int b = __ffsll((long long)cols) - 1;
+        cols &= cols - 1;
+        const uint64_t cand = s.fire[b] & alive;
+        const uint64_t x = cand & s.closer[b];
+        uint64_t kill = cand;
+        if (x) {
+          const int f = __ffsll((long long)x) - 1;
+          kill = cand & bits_below(f);
+          alive &= ~(1ull << b);
+          if (pi == b) mykill = f;
+        }
+        alive &= ~kill;
+        if (has && ((kill >> pi) & 1ull)) mykill = b;
+      }
+    }
+    // ---- emit ------------------------------------------------------------------------------
+    const bool surv = has && ((alive >> pi) & 1ull);
+    __syncthreads();
+    if (tid == 0) s.smask = 0ull;
+    __syncthreads();
+    if (surv) atomicOr(reinterpret_cast<unsigned long long*>(&s.smask), 1ull << tid);
+    const int nkeep = __popcll(alive & valid);
+    const int ndead = m - nkeep;
+    if (a.emit_redirects && tid == 0 && ndead > 0) {
+      // fill the team's chunk to its end, then continue in a fresh one (ndead < TRED)
+      const unsigned long long base = s.red_next;
+      unsigned long long b1 = base, next = base + (unsigned long long)ndead;
+      int avail = ndead;
+      if (next > s.red_end) {
+        avail = (int)(s.red_end - base);
+        b1 = atomicAdd(a.red_n, (unsigned long long)TRED);
+        next = b1 + (unsigned long long)(ndead - avail);
+        s.red_end = b1 + TRED;
+      }
+      s.red_next = next;
+      s.red_b0 = base;
+      s.red_b1 = b1;
+      s.red_avail = avail;
+    }
+    __syncthreads();
+    const uint64_t smask = s.smask;
+    if (surv) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
+    for (int t = nkeep + tid; t < R; t += TM) a.keys_out[v * R + t] = kEmpty;
+    if (tid == 0) a.deg_out[v] = nkeep;
+    if (a.emit_redirects && has && !surv) {
+      const int ri = s.prow[mykill], rj = row;
+      const int i = min(ri, rj), j = max(ri, rj);
+      const float dd = s.pd[s.roff[i] + (j - i - 1)];
+      const int32_t tgt = s.pid[mykill];
+      const int g = __popcll(~alive & valid & bits_below(pi));
+      const unsigned long long sl =
+          g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
+      a.red_tgt[sl] = tgt;
+      a.red_key[sl] = make_key(dd, idl, 0u);
+      atomicAdd(&a.count[tgt], 1);
+    }
+    if (tid == 0) {
+      if (np > 0) {
+        st_vert += 1;
+        st_rows += m;
+        st_pairs += np;
+      }
+      st_fired += ndead;
+    }
+    __syncthreads();
+  }
+  if (a.emit_redirects)
+    for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
+  if (a.stats) {
+    if (tid == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)st_vert);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
+    }
+    if (PREC == 1) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) st_check += __shfl_xor_sync(0xffffffffu, st_check, o);
+      if (lane == 0 && st_check)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[7]), (unsigned long long)st_check);
+    }
+  }
+}
+
+template <int METRIC, int PREC>
+cudaError_t launch_join_team_t(const JoinArgs& a, cudaStream_t st, const char* name) {
+  const size_t smem = sizeof(TeamSmem<PREC>);
+  static bool attr_set = false;
+  auto kern = rnd_join_team_kernel<METRIC, PREC>;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TM, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
+  ProfScope ps(name, st);
+  kern<<<(unsigned)blocks, TM, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1527,7 +1963,8 @@ __global__ void __launch_bounds__(SCAN_T) scan_apply_kernel(const int32_t* __res
 __global__ void scatter_kernel(const int32_t* __restrict__ tgt, const uint64_t* __restrict__ pk,
                                const unsigned long long* __restrict__ nred,
                                const int64_t* __restrict__ off, int32_t* __restrict__ count,
-                               uint64_t* __restrict__ bucket) {
+                               uint64_t* __restrict__ bucket, const int32_t* __restrict__ err) {
+  if (*err) return;  // a join wait gave up: the slots are incomplete, merge nothing
   const int64_t nslots = (int64_t)*nred;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1632,6 +2069,7 @@ struct SelectArgs {
   int32_t* deg_out;
   int64_t* round_new;
   int64_t* stats;
+  const int32_t* err;      // nonzero: a wait of this round gave up, leave every pool as it is
 };
 
 __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
@@ -1642,6 +2080,7 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
   long long n_new = 0, n_in = 0;
   // in place (keys_out == keys_in): every row already holds the target's base pool
   const bool in_place = a.keys_out == a.keys_in;
+  if (*a.err) return;
   for (int64_t u = (int64_t)blockIdx.x * 8 + warp; u < a.n; u += (int64_t)gridDim.x * 8) {
     int64_t b0 = 0, c = 0;
     if (a.bucket) {
@@ -1709,7 +2148,7 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
     {
       ProfScope ps("scatter", st);
       scatter_kernel<<<(unsigned)(sm_count() * 8), 256, 0, st>>>(ws.red_tgt, ws.red_key, ws.red_n, ws.off,
-                                                                 ws.count, ws.bucket);
+                                                                 ws.count, ws.bucket, ws.err);
     }
   }
   cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
@@ -1769,16 +2208,23 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
 cudaError_t dispatch_join(const PointsSet& P, const JoinArgs& a, cudaStream_t st, const char* name) {
   if (P.precision == 1 && (!P.Xb || !P.aux || !P.qflags)) return cudaErrorInvalidValue;
   cudaError_t e;
-  // pools of up to 32 entries: one warp per vertex; larger pools: batched CTAs
+  // pools of up to 32 entries: one warp per vertex; 33..64 entries: a two-warp team per
+  // vertex (batched CTAs with dimension chunks for FP32 rows longer than 128)
   const char* wname = (name[0] == 'r') ? "rnd_join_warp" : "final_prune_warp";
   if (P.metric == 0)
     e = P.precision == 1 ? launch_join_warp_t<0, 1>(a, st, wname) : launch_join_warp_t<0, 0>(a, st, wname);
   else
     e = P.precision == 1 ? launch_join_warp_t<1, 1>(a, st, wname) : launch_join_warp_t<1, 0>(a, st, wname);
   if (e != cudaSuccess) return e;
-  if (P.metric == 0)
-    return P.precision == 1 ? launch_join_t<0, 1>(a, st, name) : launch_join_t<0, 0>(a, st, name);
-  return P.precision == 1 ? launch_join_t<1, 1>(a, st, name) : launch_join_t<1, 0>(a, st, name);
+  if (P.precision == 1 || P.d <= 128) {  // pools of 33..64 entries: a two-warp team per vertex
+    const char* tname = (name[0] == 'r') ? "rnd_join_team" : "final_prune_team";
+    if (P.metric == 0)
+      return P.precision == 1 ? launch_join_team_t<0, 1>(a, st, tname) : launch_join_team_t<0, 0>(a, st, tname);
+    return P.precision == 1 ? launch_join_team_t<1, 1>(a, st, tname) : launch_join_team_t<1, 0>(a, st, tname);
+  }
+  // FP32 rows of more than 128 dimensions: batched CTAs with dimension chunks
+  if (P.metric == 0) return launch_join_t<0, 0>(a, st, name);
+  return launch_join_t<1, 0>(a, st, name);
 }
 
 }  // namespace
@@ -1790,6 +2236,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;  // list_n and red_n
+  if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, stats, st)) != cudaSuccess) return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out,
                                     deg_out, 1, stats);
@@ -1805,6 +2252,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.keys_out = keys_out;
   sa.deg_out = deg_out;
   sa.round_new = ws.round_new;
+  sa.err = ws.err;
   sa.stats = stats;
   return merge_tail(ws, sa, st);
 }
@@ -1814,6 +2262,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, nullptr, st)) != cudaSuccess) return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, 0, order, ws, keys_out,
                                     deg_out, 0, nullptr);
@@ -1829,6 +2278,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.keys_out = keys_out;
   sa.deg_out = deg_out;
   sa.round_new = ws.round_new;
+  sa.err = ws.err;
   sa.stats = nullptr;
   return merge_tail(ws, sa, st);
 }
@@ -1882,6 +2332,7 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   {
     const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
     ProfScope ps("reverse_propose", st);
@@ -1900,6 +2351,7 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
   sa.keys_out = keys_out;
   sa.deg_out = deg_out;
   sa.round_new = ws.round_new;
+  sa.err = ws.err;
   sa.stats = stats;
   return merge_tail(ws, sa, st);
 }
@@ -1936,7 +2388,13 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 namespace {
 inline int rec_words(int R) { return (2 + 2 * R + 1 + 1) & ~1; }
-inline size_t red_slots(int64_t n, int R) { return (size_t)n * R + (size_t)kMaxJoinGrid * RED_CHUNK; }
+// Redirect slots: a vertex loses at most m - 1 <= R - 1 entries (the one with the smallest
+// (dist, id) is never the farther side of a fired pair), and the units of each of the two
+// join kernels of a round fill their chunks completely before reserving the next, so each
+// kernel leaves at most (its units x its chunk) <= kMaxJoinGrid x RED_CHUNK slots unused.
+static_assert(WW * WRED <= RED_CHUNK && TRED <= RED_CHUNK, "per-CTA redirect reservation above the slack");
+static_assert(BV * 63 <= RED_CHUNK && WM <= WRED && TM <= TRED, "a batch or vertex must fit one fresh chunk");
+inline size_t red_slots(int64_t n, int R) { return (size_t)n * R + 2 * (size_t)kMaxJoinGrid * RED_CHUNK; }
 }  // namespace
 
 size_t workspace_bytes(int64_t n, int R) {

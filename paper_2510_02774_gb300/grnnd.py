@@ -73,6 +73,8 @@ _SIGS = {
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_void_p]),
     "grnnd_reverse_sample": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
@@ -298,6 +300,11 @@ def reverse_sample(keys, deg, rho: float, ws=None, stats=None, stream=None, inpl
     _check(lib().grnnd_reverse_sample(n, R, ctypes.c_float(rho), _ptr(keys), _ptr(deg), _ptr(k2), _ptr(d2), _ptr(ws),
                                       ws.numel(), _ptr(stats), _stream_ptr(stream)))
     return k2, d2
+
+
+def workspace_status(ws, n: int, R: int, stream=None) -> None:
+    """Raise GrnndError if a device-side wait of the last step on `ws` gave up (synchronises)."""
+    _check(lib().grnnd_workspace_status(_ptr(ws), ws.numel(), n, R, _stream_ptr(stream)))
 
 
 def final_prune(X, d: int, keys, deg, seed: int, t1: int, order: int = ORDER_RANDOM, metric: int = L2SQ, ws=None,

@@ -70,6 +70,10 @@ def test_step_calls_validate_layout(L):
     assert rc == G.EINVAL and b"ld" in L.grnnd_last_error()
     rc = L.grnnd_search(null, null, 1, 1, 1, null)
     assert rc == G.EINVAL
+    rc = L.grnnd_workspace_status(null, 1 << 30, 10, 4, null)
+    assert rc == G.EINVAL and b"workspace" in L.grnnd_last_error()
+    rc = L.grnnd_workspace_status(ctypes.c_void_p(1 << 20), 16, 10, 4, null)  # far too small
+    assert rc == G.EINVAL
 
 
 def test_workspace_size_scales(L):

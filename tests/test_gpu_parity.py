@@ -107,6 +107,9 @@ CASES = [
     (1200, 12, 16, 32, 1, 0, 2),     # ascending order (Alg 2)
     (1200, 12, 16, 32, 2, 0, 2),     # descending order
     (1200, 12, 16, 32, 0, 1, 2),     # inner product
+    (1200, 128, 48, 64, 0, 0, 1),    # pools of 33..64 entries, rows of exactly 128 floats
+    (1200, 37, 40, 64, 0, 1, 1),     # pools of 33..64 entries, inner product, ragged rows
+    (1200, 11, 40, 64, 2, 0, 2),     # pools of 33..64 entries, descending order
 ]
 
 
@@ -336,7 +339,7 @@ def _bf16_bound(D, ni, nj, ei, ej, d):
 
 
 @pytest.mark.parametrize("n,d,S,R,metric", [(3000, 16, 8, 16, 0), (2500, 128, 32, 64, 0), (1800, 40, 16, 32, 1),
-                                            (1500, 200, 16, 32, 0)])
+                                            (1500, 200, 16, 32, 0), (1800, 40, 32, 64, 1), (2000, 100, 40, 64, 0)])
 def test_bf16_build_is_exact_on_integer_data(G, orc, n, d, S, R, metric):
     # integers with d * max|x|^2 < 2^24: every BF16 product and FP32 partial sum is exact,
     # so the BF16 form must return the FP32 form's graph bit for bit (and the oracle's).
@@ -403,3 +406,4 @@ def test_join_round_in_place_matches_oracle(G, orc, n, d, S, R, hist):
     want, _ = orc.reverse(p, 0.6)
     keys, deg = G.reverse_sample(keys, deg, 0.6, ws=ws, inplace=True)
     assert_pool_equal(G, keys, deg, want)
+    G.workspace_status(ws, n, R)  # no device-side wait gave up
