@@ -1441,56 +1441,65 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
 
 // =====================================================================================
 // rnd_join for pools of 33..64 entries: a team of two warps (one 64-thread CTA) per
-// vertex; thread t owns pool entry t.  Same steps as the warp kernel, with the visit
-// order from a shared-memory rank, the BF16 tiles split between the two warps and the
-// FP32 pairs between the 64 threads.
+// vertex; thread t owns pool entry t (storage slot t).
+//   order   rank of (h, id) among the m entries (16-byte keys in shared memory);
+//   gather  one bulk copy per row and 128-column chunk (two stages when d > 128);
+//   tile    BF16: mma.sync m16n8k16 tiles over new rows x all rows, shared between the
+//           two warps and taken one at a time; partial dot products wait in shared memory
+//           between chunks, and the last chunk decides the fire bits straight from the
+//           accumulators.  FP32 (d <= 128): one thread per pair, canonical distance;
+//   chain   warp 0 replays the sequential outcome of the pair scan over the fire bits and
+//           records, for each entry made bottom, the entry that absorbed it;
+//   emit    survivors rewritten in place as old; redirects into reserved slots.
 // =====================================================================================
 namespace {
 
 constexpr int TM = 64;     // pool entries per team
 constexpr int TRED = 512;  // redirect slots a team reserves at a time
+constexpr int TDC = 128;   // columns per gathered chunk
 
 template <int PREC>
 struct TPrec;
 template <>
 struct TPrec<0> {
   using T = float;
-  static constexpr int DC = 128;  // whole rows (used for d <= 128)
-  static constexpr int RS = DC + 4;
+  static constexpr int RS = TDC + 4;  // row stride (elements): 528 B, conflict-free float4 reads
   static constexpr int VEC = 4;
-  static constexpr int ST = 1;
 };
 template <>
 struct TPrec<1> {
   using T = __nv_bfloat16;
-  static constexpr int DC = 64;
-  static constexpr int RS = DC + 8;
+  static constexpr int RS = TDC + 8;  // 272 B: the 8 rows of an ldmatrix phase hit distinct banks
   static constexpr int VEC = 16;
-  static constexpr int ST = 2;
 };
 
-template <int PREC>
+struct __align__(16) TeamKey {
+  uint64_t h;
+  uint32_t id;
+  uint32_t pad;
+};
+
 struct __align__(16) TeamSmem {
-  typename TPrec<PREC>::T rows[TPrec<PREC>::ST][TM][TPrec<PREC>::RS];
-  float pd[TM * (TM - 1) / 2];
-  uint64_t hk[TM];           // order key by storage slot
-  uint32_t hid[TM];
-  uint64_t pkey[TM];         // by pi position
-  int32_t pid[TM];
-  uint64_t fire[TM], closer[TM];
-  float rnrm[TM], rdq[TM];   // BF16 form, by row
-  int32_t roff[TM + 1];
-  uint8_t rpos[TM], prow[TM];
-  uint64_t newm, smask;
-  uint64_t bar[TPrec<PREC>::ST];
+  float pd[TM * (TM - 1) / 2];    // per pair: its distance (partial dot product between chunks)
+  TeamKey hk[TM];                 // order key by storage slot
+  uint64_t pkey[TM];              // pool key by pi position
+  uint64_t fire[TM], closer[TM];  // by pi position; bit a < b: pair (a, b) fired / a is closer
+  float2 rnd[TM];                 // by row: (squared norm of the BF16 row, recorded dist to v)
+  float rdq[TM];                  // by row: norm of the quantization residual
+  int32_t pid[TM];                // by pi position
+  int32_t roff[TM + 1];           // first pair index of new row i
+  uint8_t rpos[TM], prow[TM], killer[TM];
+  uint64_t newm, alive;
+  uint32_t sm32[2];
+  uint64_t bar[2];
   unsigned long long red_next, red_end, red_b0, red_b1;
   int32_t red_avail;
 };
+constexpr size_t kTeamRowsOff = (sizeof(TeamSmem) + 127) & ~(size_t)127;  // staged rows follow
 
-constexpr int kTeamTiles = 20;  // (I, J) with I < 4, J < 8 and J * 8 + 7 > I * 16
+constexpr int kTeamTiles = 20;  // (I, J) with I < 4, J < 8 and J >= 2I (some j > i in the tile)
 
 __device__ __forceinline__ void team_tile(int t, int& I, int& J) {
-  // row block I covers new rows 16I..16I+15; column blocks J with 8J + 7 > 16I
   if (t < 8) { I = 0; J = t; }
   else if (t < 14) { I = 1; J = t - 6; }
   else if (t < 18) { I = 2; J = t - 10; }
@@ -1501,20 +1510,26 @@ template <int METRIC, int PREC>
 __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using C = TPrec<PREC>;
-  TeamSmem<PREC>& s = *reinterpret_cast<TeamSmem<PREC>*>(smem_raw);
+  using T = typename C::T;
+  TeamSmem& s = *reinterpret_cast<TeamSmem*>(smem_raw);
+  T* const rowbase = reinterpret_cast<T*>(smem_raw + kTeamRowsOff);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t cnt = a.list_n[1];
   const int64_t first = a.n - cnt;  // the team list sits at the top of the record array
   int64_t p = first + blockIdx.x;
   if (p >= a.n || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
   const int R = a.R, W = a.rec_w, d = a.P.d;
+  const int nchd = (d + TDC - 1) / TDC;  // chunks per row
+  const int nst = nchd > 1 ? 2 : 1;      // stages
   if (tid == 0) {
-    for (int t = 0; t < C::ST; ++t) mbar_init(&s.bar[t], 1);
+    mbar_init(&s.bar[0], 1);
+    mbar_init(&s.bar[1], 1);
     fence_mbar_init();
     s.red_next = s.red_end = 0;
   }
   __syncthreads();
   bool exact = false;
+  float vn = 0.0f, vq = 0.0f;
   if (PREC == 1) {
     const unsigned fl = a.P.qflags[0];
     const float mxa = __uint_as_float(a.P.qflags[1]);
@@ -1536,7 +1551,10 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
     const uint64_t auxl = naux;
-    const uint64_t vaux = nvaux;
+    if (PREC == 1) {
+      vn = __uint_as_float((uint32_t)nvaux);
+      vq = __uint_as_float((uint32_t)(nvaux >> 32));
+    }
     if (p + gridDim.x < a.n) {
       const uint64_t* rn = a.rec + (p + gridDim.x) * W;
       nv = (int64_t)rn[0];
@@ -1555,23 +1573,29 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v, (uint64_t)idl)
           : (a.order == 1) ? (uint64_t)tid
                            : (uint64_t)(m - 1 - tid);
-    s.hk[tid] = h;
-    s.hid[tid] = has ? idl : 0xffffffffu;
+    {
+      TeamKey hk;
+      hk.h = h;
+      hk.id = has ? idl : 0xffffffffu;
+      hk.pad = 0u;
+      s.hk[tid] = hk;
+    }
+    if (tid == 0) s.newm = 0ull;
     __syncthreads();
     int pi = 0;
-    if (has)
+    if (has) {
+#pragma unroll 4
       for (int f = 0; f < m; ++f) {
-        const uint64_t hf = s.hk[f];
-        pi += (hf < h) || (hf == h && s.hid[f] < idl);
+        const TeamKey o = s.hk[f];
+        pi += (o.h < h) || (o.h == h && o.id < idl);
       }
-    const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
-    if (tid == 0) s.newm = 0;
-    __syncthreads();
-    if (has && !key_old(keyl)) atomicOr(reinterpret_cast<unsigned long long*>(&s.newm), 1ull << pi);
+      if (!key_old(keyl)) atomicOr(reinterpret_cast<unsigned long long*>(&s.newm), 1ull << pi);
+    }
     __syncthreads();
     const uint64_t newm = s.newm;
     const int k = __popcll(newm);
     const int np = k * (m - 1) - k * (k - 1) / 2;
+    const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
     int row = 0;
     if (has) {
       const uint64_t lo = bits_below(pi);
@@ -1582,37 +1606,33 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       s.rpos[row] = (uint8_t)pi;
       s.fire[pi] = 0ull;
       s.closer[pi] = 0ull;
-      if (PREC == 1) {
-        s.rnrm[row] = __uint_as_float((uint32_t)auxl);
-        s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
-      }
+      s.rnd[row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
+      if (PREC == 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
     }
     if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
     __syncthreads();
 
     // ---- gather + tile -------------------------------------------------------------------
-    const int nch = np > 0 ? (d + C::DC - 1) / C::DC : 0;
+    const int nch = np > 0 ? nchd : 0;
     auto issue = [&](int c, int st) {
-      const int c0 = c * C::DC;
-      const int clen = min(C::DC, d - c0);
+      const int c0 = c * TDC;
+      const int clen = min(TDC, d - c0);
       const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(typename C::T));
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(T));
       if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
       infl |= 1u << st;
       __syncthreads();
       if (has) {
-        const typename C::T* src =
-            (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
-                        : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)idl * a.P.ldb + c0);
-        bulk_g2s(&s.rows[st][row][0], src, bytes, &s.bar[st]);
+        const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
+                                   : reinterpret_cast<const T*>(a.P.Xb + (int64_t)idl * a.P.ldb + c0);
+        bulk_g2s(rowbase + ((size_t)st * TM + row) * C::RS, src, bytes, &s.bar[st]);
       }
     };
-    float cacc[kTeamTiles / 2][4];
     bool fail = false;
     if (nch > 0) issue(0, stage);
     for (int c = 0; c < nch; ++c) {
       const int st = stage;
-      if (C::ST > 1 && c + 1 < nch) issue(c + 1, stage ^ 1);
+      if (nst > 1 && c + 1 < nch) issue(c + 1, st ^ 1);
       const bool ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
       if (__syncthreads_or(!ok)) {  // uniform over the team
         fail = true;
@@ -1620,31 +1640,86 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
       phb ^= 1u << st;
       infl &= ~(1u << st);
-      const int clen = min(C::DC, d - c * C::DC);
+      const int clen = min(TDC, d - c * TDC);
+      const T* rows = rowbase + (size_t)st * TM * C::RS;
       if (PREC == 1) {
-        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[st][0][0]);
+        const __nv_bfloat16* rb16 = reinterpret_cast<const __nv_bfloat16*>(rows);
         const int ksteps = (clen + 15) >> 4;
         const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-#pragma unroll
-        for (int u = 0; u < kTeamTiles / 2; ++u) {
+        const bool first_c = (c == 0), last_c = (c + 1 == nch);
+        const int g = lane >> 2, tg = lane & 3;
+        for (int t = warp; t < kTeamTiles; t += 2) {
           int I, J;
-          team_tile(2 * u + warp, I, J);
-          if (I < KI && J < NJ) {
-            if (c == 0) cacc[u][0] = cacc[u][1] = cacc[u][2] = cacc[u][3] = 0.0f;
-            const int ra = min(I * 16 + (lane & 15), TM - 1);
-            const int rb = J * 8 + (lane & 7);
-            const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
-            const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
-            for (int ks = 0; ks < ksteps; ++ks) {
-              uint32_t fa[4], fb[2];
-              ldmatrix_x4(fa, pa + ks * 16);
-              ldmatrix_x2(fb, pb + ks * 16);
-              mma_bf16(cacc[u], fa, fb);
+          team_tile(t, I, J);
+          if (I >= KI || J >= NJ) continue;
+          // this lane's four elements: rows i0, i0 + 8 and columns j0, j0 + 1
+          const int i0 = I * 16 + g, j0 = J * 8 + 2 * tg;
+          int q[4];
+          bool ve[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+            ve[e] = (i < k) && (j > i) && (j < m);
+            q[e] = ve[e] ? s.roff[i] + (j - i - 1) : 0;
+          }
+          float acc[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
+          const int ra = min(I * 16 + (lane & 15), TM - 1);
+          const int rb = J * 8 + (lane & 7);
+          const __nv_bfloat16* pa = rb16 + ra * C::RS + ((lane >> 4) << 3);
+          const __nv_bfloat16* pb = rb16 + rb * C::RS + (((lane >> 3) & 1) << 3);
+          for (int ks = 0; ks < ksteps; ++ks) {
+            uint32_t fa[4], fb[2];
+            ldmatrix_x4(fa, pa + ks * 16);
+            ldmatrix_x2(fb, pb + ks * 16);
+            mma_bf16(acc, fa, fb);
+          }
+          if (!last_c) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (ve[e]) s.pd[q[e]] = acc[e];
+            continue;
+          }
+          // last chunk: distance and fire decision of each element
+          const float2 rI[2] = {s.rnd[min(i0, TM - 1)], s.rnd[min(i0 + 8, TM - 1)]};
+          const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (!ve[e]) continue;
+            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+            const float2 ri = rI[e >> 1], rj = rJ[e & 1];
+            const float gij = acc[e];
+            float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
+                                      : __fsub_rn(1.0f, gij);
+            const float mx = fmaxf(ri.y, rj.y);
+            bool fire = dab < mx;
+            if (!exact) {
+              const float eqi = s.rdq[i], eqj = s.rdq[j];
+              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d) +
+                                fmaxf(bf16_bound<METRIC>(ri.y, vn, ri.x, vq, eqi, d),
+                                      bf16_bound<METRIC>(rj.y, vn, rj.x, vq, eqj, d));
+              if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
+                const float* xv = a.P.X + v * a.P.ld;
+                const float* xa = a.P.X + (int64_t)s.pid[s.rpos[i]] * a.P.ld;
+                const float* xb = a.P.X + (int64_t)s.pid[s.rpos[j]] * a.P.ld;
+                dab = row_dist<METRIC>(xa, xb, d);
+                fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
+                ++st_check;
+              }
+            }
+            s.pd[q[e]] = dab;
+            if (fire) {
+              const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+              const int lo = min(pa2, pb2), hi = max(pa2, pb2);
+              atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
+              if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
+                atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
             }
           }
         }
       } else {
-        const float* rows = reinterpret_cast<const float*>(&s.rows[st][0][0]);
+        const float* rf = reinterpret_cast<const float*>(rows);
         const int full4 = clen & ~3, rem = clen & 3;
         for (int q = tid; q < np; q += TM) {
           int i = 0;  // the new row owning pair q
@@ -1652,8 +1727,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           for (int w = 32; w > 0; w >>= 1)
             if (i + w < k && s.roff[i + w] <= q) i += w;
           const int j = i + 1 + (q - s.roff[i]);
-          const float* ra = rows + i * C::RS;
-          const float* rb = rows + j * C::RS;
+          const float* ra = rf + i * C::RS;
+          const float* rb = rf + j * C::RS;
           float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           for (int u = 0; u < full4; u += 4)
             dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
@@ -1663,9 +1738,9 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
                                mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
           const float dab = dist_finish4<METRIC>(acc);
           s.pd[q] = dab;
-          const int pa = s.rpos[i], pb = s.rpos[j];
-          const int lo = min(pa, pb), hi = max(pa, pb);
-          if (dab < fmaxf(key_dist(s.pkey[pa]), key_dist(s.pkey[pb]))) {
+          if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y)) {
+            const int pa = s.rpos[i], pb = s.rpos[j];
+            const int lo = min(pa, pb), hi = max(pa, pb);
             atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
             if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
               atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
@@ -1673,101 +1748,52 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         }
       }
       __syncthreads();
-      stage ^= (C::ST > 1) ? 1 : 0;
+      if (nst > 1) stage ^= 1;
     }
     if (fail) {  // a bounded wait gave up: report, let the copies in flight land, stop
       if (tid == 0) atomicExch(a.err, kErrTimeout);
-      for (int t = 0; t < C::ST; ++t)
+      for (int t = 0; t < 2; ++t)
         if ((infl >> t) & 1u) mbar_wait(&s.bar[t], (phb >> t) & 1u, kWaitLimit);
       if (a.emit_redirects)
         for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
       return;
     }
-    if (PREC == 1 && nch > 0) {  // accumulators to shared memory, then one thread per pair
-      const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-      const int g = lane >> 2, tg = lane & 3;
-#pragma unroll
-      for (int u = 0; u < kTeamTiles / 2; ++u) {
-        int I, J;
-        team_tile(2 * u + warp, I, J);
-        if (I < KI && J < NJ) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int i = I * 16 + g + ((e >> 1) << 3);
-            const int j = J * 8 + 2 * tg + (e & 1);
-            if (i < k && j > i && j < m) s.pd[s.roff[i] + (j - i - 1)] = cacc[u][e];
-          }
-        }
-      }
-      __syncthreads();
-      const float vn = __uint_as_float((uint32_t)vaux), vq = __uint_as_float((uint32_t)(vaux >> 32));
-      for (int q = tid; q < np; q += TM) {
-        int i = 0;
-#pragma unroll
-        for (int w = 32; w > 0; w >>= 1)
-          if (i + w < k && s.roff[i + w] <= q) i += w;
-        const int j = i + 1 + (q - s.roff[i]);
-        const float gij = s.pd[q];
-        float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(s.rnrm[i], gij), __fsub_rn(s.rnrm[j], gij))
-                                  : __fsub_rn(1.0f, gij);
-        const int pa = s.rpos[i], pb = s.rpos[j];
-        const int lo = min(pa, pb), hi = max(pa, pb);
-        const float dva = key_dist(s.pkey[pa]), dvb = key_dist(s.pkey[pb]);
-        const float mx = fmaxf(dva, dvb);
-        bool fire = dab < mx;
-        if (!exact) {
-          const float tol = bf16_bound<METRIC>(dab, s.rnrm[i], s.rnrm[j], s.rdq[i], s.rdq[j], d) +
-                            fmaxf(bf16_bound<METRIC>(dva, vn, s.rnrm[i], vq, s.rdq[i], d),
-                                  bf16_bound<METRIC>(dvb, vn, s.rnrm[j], vq, s.rdq[j], d));
-          if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-            const float* xv = a.P.X + v * a.P.ld;
-            const float* xa = a.P.X + (int64_t)s.pid[pa] * a.P.ld;
-            const float* xb = a.P.X + (int64_t)s.pid[pb] * a.P.ld;
-            dab = row_dist<METRIC>(xa, xb, d);
-            fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
-            ++st_check;
-          }
-        }
-        s.pd[q] = dab;
-        if (fire) {
-          atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
-          if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
-            atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
-        }
-      }
-      __syncthreads();
-    }
 
-    // ---- prune: every thread replays the chain over the columns with fire bits -----------
-    uint64_t alive = valid;
-    int mykill = -1;
-    {
-      const unsigned c0 = __ballot_sync(0xffffffffu, has && s.fire[tid] != 0ull);
-      if (lane == 0) reinterpret_cast<uint32_t*>(&s.smask)[warp] = c0;
-      __syncthreads();
-      uint64_t cols = s.smask;
-      while (cols) {
-        const int b = __ffsll((long long)cols) - 1;
-        cols &= cols - 1;
-        const uint64_t cand = s.fire[b] & alive;
-        const uint64_t x = cand & s.closer[b];
+    // ---- prune: warp 0 replays the chain over the columns with fire bits -----------------
+    if (warp == 0) {
+      uint64_t cl = (uint64_t)__ballot_sync(0xffffffffu, lane < m && s.fire[lane] != 0ull) |
+                    ((uint64_t)__ballot_sync(0xffffffffu, lane + 32 < m && s.fire[lane + 32] != 0ull) << 32);
+      uint64_t alive = valid;
+      int b = cl ? __ffsll((long long)cl) - 1 : 0;
+      uint64_t fb = s.fire[b], cb = s.closer[b];
+      while (cl) {
+        cl &= cl - 1;
+        const int bn = cl ? __ffsll((long long)cl) - 1 : 0;
+        const uint64_t fn = s.fire[bn], cn = s.closer[bn];  // the next column, loaded early
+        const uint64_t cand = fb & alive;
+        const uint64_t x = cand & cb;
         uint64_t kill = cand;
-        if (x) {
+        if (x) {  // b meets a closer partner first: entries fired before it die, then b itself
           const int f = __ffsll((long long)x) - 1;
           kill = cand & bits_below(f);
           alive &= ~(1ull << b);
-          if (pi == b) mykill = f;
+          if (lane == 0) s.killer[b] = (uint8_t)f;
         }
         alive &= ~kill;
-        if (has && ((kill >> pi) & 1ull)) mykill = b;
+        if ((kill >> lane) & 1ull) s.killer[lane] = (uint8_t)b;
+        if ((kill >> (lane + 32)) & 1ull) s.killer[lane + 32] = (uint8_t)b;
+        b = bn;
+        fb = fn;
+        cb = cn;
       }
+      if (lane == 0) s.alive = alive;
     }
+    __syncthreads();
     // ---- emit ------------------------------------------------------------------------------
+    const uint64_t alive = s.alive;
     const bool surv = has && ((alive >> pi) & 1ull);
-    __syncthreads();
-    if (tid == 0) s.smask = 0ull;
-    __syncthreads();
-    if (surv) atomicOr(reinterpret_cast<unsigned long long*>(&s.smask), 1ull << tid);
+    const unsigned sb = __ballot_sync(0xffffffffu, surv);
+    if (lane == 0) s.sm32[warp] = sb;
     const int nkeep = __popcll(alive & valid);
     const int ndead = m - nkeep;
     if (a.emit_redirects && tid == 0 && ndead > 0) {
@@ -1787,15 +1813,16 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       s.red_avail = avail;
     }
     __syncthreads();
-    const uint64_t smask = s.smask;
+    const uint64_t smask = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);  // survivors by slot
     if (surv) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
     for (int t = nkeep + tid; t < R; t += TM) a.keys_out[v * R + t] = kEmpty;
     if (tid == 0) a.deg_out[v] = nkeep;
     if (a.emit_redirects && has && !surv) {
-      const int ri = s.prow[mykill], rj = row;
+      const int kp = s.killer[pi];
+      const int ri = s.prow[kp], rj = row;
       const int i = min(ri, rj), j = max(ri, rj);
       const float dd = s.pd[s.roff[i] + (j - i - 1)];
-      const int32_t tgt = s.pid[mykill];
+      const int32_t tgt = s.pid[kp];
       const int g = __popcll(~alive & valid & bits_below(pi));
       const unsigned long long sl =
           g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
@@ -1833,11 +1860,14 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
 
 template <int METRIC, int PREC>
 cudaError_t launch_join_team_t(const JoinArgs& a, cudaStream_t st, const char* name) {
-  const size_t smem = sizeof(TeamSmem<PREC>);
+  using C = TPrec<PREC>;
+  const int nchd = (a.P.d + TDC - 1) / TDC;
+  const size_t smem = kTeamRowsOff + (size_t)(nchd > 1 ? 2 : 1) * TM * C::RS * sizeof(typename C::T);
+  const size_t smem_max = kTeamRowsOff + (size_t)2 * TM * C::RS * sizeof(typename C::T);
   static bool attr_set = false;
   auto kern = rnd_join_team_kernel<METRIC, PREC>;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
