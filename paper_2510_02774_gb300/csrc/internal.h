@@ -18,11 +18,11 @@ struct Workspace {
   int32_t* count = nullptr;                // n proposals per target (zeroed per step)
   int64_t* off = nullptr;                  // n+1 exclusive prefix of count
   int64_t* bsum = nullptr;                 // scan block sums
-  int32_t* list = nullptr;                 // n vertices with a new entry
   uint8_t* active = nullptr;               // n flags: the vertex is in the list
-  uint64_t* rec = nullptr;                 // n work records of rec_w words, in list order
-  int rec_w = 0;
-  int32_t* list_n = nullptr;               // length of the list
+  uint64_t* rec[4] = {};                   // work records by pool-size class (entries <= 8,
+  int rec_w[4] = {};                       // <= 16, <= 32, more): n records of rec_w[c]
+  int rec_cap[4] = {};                     // words each, holding up to rec_cap[c] entries
+  int32_t* list_n = nullptr;               // [4] records per class
   unsigned long long* red_n = nullptr;     // number of redirects / reverse proposals
   int32_t* err = nullptr;                  // device status word (bounded waits)
   int64_t* round_new = nullptr;            // new entries written by the last merge

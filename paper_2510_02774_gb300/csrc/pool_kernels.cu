@@ -163,18 +163,26 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 }
 
 // =====================================================================================
-// prep: active flag and list of the vertices whose pool holds a new entry, and for each
-// of them a contiguous work record (in list order) that the join prefetches in bulk:
-//   word 0: v    word 1: m    words 2 .. 2+R: the pool keys    (BF16 form, aux != null)
-//   words 2+R .. 2+2R: per-entry (norm^2, residual) of the quantized row, word 2+2R: the
-//   same for v.  Also counts the entries of every pool (each one is proposed once,
-//   explicitly or in place).
+// prep: active flag of the vertices whose pool holds a new entry, and for each of them a
+// contiguous work record that the join prefetches in one piece.  Records go to one of four
+// regions by pool size (entries <= 8, <= 16, <= 32, more; everything to the last region
+// when the warp kernels cannot take the rows), so that a warp can take several small pools
+// at once.  A record of a region holding up to cap entries:
+//   word 0: v    word 1: m    words 2 .. 2+m: the pool keys
+//   (BF16 form) words 2+cap .. 2+cap+m: per entry (norm^2, residual) of the quantized row;
+//   word 2+2cap: the same for v.
+// Also counts the entries of every pool (each one is proposed once, explicitly or in place).
 // =====================================================================================
+struct RecSet {
+  uint64_t* rec[4];
+  int w[4];
+  int cap[4];
+};
+
 __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
                             int64_t n, int R, uint8_t* __restrict__ active,
-                            int32_t* __restrict__ list_n, int small_max,
-                            uint64_t* __restrict__ rec, int rec_w, const float2* __restrict__ aux,
-                            int64_t* __restrict__ stats) {
+                            int32_t* __restrict__ list_n, int warp_ok, RecSet rs,
+                            const float2* __restrict__ aux, int64_t* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
   long long props = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -188,40 +196,53 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
       for (int j = 0; j < m && !act; ++j) act = !(keys[v * R + j] & 1ull);
       active[v] = act ? 1 : 0;
     }
-    // small pools (warp kernel) take record positions from 0 up, larger ones from n - 1 down
-    const unsigned bs = __ballot_sync(0xffffffffu, act && m <= small_max);
-    const unsigned bl = __ballot_sync(0xffffffffu, act && m > small_max);
-    int offs = 0, offl = 0;
-    if (lane == 0 && bs) offs = atomicAdd(&list_n[0], __popc(bs));
-    if (lane == 0 && bl) offl = atomicAdd(&list_n[1], __popc(bl));
-    offs = __shfl_sync(0xffffffffu, offs, 0);
-    offl = __shfl_sync(0xffffffffu, offl, 0);
+    const int cls = !warp_ok ? 3 : (m <= 8 ? 0 : (m <= 16 ? 1 : (m <= 32 ? 2 : 3)));
+    unsigned bc[4];
+    int off[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      bc[c] = __ballot_sync(0xffffffffu, act && cls == c);
+      int o = 0;
+      if (lane == 0 && bc[c]) o = atomicAdd(&list_n[c], __popc(bc[c]));
+      off[c] = __shfl_sync(0xffffffffu, o, 0);
+    }
     // the warp writes the records of its active vertices, one after the other
-    unsigned left = bs | bl;
+    unsigned left = bc[0] | bc[1] | bc[2] | bc[3];
     while (left) {
       const int l = __ffs(left) - 1;
       left &= left - 1;
       const int64_t u = base + l;
       const int mu = __shfl_sync(0xffffffffu, m, l);
+      const int cu = __shfl_sync(0xffffffffu, cls, l);
       const unsigned below_l = (1u << l) - 1u;
-      const int64_t slotpos = ((bs >> l) & 1u) ? (int64_t)(offs + __popc(bs & below_l))
-                                               : n - 1 - (int64_t)(offl + __popc(bl & below_l));
-      uint64_t* r = rec + slotpos * rec_w;
+      unsigned bcu = bc[0];
+      int offu = off[0], W = rs.w[0], cap = rs.cap[0];
+      uint64_t* rg = rs.rec[0];
+#pragma unroll
+      for (int c = 1; c < 4; ++c)
+        if (cu == c) {
+          bcu = bc[c];
+          offu = off[c];
+          W = rs.w[c];
+          cap = rs.cap[c];
+          rg = rs.rec[c];
+        }
+      uint64_t* r = rg + (int64_t)(offu + __popc(bcu & below_l)) * W;
       if (lane == 0) {
         r[0] = (uint64_t)u;
         r[1] = (uint64_t)mu;
       }
-      for (int j = lane; j < R; j += 32) {
+      for (int j = lane; j < mu; j += 32) {
         const uint64_t k = keys[u * R + j];
         r[2 + j] = k;
         if (aux) {
-          const float2 q = j < mu ? aux[key_id(k)] : make_float2(0.0f, 0.0f);
-          r[2 + R + j] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
+          const float2 q = aux[key_id(k)];
+          r[2 + cap + j] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
         }
       }
       if (aux && lane == 0) {
         const float2 q = aux[u];
-        r[2 + 2 * R] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
+        r[2 + 2 * cap] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
       }
     }
   }
@@ -361,9 +382,10 @@ struct JoinArgs {
   int R;
   const uint64_t* keys_in;
   const int32_t* deg_in;
-  const int32_t* list_n;
-  const uint64_t* rec;   // work records in list order
-  int rec_w;             // words per record
+  const int32_t* list_n;    // records per pool-size class
+  const uint64_t* rec[4];   // work records by class (entries <= 8, <= 16, <= 32, more)
+  int rec_w[4];             // words per record
+  int rec_cap[4];           // entries a record holds (the last class: R)
   uint64_t seed;
   int t1, t2, order;
   uint64_t* keys_out;  // survivors (in place for the round, final graph for the last pass)
@@ -393,16 +415,16 @@ template <int PREC>
 __device__ __forceinline__ void join_prefetch(JoinSmem<PREC>& s, int64_t pos, int64_t end, const JoinArgs& a) {
   const int64_t cnt = min((int64_t)BV, end - pos);
   if (cnt <= 0) return;
-  const uint32_t bytes = (uint32_t)(cnt * a.rec_w * 8);
+  const uint32_t bytes = (uint32_t)(cnt * a.rec_w[3] * 8);
   mbar_expect_tx(&s.wbar, bytes);
-  bulk_g2s(s.window, a.rec + pos * a.rec_w, bytes, &s.wbar);
+  bulk_g2s(s.window, a.rec[3] + pos * a.rec_w[3], bytes, &s.wbar);
 }
 
 template <int PREC>
 __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t end,
                                uint32_t& wph, const JoinArgs& a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int R = a.R, W = a.rec_w;
+  const int R = a.R, W = a.rec_w[3];
   if (pos >= end) return 0;
   const bool ok = mbar_wait(&s.wbar, wph, kWaitLimit);
   wph ^= 1u;
@@ -675,11 +697,11 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
   JoinSmem<PREC>& s = *reinterpret_cast<JoinSmem<PREC>*>(smem_raw);
   using C = Prec<PREC>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // the pools of more than 32 entries: records at positions [n - cnt, n)
-  const int64_t cnt = a.list_n[1];
+  // the pools of the last size class: records [0, cnt) of that class
+  const int64_t cnt = a.list_n[3];
   const int64_t per = (cnt + gridDim.x - 1) / gridDim.x;
-  int64_t pos = a.n - cnt + (int64_t)blockIdx.x * per;
-  const int64_t end = min(a.n, pos + per);
+  int64_t pos = (int64_t)blockIdx.x * per;
+  const int64_t end = min(cnt, pos + per);
   if (pos >= end || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
   if (tid == 0) {
     mbar_init(&s.bar[0], 1);
@@ -1041,73 +1063,125 @@ cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name) 
 }  // namespace
 
 // =====================================================================================
-// rnd_join for pools of at most 32 entries: one warp per vertex, end to end, with no
-// block-wide barrier (the common case: every pool of the first round, most later ones).
-//
-//   order    warp bitonic sort of (h(seed,t1,t2,v,id), id) (or the key order) -> pi
+// rnd_join for pools of at most 32 entries: a warp takes one vertex of 17..32 entries,
+// two of 9..16 or four of at most 8 at a time (lane groups of VW = 32, 16 or 8 lanes),
+// end to end, with no block-wide barrier.
+//   order    bitonic sort of (h(seed,t1,t2,v,id), id) (or the key order) within each
+//            lane group -> pi
 //   gather   one bulk copy per row (lane p: the row of pi position p), new rows first,
-//            completing on the warp's own mbarrier; BF16 rows arrive in chunks of 64
-//            dimensions through two stages, FP32 rows (d <= 128) whole
-//   tile     BF16: up to 6 mma.sync m16n8k16 tiles, FP32 accumulators kept across chunks,
-//            the fire decision taken from the accumulators; FP32: one lane per pair, the
-//            canonical four-accumulator distance
-//   prune    every lane replays the mask chain (the data are broadcast), so each lane
-//            learns whether its entry survives and, if not, its absorber
+//            completing on the warp's own mbarrier, in chunks of 128 dimensions
+//   tile     BF16: mma.sync m16n8k16 tiles (six for one vertex, the four diagonal ones
+//            for lane groups), FP32 accumulators kept across chunks, fire decisions taken
+//            from the accumulators; FP32 (d <= 128): each group's lanes take its pairs
+//            one by one with the canonical four-accumulator distance
+//   prune    every lane replays its group's mask chain (the data are broadcast), so each
+//            lane learns whether its entry survives and, if not, its absorber
 //   emit     survivors in key order in place; redirects into per-warp slot chunks
 // =====================================================================================
 namespace {
 
-constexpr int WW = 4;    // warps per CTA
-constexpr int WM = 32;   // pool entries per warp-handled vertex at most
+constexpr int WW = 4;      // warps per CTA
+constexpr int WM = 32;     // pool entries a warp holds at a time
 constexpr int WRED = 256;  // redirect slots a warp reserves at a time
+constexpr int WDC = 128;   // dimensions per gathered chunk
 
 template <int PREC>
 struct WPrec;
 template <>
 struct WPrec<0> {
   using T = float;
-  static constexpr int DC = 128;  // whole rows (the path is used for d <= 128)
-  static constexpr int RS = DC + 4;
+  static constexpr int RS = WDC + 4;
   static constexpr int VEC = 4;
-  static constexpr int ST = 1;    // stages
 };
 template <>
 struct WPrec<1> {
   using T = __nv_bfloat16;
-  static constexpr int DC = 64;
-  static constexpr int RS = DC + 8;
+  static constexpr int RS = WDC + 8;
   static constexpr int VEC = 16;
-  static constexpr int ST = 2;
 };
 
 template <int PREC>
 struct __align__(16) WarpSlot {
-  typename WPrec<PREC>::T rows[WPrec<PREC>::ST][WM][WPrec<PREC>::RS];
-  float pd[WM * (WM - 1) / 2];
-  uint64_t pkey[WM];         // by pi position
+  typename WPrec<PREC>::T rows[WM][WPrec<PREC>::RS];  // by row: group base + local row
+  float pd[WM * (WM - 1) / 2];  // group g's pairs from g * VW (VW - 1) / 2
+  uint64_t pkey[WM];            // by position: group base + local pi position
   int32_t pid[WM];
-  uint32_t fire[WM], closer[WM];
-  float rnrm[WM], rdq[WM];   // BF16 form, by row
-  int32_t roff[WM];          // local pair index of the first pair of new row i
-  uint8_t rpos[WM], prow[WM];
-  uint64_t bar[WPrec<PREC>::ST];
+  uint32_t fire[WM], closer[WM];  // by position; bits: earlier local positions
+  float2 rnd[WM];               // by row: (squared norm of the BF16 row, recorded dist to v)
+  float rdq[WM];                // by row: norm of the quantization residual
+  int32_t roff[WM];             // by row: local index of the first pair of new row i
+  uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
+  int64_t gv[4];                // per group: vertex
+  float2 gq[4];                 // per group: (squared norm, residual) of v's BF16 row
+  int32_t gk[4], gm[4];         // per group: new entries, entries
+  uint64_t bar;
   unsigned long long red_next, red_end;
 };
 
 __device__ __forceinline__ uint32_t lanes_below32(int p) { return p == 0 ? 0u : (0xffffffffu >> (32 - p)); }
+__device__ __forceinline__ uint32_t low_bits32(int w) { return w >= 32 ? 0xffffffffu : ((1u << w) - 1u); }
+
+// One work item: the vertices of lane group lane / VW; class 2 items first (one vertex of
+// 17..32 entries), then class 1 (two of 9..16), then class 0 (four of at most 8).
+struct WItem {
+  int cls;
+  int m;
+  int64_t v;
+  uint64_t key, aux, vaux;
+};
+
+template <int PREC>
+__device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int64_t n2, int64_t n1, int lane,
+                                               WItem& x) {
+  int cls;
+  int64_t it;
+  if (w < n2) {
+    cls = 2;
+    it = w;
+  } else if (w < n2 + n1) {
+    cls = 1;
+    it = w - n2;
+  } else {
+    cls = 0;
+    it = w - n2 - n1;
+  }
+  const int lw = 3 + cls;  // log2 of the group width
+  const int g = lane >> lw, gl = lane & ((1 << lw) - 1);
+  const int64_t rr = it * (32 >> lw) + g;
+  x.cls = cls;
+  x.m = 0;
+  x.v = -1;
+  x.key = kEmpty;
+  x.aux = 0ull;
+  x.vaux = 0ull;
+  if (rr < (int64_t)a.list_n[cls]) {
+    const int cap = a.rec_cap[cls];
+    const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
+    x.v = (int64_t)r[0];
+    x.m = (int)r[1];
+    if (gl < x.m) {
+      x.key = r[2 + gl];
+      if (PREC == 1) x.aux = r[2 + cap + gl];
+    }
+    if (PREC == 1) x.vaux = r[2 + 2 * cap];
+  }
+}
 
 template <int METRIC, int PREC>
 __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using C = WPrec<PREC>;
+  using T = typename C::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSlot<PREC>& s = reinterpret_cast<WarpSlot<PREC>*>(smem_raw)[wid];
-  const int64_t cnt = a.list_n[0];
+  const int64_t n2 = a.list_n[2], n1 = (a.list_n[1] + 1) / 2, n0 = (a.list_n[0] + 3) / 4;
+  const int64_t items = n2 + n1 + n0;
   const int64_t gw = (int64_t)blockIdx.x * WW + wid, GW = (int64_t)gridDim.x * WW;
-  if (gw >= cnt || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
-  const int R = a.R, W = a.rec_w, d = a.P.d;
+  if (gw >= items || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
+  const int R = a.R, d = a.P.d;
+  const int nchd = (d + WDC - 1) / WDC;
   if (lane == 0) {
-    for (int t = 0; t < C::ST; ++t) mbar_init(&s.bar[t], 1);
+    mbar_init(&s.bar, 1);
     fence_mbar_init();
     s.red_next = s.red_end = 0;
   }
@@ -1118,51 +1192,41 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const float mxa = __uint_as_float(a.P.qflags[1]);
     exact = (fl == 0u) && ((double)d * (double)mxa * (double)mxa < 16777216.0);
   }
-  uint32_t phb = 0u, infl = 0u;  // mbarrier phase bit and copies-in-flight bit per stage
-  int stage = 0;
+  uint32_t phb = 0u;  // mbarrier phase
+  bool inflight = false;
   long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
 
-  // prefetch of the first record (registers; consumed one iteration later)
-  const uint64_t* r0 = a.rec + gw * W;
-  int64_t nv = (int64_t)r0[0];
-  int nm = (int)r0[1];
-  uint64_t nkey = lane < R ? r0[2 + lane] : kEmpty;
-  uint64_t naux = (PREC == 1 && lane < R) ? r0[2 + R + lane] : 0ull;
-  uint64_t nvaux = PREC == 1 ? r0[2 + 2 * R] : 0ull;
-
-  for (int64_t p = gw; p < cnt; p += GW) {
-    const int64_t v = nv;
-    const int m = nm;
-    const uint64_t keyl = lane < m ? nkey : kEmpty;
-    const uint64_t auxl = naux;
-    const uint64_t vaux = nvaux;
-    if (p + GW < cnt) {  // next record
-      const uint64_t* rn = a.rec + (p + GW) * W;
-      nv = (int64_t)rn[0];
-      nm = (int)rn[1];
-      nkey = lane < R ? rn[2 + lane] : kEmpty;
-      if (PREC == 1) {
-        naux = lane < R ? rn[2 + R + lane] : 0ull;
-        nvaux = rn[2 + 2 * R];
-      }
-    }
-    // ---- visit order: bitonic sort of (h, id, slot) over the 32 lanes ----------------------
+  WItem nx;
+  warp_item_load<PREC>(a, gw, n2, n1, lane, nx);
+  for (int64_t w = gw; w < items; w += GW) {
+    const WItem cur = nx;
+    if (w + GW < items) warp_item_load<PREC>(a, w + GW, n2, n1, lane, nx);
+    const int cls = cur.cls, lw = 3 + cls, VW = 1 << lw, G = 32 >> lw;
+    const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
+    const uint32_t gmask = low_bits32(VW);
+    const int m = cur.m;
+    const int64_t v = cur.v;
+    const uint64_t keyl = cur.key;
+    // ---- visit order: bitonic sort of (h, id, source lane) within each lane group ---------
     const uint32_t idl = key_id(keyl);
     uint64_t h = ~0ull;
     uint32_t hid = 0xffffffffu, hs = (uint32_t)lane;
-    if (lane < m)
+    if (gl < m) {
       h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v, (uint64_t)idl)
-          : (a.order == 1) ? (uint64_t)lane
-                           : (uint64_t)(m - 1 - lane);
-    if (lane < m) hid = idl;
+          : (a.order == 1) ? (uint64_t)gl
+                           : (uint64_t)(m - 1 - gl);
+      hid = idl;
+    }
 #pragma unroll
     for (int kk = 2; kk <= 32; kk <<= 1) {
+      if (kk > VW) break;
 #pragma unroll
       for (int jj = kk >> 1; jj > 0; jj >>= 1) {
         const uint64_t oh = __shfl_xor_sync(0xffffffffu, h, jj);
         const uint32_t oid = __shfl_xor_sync(0xffffffffu, hid, jj);
         const uint32_t os = __shfl_xor_sync(0xffffffffu, hs, jj);
-        const bool up = (lane & kk) == 0, lower = (lane & jj) == 0;
+        const bool up = (kk == VW) || ((lane & kk) == 0);
+        const bool lower = (lane & jj) == 0;
         const bool other_less = (oh < h) || (oh == h && oid < hid);
         const bool take = (lower == up) ? other_less : !other_less;
         if (take) {
@@ -1172,72 +1236,74 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
         }
       }
     }
-    // lane p now holds pi position p: its storage slot hs
-    const int slot = (int)hs;
-    const uint64_t key = __shfl_sync(0xffffffffu, keyl, slot & 31);
-    const uint64_t aux = __shfl_sync(0xffffffffu, auxl, slot & 31);
-    const bool valid_p = lane < m;
-    const uint32_t validm = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
-    const uint32_t newm = __ballot_sync(0xffffffffu, valid_p && !key_old(key));
+    // lane gb + p now holds local pi position p: its source lane hs (storage slot hs - gb)
+    const int slot = (int)hs - gb;
+    const uint64_t key = __shfl_sync(0xffffffffu, keyl, (int)hs);
+    const uint64_t aux = __shfl_sync(0xffffffffu, cur.aux, (int)hs);
+    const bool valid_p = gl < m;
+    const uint32_t validm = low_bits32(m);
+    const uint32_t newm = (__ballot_sync(0xffffffffu, valid_p && !key_old(key)) >> gb) & gmask;
     const int k = __popc(newm);
     const int np = k * (m - 1) - k * (k - 1) / 2;
-    const uint32_t below = lanes_below32(lane);
-    const int row = ((newm >> lane) & 1u) ? __popc(newm & below) : k + __popc(~newm & validm & below);
+    const uint32_t below = lanes_below32(gl);
+    const int row = ((newm >> gl) & 1u) ? __popc(newm & below) : k + __popc(~newm & validm & below);
     const int32_t id = (int32_t)key_id(key);
+    const int P = gb + gl;
     if (valid_p) {
-      s.pkey[lane] = key;
-      s.pid[lane] = id;
-      s.prow[lane] = (uint8_t)row;
-      s.rpos[row] = (uint8_t)lane;
-      s.fire[lane] = 0u;
-      s.closer[lane] = 0u;
-      if (row < k) s.roff[row] = row * (m - 1) - row * (row - 1) / 2;
-      if (PREC == 1) {
-        s.rnrm[row] = __uint_as_float((uint32_t)aux);
-        s.rdq[row] = __uint_as_float((uint32_t)(aux >> 32));
-      }
+      s.pkey[P] = key;
+      s.pid[P] = id;
+      s.prow[P] = (uint8_t)row;
+      s.rpos[gb + row] = (uint8_t)gl;
+      s.fire[P] = 0u;
+      s.closer[P] = 0u;
+      if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
+      s.rnd[gb + row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)aux) : 0.0f, key_dist(key));
+      if (PREC == 1) s.rdq[gb + row] = __uint_as_float((uint32_t)(aux >> 32));
+    }
+    if (gl == 0) {
+      s.gk[g] = k;
+      s.gm[g] = m;
+      s.gv[g] = v;
+      s.gq[g] = make_float2(__uint_as_float((uint32_t)cur.vaux), __uint_as_float((uint32_t)(cur.vaux >> 32)));
     }
     __syncwarp();
 
     // ---- gather + tile ---------------------------------------------------------------
-    const int nch = np > 0 ? (d + C::DC - 1) / C::DC : 0;
-    auto issue = [&](int c, int st) {
-      const int c0 = c * C::DC;
-      const int clen = min(C::DC, d - c0);
-      const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(typename C::T));
-      if (lane == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
-      infl |= 1u << st;
-      __syncwarp();
-      if (valid_p) {
-        const typename C::T* src =
-            (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)id * a.P.ld + c0)
-                        : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)id * a.P.ldb + c0);
-        bulk_g2s(&s.rows[st][row][0], src, bytes, &s.bar[st]);
-      }
-    };
+    const bool need = valid_p && np > 0;  // rows of groups with pairs only
+    const uint32_t needm = __ballot_sync(0xffffffffu, need);
+    const int nch = needm ? nchd : 0;
+    const int pdb = g * ((VW * (VW - 1)) >> 1);
     bool ok = true;
     float cacc[6][4];
-    if (nch > 0) issue(0, stage);
     for (int c = 0; c < nch; ++c) {
-      const int st = stage;
-      if (C::ST > 1 && c + 1 < nch) issue(c + 1, stage ^ 1);
-      ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
+      const int c0 = c * WDC;
+      const int clen = min(WDC, d - c0);
+      const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(T));
+      if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
+      inflight = true;
+      __syncwarp();
+      if (need) {
+        const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id * a.P.ld + c0)
+                                   : reinterpret_cast<const T*>(a.P.Xb + (int64_t)id * a.P.ldb + c0);
+        bulk_g2s(&s.rows[gb + row][0], src, bytes, &s.bar);
+      }
+      ok = mbar_wait(&s.bar, phb, kWaitLimit);
       if (!__all_sync(0xffffffffu, ok)) break;
-      phb ^= 1u << st;
-      infl &= ~(1u << st);
-      const int clen = min(C::DC, d - c * C::DC);
+      phb ^= 1u;
+      inflight = false;
       if (PREC == 1) {
-        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[st][0][0]);
+        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[0][0]);
         const int ksteps = (clen + 15) >> 4;
-        const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+        const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
-          // tiles (I, J): (0,0..3), (1,2), (1,3)
+          // tiles (I, J): (0,0..3), (1,2), (1,3); lane groups use the diagonal ones only
           const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
-          if (I < KI && J < NJ) {
+          const bool use = (VW == 32) ? (I < KI && J < NJ) : (t != 2 && t != 3);
+          if (use) {
             if (c == 0) cacc[t][0] = cacc[t][1] = cacc[t][2] = cacc[t][3] = 0.0f;
-            const int ra = min(I * 16 + (lane & 15), WM - 1);
+            const int ra = I * 16 + (lane & 15);
             const int rb = J * 8 + (lane & 7);
             const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
             const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
@@ -1250,16 +1316,16 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           }
         }
       } else {
-        const float* rows = reinterpret_cast<const float*>(&s.rows[st][0][0]);
+        const float* rows = reinterpret_cast<const float*>(&s.rows[0][0]);
         const int full4 = clen & ~3, rem = clen & 3;
-        for (int q = lane; q < np; q += 32) {
-          int i = 0;  // the new row owning pair q (rows of a vertex: at most 32)
+        for (int q = gl; q < np; q += VW) {
+          int i = 0;  // the new local row owning pair q
 #pragma unroll
-          for (int w = 16; w > 0; w >>= 1)
-            if (i + w < k && s.roff[i + w] <= q) i += w;
-          const int j = i + 1 + (q - s.roff[i]);
-          const float* ra = rows + i * C::RS;
-          const float* rb = rows + j * C::RS;
+          for (int w2 = 16; w2 > 0; w2 >>= 1)
+            if (i + w2 < k && s.roff[gb + i + w2] <= q) i += w2;
+          const int j = i + 1 + (q - s.roff[gb + i]);
+          const float* ra = rows + (gb + i) * C::RS;
+          const float* rb = rows + (gb + j) * C::RS;
           float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           for (int u = 0; u < full4; u += 4)
             dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
@@ -1268,64 +1334,68 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
             dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
                                mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
           const float dab = dist_finish4<METRIC>(acc);
-          s.pd[q] = dab;
-          const int pa = s.rpos[i], pb = s.rpos[j];
-          const int lo = min(pa, pb), hi = max(pa, pb);
-          if (dab < fmaxf(key_dist(s.pkey[pa]), key_dist(s.pkey[pb]))) {
-            atomicOr(&s.fire[hi], 1u << lo);
-            if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1)) atomicOr(&s.closer[hi], 1u << lo);
+          s.pd[pdb + q] = dab;
+          if (dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y)) {
+            const int pa = s.rpos[gb + i], pb = s.rpos[gb + j];
+            const int lo = min(pa, pb), hi = max(pa, pb);
+            atomicOr(&s.fire[gb + hi], 1u << lo);
+            if ((s.pkey[gb + lo] >> 1) < (s.pkey[gb + hi] >> 1)) atomicOr(&s.closer[gb + hi], 1u << lo);
           }
         }
       }
       __syncwarp();
-      stage ^= (C::ST > 1) ? 1 : 0;
     }
     if (!__all_sync(0xffffffffu, ok)) {  // a bounded wait gave up: report and stop the warp
       if (lane == 0) atomicExch(a.err, kErrTimeout);
-      for (int t = 0; t < C::ST; ++t)  // let this warp's copies in flight land
-        if ((infl >> t) & 1u) mbar_wait(&s.bar[t], (phb >> t) & 1u, kWaitLimit);
+      if (inflight) mbar_wait(&s.bar, phb, kWaitLimit);  // let this warp's copies land
       if (a.emit_redirects)
         for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
       return;
     }
     if (PREC == 1 && nch > 0) {  // D from the accumulators and the fire decision
       const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-      const int g = lane >> 2, tg = lane & 3;
+      const int g8 = lane >> 2, tg = lane & 3;
 #pragma unroll
       for (int t = 0; t < 6; ++t) {
         const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
-        if (I < KI && J < NJ) {
+        const bool use = (VW == 32) ? (I < KI && J < NJ) : (t != 2 && t != 3);
+        if (use) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int i = I * 16 + g + ((e >> 1) << 3);
+            const int i = I * 16 + g8 + ((e >> 1) << 3);  // rows of the warp's row space
             const int j = J * 8 + 2 * tg + (e & 1);
-            if (i < k && j > i && j < m) {
+            const int ge = i >> lw;  // the lane group both rows must belong to
+            if ((j >> lw) != ge) continue;
+            const int eb = ge << lw, li = i - eb, lj = j - eb;
+            const int ke = s.gk[ge], me = s.gm[ge];
+            if (li < ke && lj > li && lj < me) {
               const float gij = cacc[t][e];
-              float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(s.rnrm[i], gij), __fsub_rn(s.rnrm[j], gij))
+              const float2 ri = s.rnd[i], rj = s.rnd[j];
+              float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
                                         : __fsub_rn(1.0f, gij);
-              const int pa = s.rpos[i], pb = s.rpos[j];
-              const int lo = min(pa, pb), hi = max(pa, pb);
-              const float dva = key_dist(s.pkey[pa]), dvb = key_dist(s.pkey[pb]);
-              const float mx = fmaxf(dva, dvb);
+              const float mx = fmaxf(ri.y, rj.y);
               bool fire = dab < mx;
+              const int pa = s.rpos[i], pb = s.rpos[j];
               if (!exact) {
-                const float vn = __uint_as_float((uint32_t)vaux), vq = __uint_as_float((uint32_t)(vaux >> 32));
-                const float tol = bf16_bound<METRIC>(dab, s.rnrm[i], s.rnrm[j], s.rdq[i], s.rdq[j], d) +
-                                  fmaxf(bf16_bound<METRIC>(dva, vn, s.rnrm[i], vq, s.rdq[i], d),
-                                        bf16_bound<METRIC>(dvb, vn, s.rnrm[j], vq, s.rdq[j], d));
+                const float2 vq = s.gq[ge];
+                const float eqi = s.rdq[i], eqj = s.rdq[j];
+                const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d) +
+                                  fmaxf(bf16_bound<METRIC>(ri.y, vq.x, ri.x, vq.y, eqi, d),
+                                        bf16_bound<METRIC>(rj.y, vq.x, rj.x, vq.y, eqj, d));
                 if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-                  const float* xv = a.P.X + v * a.P.ld;
-                  const float* xa = a.P.X + (int64_t)s.pid[pa] * a.P.ld;
-                  const float* xb = a.P.X + (int64_t)s.pid[pb] * a.P.ld;
+                  const float* xv = a.P.X + s.gv[ge] * a.P.ld;
+                  const float* xa = a.P.X + (int64_t)s.pid[eb + pa] * a.P.ld;
+                  const float* xb = a.P.X + (int64_t)s.pid[eb + pb] * a.P.ld;
                   dab = row_dist<METRIC>(xa, xb, d);
                   fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
                   ++st_check;
                 }
               }
-              s.pd[s.roff[i] + (j - i - 1)] = dab;
+              s.pd[ge * ((VW * (VW - 1)) >> 1) + s.roff[i] + (lj - li - 1)] = dab;
               if (fire) {
-                atomicOr(&s.fire[hi], 1u << lo);
-                if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1)) atomicOr(&s.closer[hi], 1u << lo);
+                const int lo = min(pa, pb), hi = max(pa, pb);
+                atomicOr(&s.fire[eb + hi], 1u << lo);
+                if ((s.pkey[eb + lo] >> 1) < (s.pkey[eb + hi] >> 1)) atomicOr(&s.closer[eb + hi], 1u << lo);
               }
             }
           }
@@ -1334,63 +1404,76 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       __syncwarp();
     }
 
-    // ---- prune: every lane replays the chain over the columns that have fire bits ------
+    // ---- prune: every lane replays its group's chain over the columns with fire bits ----
     uint32_t alive = validm;
     int mykill = -1;
     {
-      uint32_t cols = __ballot_sync(0xffffffffu, valid_p && s.fire[lane] != 0u);
+      uint32_t cols = (__ballot_sync(0xffffffffu, valid_p && s.fire[P] != 0u) >> gb) & gmask;
       while (cols) {
         const int b = __ffs(cols) - 1;
         cols &= cols - 1;
-        const uint32_t cand = s.fire[b] & alive;
-        const uint32_t x = cand & s.closer[b];
+        const uint32_t cand = s.fire[gb + b] & alive;
+        const uint32_t x = cand & s.closer[gb + b];
         uint32_t kill = cand;
         if (x) {
           const int f = __ffs(x) - 1;
           kill = cand & lanes_below32(f);
           alive &= ~(1u << b);
-          if (lane == b) mykill = f;
+          if (gl == b) mykill = f;
         }
         alive &= ~kill;
-        if ((kill >> lane) & 1u) mykill = b;
+        if ((kill >> gl) & 1u) mykill = b;
       }
     }
+    __syncwarp();
     // ---- emit ----------------------------------------------------------------------------
-    const bool surv = valid_p && ((alive >> lane) & 1u);
-    const uint32_t smask = __reduce_or_sync(0xffffffffu, surv ? (1u << slot) : 0u);
+    const bool surv = valid_p && ((alive >> gl) & 1u);
+    const uint32_t smask = (__reduce_or_sync(0xffffffffu, surv ? (1u << hs) : 0u) >> gb) & gmask;
     const int nkeep = __popc(alive & validm);
-    if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
-    for (int t = nkeep + lane; t < R; t += 32) a.keys_out[v * R + t] = kEmpty;
-    if (lane == 0) a.deg_out[v] = nkeep;
+    if (m > 0) {
+      if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
+      for (int t = nkeep + gl; t < R; t += VW) a.keys_out[v * R + t] = kEmpty;
+      if (gl == 0) a.deg_out[v] = nkeep;
+    }
     const int ndead = m - nkeep;
-    if (a.emit_redirects && ndead > 0) {
-      // fill the warp's chunk to its end, then continue in a fresh one (ndead < WRED)
+    // redirects of all groups: one reservation per warp, groups in order
+    int pre = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int nd = __shfl_sync(0xffffffffu, ndead, (q << lw) & 31);
+      if (q < G) {
+        if (q < g) pre += nd;
+        tot += nd;
+      }
+    }
+    if (a.emit_redirects && tot > 0) {
+      // fill the warp's chunk to its end, then continue in a fresh one (tot < WRED)
       const unsigned long long base = s.red_next, end = s.red_end;
-      unsigned long long b1 = base, next = base + (unsigned long long)ndead;
-      int avail = ndead;
+      unsigned long long b1 = base, next = base + (unsigned long long)tot;
+      int avail = tot;
       if (next > end) {
         avail = (int)(end - base);
         unsigned long long nb2 = 0;
         if (lane == 0) nb2 = atomicAdd(a.red_n, (unsigned long long)WRED);
         b1 = __shfl_sync(0xffffffffu, nb2, 0);
-        next = b1 + (unsigned long long)(ndead - avail);
+        next = b1 + (unsigned long long)(tot - avail);
         if (lane == 0) s.red_end = b1 + WRED;
       }
       __syncwarp();
       if (lane == 0) s.red_next = next;
       if (valid_p && !surv) {
-        const int ri = s.prow[mykill], rj = row;
+        const int ri = s.prow[gb + mykill], rj = row;
         const int i = min(ri, rj), j = max(ri, rj);
-        const float dd = s.pd[s.roff[i] + (j - i - 1)];
-        const int32_t tgt = s.pid[mykill];
-        const int g = __popc(~alive & validm & below);
-        const unsigned long long sl = g < avail ? base + (unsigned long long)g : b1 + (unsigned long long)(g - avail);
+        const float dd = s.pd[pdb + s.roff[gb + i] + (j - i - 1)];
+        const int32_t tgt = s.pid[gb + mykill];
+        const int rk = pre + __popc(~alive & validm & below);
+        const unsigned long long sl = rk < avail ? base + (unsigned long long)rk : b1 + (unsigned long long)(rk - avail);
         a.red_tgt[sl] = tgt;
         a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
         atomicAdd(&a.count[tgt], 1);
       }
     }
-    if (lane == 0) {
+    if (gl == 0 && m > 0) {
       if (np > 0) {
         st_vert += 1;
         st_rows += m;
@@ -1403,16 +1486,20 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   if (a.emit_redirects)
     for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
   if (a.stats) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      st_vert += __shfl_xor_sync(0xffffffffu, st_vert, o);
+      st_rows += __shfl_xor_sync(0xffffffffu, st_rows, o);
+      st_pairs += __shfl_xor_sync(0xffffffffu, st_pairs, o);
+      st_fired += __shfl_xor_sync(0xffffffffu, st_fired, o);
+      st_check += __shfl_xor_sync(0xffffffffu, st_check, o);
+    }
     if (lane == 0) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)st_vert);
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
-    }
-    if (PREC == 1) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) st_check += __shfl_xor_sync(0xffffffffu, st_check, o);
-      if (lane == 0 && st_check)
+      if (PREC == 1 && st_check)
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[7]), (unsigned long long)st_check);
     }
   }
@@ -1438,6 +1525,7 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
 }
 
 }  // namespace
+
 
 // =====================================================================================
 // rnd_join for pools of 33..64 entries: a team of two warps (one 64-thread CTA) per
@@ -1514,11 +1602,10 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   TeamSmem& s = *reinterpret_cast<TeamSmem*>(smem_raw);
   T* const rowbase = reinterpret_cast<T*>(smem_raw + kTeamRowsOff);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t cnt = a.list_n[1];
-  const int64_t first = a.n - cnt;  // the team list sits at the top of the record array
-  int64_t p = first + blockIdx.x;
-  if (p >= a.n || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
-  const int R = a.R, W = a.rec_w, d = a.P.d;
+  const int64_t cnt = a.list_n[3];  // records of the last size class
+  int64_t p = blockIdx.x;
+  if (p >= cnt || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
+  const int R = a.R, W = a.rec_w[3], d = a.P.d;
   const int nchd = (d + TDC - 1) / TDC;  // chunks per row
   const int nst = nchd > 1 ? 2 : 1;      // stages
   if (tid == 0) {
@@ -1539,14 +1626,14 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   int stage = 0;
   long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
 
-  const uint64_t* r0 = a.rec + p * W;
+  const uint64_t* r0 = a.rec[3] + p * W;
   int64_t nv = (int64_t)r0[0];
   int nm = (int)r0[1];
-  uint64_t nkey = tid < R ? r0[2 + tid] : kEmpty;
-  uint64_t naux = (PREC == 1 && tid < R) ? r0[2 + R + tid] : 0ull;
+  uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
+  uint64_t naux = (PREC == 1 && tid < nm) ? r0[2 + R + tid] : 0ull;
   uint64_t nvaux = PREC == 1 ? r0[2 + 2 * R] : 0ull;
 
-  for (; p < a.n; p += gridDim.x) {
+  for (; p < cnt; p += gridDim.x) {
     const int64_t v = nv;
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
@@ -1555,13 +1642,13 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       vn = __uint_as_float((uint32_t)nvaux);
       vq = __uint_as_float((uint32_t)(nvaux >> 32));
     }
-    if (p + gridDim.x < a.n) {
-      const uint64_t* rn = a.rec + (p + gridDim.x) * W;
+    if (p + gridDim.x < cnt) {
+      const uint64_t* rn = a.rec[3] + (p + gridDim.x) * W;
       nv = (int64_t)rn[0];
       nm = (int)rn[1];
-      nkey = tid < R ? rn[2 + tid] : kEmpty;
+      nkey = tid < nm ? rn[2 + tid] : kEmpty;
       if (PREC == 1) {
-        naux = tid < R ? rn[2 + R + tid] : 0ull;
+        naux = tid < nm ? rn[2 + R + tid] : 0ull;
         nvaux = rn[2 + 2 * R];
       }
     }
@@ -2192,11 +2279,16 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
                      const PointsSet& P, int64_t* stats, cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>(ceil_div(ws.n, 256), (int64_t)sm_count() * 8);
   ProfScope ps("prep", st);
-  // FP32 rows of more than 128 dimensions do not fit the warp kernel's single stage
-  const int small_max = (P.precision == 0 && P.d > 128) ? 0 : 32;
-  prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n,
-                                                small_max, ws.rec, ws.rec_w,
-                                                P.precision == 1 ? P.aux : nullptr, stats);
+  // the warp kernels take FP32 rows of up to 128 dimensions (BF16 rows of any length)
+  const int warp_ok = (P.precision == 0 && P.d > 128) ? 0 : 1;
+  RecSet rs;
+  for (int c = 0; c < 4; ++c) {
+    rs.rec[c] = ws.rec[c];
+    rs.w[c] = ws.rec_w[c];
+    rs.cap[c] = ws.rec_cap[c];
+  }
+  prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
+                                                rs, P.precision == 1 ? P.aux : nullptr, stats);
   return cudaGetLastError();
 }
 
@@ -2217,8 +2309,11 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   a.keys_in = keys_in;
   a.deg_in = deg_in;
   a.list_n = ws.list_n;
-  a.rec = ws.rec;
-  a.rec_w = ws.rec_w;
+  for (int c = 0; c < 4; ++c) {
+    a.rec[c] = ws.rec[c];
+    a.rec_w[c] = ws.rec_w[c];
+    a.rec_cap[c] = ws.rec_cap[c];
+  }
   a.seed = seed;
   a.t1 = t1;
   a.t2 = t2;
@@ -2265,7 +2360,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;  // list_n and red_n
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;  // list_n and red_n
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, stats, st)) != cudaSuccess) return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out,
@@ -2291,7 +2386,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          const int32_t* deg_in, uint64_t seed, int t1, int order,
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, nullptr, st)) != cudaSuccess) return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, 0, order, ws, keys_out,
@@ -2361,7 +2456,7 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
                            int32_t* deg_out, int64_t* stats, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 16, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   {
     const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
@@ -2417,7 +2512,15 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }
 
 namespace {
-inline int rec_words(int R) { return (2 + 2 * R + 1 + 1) & ~1; }
+// work records of a size class holding up to cap entries: v, m, cap keys, cap (norm^2,
+// residual) pairs of the BF16 rows, the same pair for v
+inline int rec_cap_of(int R, int c) { return std::min(R, 8 << c); }
+inline int rec_words(int cap) { return (2 + 2 * cap + 1 + 1) & ~1; }
+inline size_t rec_bytes(int64_t n, int R) {
+  size_t b = 0;
+  for (int c = 0; c < 4; ++c) b += al256((size_t)n * rec_words(c == 3 ? R : rec_cap_of(R, c)) * 8);
+  return b;
+}
 // Redirect slots: a vertex loses at most m - 1 <= R - 1 entries (the one with the smallest
 // (dist, id) is never the farther side of a fired pair), and the units of each of the two
 // join kernels of a round fill their chunks completely before reserving the next, so each
@@ -2431,8 +2534,8 @@ size_t workspace_bytes(int64_t n, int R) {
   const size_t slots = red_slots(n, R);
   const size_t nb = (size_t)ceil_div(n, SCAN_TILE) + 1;
   return al256(slots * 4) + al256(slots * 8) + al256((size_t)n * R * 8) + al256((size_t)n * 4) +
-         al256(((size_t)n + 1) * 8) + al256(nb * 8) + al256((size_t)n * 4) + al256((size_t)n) +
-         al256((size_t)n * rec_words(R) * 8) + al256(16) + al256(4) + al256(8);
+         al256(((size_t)n + 1) * 8) + al256(nb * 8) + al256((size_t)n) + rec_bytes(n, R) + al256(24) +
+         al256(4) + al256(8);
 }
 
 bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) {
@@ -2455,16 +2558,17 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   p += al256(((size_t)n + 1) * 8);
   ws->bsum = reinterpret_cast<int64_t*>(p);
   p += al256(nb * 8);
-  ws->list = reinterpret_cast<int32_t*>(p);
-  p += al256((size_t)n * 4);
   ws->active = reinterpret_cast<uint8_t*>(p);
   p += al256((size_t)n);
-  ws->rec = reinterpret_cast<uint64_t*>(p);
-  ws->rec_w = rec_words(R);
-  p += al256((size_t)n * rec_words(R) * 8);
-  ws->list_n = reinterpret_cast<int32_t*>(p);  // [0] list length, then the redirect count
-  ws->red_n = reinterpret_cast<unsigned long long*>(p + 8);
-  p += al256(16);
+  for (int c = 0; c < 4; ++c) {
+    ws->rec_cap[c] = c == 3 ? R : rec_cap_of(R, c);
+    ws->rec_w[c] = rec_words(ws->rec_cap[c]);
+    ws->rec[c] = reinterpret_cast<uint64_t*>(p);
+    p += al256((size_t)n * ws->rec_w[c] * 8);
+  }
+  ws->list_n = reinterpret_cast<int32_t*>(p);  // [4] records per class, then the redirect count
+  ws->red_n = reinterpret_cast<unsigned long long*>(p + 16);
+  p += al256(24);
   ws->err = reinterpret_cast<int32_t*>(p);
   p += al256(4);
   ws->round_new = reinterpret_cast<int64_t*>(p);
