@@ -39,7 +39,7 @@ TRAFFIC = {"kernel": "rnd_join", "bytes_per_launch": None, "source_sha256": None
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (default: the full workload)")
