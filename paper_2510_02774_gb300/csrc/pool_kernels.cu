@@ -1104,13 +1104,14 @@ template <int PREC>
 struct __align__(16) WarpSlot {
   typename WPrec<PREC>::T rows[WM][WPrec<PREC>::RS];  // by row: group base + local row
   float pd[WM * (WM - 1) / 2];  // group g's pairs from g * VW (VW - 1) / 2
-  uint64_t pkey[WM];            // by position: group base + local pi position
-  int32_t pid[WM];
+  int32_t pid[WM];              // by position: group base + local pi position
   uint32_t fire[WM], closer[WM];  // by position; bits: earlier local positions
   float2 rnd[WM];               // by row: (squared norm of the BF16 row, recorded dist to v)
   float rdq[WM];                // by row: norm of the quantization residual
   int32_t roff[WM];             // by row: local index of the first pair of new row i
   uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
+  uint8_t inv[WM];              // by storage slot (group base + slot): local position
+  uint8_t F[WM][WM];            // F[p][q], q < p: pair (q, p) of a group fired (0 / 1)
   int64_t gv[4];                // per group: vertex
   float2 gq[4];                 // per group: (squared norm, residual) of v's BF16 row
   int32_t gk[4], gm[4];         // per group: new entries, entries
@@ -1194,7 +1195,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   }
   uint32_t phb = 0u;  // mbarrier phase
   bool inflight = false;
-  long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
+  int st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;  // per lane; summed at the end
 
   WItem nx;
   warp_item_load<PREC>(a, gw, n2, n1, lane, nx);
@@ -1250,12 +1251,10 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const int32_t id = (int32_t)key_id(key);
     const int P = gb + gl;
     if (valid_p) {
-      s.pkey[P] = key;
       s.pid[P] = id;
       s.prow[P] = (uint8_t)row;
       s.rpos[gb + row] = (uint8_t)gl;
-      s.fire[P] = 0u;
-      s.closer[P] = 0u;
+      s.inv[hs] = (uint8_t)gl;  // storage slot -> pi position
       if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
       s.rnd[gb + row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)aux) : 0.0f, key_dist(key));
       if (PREC == 1) s.rdq[gb + row] = __uint_as_float((uint32_t)(aux >> 32));
@@ -1267,6 +1266,21 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       s.gq[g] = make_float2(__uint_as_float((uint32_t)cur.vaux), __uint_as_float((uint32_t)(cur.vaux >> 32)));
     }
     __syncwarp();
+    // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
+    // closer mask of a position is the prefix OR, over the slots before its own, of the
+    // slots' position bits
+    uint32_t closer_p;
+    {
+      const uint32_t bit = gl < m ? (1u << s.inv[lane]) : 0u;  // this lane as storage slot
+      uint32_t x = bit;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        if (dd >= VW) break;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, dd, VW);
+        if (gl >= dd) x |= y;
+      }
+      closer_p = __shfl_sync(0xffffffffu, x ^ bit, (int)hs);
+    }
 
     // ---- gather + tile ---------------------------------------------------------------
     const bool need = valid_p && np > 0;  // rows of groups with pairs only
@@ -1274,7 +1288,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const int nch = needm ? nchd : 0;
     const int pdb = g * ((VW * (VW - 1)) >> 1);
     bool ok = true;
-    float cacc[6][4];
     for (int c = 0; c < nch; ++c) {
       const int c0 = c * WDC;
       const int clen = min(WDC, d - c0);
@@ -1293,26 +1306,84 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       phb ^= 1u;
       inflight = false;
       if (PREC == 1) {
+        // tiles one at a time; partial dot products wait in pd between chunks (d > 128),
+        // and the last chunk takes the fire decisions straight from the accumulators
         const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[0][0]);
         const int ksteps = (clen + 15) >> 4;
         const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
-#pragma unroll
+        const bool first_c = (c == 0), last_c = (c + 1 == nch);
+        const int g8 = lane >> 2, tg = lane & 3;
+        const int npg = (VW * (VW - 1)) >> 1;  // pairs per lane group
         for (int t = 0; t < 6; ++t) {
           // tiles (I, J): (0,0..3), (1,2), (1,3); lane groups use the diagonal ones only
           const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
           const bool use = (VW == 32) ? (I < KI && J < NJ) : (t != 2 && t != 3);
-          if (use) {
-            if (c == 0) cacc[t][0] = cacc[t][1] = cacc[t][2] = cacc[t][3] = 0.0f;
-            const int ra = I * 16 + (lane & 15);
-            const int rb = J * 8 + (lane & 7);
-            const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
-            const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
-            for (int ks = 0; ks < ksteps; ++ks) {
-              uint32_t fa[4], fb[2];
-              ldmatrix_x4(fa, pa + ks * 16);
-              ldmatrix_x2(fb, pb + ks * 16);
-              mma_bf16(cacc[t], fa, fb);
+          if (!use) continue;
+          // this lane's elements: rows i0, i0 + 8 of the warp's row space, columns j0, j0 + 1
+          const int i0 = I * 16 + g8, j0 = J * 8 + 2 * tg;
+          int q[4];
+          bool ve[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+            const int ge = i >> lw;  // the lane group both rows must belong to
+            const int eb = ge << lw, li = i - eb, lj = j - eb;
+            const int ke = (VW == 32) ? k : s.gk[ge], me = (VW == 32) ? m : s.gm[ge];
+            ve[e] = ((j >> lw) == ge) && li < ke && lj > li && lj < me;
+            q[e] = ve[e] ? ge * npg + s.roff[i] + (lj - li - 1) : 0;
+          }
+          float acc[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
+          const int ra = I * 16 + (lane & 15);
+          const int rb = J * 8 + (lane & 7);
+          const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
+          const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
+          for (int ks = 0; ks < ksteps; ++ks) {
+            uint32_t fa[4], fb[2];
+            ldmatrix_x4(fa, pa + ks * 16);
+            ldmatrix_x2(fb, pb + ks * 16);
+            mma_bf16(acc, fa, fb);
+          }
+          if (!last_c) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (ve[e]) s.pd[q[e]] = acc[e];
+            continue;
+          }
+          const float2 rI[2] = {s.rnd[i0], s.rnd[i0 + 8]};
+          const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
+          const int pI[2] = {s.rpos[i0], s.rpos[i0 + 8]};
+          const int pJ[2] = {s.rpos[j0], s.rpos[j0 + 1]};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (!ve[e]) continue;
+            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+            const int ge = i >> lw, eb = ge << lw;
+            const float gij = acc[e];
+            const float2 ri = rI[e >> 1], rj = rJ[e & 1];
+            float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
+                                      : __fsub_rn(1.0f, gij);
+            const float mx = fmaxf(ri.y, rj.y);
+            bool fire = dab < mx;
+            const int pa2 = pI[e >> 1], pb2 = pJ[e & 1];
+            if (!exact) {
+              const float2 vq = s.gq[ge];
+              const float eqi = s.rdq[i], eqj = s.rdq[j];
+              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d) +
+                                fmaxf(bf16_bound<METRIC>(ri.y, vq.x, ri.x, vq.y, eqi, d),
+                                      bf16_bound<METRIC>(rj.y, vq.x, rj.x, vq.y, eqj, d));
+              if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
+                const float* xv = a.P.X + s.gv[ge] * a.P.ld;
+                const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
+                const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
+                dab = row_dist<METRIC>(xa, xb, d);
+                fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
+                ++st_check;
+              }
             }
+            s.pd[q[e]] = dab;
+            s.F[eb + max(pa2, pb2)][min(pa2, pb2)] = fire ? 1 : 0;
           }
         }
       } else {
@@ -1335,12 +1406,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
                                mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
           const float dab = dist_finish4<METRIC>(acc);
           s.pd[pdb + q] = dab;
-          if (dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y)) {
-            const int pa = s.rpos[gb + i], pb = s.rpos[gb + j];
-            const int lo = min(pa, pb), hi = max(pa, pb);
-            atomicOr(&s.fire[gb + hi], 1u << lo);
-            if ((s.pkey[gb + lo] >> 1) < (s.pkey[gb + hi] >> 1)) atomicOr(&s.closer[gb + hi], 1u << lo);
-          }
+          const int pa = s.rpos[gb + i], pb = s.rpos[gb + j];
+          s.F[gb + max(pa, pb)][min(pa, pb)] = dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y) ? 1 : 0;
         }
       }
       __syncwarp();
@@ -1352,57 +1419,19 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
         for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
       return;
     }
-    if (PREC == 1 && nch > 0) {  // D from the accumulators and the fire decision
-      const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-      const int g8 = lane >> 2, tg = lane & 3;
-#pragma unroll
-      for (int t = 0; t < 6; ++t) {
-        const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
-        const bool use = (VW == 32) ? (I < KI && J < NJ) : (t != 2 && t != 3);
-        if (use) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int i = I * 16 + g8 + ((e >> 1) << 3);  // rows of the warp's row space
-            const int j = J * 8 + 2 * tg + (e & 1);
-            const int ge = i >> lw;  // the lane group both rows must belong to
-            if ((j >> lw) != ge) continue;
-            const int eb = ge << lw, li = i - eb, lj = j - eb;
-            const int ke = s.gk[ge], me = s.gm[ge];
-            if (li < ke && lj > li && lj < me) {
-              const float gij = cacc[t][e];
-              const float2 ri = s.rnd[i], rj = s.rnd[j];
-              float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
-                                        : __fsub_rn(1.0f, gij);
-              const float mx = fmaxf(ri.y, rj.y);
-              bool fire = dab < mx;
-              const int pa = s.rpos[i], pb = s.rpos[j];
-              if (!exact) {
-                const float2 vq = s.gq[ge];
-                const float eqi = s.rdq[i], eqj = s.rdq[j];
-                const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d) +
-                                  fmaxf(bf16_bound<METRIC>(ri.y, vq.x, ri.x, vq.y, eqi, d),
-                                        bf16_bound<METRIC>(rj.y, vq.x, rj.x, vq.y, eqj, d));
-                if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-                  const float* xv = a.P.X + s.gv[ge] * a.P.ld;
-                  const float* xa = a.P.X + (int64_t)s.pid[eb + pa] * a.P.ld;
-                  const float* xb = a.P.X + (int64_t)s.pid[eb + pb] * a.P.ld;
-                  dab = row_dist<METRIC>(xa, xb, d);
-                  fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
-                  ++st_check;
-                }
-              }
-              s.pd[ge * ((VW * (VW - 1)) >> 1) + s.roff[i] + (lj - li - 1)] = dab;
-              if (fire) {
-                const int lo = min(pa, pb), hi = max(pa, pb);
-                atomicOr(&s.fire[eb + hi], 1u << lo);
-                if ((s.pkey[eb + lo] >> 1) < (s.pkey[eb + hi] >> 1)) atomicOr(&s.closer[eb + hi], 1u << lo);
-              }
-            }
-          }
-        }
-      }
-      __syncwarp();
+    // fire masks: position p gathers the bytes F[p][0..p-1] of the pairs it closes
+    if (valid_p && nch > 0) {
+      uint32_t fm = 0u;
+      const uint32_t* fw = reinterpret_cast<const uint32_t*>(&s.F[P][0]);
+      // the low bit of each byte (bytes never written may hold anything), four bits per word
+      for (int w4 = 0; 4 * w4 < gl; ++w4) fm |= (((fw[w4] & 0x01010101u) * 0x10204080u) >> 28) << (4 * w4);
+      const bool isnew = (newm >> gl) & 1u;
+      s.fire[P] = fm & below & (isnew ? validm : newm);  // evaluated pairs only
+    } else if (valid_p) {
+      s.fire[P] = 0u;
     }
+    if (valid_p) s.closer[P] = closer_p;
+    __syncwarp();
 
     // ---- prune: every lane replays its group's chain over the columns with fire bits ----
     uint32_t alive = validm;
