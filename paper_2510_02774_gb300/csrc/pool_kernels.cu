@@ -1598,15 +1598,17 @@ struct __align__(16) TeamKey {
 
 struct __align__(16) TeamSmem {
   float pd[TM * (TM - 1) / 2];    // per pair: its distance (partial dot product between chunks)
-  TeamKey hk[TM];                 // order key by storage slot
-  uint64_t pkey[TM];              // pool key by pi position
+  union {
+    TeamKey hk[TM];               // order key by storage slot (visit order)
+    uint8_t F[TM][TM];            // F[p][q], q < p: pair (q, p) fired (0 / 1) (tile .. chain)
+  };
   uint64_t fire[TM], closer[TM];  // by pi position; bit a < b: pair (a, b) fired / a is closer
   float2 rnd[TM];                 // by row: (squared norm of the BF16 row, recorded dist to v)
   float rdq[TM];                  // by row: norm of the quantization residual
   int32_t pid[TM];                // by pi position
   int32_t roff[TM + 1];           // first pair index of new row i
   uint8_t rpos[TM], prow[TM], killer[TM];
-  uint64_t newm, alive;
+  uint64_t newm, alive, wtot;
   uint32_t sm32[2];
   uint64_t bar[2];
   unsigned long long red_next, red_end, red_b0, red_b1;
@@ -1707,7 +1709,18 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
       if (!key_old(keyl)) atomicOr(reinterpret_cast<unsigned long long*>(&s.newm), 1ull << pi);
     }
+    // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
+    // closer mask of a position is the OR of the position bits of the slots before its own
+    const uint64_t pbit = has ? (1ull << pi) : 0ull;
+    uint64_t pre = pbit;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
+      if (lane >= dd) pre |= y;
+    }
+    if (warp == 0 && lane == 31) s.wtot = pre;
     __syncthreads();
+    if (warp == 1) pre |= s.wtot;
     const uint64_t newm = s.newm;
     const int k = __popcll(newm);
     const int np = k * (m - 1) - k * (k - 1) / 2;
@@ -1716,12 +1729,10 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     if (has) {
       const uint64_t lo = bits_below(pi);
       row = ((newm >> pi) & 1ull) ? __popcll(newm & lo) : k + __popcll(~newm & valid & lo);
-      s.pkey[pi] = keyl;
       s.pid[pi] = (int32_t)idl;
       s.prow[pi] = (uint8_t)row;
       s.rpos[row] = (uint8_t)pi;
-      s.fire[pi] = 0ull;
-      s.closer[pi] = 0ull;
+      s.closer[pi] = pre ^ pbit;
       s.rnd[row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
       if (PREC == 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
     }
@@ -1825,13 +1836,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
               }
             }
             s.pd[q[e]] = dab;
-            if (fire) {
-              const int pa2 = s.rpos[i], pb2 = s.rpos[j];
-              const int lo = min(pa2, pb2), hi = max(pa2, pb2);
-              atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
-              if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
-                atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
-            }
+            const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+            s.F[max(pa2, pb2)][min(pa2, pb2)] = fire ? 1 : 0;
           }
         }
       } else {
@@ -1854,13 +1860,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
                                mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
           const float dab = dist_finish4<METRIC>(acc);
           s.pd[q] = dab;
-          if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y)) {
-            const int pa = s.rpos[i], pb = s.rpos[j];
-            const int lo = min(pa, pb), hi = max(pa, pb);
-            atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[hi]), 1ull << lo);
-            if ((s.pkey[lo] >> 1) < (s.pkey[hi] >> 1))
-              atomicOr(reinterpret_cast<unsigned long long*>(&s.closer[hi]), 1ull << lo);
-          }
+          const int pa = s.rpos[i], pb = s.rpos[j];
+          s.F[max(pa, pb)][min(pa, pb)] = dab < fmaxf(s.rnd[i].y, s.rnd[j].y) ? 1 : 0;
         }
       }
       __syncthreads();
@@ -1875,6 +1876,19 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       return;
     }
 
+    // fire masks: thread p gathers the bytes F[p][0..p-1] (the low bit of each: bytes that no
+    // pair wrote may hold anything) and keeps the pairs that were evaluated
+    if (tid < m) {
+      uint64_t fm = 0ull;
+      if (nch > 0) {
+        const uint32_t* fw = reinterpret_cast<const uint32_t*>(&s.F[tid][0]);
+        for (int w4 = 0; 4 * w4 < tid; ++w4)
+          fm |= (uint64_t)((((fw[w4] & 0x01010101u) * 0x10204080u) >> 28)) << (4 * w4);
+        fm &= bits_below(tid) & (((newm >> tid) & 1ull) ? valid : newm);
+      }
+      s.fire[tid] = fm;
+    }
+    __syncthreads();
     // ---- prune: warp 0 replays the chain over the columns with fire bits -----------------
     if (warp == 0) {
       uint64_t cl = (uint64_t)__ballot_sync(0xffffffffu, lane < m && s.fire[lane] != 0ull) |
