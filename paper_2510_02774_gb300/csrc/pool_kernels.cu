@@ -2136,46 +2136,6 @@ __global__ void scatter_kernel(const int32_t* __restrict__ tgt, const uint64_t* 
 }
 
 // ---- per-target select -----------------------------------------------------------------
-// idkey = (id << 33) | (ordered dist << 1) | old: sorting by it makes copies of one id
-// adjacent, smallest distance first.
-__device__ __forceinline__ uint64_t to_idkey(uint64_t k) {
-  if (k == kEmpty) return kEmpty;
-  return ((uint64_t)key_id(k) << 33) | ((k >> 32) << 1) | (k & 1ull);
-}
-__device__ __forceinline__ uint64_t from_idkey(uint64_t q) {
-  if (q == kEmpty) return kEmpty;
-  return (((q >> 1) & 0xFFFFFFFFull) << 32) | ((q >> 33) << 1) | (q & 1ull);
-}
-
-// Sort 32*E keys, keep one copy per id (smallest distance, old if any copy is old), and
-// sort the survivors by key; duplicates and padding end as kEmpty at the back.
-template <int E>
-__device__ __forceinline__ void select_pass(uint64_t (&x)[E], uint64_t* buf) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < E; ++j) x[j] = to_idkey(x[j]);
-  warp_sort_u64<E>(x);
-#pragma unroll
-  for (int j = 0; j < E; ++j) buf[j * 32 + lane] = x[j];
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int e = j * 32 + lane;
-    const uint64_t q = x[j];
-    if (q == kEmpty) continue;
-    const uint64_t id = q >> 33;
-    if (e > 0 && (buf[e - 1] >> 33) == id && buf[e - 1] != kEmpty) {
-      x[j] = kEmpty;  // a later copy of the same id
-      continue;
-    }
-    uint64_t old = q & 1ull;
-    for (int f = e + 1; f < 32 * E && buf[f] != kEmpty && (buf[f] >> 33) == id; ++f) old |= buf[f] & 1ull;
-    x[j] = from_idkey(q | old);
-  }
-  __syncwarp();
-  warp_sort_u64<E>(x);
-}
-
 // Inserts key b into a sorted, duplicate-free list (x0 holds elements 0..31 by lane, x1
 // elements 32..63) that keeps the R smallest keys: a copy of an id already listed keeps
 // the smaller key and the old bit of either copy.
@@ -2217,6 +2177,125 @@ __device__ __forceinline__ void list_insert(uint64_t& x0, uint64_t& x1, uint64_t
   if (lane + 32 >= R) x1 = kEmpty;
 }
 
+// Per-warp scratch of merge_chunk.
+struct __align__(16) MergeScratch {
+  uint64_t row[64];   // the row as it came in (by index), then its kept entries, compacted
+  uint64_t prop[32];  // the kept proposals, compacted
+  uint64_t out[96];   // the merged row by rank
+  uint32_t hid[128];  // hash of the row's ids (open addressing) ...
+  uint8_t hix[128];   // ... and their row indices
+  uint8_t rrm[64];    // row entry replaced by a nearer proposal
+  uint8_t rold[64];   // row entry kept, with the old bit of a proposal
+};
+
+__device__ __forceinline__ uint32_t id_slot(uint32_t id) { return (id * 0x9E3779B1u) >> 25; }
+
+// Merges up to 32 proposals (key b per lane, kEmpty for none) into the sorted, duplicate-free
+// row (x0: elements 0..31 by lane, x1: 32..63) that keeps the R smallest keys, under the
+// merge rule (one copy per id: the smaller key, old if any copy is old):
+//   proposals sorted; one copy per id among them (__match_any_sync); ids already in the row
+//   found through a small hash of the row's ids, the nearer copy kept; then every kept
+//   element's rank = its index in its own sorted list + the number of smaller keys in the
+//   other list (binary search), which places it in the merged row.
+__device__ __forceinline__ void merge_chunk(uint64_t& x0, uint64_t& x1, uint64_t b, int R, MergeScratch& ms) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t below = lane == 0 ? 0u : (0xffffffffu >> (32 - lane));
+  {
+    uint64_t t[1] = {b};
+    warp_sort_u64<1>(t);
+    b = t[0];
+  }
+  const bool hb = b != kEmpty;
+  const uint32_t idb = key_id(b);
+  const unsigned same = __match_any_sync(0xffffffffu, hb ? idb : 0xffffffffu);
+  const unsigned olds = __ballot_sync(0xffffffffu, hb && (b & 1ull));
+  bool keep = hb && lane == __ffs(same) - 1;  // sorted: the first copy is the nearest
+  if (keep && (olds & same)) b |= 1ull;
+  ms.row[lane] = x0;
+  ms.row[lane + 32] = x1;
+  ms.rrm[lane] = ms.rrm[lane + 32] = 0;
+  ms.rold[lane] = ms.rold[lane + 32] = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ms.hid[lane + 32 * q] = 0xffffffffu;
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // the row's ids are distinct: each insert finds a free slot
+    const uint64_t xk = h ? x1 : x0;
+    if (xk != kEmpty) {
+      const uint32_t id = key_id(xk);
+      uint32_t sl = id_slot(id);
+      for (int probe = 0; probe < 128; ++probe) {
+        if (atomicCAS(&ms.hid[sl], 0xffffffffu, id) == 0xffffffffu) {
+          ms.hix[sl] = (uint8_t)(lane + 32 * h);
+          break;
+        }
+        sl = (sl + 1) & 127u;
+      }
+    }
+  }
+  __syncwarp();
+  if (keep) {  // the id is listed already: the nearer copy stays, old if either is old
+    uint32_t sl = id_slot(idb);
+    for (int probe = 0; probe < 128; ++probe) {
+      const uint32_t h = ms.hid[sl];
+      if (h == idb) {
+        const int e = ms.hix[sl];
+        const uint64_t re = ms.row[e];
+        if ((b >> 1) < (re >> 1)) {
+          ms.rrm[e] = 1;
+          b |= re & 1ull;
+        } else {
+          keep = false;
+          if (b & 1ull) ms.rold[e] = 1;
+        }
+        break;
+      }
+      if (h == 0xffffffffu) break;
+      sl = (sl + 1) & 127u;
+    }
+  }
+  __syncwarp();
+  const bool k0 = x0 != kEmpty && !ms.rrm[lane], k1 = x1 != kEmpty && !ms.rrm[lane + 32];
+  if (ms.rold[lane]) x0 |= 1ull;
+  if (ms.rold[lane + 32]) x1 |= 1ull;
+  const unsigned kb = __ballot_sync(0xffffffffu, keep);
+  const unsigned r0 = __ballot_sync(0xffffffffu, k0), r1 = __ballot_sync(0xffffffffu, k1);
+  const int nb = __popc(kb), nr = __popc(r0) + __popc(r1);
+  const int ib = __popc(kb & below), i0 = __popc(r0 & below), i1 = __popc(r0) + __popc(r1 & below);
+  __syncwarp();
+  if (keep) ms.prop[ib] = b;
+  if (k0) ms.row[i0] = x0;
+  if (k1) ms.row[i1] = x1;
+  __syncwarp();
+  // rank = own index + number of smaller keys in the other list
+  if (keep) {
+    int lo = 0, hi = nr;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((ms.row[mid] >> 1) < (b >> 1)) lo = mid + 1; else hi = mid;
+    }
+    ms.out[ib + lo] = b;
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool kk = h ? k1 : k0;
+    if (kk) {
+      const uint64_t xk = h ? x1 : x0;
+      int lo = 0, hi = nb;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((ms.prop[mid] >> 1) < (xk >> 1)) lo = mid + 1; else hi = mid;
+      }
+      ms.out[(h ? i1 : i0) + lo] = xk;
+    }
+  }
+  __syncwarp();
+  const int tot = min(nb + nr, R);
+  x0 = lane < tot ? ms.out[lane] : kEmpty;
+  x1 = lane + 32 < tot ? ms.out[lane + 32] : kEmpty;
+  __syncwarp();
+}
+
 struct SelectArgs {
   int64_t n;
   int R;
@@ -2233,9 +2312,9 @@ struct SelectArgs {
 };
 
 __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
-  __shared__ uint64_t bufs[8][128];
+  __shared__ MergeScratch scratch[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint64_t* buf = bufs[warp];
+  MergeScratch& ms = scratch[warp];
   const int R = a.R;
   long long n_new = 0, n_in = 0;
   // in place (keys_out == keys_in): every row already holds the target's base pool
@@ -2256,27 +2335,18 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
     if (c == 0) {
       out0 = lane < na ? base[lane] : kEmpty;
       out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
-    } else if (c <= 32) {  // a few proposals: insert them one by one into the sorted row
+    } else if (c <= 4) {  // a few proposals: insert them one by one into the sorted row
       out0 = lane < na ? base[lane] : kEmpty;
       out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
       const uint64_t bl = lane < c ? a.bucket[b0 + lane] : kEmpty;
       for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
-    } else {
-      uint64_t x[4];
-      x[0] = lane < na ? base[lane] : kEmpty;
-      x[1] = lane + 32 < na ? base[32 + lane] : kEmpty;
-      for (int64_t done = 0; done < c; done += 64) {
-#pragma unroll
-        for (int j = 2; j < 4; ++j) {
-          const int64_t e = done + (j - 2) * 32 + lane;
-          x[j] = e < c ? a.bucket[b0 + e] : kEmpty;
-        }
-        select_pass<4>(x, buf);
-        if (lane + 32 >= R) x[1] = kEmpty;
-        if (lane >= R) x[0] = kEmpty;
+    } else {  // chunks of 32 proposals merged into the row
+      out0 = lane < na ? base[lane] : kEmpty;
+      out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+      for (int64_t done = 0; done < c; done += 32) {
+        const uint64_t bl = done + lane < c ? a.bucket[b0 + done + lane] : kEmpty;
+        merge_chunk(out0, out1, bl, R, ms);
       }
-      out0 = x[0];
-      out1 = x[1];
     }
     if (lane >= R) out0 = kEmpty;
     if (lane + 32 >= R) out1 = kEmpty;
