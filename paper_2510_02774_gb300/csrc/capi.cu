@@ -353,6 +353,31 @@ int grnnd_keys_to_graph(int64_t n, int32_t R, const uint64_t* keys, int32_t* ids
 // Whole build
 // ---------------------------------------------------------------------------------------
 
+namespace {
+// Pinned host slots for the per-round probe of the build driver (one pair per host thread;
+// released at thread exit).
+struct RoundProbe {
+  int64_t fresh;
+  int32_t err;
+  int32_t pad;
+};
+struct ProbeHolder {
+  RoundProbe* p = nullptr;
+  ~ProbeHolder() {
+    if (p) cudaFreeHost(p);
+  }
+};
+RoundProbe* round_probe() {
+  thread_local ProbeHolder h;
+  if (!h.p) {
+    void* q = nullptr;
+    if (cudaHostAlloc(&q, 2 * sizeof(RoundProbe), cudaHostAllocPortable) != cudaSuccess) return nullptr;
+    h.p = static_cast<RoundProbe*>(q);
+  }
+  return h.p;
+}
+}  // namespace
+
 int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
                    grnnd_graph** graph_out) {
   if (graph_out) *graph_out = nullptr;
@@ -437,21 +462,40 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   }
 
   GR_CU(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st));
+  // Each round's new-entry count and status word are copied to pinned host memory and read
+  // one round late, while the next round runs, so the GPU never waits for the host between
+  // rounds.  A round after one that left no new entry is an identity (no vertex is active),
+  // so stopping one round late gives the same pools.
+  RoundProbe* probe = round_probe();
+  if (!probe) return fail(GRNND_ENOMEM, "pinned host memory for the round probe");
+  cudaEvent_t rev[2] = {nullptr, nullptr};
+  for (int e = 0; e < 2; ++e) GR_CU(cudaEventCreateWithFlags(&rev[e], cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 2; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } ev_guard{rev};
   int64_t rounds = 0;
   for (int32_t t1 = 1; t1 <= p->T1; ++t1) {
+    int prev = -1;
     for (int32_t t2 = 1; t2 <= p->T2; ++t2) {
       // the round updates the pool in place: survivors are rewritten in their own row and
       // only rows that receive proposals are merged (the role of Sec 3.5's second buffer)
       GR_CU(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
                                 stats, st));
+      const int cur = (int)(rounds & 1);
       ++rounds;
-      int64_t fresh = 0;
-      int32_t rerr = 0;
-      GR_CU(cudaMemcpyAsync(&fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
-      GR_CU(cudaMemcpyAsync(&rerr, ws.err, 4, cudaMemcpyDeviceToHost, st));
-      GR_CU(cudaStreamSynchronize(st));
-      if (rerr) return fail(GRNND_ETIMEOUT, "a device-side wait of a round reached its iteration limit");
-      if (fresh == 0) break;  // no new entry anywhere: the remaining rounds are identities
+      GR_CU(cudaMemcpyAsync(&probe[cur].fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
+      GR_CU(cudaMemcpyAsync(&probe[cur].err, ws.err, 4, cudaMemcpyDeviceToHost, st));
+      GR_CU(cudaEventRecord(rev[cur], st));
+      if (prev >= 0) {  // the previous round's outcome, read while this one runs
+        GR_CU(cudaEventSynchronize(rev[prev]));
+        if (probe[prev].err) return fail(GRNND_ETIMEOUT, "a device-side wait of a round reached its iteration limit");
+        if (probe[prev].fresh == 0) break;  // no new entry anywhere: the rest are identities
+      }
+      prev = cur;
     }
     if (t1 != p->T1) {
       GR_CU(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolA, degA, nullptr, st));
