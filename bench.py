@@ -49,6 +49,10 @@ def _args():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16 (the last one is the headline)")
+    ap.add_argument("--report", choices=["precision"], default=None,
+                    help="precision: per-form distance error against FP64 and recall loss on a "
+                         "GIST-shaped (d=960, continuous) or DEEP-shaped (d=96, IP) set of --n points")
+    ap.add_argument("--shape", choices=["gist", "deep"], default="gist")
     return ap.parse_args()
 
 
@@ -173,9 +177,74 @@ def _source_sha():
         return hashlib.sha256(f.read()).hexdigest()
 
 
+def run_precision_report(args):
+    """Each form's distance error against FP64 and its recall loss, on continuous data.
+
+    Builds the graph of the same points with the FP32 form and the BF16 form, then:
+      * recall@10 of a beam-64 search of 1000 held-out queries against exact k-NN (GPU brute
+        force); the BF16 form's loss is FP32 recall - BF16 recall;
+      * the recorded distance of every edge against the FP64 distance recomputed on the host
+        (relative error |d_rec - d_64| / max(d_64, tiny)), and how many prune decisions the
+        BF16 form re-took in FP32."""
+    import numpy as np
+    import torch
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd, synth
+    n, nq, k, beam = args.n, 1000, 10, 64
+    if args.shape == "gist":
+        X, Q = synth.gist_like(n, nq, seed=args.seed)
+        metric, kw = grnnd.L2SQ, dict(S=32, R=64, T1=4, T2=15, rho=0.6, seed=args.seed)
+        shape = f"GIST1M-shaped synthetic: n={n}, d=960, 500-cluster mixture, per-dimension scales log-uniform in [0.1, 10]; S 32, R 64, T1 4, T2 15"
+    else:
+        X, Q = synth.deep_like(n, nq, seed=args.seed)
+        metric, kw = grnnd.IP, dict(S=16, R=32, T1=3, T2=10, rho=0.6, seed=args.seed)
+        shape = f"DEEP-shaped synthetic: n={n}, d=96, unit vectors, 50-cluster vMF-like mixture, inner product; S 16, R 32, T1 3, T2 10"
+    d = X.shape[1]
+    Xd = torch.from_numpy(X).cuda()
+    Xp, _ = grnnd.device_points(X)
+    Qp, _ = grnnd.device_points(Q)
+    gt, _ = grnnd.brute_knn(Xp, d, Qp, k, metric=metric)
+    gt = gt.cpu().numpy()
+    X64 = X.astype(np.float64)
+    out = {"report": "precision", "workload": shape, "queries": nq, "k": k, "beam": beam, "forms": {}}
+    for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16)):
+        g = grnnd.build(Xd, precision=prec, metric=metric, **kw)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        g2 = grnnd.build(Xd, precision=prec, metric=metric, **kw)
+        t1.record()
+        torch.cuda.synchronize()
+        found = g2.search(torch.from_numpy(Q).cuda(), k, beam).cpu().numpy()
+        rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(found, gt)]))
+        ids, dist, deg = g2.to_numpy()
+        rows = np.repeat(np.arange(n), deg)
+        cols = np.concatenate([ids[v, :deg[v]] for v in range(n)])
+        rec_d = np.concatenate([dist[v, :deg[v]] for v in range(n)]).astype(np.float64)
+        if metric == grnnd.L2SQ:
+            d64 = ((X64[rows] - X64[cols]) ** 2).sum(1)
+        else:
+            d64 = 1.0 - (X64[rows] * X64[cols]).sum(1)
+        rel = np.abs(rec_d - d64) / np.maximum(np.abs(d64), 1e-30)
+        st = g2.stats()
+        out["forms"][name] = {"build_ms": t0.elapsed_time(t1), "recall@10": rec, "edges": int(deg.sum()),
+                              "dist_rel_err_max": float(rel.max()), "dist_rel_err_mean": float(rel.mean()),
+                              "dist_rel_err_p99": float(np.quantile(rel, 0.99)),
+                              "rechecks": int(st["rechecks"]), "pair_distances": int(st["pair_distances"])}
+        del g, g2
+    out["bf16_recall_loss"] = out["forms"]["fp32"]["recall@10"] - out["forms"]["bf16"]["recall@10"]
+    out["bf16_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"]["bf16"]["build_ms"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist()
+    if args.report == "precision":
+        run_precision_report(args)
+        return
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist

@@ -864,15 +864,12 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
           bool fire = dab < mx;
           if (PREC == 1 && !exact) {
             const float tol =
-                bf16_bound<METRIC>(dab, B.rnrm[rb + i], B.rnrm[rb + j], B.rdq[rb + i], B.rdq[rb + j], a.P.d) +
-                fmaxf(bf16_bound<METRIC>(dva, B.vnrm[vb], B.rnrm[rb + i], B.vdq[vb], B.rdq[rb + i], a.P.d),
-                      bf16_bound<METRIC>(dvb, B.vnrm[vb], B.rnrm[rb + j], B.vdq[vb], B.rdq[rb + j], a.P.d));
-            if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-              const float* xv = a.P.X + B.v[vb] * a.P.ld;
+                bf16_bound<METRIC>(dab, B.rnrm[rb + i], B.rnrm[rb + j], B.rdq[rb + i], B.rdq[rb + j], a.P.d);
+            if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
               const float* xa = a.P.X + (int64_t)B.pid[rb + pa] * a.P.ld;
               const float* xb = a.P.X + (int64_t)B.pid[rb + pb] * a.P.ld;
               const float d_ab = row_dist<METRIC>(xa, xb, a.P.d);
-              fire = d_ab < fmaxf(row_dist<METRIC>(xv, xa, a.P.d), row_dist<METRIC>(xv, xb, a.P.d));
+              fire = d_ab < mx;
               s.pd[q] = d_ab;
               ++st_check;
             }
@@ -1370,15 +1367,12 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
             if (!exact) {
               const float2 vq = s.gq[ge];
               const float eqi = s.rdq[i], eqj = s.rdq[j];
-              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d) +
-                                fmaxf(bf16_bound<METRIC>(ri.y, vq.x, ri.x, vq.y, eqi, d),
-                                      bf16_bound<METRIC>(rj.y, vq.x, rj.x, vq.y, eqj, d));
-              if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-                const float* xv = a.P.X + s.gv[ge] * a.P.ld;
+              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
+              if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
                 const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
                 const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
                 dab = row_dist<METRIC>(xa, xb, d);
-                fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
+                fire = dab < mx;
                 ++st_check;
               }
             }
@@ -1823,15 +1817,12 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
             bool fire = dab < mx;
             if (!exact) {
               const float eqi = s.rdq[i], eqj = s.rdq[j];
-              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d) +
-                                fmaxf(bf16_bound<METRIC>(ri.y, vn, ri.x, vq, eqi, d),
-                                      bf16_bound<METRIC>(rj.y, vn, rj.x, vq, eqj, d));
-              if (fabsf(dab - mx) <= tol) {  // re-decide with canonical FP32 distances
-                const float* xv = a.P.X + v * a.P.ld;
+              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
+              if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
                 const float* xa = a.P.X + (int64_t)s.pid[s.rpos[i]] * a.P.ld;
                 const float* xb = a.P.X + (int64_t)s.pid[s.rpos[j]] * a.P.ld;
                 dab = row_dist<METRIC>(xa, xb, d);
-                fire = dab < fmaxf(row_dist<METRIC>(xv, xa, d), row_dist<METRIC>(xv, xb, d));
+                fire = dab < mx;
                 ++st_check;
               }
             }
