@@ -169,8 +169,7 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 // when the warp kernels cannot take the rows), so that a warp can take several small pools
 // at once.  A record of a region holding up to cap entries:
 //   word 0: v    word 1: m    words 2 .. 2+m: the pool keys
-//   (BF16 form) words 2+cap .. 2+cap+m: per entry (norm^2, residual) of the quantized row;
-//   word 2+2cap: the same for v.
+//   (BF16 form) words 2+cap .. 2+cap+m: per entry (norm^2, residual) of the quantized row.
 // Also counts the entries of every pool (each one is proposed once, explicitly or in place).
 // =====================================================================================
 struct RecSet {
@@ -240,10 +239,6 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
           r[2 + cap + j] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
         }
       }
-      if (aux && lane == 0) {
-        const float2 q = aux[u];
-        r[2 + 2 * cap] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
-      }
     }
   }
   if (stats) {
@@ -290,7 +285,7 @@ constexpr int SPW = 12;                        // FP32 tile: row segments per wa
 constexpr int BSEG = 288;                      // row segments per batch at most
 constexpr int BT = 64;                         // mma output tiles per batch at most
 constexpr int TPW = BT / JW;                   // mma tiles per warp
-constexpr int RECW_MAX = 2 + 2 * kMaxR + 2;    // work-record words (R = 64, BF16 form)
+constexpr int RECW_MAX = 2 + 2 * kMaxR;        // work-record words (R = 64, BF16 form)
 constexpr int RED_CHUNK = 1024;                // redirect slots reserved per CTA at a time
 
 // A row segment is up to 32 consecutive pairs (i, j0..j0+31) of one new row i: one warp
@@ -333,7 +328,6 @@ struct __align__(16) Batch {
   int64_t v[BV];
   int32_t m[BV], k[BV], np[BV];
   int32_t rowbase[BV + 1], pairbase[BV + 1], tilebase[BV + 1], segbase[BV + 1];
-  float vnrm[BV], vdq[BV];
   uint16_t tiles[BT];       // (vb << 8) | (I << 4) | J
   int nb, nent, ncopy, npairs, ntiles, nseg, nchunks;
 };
@@ -468,11 +462,6 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
         s.cnp[c] = k * (m - 1) - k * (k - 1) / 2;
         s.cnt_[c] = (PREC == 1) ? tiles_of(m, k) : 0;
         s.cns[c] = min(k, m - 1) + min(k, max(0, m - 33));
-        if (PREC == 1) {
-          const uint64_t q = r[2 + 2 * R];
-          B.vnrm[c] = __uint_as_float((uint32_t)q);  // read only when c is taken
-          B.vdq[c] = __uint_as_float((uint32_t)(q >> 32));
-        }
       }
     } else if (lane == 0) {
       s.cv[c] = -1;
@@ -1109,8 +1098,6 @@ struct __align__(16) WarpSlot {
   uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
   uint8_t inv[WM];              // by storage slot (group base + slot): local position
   uint8_t F[WM][WM];            // F[p][q], q < p: pair (q, p) of a group fired (0 / 1)
-  int64_t gv[4];                // per group: vertex
-  float2 gq[4];                 // per group: (squared norm, residual) of v's BF16 row
   int32_t gk[4], gm[4];         // per group: new entries, entries
   uint64_t bar;
   unsigned long long red_next, red_end;
@@ -1125,7 +1112,7 @@ struct WItem {
   int cls;
   int m;
   int64_t v;
-  uint64_t key, aux, vaux;
+  uint64_t key, aux;
 };
 
 template <int PREC>
@@ -1151,7 +1138,6 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
   x.v = -1;
   x.key = kEmpty;
   x.aux = 0ull;
-  x.vaux = 0ull;
   if (rr < (int64_t)a.list_n[cls]) {
     const int cap = a.rec_cap[cls];
     const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
@@ -1161,7 +1147,6 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
       x.key = r[2 + gl];
       if (PREC == 1) x.aux = r[2 + cap + gl];
     }
-    if (PREC == 1) x.vaux = r[2 + 2 * cap];
   }
 }
 
@@ -1259,8 +1244,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     if (gl == 0) {
       s.gk[g] = k;
       s.gm[g] = m;
-      s.gv[g] = v;
-      s.gq[g] = make_float2(__uint_as_float((uint32_t)cur.vaux), __uint_as_float((uint32_t)(cur.vaux >> 32)));
     }
     __syncwarp();
     // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
@@ -1365,7 +1348,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
             bool fire = dab < mx;
             const int pa2 = pI[e >> 1], pb2 = pJ[e & 1];
             if (!exact) {
-              const float2 vq = s.gq[ge];
               const float eqi = s.rdq[i], eqj = s.rdq[j];
               const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
               if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
@@ -1641,7 +1623,6 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   }
   __syncthreads();
   bool exact = false;
-  float vn = 0.0f, vq = 0.0f;
   if (PREC == 1) {
     const unsigned fl = a.P.qflags[0];
     const float mxa = __uint_as_float(a.P.qflags[1]);
@@ -1656,26 +1637,18 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   int nm = (int)r0[1];
   uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
   uint64_t naux = (PREC == 1 && tid < nm) ? r0[2 + R + tid] : 0ull;
-  uint64_t nvaux = PREC == 1 ? r0[2 + 2 * R] : 0ull;
 
   for (; p < cnt; p += gridDim.x) {
     const int64_t v = nv;
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
     const uint64_t auxl = naux;
-    if (PREC == 1) {
-      vn = __uint_as_float((uint32_t)nvaux);
-      vq = __uint_as_float((uint32_t)(nvaux >> 32));
-    }
     if (p + gridDim.x < cnt) {
       const uint64_t* rn = a.rec[3] + (p + gridDim.x) * W;
       nv = (int64_t)rn[0];
       nm = (int)rn[1];
       nkey = tid < nm ? rn[2 + tid] : kEmpty;
-      if (PREC == 1) {
-        naux = tid < nm ? rn[2 + R + tid] : 0ull;
-        nvaux = rn[2 + 2 * R];
-      }
+      if (PREC == 1) naux = tid < nm ? rn[2 + R + tid] : 0ull;
     }
     // ---- visit order: rank of (h, id) among the m entries --------------------------------
     const uint32_t idl = key_id(keyl);
@@ -2617,9 +2590,9 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 namespace {
 // work records of a size class holding up to cap entries: v, m, cap keys, cap (norm^2,
-// residual) pairs of the BF16 rows, the same pair for v
+// residual) pairs of the BF16 rows (an even number of words: 16-byte aligned records)
 inline int rec_cap_of(int R, int c) { return std::min(R, 8 << c); }
-inline int rec_words(int cap) { return (2 + 2 * cap + 1 + 1) & ~1; }
+inline int rec_words(int cap) { return 2 + 2 * cap; }
 inline size_t rec_bytes(int64_t n, int R) {
   size_t b = 0;
   for (int c = 0; c < 4; ++c) b += al256((size_t)n * rec_words(c == 3 ? R : rec_cap_of(R, c)) * 8);
