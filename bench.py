@@ -49,7 +49,7 @@ def _args():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16 (the last one is the headline)")
-    ap.add_argument("--report", choices=["precision"], default=None,
+    ap.add_argument("--report", choices=["precision", "ablation"], default=None,
                     help="precision: per-form distance error against FP64 and recall loss on a "
                          "GIST-shaped (d=960, continuous) or DEEP-shaped (d=96, IP) set of --n points")
     ap.add_argument("--shape", choices=["gist", "deep"], default="gist")
@@ -239,11 +239,70 @@ def run_precision_report(args):
     print(json.dumps(out), flush=True)
 
 
+def run_ablation_report(args):
+    """Sec 4.3-style ablations on the SIFT-shaped set (--n points, BF16 form): pair-visit order
+    (ascending / descending / random), reverse-sampling ratio rho, the T1 x T2 split, and the
+    search beam (queries per second against recall@10).  One JSON line per setting."""
+    import numpy as np
+    import torch
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd, synth
+    n, nq, k = args.n, 10000, 10
+    X, Q = synth.sift_like(n, nq, seed=args.seed)
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    Xp, _ = grnnd.device_points(X)
+    Qp, _ = grnnd.device_points(Q)
+    gt = grnnd.brute_knn(Xp, X.shape[1], Qp, k)[0].cpu().numpy()
+    base = dict(S=32, R=64, T1=4, T2=15, rho=0.6, seed=args.seed, order=grnnd.ORDER_RANDOM)
+
+    def recall(found):
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(found, gt)]))
+
+    def run(tag, **over):
+        kw = dict(base, **over)
+        grnnd.build(Xd, precision=grnnd.BF16, **kw)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g = grnnd.build(Xd, precision=grnnd.BF16, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ids, dist, deg = g.to_numpy()
+        line = {"report": "ablation", "sweep": tag, "n": n, **{k2: v for k2, v in kw.items() if k2 != "seed"},
+                "build_ms": e0.elapsed_time(e1), "points_per_s": n / (e0.elapsed_time(e1) / 1e3),
+                "recall@10_beam64": recall(g.search(Qd, k, 64).cpu().numpy()),
+                "mean_degree": float(deg.mean())}
+        print(json.dumps(line), flush=True)
+        return g
+
+    for name, o in (("ascending", grnnd.ORDER_ASC), ("descending", grnnd.ORDER_DESC), ("random", grnnd.ORDER_RANDOM)):
+        run("order:" + name, order=o)
+    for rho in (0.0, 0.3, 0.6, 0.9, 1.0):
+        run("rho", rho=rho)
+    for t1, t2 in ((1, 60), (2, 30), (3, 20), (4, 15), (6, 10), (10, 6)):
+        run("T1xT2", T1=t1, T2=t2)
+    g = run("beam-graph")
+    for beam in (10, 16, 24, 32, 48, 64, 96, 128, 192, 256):
+        g.search(Qd, k, beam)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        found = g.search(Qd, k, beam)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"report": "ablation", "sweep": "search_beam", "n": n, "queries": nq, "beam": beam,
+                          "qps": nq / (ms / 1e3), "recall@10": recall(found.cpu().numpy())}), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist()
     if args.report == "precision":
         run_precision_report(args)
+        return
+    if args.report == "ablation":
+        run_ablation_report(args)
         return
     if args.impl == "reference":
         if world > 1:
