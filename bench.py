@@ -49,7 +49,7 @@ def _args():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16 (the last one is the headline)")
-    ap.add_argument("--report", choices=["precision", "ablation"], default=None,
+    ap.add_argument("--report", choices=["precision", "ablation", "batched"], default=None,
                     help="precision: per-form distance error against FP64 and recall loss on a "
                          "GIST-shaped (d=960, continuous) or DEEP-shaped (d=96, IP) set of --n points")
     ap.add_argument("--shape", choices=["gist", "deep"], default="gist")
@@ -295,6 +295,66 @@ def run_ablation_report(args):
                           "qps": nq / (ms / 1e3), "recall@10": recall(found.cpu().numpy())}), flush=True)
 
 
+def run_batched_report(args):
+    """The batched form: 512 independent builds of n log-uniform in [1k, 50k] DEEP-shaped
+    unit vectors (d = 96, a 50-cluster mixture per build, inner product, BF16 tiles; S 16,
+    R 32, T1 3, T2 10) in one grnnd_build_batch pass, against the same builds one
+    grnnd_build_ex call after another.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd, synth
+    nbuild = 512
+    g = np.random.default_rng(args.seed)
+    sizes = np.exp(g.uniform(np.log(1000), np.log(50000), nbuild)).astype(np.int64)
+    parts = [synth.deep_like(int(m), 0, seed=1000 + b) for b, m in enumerate(sizes)]
+    X = torch.from_numpy(np.concatenate(parts)).cuda()
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    total = int(off[-1])
+    kw = dict(S=16, R=32, T1=3, T2=10, rho=0.6, seed=args.seed, metric=grnnd.IP, precision=grnnd.BF16)
+    del parts
+    # warm-up of both paths
+    grnnd.build_batch(X[: int(off[8])], off[:9], **kw)
+    grnnd.build(X[: int(off[1])], **kw)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        ts = []
+        out = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append((e0.elapsed_time(e1), (time.perf_counter() - t) * 1e3))
+            if reps > 1:
+                del out
+                out = None
+        return ts, out
+
+    tb, _ = timed(lambda: grnnd.build_batch(X, off, **kw), max(3, args.steps))
+    ts, _ = timed(lambda: [grnnd.build(X[int(off[b]):int(off[b + 1])], **kw) for b in range(nbuild)], 1)
+    # the same results both ways (a sample of builds)
+    gs = grnnd.build_batch(X, off, **kw)
+    same = True
+    for b in (0, 1, nbuild // 2, nbuild - 1):
+        one = grnnd.build(X[int(off[b]):int(off[b + 1])], **kw)
+        same &= bool((gs[b].to_numpy()[0] == one.to_numpy()[0]).all()) and gs[b].entry == one.entry
+    bms = sorted(t[1] for t in tb)
+    line = {"report": "batched", "workload": "512 builds, n log-uniform in [1000, 50000], DEEP-shaped d=96 unit "
+                                              "vectors (50-cluster mixture per build), IP, BF16; S 16, R 32, T1 3, T2 10",
+            "builds": nbuild, "points": total, "min_n": int(sizes.min()), "max_n": int(sizes.max()),
+            "batched_ms_p50": bms[len(bms) // 2], "batched_points_per_s": total / (bms[len(bms) // 2] / 1e3),
+            "batched_builds_per_s": nbuild / (bms[len(bms) // 2] / 1e3),
+            "sequential_ms": ts[0][1], "sequential_points_per_s": total / (ts[0][1] / 1e3),
+            "speedup": ts[0][1] / bms[len(bms) // 2], "same_graphs_sampled": same}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist()
@@ -303,6 +363,9 @@ def main():
         return
     if args.report == "ablation":
         run_ablation_report(args)
+        return
+    if args.report == "batched":
+        run_batched_report(args)
         return
     if args.impl == "reference":
         if world > 1:

@@ -106,6 +106,21 @@ GRNND_API int grnnd_build(const float *points, int64_t n, int32_t d, int32_t met
 GRNND_API int grnnd_build_ex(const float *points, int64_t n, int32_t d, const grnnd_params *p,
                    grnnd_graph **graph_out);
 
+/* Batched form (no counterpart in the paper, which builds one graph per call): nbuild
+ * independent builds in one pass.  Build b takes the rows points[offsets[b] ..
+ * offsets[b+1]) (d floats each, host or device memory, as for grnnd_build_ex) and gets
+ * graphs_out[b]: the graph grnnd_build_ex returns for those rows alone with the same
+ * params, ids local to the build.  Every build shares p.  Each round runs all builds in the
+ * same kernels (random draws and visit orders use ids local to each build); the pass runs
+ * all T1 x T2 rounds (a round after one that left no new entry is an identity, so the
+ * result is the same), is recorded as one CUDA graph and launched once on p->stream.  The
+ * graphs share one device allocation, released with the last of them (grnnd_free each).
+ * offsets: host int64[nbuild + 1], offsets[0] = 0, every build >= max(2, S + 1) points,
+ * total <= 2^31 - 2.  Graph stats hold the counters of the whole pass.  On failure every
+ * graphs_out[b] is NULL. */
+GRNND_API int grnnd_build_batch(const float *points, const int64_t *offsets, int32_t nbuild,
+                                int32_t d, const grnnd_params *p, grnnd_graph **graphs_out);
+
 /* Candidate-list search (Sec 4.2): best-first expansion from the entry point
  * (the point nearest the dataset mean) with a candidate list of `beam`
  * entries; stops when every listed candidate is expanded and writes the k

@@ -8,11 +8,23 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "grnnd.h"
 #include "internal.h"
+
+// Device memory of one build call; the graphs of a batched build share it, and it is freed
+// with the last of them.
+struct GraphBlock {
+  void* points = nullptr;
+  void* graph = nullptr;
+  ~GraphBlock() {
+    if (points) cudaFree(points);
+    if (graph) cudaFree(graph);
+  }
+};
 
 struct grnnd_graph {
   int64_t n = 0;
@@ -22,6 +34,7 @@ struct grnnd_graph {
   float* dists = nullptr;    // n x R
   int32_t* deg = nullptr;    // n
   int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::shared_ptr<GraphBlock> mem;
 };
 
 namespace {
@@ -110,6 +123,7 @@ thread_local Profiler g_prof;
 
 namespace grnnd {
 void set_last_error(const std::string& msg) { g_err = msg; }
+bool prof_on() { return g_prof.on; }
 
 void prof_start(const char* name, cudaStream_t st) {
   if (!g_prof.on) return;
@@ -378,24 +392,28 @@ RoundProbe* round_probe() {
 }
 }  // namespace
 
-int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
-                   grnnd_graph** graph_out) {
-  if (graph_out) *graph_out = nullptr;
-  if (!graph_out) return fail(GRNND_EINVAL, "graph_out is NULL");
+namespace {
+
+int check_params(const grnnd_params* p) {
   if (!p) return fail(GRNND_EINVAL, "params is NULL");
-  if (!points) return fail(GRNND_EINVAL, "points is NULL");
-  if (n < 2 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n must be in [2, 2^31 - 2]");
-  if (d < 1) return fail(GRNND_EINVAL, "d must be >= 1");
   int rc = check_R(p->R);
   if (rc) return rc;
-  if (p->S < 1 || p->S > p->R || (int64_t)p->S > n - 1)
-    return fail(GRNND_EINVAL, "need 1 <= S <= min(R, n-1)");
+  if (p->S < 1 || p->S > p->R) return fail(GRNND_EINVAL, "need 1 <= S <= R");
   if (p->T1 < 1 || p->T2 < 1) return fail(GRNND_EINVAL, "T1 and T2 must be >= 1");
   if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return fail(GRNND_EINVAL, "rho must be in [0, 1]");
   if (p->metric != GRNND_L2SQ && p->metric != GRNND_IP) return fail(GRNND_EINVAL, "unknown metric");
   if (p->order < 0 || p->order > 2) return fail(GRNND_EINVAL, "unknown order");
   if (p->precision != GRNND_FP32 && p->precision != GRNND_BF16)
     return fail(GRNND_EINVAL, "unknown precision");
+  return GRNND_OK;
+}
+
+// One build call over n points: a single build (offsets == nullptr) or nbuild independent
+// builds of the rows [offsets[b], offsets[b+1]) (ids local to each build, one graph each).
+// A batched call records the whole pass in one CUDA graph and launches it once.
+int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p, const int64_t* offsets,
+               int32_t nbuild, grnnd_graph** graphs_out) {
+  const bool batched = offsets != nullptr;
   const int32_t R = p->R, ld = round4(d);
   const bool bf16 = p->precision == GRNND_BF16;
   const int32_t ldb = (d + 15) & ~15;
@@ -405,20 +423,22 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   const size_t q_b = bf16 ? al256((size_t)n * ldb * 2) + al256((size_t)n * 8) + 256 : 0;
   const size_t pool_b = al256((size_t)n * R * 8), deg_b = al256((size_t)n * 4);
   const size_t ws_b = grnnd::workspace_bytes(n, R);
-  const size_t ent_b = grnnd::entry_workspace_bytes(n, d);
+  size_t ent_b = grnnd::entry_workspace_bytes(n, d);
   const size_t graph_b = al256((size_t)n * R * 4) * 2 + deg_b;
-  const size_t stats_b = 256;
-  const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b + q_b;
+  const size_t stats_b = 256 + al256((size_t)nbuild * 4);  // counters, then one entry per build
+  const size_t seg_b = batched ? al256((size_t)n * 8) : 0;
+  const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b + q_b + seg_b;
   if (p->hbm_budget && pts_b + graph_b + scratch_b > p->hbm_budget)
     return fail(GRNND_ENOMEM, "build needs " + std::to_string(pts_b + graph_b + scratch_b) +
                                   " bytes, above hbm_budget " + std::to_string(p->hbm_budget));
 
-  DevMem mpts, mgraph, mscratch;
-  GR_CU(mpts.alloc(pts_b));
-  GR_CU(mgraph.alloc(graph_b));
+  auto block = std::make_shared<GraphBlock>();
+  DevMem mscratch;
+  GR_CU(cudaMalloc(&block->points, pts_b));
+  GR_CU(cudaMalloc(&block->graph, graph_b));
   GR_CU(mscratch.alloc(scratch_b));
-  float* X = static_cast<float*>(mpts.p);
-  char* gp = static_cast<char*>(mgraph.p);
+  float* X = static_cast<float*>(block->points);
+  char* gp = static_cast<char*>(block->graph);
   int32_t* gids = reinterpret_cast<int32_t*>(gp);
   float* gd = reinterpret_cast<float*>(gp + al256((size_t)n * R * 4));
   int32_t* gdeg = reinterpret_cast<int32_t*>(gp + 2 * al256((size_t)n * R * 4));
@@ -428,15 +448,25 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   int32_t* degA = reinterpret_cast<int32_t*>(sp + 2 * pool_b);
   int32_t* degB = reinterpret_cast<int32_t*>(sp + 2 * pool_b + deg_b);
   int64_t* stats = reinterpret_cast<int64_t*>(sp + 2 * pool_b + 2 * deg_b);
+  int32_t* d_entry = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(stats) + 256);
   void* wsp = sp + 2 * pool_b + 2 * deg_b + stats_b;
   const size_t wsp_b = std::max(ws_b, ent_b);
   char* qp = sp + 2 * pool_b + 2 * deg_b + stats_b + al256(wsp_b);
+  int2* vseg = batched ? reinterpret_cast<int2*>(qp + q_b) : nullptr;
 
-  // points -> padded device rows
+  // points -> padded device rows; the segment of every vertex
   const cudaMemcpyKind kind = is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (ld != d) GR_CU(cudaMemsetAsync(X, 0, (size_t)n * ld * 4, st));
   GR_CU(cudaMemcpy2DAsync(X, (size_t)ld * 4, points, (size_t)d * 4, (size_t)d * 4, (size_t)n, kind, st));
-  GR_CU(cudaMemsetAsync(stats, 0, stats_b, st));
+  GR_CU(cudaMemsetAsync(stats, 0, 256, st));
+  std::vector<int2> hseg;
+  if (batched) {
+    hseg.resize((size_t)n);
+    for (int32_t b = 0; b < nbuild; ++b)
+      for (int64_t v = offsets[b]; v < offsets[b + 1]; ++v)
+        hseg[(size_t)v] = make_int2((int)offsets[b], (int)(offsets[b + 1] - offsets[b]));
+    GR_CU(cudaMemcpyAsync(vseg, hseg.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+  }
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(wsp, wsp_b, n, R, &ws)) return fail(GRNND_EINVAL, "internal workspace");
   GR_CU(cudaMemsetAsync(ws.err, 0, 4, st));
@@ -451,25 +481,61 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
   P.ld = ld;
   P.d = d;
   P.metric = p->metric;
+  P.vseg = vseg;
   if (bf16) {
     P.precision = 1;
     P.Xb = qp;
     P.ldb = ldb;
     P.aux = reinterpret_cast<const float2*>(qp + al256((size_t)n * ldb * 2));
     P.qflags = reinterpret_cast<const unsigned*>(qp + al256((size_t)n * ldb * 2) + al256((size_t)n * 8));
-    GR_CU(grnnd::launch_quantize(X, n, d, ld, qp, ldb, const_cast<float2*>(P.aux),
-                                 const_cast<unsigned*>(P.qflags), st));
   }
 
-  GR_CU(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st));
-  // Each round's new-entry count and status word are copied to pinned host memory and read
-  // one round late, while the next round runs, so the GPU never waits for the host between
-  // rounds.  A round after one that left no new entry is an identity (no vertex is active),
-  // so stopping one round late gives the same pools.
-  RoundProbe* probe = round_probe();
-  if (!probe) return fail(GRNND_ENOMEM, "pinned host memory for the round probe");
+  // A batched pass runs every round (a round after one that left no new entry is an
+  // identity) and is recorded as one CUDA graph; a single build reads each round's
+  // new-entry count one round late from pinned memory and stops after the first identity.
+  const bool capture = batched && !grnnd::prof_on();
+  GR_CU(grnnd::prepare_join_kernels(P));  // kernel set-up stays outside the capture
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cst = nullptr;  // the capture runs on a private stream (the caller's may be
+                               // the legacy default stream, which cannot be captured)
+  struct GraphGuard {
+    cudaGraph_t* g;
+    cudaGraphExec_t* x;
+    cudaStream_t* s;
+    ~GraphGuard() {
+      if (*x) cudaGraphExecDestroy(*x);
+      if (*g) cudaGraphDestroy(*g);
+      if (*s) cudaStreamDestroy(*s);
+    }
+  } graph_guard{&graph, &gexec, &cst};
+  const cudaStream_t user_st = st;
+  if (capture) {
+    GR_CU(cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking));
+    st = cst;
+    GR_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  }
+  auto end_capture = [&]() {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(st, &g);
+    if (g) cudaGraphDestroy(g);
+  };
+#define GR_CAP(call)                                                                           \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      if (capture) end_capture();                                                              \
+      cudaGetLastError();                                                                      \
+      return fail(GRNND_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    }                                                                                          \
+  } while (0)
+
+  if (bf16)
+    GR_CAP(grnnd::launch_quantize(X, n, d, ld, qp, ldb, const_cast<float2*>(P.aux),
+                                  const_cast<unsigned*>(P.qflags), st));
+  GR_CAP(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st, vseg));
+  RoundProbe* probe = nullptr;
   cudaEvent_t rev[2] = {nullptr, nullptr};
-  for (int e = 0; e < 2; ++e) GR_CU(cudaEventCreateWithFlags(&rev[e], cudaEventDisableTiming));
   struct EvGuard {
     cudaEvent_t* e;
     ~EvGuard() {
@@ -477,16 +543,22 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
         if (e[i]) cudaEventDestroy(e[i]);
     }
   } ev_guard{rev};
+  if (!capture) {
+    probe = round_probe();
+    if (!probe) return fail(GRNND_ENOMEM, "pinned host memory for the round probe");
+    for (int e = 0; e < 2; ++e) GR_CU(cudaEventCreateWithFlags(&rev[e], cudaEventDisableTiming));
+  }
   int64_t rounds = 0;
   for (int32_t t1 = 1; t1 <= p->T1; ++t1) {
     int prev = -1;
     for (int32_t t2 = 1; t2 <= p->T2; ++t2) {
       // the round updates the pool in place: survivors are rewritten in their own row and
       // only rows that receive proposals are merged (the role of Sec 3.5's second buffer)
-      GR_CU(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
-                                stats, st));
+      GR_CAP(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
+                                 stats, st));
       const int cur = (int)(rounds & 1);
       ++rounds;
+      if (capture) continue;
       GR_CU(cudaMemcpyAsync(&probe[cur].fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
       GR_CU(cudaMemcpyAsync(&probe[cur].err, ws.err, 4, cudaMemcpyDeviceToHost, st));
       GR_CU(cudaEventRecord(rev[cur], st));
@@ -498,52 +570,99 @@ int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params
       prev = cur;
     }
     if (t1 != p->T1) {
-      GR_CU(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolA, degA, nullptr, st));
+      GR_CAP(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolA, degA, nullptr, st));
     }
   }
   uint64_t* gkeys = poolA;
   int32_t* gdg = degA;
   if (p->final_prune) {
-    GR_CU(grnnd::launch_final(P, n, R, poolA, degA, p->seed, p->T1 + 1, p->order, ws, poolB, degB, st));
+    GR_CAP(grnnd::launch_final(P, n, R, poolA, degA, p->seed, p->T1 + 1, p->order, ws, poolB, degB, st));
     gkeys = poolB;
     gdg = degB;
   }
-  GR_CU(grnnd::launch_keys_to_graph(n, R, gkeys, gids, gd, nullptr, st));
-  GR_CU(cudaMemcpyAsync(gdeg, gdg, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
-  int32_t h_err = 0;
-  GR_CU(cudaMemcpyAsync(&h_err, ws.err, 4, cudaMemcpyDeviceToHost, st));
-  // the entry workspace reuses the (now idle) round workspace
-  int32_t* d_entry = reinterpret_cast<int32_t*>(stats + 16);
-  GR_CU(grnnd::launch_entry(X, n, d, ld, p->metric, d_entry, wsp, wsp_b, st));
-  int32_t h_entry = 0;
-  int64_t h_stats[8];
-  GR_CU(cudaMemcpyAsync(&h_entry, d_entry, 4, cudaMemcpyDeviceToHost, st));
-  GR_CU(cudaMemcpyAsync(h_stats, stats, 64, cudaMemcpyDeviceToHost, st));
+  GR_CAP(grnnd::launch_keys_to_graph(n, R, gkeys, gids, gd, nullptr, st));
+  if (batched) GR_CAP(grnnd::launch_localize_ids(n, R, gids, vseg, st));
+  GR_CAP(cudaMemcpyAsync(gdeg, gdg, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+  // the entry workspace reuses the (now idle) round workspace; the round status word
+  // moves to the stats block first
+  GR_CAP(cudaMemcpyAsync(stats + 8, ws.err, 4, cudaMemcpyDeviceToDevice, st));
+  for (int32_t b = 0; b < nbuild; ++b) {
+    const int64_t lo = batched ? offsets[b] : 0, nb = batched ? offsets[b + 1] - offsets[b] : n;
+    GR_CAP(grnnd::launch_entry(X + lo * ld, nb, d, ld, p->metric, d_entry + b, wsp, wsp_b, st));
+  }
+#undef GR_CAP
+  if (capture) {
+    GR_CU(cudaStreamEndCapture(st, &graph));
+    st = user_st;
+    GR_CU(cudaGraphInstantiate(&gexec, graph, 0));
+    GR_CU(cudaGraphLaunch(gexec, st));
+  }
+  std::vector<int32_t> h_entry((size_t)nbuild);
+  int64_t h_stats[9];
+  GR_CU(cudaMemcpyAsync(h_entry.data(), d_entry, (size_t)nbuild * 4, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaMemcpyAsync(h_stats, stats, 72, cudaMemcpyDeviceToHost, st));
   GR_CU(cudaStreamSynchronize(st));
-  if (h_err) return fail(GRNND_ETIMEOUT, "a device-side wait reached its iteration limit");
+  if ((int32_t)h_stats[8]) return fail(GRNND_ETIMEOUT, "a device-side wait reached its iteration limit");
 
-  grnnd_graph* g = new grnnd_graph();
-  g->n = n;
-  g->d = d;
-  g->ld = ld;
-  g->R = R;
-  g->metric = p->metric;
-  g->entry = h_entry;
-  g->points = static_cast<float*>(mpts.release());
-  char* gbase = static_cast<char*>(mgraph.release());
-  g->ids = reinterpret_cast<int32_t*>(gbase);
-  g->dists = reinterpret_cast<float*>(gbase + al256((size_t)n * R * 4));
-  g->deg = reinterpret_cast<int32_t*>(gbase + 2 * al256((size_t)n * R * 4));
-  g->stats[0] = rounds;
-  g->stats[1] = h_stats[0];
-  g->stats[2] = h_stats[1];
-  g->stats[3] = h_stats[2];
-  g->stats[4] = h_stats[3];
-  g->stats[5] = h_stats[4];
-  g->stats[6] = h_stats[6];
-  g->stats[7] = h_stats[7];
-  *graph_out = g;
+  for (int32_t b = 0; b < nbuild; ++b) {
+    const int64_t lo = batched ? offsets[b] : 0, nb = batched ? offsets[b + 1] - offsets[b] : n;
+    grnnd_graph* g = new grnnd_graph();
+    g->n = nb;
+    g->d = d;
+    g->ld = ld;
+    g->R = R;
+    g->metric = p->metric;
+    g->entry = h_entry[(size_t)b];
+    g->points = X + lo * ld;
+    g->ids = gids + lo * R;
+    g->dists = gd + lo * R;
+    g->deg = gdeg + lo;
+    g->stats[0] = rounds;  // a batched call reports the counters of the whole pass
+    g->stats[1] = h_stats[0];
+    g->stats[2] = h_stats[1];
+    g->stats[3] = h_stats[2];
+    g->stats[4] = h_stats[3];
+    g->stats[5] = h_stats[4];
+    g->stats[6] = h_stats[6];
+    g->stats[7] = h_stats[7];
+    g->mem = block;
+    graphs_out[b] = g;
+  }
   return GRNND_OK;
+}
+
+}  // namespace
+
+int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
+                   grnnd_graph** graph_out) {
+  if (graph_out) *graph_out = nullptr;
+  if (!graph_out) return fail(GRNND_EINVAL, "graph_out is NULL");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!points) return fail(GRNND_EINVAL, "points is NULL");
+  if (n < 2 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n must be in [2, 2^31 - 2]");
+  if (d < 1) return fail(GRNND_EINVAL, "d must be >= 1");
+  if ((int64_t)p->S > n - 1) return fail(GRNND_EINVAL, "need 1 <= S <= min(R, n-1)");
+  return build_core(points, n, d, p, nullptr, 1, graph_out);
+}
+
+int grnnd_build_batch(const float* points, const int64_t* offsets, int32_t nbuild, int32_t d,
+                      const grnnd_params* p, grnnd_graph** graphs_out) {
+  if (!graphs_out) return fail(GRNND_EINVAL, "graphs_out is NULL");
+  if (nbuild < 1) return fail(GRNND_EINVAL, "need nbuild >= 1");
+  for (int32_t b = 0; b < nbuild; ++b) graphs_out[b] = nullptr;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!points || !offsets) return fail(GRNND_EINVAL, "points/offsets is NULL");
+  if (d < 1) return fail(GRNND_EINVAL, "d must be >= 1");
+  if (offsets[0] != 0) return fail(GRNND_EINVAL, "offsets[0] must be 0");
+  for (int32_t b = 0; b < nbuild; ++b) {
+    const int64_t nb = offsets[b + 1] - offsets[b];
+    if (nb < 2) return fail(GRNND_EINVAL, "every build needs >= 2 points");
+    if ((int64_t)p->S > nb - 1) return fail(GRNND_EINVAL, "need S <= (points of every build) - 1");
+  }
+  if (offsets[nbuild] > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "total points must be <= 2^31 - 2");
+  return build_core(points, offsets[nbuild], d, p, offsets, nbuild, graphs_out);
 }
 
 int grnnd_build(const float* points, int64_t n, int32_t d, int32_t metric, int32_t S, int32_t R,
@@ -621,10 +740,7 @@ int grnnd_graph_stats(const grnnd_graph* g, int64_t* out, int32_t count) {
 }
 
 void grnnd_free(grnnd_graph* g) {
-  if (!g) return;
-  cudaFree(g->points);
-  cudaFree(g->ids);  // ids, dists and deg share one allocation
-  delete g;
+  delete g;  // the device memory goes with the last graph that shares it
 }
 
 }  // extern "C"

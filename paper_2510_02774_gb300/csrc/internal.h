@@ -38,16 +38,27 @@ struct PointsSet {
   const float2* aux = nullptr;
   const unsigned* qflags = nullptr;
   int d = 0, metric = 0, precision = 0;
+  // Batched builds: per vertex (first id, number of points) of the build it belongs to;
+  // null for one build.  Random draws and visit orders use ids local to the build.
+  const int2* vseg = nullptr;
 };
 
 size_t workspace_bytes(int64_t n, int R);
 bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws);
 
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
-                             uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st);
+                             uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st,
+                             const int2* vseg = nullptr);
+
+// Batched builds: subtracts each row's build base from its ids (-1 stays -1).
+cudaError_t launch_localize_ids(int64_t n, int R, int32_t* ids, const int2* vseg, cudaStream_t st);
 
 cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xb, int ldb,
                             float2* aux, unsigned* qflags, cudaStream_t st);
+
+// One-time launch set-up of the join kernels that points P will use (shared-memory opt-in,
+// occupancy); launches inside a stream capture rely on it having run.
+cudaError_t prepare_join_kernels(const PointsSet& P);
 
 // One round of Alg 4: prep + rnd_join + scan + scatter + select (keys_out != keys_in).
 cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
@@ -94,6 +105,7 @@ void set_last_error(const std::string& msg);
 
 // Per-kernel event profiler of the calling thread (no-ops unless enabled).
 void prof_start(const char* name, cudaStream_t st);
+bool prof_on();  // the per-kernel event profiler is recording
 void prof_stop(cudaStream_t st);
 
 struct ProfScope {

@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include <mutex>
 
 namespace grnnd {
 
@@ -21,6 +22,40 @@ namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int64_t kMaxJoinGrid = 2048;  // CTAs of the join at most (sizes the redirect slack)
+
+// Per-kernel launch set-up kept out of stream captures: the dynamic shared-memory opt-in
+// (once) and the resident blocks per SM (cached per shared-memory size).  Shared by host
+// threads, so guarded by a mutex.
+struct KernelSetup {
+  bool attr = false;
+  size_t smem[2] = {0, 0};
+  int per_sm[2] = {0, 0};
+};
+std::mutex g_setup_mu;
+
+template <typename K>
+cudaError_t setup_kernel(KernelSetup& ks, K kern, int threads, size_t smem_max, size_t smem, int* per_sm) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!ks.attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    if (e != cudaSuccess) return e;
+    ks.attr = true;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (ks.per_sm[i] > 0 && ks.smem[i] == smem) {
+      *per_sm = ks.per_sm[i];
+      return cudaSuccess;
+    }
+  int v = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (v < 1) v = 1;
+  const int slot = ks.per_sm[0] == 0 ? 0 : 1;
+  ks.smem[slot] = smem;
+  ks.per_sm[slot] = v;
+  *per_sm = v;
+  return cudaSuccess;
+}
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -52,18 +87,22 @@ template <int METRIC>
 __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__ X, int64_t n,
                                                         int d, int ld, int S, int R, uint64_t seed,
                                                         uint64_t* __restrict__ keys,
-                                                        int32_t* __restrict__ deg) {
+                                                        int32_t* __restrict__ deg,
+                                                        const int2* __restrict__ vseg) {
   __shared__ int32_t acc_ids[8][kMaxR];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* acc = acc_ids[warp];
-  const uint64_t nm1 = (uint64_t)(n - 1);
   const unsigned below = lanemask_lt();
   for (int64_t v = (int64_t)blockIdx.x * 8 + warp; v < n; v += (int64_t)gridDim.x * 8) {
+    // the vertex's build: ids [lo, lo + nb); draws use the local id v - lo
+    const int64_t lo = vseg ? vseg[v].x : 0;
+    const uint64_t nm1 = (uint64_t)((vseg ? (int64_t)vseg[v].y : n) - 1);
+    const uint64_t vl = (uint64_t)(v - lo);
     int cnt = 0;
-    // S <= n - 1, so the draws cover enough distinct ids long before the bound.
+    // S <= nb - 1, so the draws cover enough distinct ids long before the bound.
     for (uint64_t base = 0; cnt < S && base < (1ull << 32); base += 32) {
-      const uint64_t r = counter_hash(seed, 0, 0, (uint64_t)v, base + lane) % nm1;
-      const int32_t u = (int32_t)(r + (r >= (uint64_t)v ? 1u : 0u));
+      const uint64_t r = counter_hash(seed, 0, 0, vl, base + lane) % nm1;
+      const int32_t u = (int32_t)(lo + (int64_t)(r + (r >= vl ? 1u : 0u)));
       bool dup = false;
       for (int j = 0; j < cnt; ++j) dup |= (acc[j] == u);
       const unsigned same = __match_any_sync(0xffffffffu, u);
@@ -97,13 +136,28 @@ __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__
 }
 
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
-                             uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st) {
+                             uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st,
+                             const int2* vseg) {
   const int64_t blocks = std::min<int64_t>(ceil_div(n, 8), (int64_t)sm_count() * 16);
   ProfScope ps("rnd_init", st);
   if (metric == 0)
-    rnd_init_kernel<0><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg);
+    rnd_init_kernel<0><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
   else
-    rnd_init_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg);
+    rnd_init_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
+  return cudaGetLastError();
+}
+
+__global__ void localize_ids_kernel(int64_t n, int R, int32_t* __restrict__ ids, const int2* __restrict__ vseg) {
+  const int64_t total = n * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = ids[i];
+    if (u >= 0) ids[i] = u - vseg[i / R].x;
+  }
+}
+
+cudaError_t launch_localize_ids(int64_t n, int R, int32_t* ids, const int2* vseg, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 8);
+  localize_ids_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, R, ids, vseg);
   return cudaGetLastError();
 }
 
@@ -168,7 +222,7 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 // regions by pool size (entries <= 8, <= 16, <= 32, more; everything to the last region
 // when the warp kernels cannot take the rows), so that a warp can take several small pools
 // at once.  A record of a region holding up to cap entries:
-//   word 0: v    word 1: m    words 2 .. 2+m: the pool keys
+//   word 0: v | (first id of v's build) << 32    word 1: m    words 2 .. 2+m: the pool keys
 //   (BF16 form) words 2+cap .. 2+cap+m: per entry (norm^2, residual) of the quantized row.
 // Also counts the entries of every pool (each one is proposed once, explicitly or in place).
 // =====================================================================================
@@ -181,7 +235,8 @@ struct RecSet {
 __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
                             int64_t n, int R, uint8_t* __restrict__ active,
                             int32_t* __restrict__ list_n, int warp_ok, RecSet rs,
-                            const float2* __restrict__ aux, int64_t* __restrict__ stats) {
+                            const float2* __restrict__ aux, const int2* __restrict__ vseg,
+                            int64_t* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
   long long props = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -228,7 +283,7 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
         }
       uint64_t* r = rg + (int64_t)(offu + __popc(bcu & below_l)) * W;
       if (lane == 0) {
-        r[0] = (uint64_t)u;
+        r[0] = (uint64_t)u | ((uint64_t)(vseg ? vseg[u].x : 0) << 32);
         r[1] = (uint64_t)mu;
       }
       for (int j = lane; j < mu; j += 32) {
@@ -430,6 +485,7 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
   uint64_t kx[2][2];
   float2 ax[2][2];
   int64_t vx[2];
+  uint32_t lox[2];  // first id of the vertex's build (visit orders use local ids)
   int mx[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -440,9 +496,10 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
     kx[h][0] = kx[h][1] = kEmpty;
     if (p < end) {
       const uint64_t* r = s.window + c * W;
-      const int64_t v = (int64_t)r[0];
+      const int64_t v = (int64_t)(r[0] & 0xffffffffull);
       const int m = (int)r[1];
       vx[h] = v;
+      lox[h] = (uint32_t)(r[0] >> 32);
       mx[h] = m;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -529,8 +586,8 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
     for (int j = 0; j < 2; ++j) {
       const int e = j * 32 + lane;
       id[j] = key_id(kx[h][j]);
-      hk[j] = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v,
-                                              (uint64_t)id[j])
+      hk[j] = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)(v - lox[h]),
+                                              (uint64_t)(id[j] - lox[h]))
               : (a.order == 1) ? (uint64_t)e
                                : (uint64_t)(m - 1 - e);
     }
@@ -1027,17 +1084,13 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
 }
 
 template <int METRIC, int PREC>
-cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name) {
+cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name, bool setup_only = false) {
   const size_t smem = sizeof(JoinSmem<PREC>);
-  static bool attr_set = false;
+  static KernelSetup ks;
   auto kern = rnd_join_kernel<METRIC, PREC>;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JT, smem);
+  cudaError_t e = setup_kernel(ks, kern, JT, smem, smem, &per_sm);
+  if (e != cudaSuccess || setup_only) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t blocks = std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(a.n, 1), (int64_t)sm_count() * per_sm),
                                             kMaxJoinGrid);
@@ -1111,6 +1164,7 @@ __device__ __forceinline__ uint32_t low_bits32(int w) { return w >= 32 ? 0xfffff
 struct WItem {
   int cls;
   int m;
+  uint32_t lo;  // first id of the vertex's build
   int64_t v;
   uint64_t key, aux;
 };
@@ -1135,13 +1189,15 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
   const int64_t rr = it * (32 >> lw) + g;
   x.cls = cls;
   x.m = 0;
+  x.lo = 0u;
   x.v = -1;
   x.key = kEmpty;
   x.aux = 0ull;
   if (rr < (int64_t)a.list_n[cls]) {
     const int cap = a.rec_cap[cls];
     const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
-    x.v = (int64_t)r[0];
+    x.v = (int64_t)(r[0] & 0xffffffffull);
+    x.lo = (uint32_t)(r[0] >> 32);
     x.m = (int)r[1];
     if (gl < x.m) {
       x.key = r[2 + gl];
@@ -1195,7 +1251,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     uint64_t h = ~0ull;
     uint32_t hid = 0xffffffffu, hs = (uint32_t)lane;
     if (gl < m) {
-      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v, (uint64_t)idl)
+      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)(v - cur.lo),
+                                          (uint64_t)(idl - cur.lo))
           : (a.order == 1) ? (uint64_t)gl
                            : (uint64_t)(m - 1 - gl);
       hid = idl;
@@ -1511,17 +1568,13 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
 }
 
 template <int METRIC, int PREC>
-cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* name) {
+cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* name, bool setup_only = false) {
   const size_t smem = sizeof(WarpSlot<PREC>) * WW;
-  static bool attr_set = false;
+  static KernelSetup ks;
   auto kern = rnd_join_warp_kernel<METRIC, PREC>;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WW * 32, smem);
+  cudaError_t e = setup_kernel(ks, kern, WW * 32, smem, smem, &per_sm);
+  if (e != cudaSuccess || setup_only) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
   ProfScope ps(name, st);
@@ -1633,19 +1686,22 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   long long st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;
 
   const uint64_t* r0 = a.rec[3] + p * W;
-  int64_t nv = (int64_t)r0[0];
+  int64_t nv = (int64_t)(r0[0] & 0xffffffffull);
+  uint32_t nlo = (uint32_t)(r0[0] >> 32);
   int nm = (int)r0[1];
   uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
   uint64_t naux = (PREC == 1 && tid < nm) ? r0[2 + R + tid] : 0ull;
 
   for (; p < cnt; p += gridDim.x) {
     const int64_t v = nv;
+    const uint32_t lo = nlo;  // first id of the vertex's build
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
     const uint64_t auxl = naux;
     if (p + gridDim.x < cnt) {
       const uint64_t* rn = a.rec[3] + (p + gridDim.x) * W;
-      nv = (int64_t)rn[0];
+      nv = (int64_t)(rn[0] & 0xffffffffull);
+      nlo = (uint32_t)(rn[0] >> 32);
       nm = (int)rn[1];
       nkey = tid < nm ? rn[2 + tid] : kEmpty;
       if (PREC == 1) naux = tid < nm ? rn[2 + R + tid] : 0ull;
@@ -1655,7 +1711,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     const bool has = tid < m;
     uint64_t h = ~0ull;
     if (has)
-      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)v, (uint64_t)idl)
+      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)(v - lo),
+                                          (uint64_t)(idl - lo))
           : (a.order == 1) ? (uint64_t)tid
                            : (uint64_t)(m - 1 - tid);
     {
@@ -1953,20 +2010,16 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
 }
 
 template <int METRIC, int PREC>
-cudaError_t launch_join_team_t(const JoinArgs& a, cudaStream_t st, const char* name) {
+cudaError_t launch_join_team_t(const JoinArgs& a, cudaStream_t st, const char* name, bool setup_only = false) {
   using C = TPrec<PREC>;
   const int nchd = (a.P.d + TDC - 1) / TDC;
   const size_t smem = kTeamRowsOff + (size_t)(nchd > 1 ? 2 : 1) * TM * C::RS * sizeof(typename C::T);
   const size_t smem_max = kTeamRowsOff + (size_t)2 * TM * C::RS * sizeof(typename C::T);
-  static bool attr_set = false;
+  static KernelSetup ks;
   auto kern = rnd_join_team_kernel<METRIC, PREC>;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TM, smem);
+  cudaError_t e = setup_kernel(ks, kern, TM, smem_max, smem, &per_sm);
+  if (e != cudaSuccess || setup_only) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
   ProfScope ps(name, st);
@@ -2365,7 +2418,7 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
     rs.cap[c] = ws.rec_cap[c];
   }
   prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
-                                                rs, P.precision == 1 ? P.aux : nullptr, stats);
+                                                rs, P.precision == 1 ? P.aux : nullptr, P.vseg, stats);
   return cudaGetLastError();
 }
 
@@ -2407,29 +2460,37 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   return a;
 }
 
-cudaError_t dispatch_join(const PointsSet& P, const JoinArgs& a, cudaStream_t st, const char* name) {
-  if (P.precision == 1 && (!P.Xb || !P.aux || !P.qflags)) return cudaErrorInvalidValue;
+cudaError_t dispatch_join(const PointsSet& P, const JoinArgs& a, cudaStream_t st, const char* name,
+                          bool setup_only = false) {
+  if (P.precision == 1 && (!P.Xb || !P.aux || !P.qflags) && !setup_only) return cudaErrorInvalidValue;
   cudaError_t e;
   // pools of up to 32 entries: one warp per vertex; 33..64 entries: a two-warp team per
   // vertex (batched CTAs with dimension chunks for FP32 rows longer than 128)
   const char* wname = (name[0] == 'r') ? "rnd_join_warp" : "final_prune_warp";
+  const bool so = setup_only;
   if (P.metric == 0)
-    e = P.precision == 1 ? launch_join_warp_t<0, 1>(a, st, wname) : launch_join_warp_t<0, 0>(a, st, wname);
+    e = P.precision == 1 ? launch_join_warp_t<0, 1>(a, st, wname, so) : launch_join_warp_t<0, 0>(a, st, wname, so);
   else
-    e = P.precision == 1 ? launch_join_warp_t<1, 1>(a, st, wname) : launch_join_warp_t<1, 0>(a, st, wname);
+    e = P.precision == 1 ? launch_join_warp_t<1, 1>(a, st, wname, so) : launch_join_warp_t<1, 0>(a, st, wname, so);
   if (e != cudaSuccess) return e;
   if (P.precision == 1 || P.d <= 128) {  // pools of 33..64 entries: a two-warp team per vertex
     const char* tname = (name[0] == 'r') ? "rnd_join_team" : "final_prune_team";
     if (P.metric == 0)
-      return P.precision == 1 ? launch_join_team_t<0, 1>(a, st, tname) : launch_join_team_t<0, 0>(a, st, tname);
-    return P.precision == 1 ? launch_join_team_t<1, 1>(a, st, tname) : launch_join_team_t<1, 0>(a, st, tname);
+      return P.precision == 1 ? launch_join_team_t<0, 1>(a, st, tname, so) : launch_join_team_t<0, 0>(a, st, tname, so);
+    return P.precision == 1 ? launch_join_team_t<1, 1>(a, st, tname, so) : launch_join_team_t<1, 0>(a, st, tname, so);
   }
   // FP32 rows of more than 128 dimensions: batched CTAs with dimension chunks
-  if (P.metric == 0) return launch_join_t<0, 0>(a, st, name);
-  return launch_join_t<1, 0>(a, st, name);
+  if (P.metric == 0) return launch_join_t<0, 0>(a, st, name, so);
+  return launch_join_t<1, 0>(a, st, name, so);
 }
 
 }  // namespace
+
+cudaError_t prepare_join_kernels(const PointsSet& P) {
+  JoinArgs a{};
+  a.P.d = P.d;
+  return dispatch_join(P, a, nullptr, "rnd_join", true);
+}
 
 cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,

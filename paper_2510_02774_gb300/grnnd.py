@@ -73,6 +73,8 @@ _SIGS = {
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_build_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_void_p]),
     "grnnd_reverse_sample": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p,
@@ -248,6 +250,33 @@ def build(points, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precisio
     n_, d_, R_, e_ = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().grnnd_graph_info(h, ctypes.byref(n_), ctypes.byref(d_), ctypes.byref(R_), ctypes.byref(e_)))
     return Graph(h, n_.value, d_.value, R_.value, e_.value)
+
+
+def _graph_of(h) -> Graph:
+    n_, d_, R_, e_ = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().grnnd_graph_info(h, ctypes.byref(n_), ctypes.byref(d_), ctypes.byref(R_), ctypes.byref(e_)))
+    return Graph(h, n_.value, d_.value, R_.value, e_.value)
+
+
+def build_batch(points, offsets, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32,
+                order=ORDER_RANDOM, final_prune=True, stream=None, hbm_budget=0) -> list:
+    """grnnd_build_batch: independent builds of the row ranges [offsets[b], offsets[b+1]) of
+    `points` (numpy or torch, shape (n, d)) in one pass; returns one Graph per build."""
+    if isinstance(points, np.ndarray):
+        pts = np.ascontiguousarray(points, dtype=np.float32)
+        ptr = pts.ctypes.data_as(ctypes.c_void_p)
+        st = None
+    else:
+        pts = points.contiguous()
+        ptr = ctypes.c_void_p(pts.data_ptr())
+        st = _stream_ptr(stream).value if pts.is_cuda else None
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nb = len(off) - 1
+    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, hbm_budget)
+    hs = (ctypes.c_void_p * nb)()
+    _check(lib().grnnd_build_batch(ptr, off.ctypes.data_as(ctypes.c_void_p), nb, pts.shape[1], ctypes.byref(p),
+                                   ctypes.cast(hs, ctypes.c_void_p)))
+    return [_graph_of(ctypes.c_void_p(hs[b])) for b in range(nb)]
 
 
 def search(graph: Graph, queries, k: int = 10, beam: int = 64):

@@ -91,3 +91,22 @@ def test_key_codec_orders_like_dist_then_id():
     assert d2[0, :3].tolist() == [0.5, 0.5, -2.0]
     order = np.argsort(k[0, :3])
     assert order.tolist() == [2, 1, 0]  # (-2, 2) < (0.5, 1) < (0.5, 3)
+
+
+def test_build_batch_validates_before_any_launch(L):
+    import ctypes
+    p = G.params(S=4, R=8)
+    null = ctypes.c_void_p(0)
+    hs = (ctypes.c_void_p * 3)()
+    pts = ctypes.c_void_p(1 << 20)
+    ok = (ctypes.c_int64 * 4)(0, 10, 20, 30)
+    assert L.grnnd_build_batch(pts, ok, 3, 4, ctypes.byref(p), null) == G.EINVAL
+    assert L.grnnd_build_batch(pts, ok, 0, 4, ctypes.byref(p), hs) == G.EINVAL
+    bad0 = (ctypes.c_int64 * 4)(1, 10, 20, 30)
+    assert L.grnnd_build_batch(pts, bad0, 3, 4, ctypes.byref(p), hs) == G.EINVAL
+    assert b"offsets[0]" in L.grnnd_last_error()
+    tiny = (ctypes.c_int64 * 4)(0, 10, 11, 30)  # a build of one point
+    assert L.grnnd_build_batch(pts, tiny, 3, 4, ctypes.byref(p), hs) == G.EINVAL
+    small = (ctypes.c_int64 * 4)(0, 10, 14, 30)  # S = 4 needs 5 points
+    assert L.grnnd_build_batch(pts, small, 3, 4, ctypes.byref(p), hs) == G.EINVAL
+    assert all(h is None for h in hs)

@@ -407,3 +407,43 @@ def test_join_round_in_place_matches_oracle(G, orc, n, d, S, R, hist):
     keys, deg = G.reverse_sample(keys, deg, 0.6, ws=ws, inplace=True)
     assert_pool_equal(G, keys, deg, want)
     G.workspace_status(ws, n, R)  # no device-side wait gave up
+
+
+# ---------------------------------------------------------------------------------------
+# batched builds: each build of a batch equals the same build alone
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,metric", [("fp32", 0), ("bf16", 0), ("bf16", 1), ("fp32", 1)])
+def test_build_batch_equals_single_builds(G, precision, metric):
+    sizes = [300, 9, 1000, 57, 2000, 128]
+    parts = [synth.small_integers(m, 24, -8, 8, seed=100 + i) for i, m in enumerate(sizes)]
+    X = np.concatenate(parts)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    prec = {"fp32": G.FP32, "bf16": G.BF16}[precision]
+    kw = dict(S=8, R=16, T1=2, T2=4, rho=0.6, seed=11, metric=metric, precision=prec)
+    gs = G.build_batch(torch.from_numpy(X).cuda(), off, **kw)
+    Q = synth.small_integers(50, 24, -8, 8, seed=999)
+    for b, part in enumerate(parts):
+        one = G.build(torch.from_numpy(part).cuda(), **kw)
+        a, o = gs[b].to_numpy(), one.to_numpy()
+        assert gs[b].n == len(part) and gs[b].entry == one.entry
+        assert (a[2] == o[2]).all() and (a[0] == o[0]).all() and (a[1] == o[1]).all(), b
+        qa = gs[b].search(torch.from_numpy(Q).cuda(), 5, 16).cpu().numpy()
+        qo = one.search(torch.from_numpy(Q).cuda(), 5, 16).cpu().numpy()
+        assert (qa == qo).all()
+
+
+def test_build_batch_mixed_data_and_free_order(G):
+    # an integer build next to a continuous one (the BF16 form's exact mode is decided over
+    # the whole pass); graphs freed in any order keep the others valid
+    a = synth.small_integers(700, 40, -8, 8, seed=5)
+    b = synth.gaussian_mixture(900, 40, seed=6)
+    X = np.concatenate([a, b]).astype(np.float32)
+    kw = dict(S=12, R=24, T1=2, T2=5, seed=3, precision=G.BF16)
+    gs = G.build_batch(X, [0, 700, 1600], **kw)
+    ga, gb = G.build(a, **kw), G.build(b, **kw)
+    assert (gs[0].to_numpy()[0] == ga.to_numpy()[0]).all()
+    del gs[0]
+    import gc
+    gc.collect()
+    assert (gs[0].to_numpy()[0] == gb.to_numpy()[0]).all()
