@@ -336,7 +336,10 @@ def run_batched_report(args):
                 out = None
         return ts, out
 
-    tb, _ = timed(lambda: grnnd.build_batch(X, off, **kw), max(3, args.steps))
+    # the autotuner on a batch of 64 of the builds, then the whole batched pass with its choice
+    tune = grnnd.autotune(X[: int(off[64])], offsets=off[:65], **kw)
+    tb0, _ = timed(lambda: grnnd.build_batch(X, off, **kw), max(3, args.steps))
+    tb, _ = timed(lambda: grnnd.build_batch(X, off, tuning=tune, **kw), max(3, args.steps))
     ts, _ = timed(lambda: [grnnd.build(X[int(off[b]):int(off[b + 1])], **kw) for b in range(nbuild)], 1)
     # the same results both ways (a sample of builds)
     gs = grnnd.build_batch(X, off, **kw)
@@ -345,13 +348,19 @@ def run_batched_report(args):
         one = grnnd.build(X[int(off[b]):int(off[b + 1])], **kw)
         same &= bool((gs[b].to_numpy()[0] == one.to_numpy()[0]).all()) and gs[b].entry == one.entry
     bms = sorted(t[1] for t in tb)
+    grnnd.profile_begin()
+    grnnd.build_batch(X, off, tuning=tune, **kw)  # not captured while profiling
+    torch.cuda.synchronize()
+    kern = {k2: round(v[1], 2) for k2, v in sorted(grnnd.profile_end().items(), key=lambda kv: -kv[1][1])}
     line = {"report": "batched", "workload": "512 builds, n log-uniform in [1000, 50000], DEEP-shaped d=96 unit "
                                               "vectors (50-cluster mixture per build), IP, BF16; S 16, R 32, T1 3, T2 10",
             "builds": nbuild, "points": total, "min_n": int(sizes.min()), "max_n": int(sizes.max()),
             "batched_ms_p50": bms[len(bms) // 2], "batched_points_per_s": total / (bms[len(bms) // 2] / 1e3),
             "batched_builds_per_s": nbuild / (bms[len(bms) // 2] / 1e3),
             "sequential_ms": ts[0][1], "sequential_points_per_s": total / (ts[0][1] / 1e3),
-            "speedup": ts[0][1] / bms[len(bms) // 2], "same_graphs_sampled": same}
+            "speedup": ts[0][1] / bms[len(bms) // 2], "same_graphs_sampled": same,
+            "tuning": tune.as_dict(), "batched_default_tuning_ms_p50": sorted(t[1] for t in tb0)[len(tb0) // 2],
+            "kernels_ms_profiled_pass": kern}
     print(json.dumps(line), flush=True)
 
 

@@ -74,6 +74,19 @@ typedef enum { GRNND_ORDER_RANDOM = 0, GRNND_ORDER_ASC = 1, GRNND_ORDER_DESC = 2
 
 typedef struct grnnd_graph grnnd_graph; /* opaque, library-owned */
 
+/* Launch shape of the join (no counterpart in the paper).  A pool of m entries is joined
+ * by a lane group of 8 lanes (four pools per warp) if m <= group_max[0], else of 16 lanes
+ * (two per warp) if m <= group_max[1], else of 32 lanes if m <= group_max[2], else by a
+ * 64-thread CTA; 0 <= group_max[c] <= 8 << c.  warp_ctas_per_sm / team_ctas_per_sm cap the
+ * resident CTAs per SM of the two join kernels (0: as many as fit).  Only speed depends on
+ * it: every tuning gives the same graph.  Defaults {8, 16, 32}, 0, 0. */
+typedef struct grnnd_tuning {
+    int32_t group_max[3];
+    int32_t warp_ctas_per_sm;
+    int32_t team_ctas_per_sm;
+    float ms;             /* grnnd_autotune: build time of the chosen tuning on the sample */
+} grnnd_tuning;
+
 /* Parameters of a build (Table 1: S, R, T1, T2, rho). */
 typedef struct grnnd_params {
     int32_t S;            /* initial random neighbours per vertex, 1 <= S <= min(R, n-1) */
@@ -88,11 +101,21 @@ typedef struct grnnd_params {
     int32_t final_prune;  /* 1: return the survivors of one more prune pass; 0: the last pool */
     void *stream;         /* cudaStream_t for all work of the build; NULL = legacy default */
     uint64_t hbm_budget;  /* bytes the build may allocate; 0 = no limit */
+    const grnnd_tuning *tuning; /* join launch shape; NULL = defaults */
 } grnnd_params;
 
 /* Fills *p with defaults: S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, L2SQ, FP32,
- * random order, final_prune=1, stream=NULL, no budget. */
+ * random order, final_prune=1, stream=NULL, no budget, default tuning. */
 GRNND_API void grnnd_params_default(grnnd_params *p);
+
+/* Autotuner: builds the given points (a sample of the workload to tune for: host or device
+ * rows, as for grnnd_build_ex; with offsets != NULL a batch of nbuild builds, as for
+ * grnnd_build_batch) once per candidate tuning and writes the fastest to *best (with its
+ * time in best->ms).  Candidates: the lane-group routing {8,16,32}, {0,16,32}, {0,0,32},
+ * {8,16,16} and {0,16,16}, then 1..3 warp-kernel CTAs and 2, 4 or 6 team CTAs per SM around
+ * the best, one axis at a time.  p->tuning is ignored.  Synchronous. */
+GRNND_API int grnnd_autotune(const float *points, int64_t n, int32_t d, const int64_t *offsets,
+                             int32_t nbuild, const grnnd_params *p, grnnd_tuning *best);
 
 /* Builds a graph over n points of dimension d (Alg 3).  `points` is host or
  * device memory, n rows of d contiguous floats; every value must be finite.

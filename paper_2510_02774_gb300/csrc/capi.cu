@@ -5,6 +5,7 @@
 // reverse-edge sampling (Sec 3.6) after every outer iteration but the last, then the
 // optional final prune, the export to (ids, dists) rows and the search entry.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -197,6 +198,7 @@ void grnnd_params_default(grnnd_params* p) {
   p->final_prune = 1;
   p->stream = nullptr;
   p->hbm_budget = 0;
+  p->tuning = nullptr;
 }
 
 size_t grnnd_workspace_size(int64_t n, int32_t R) {
@@ -405,6 +407,13 @@ int check_params(const grnnd_params* p) {
   if (p->order < 0 || p->order > 2) return fail(GRNND_EINVAL, "unknown order");
   if (p->precision != GRNND_FP32 && p->precision != GRNND_BF16)
     return fail(GRNND_EINVAL, "unknown precision");
+  if (const grnnd_tuning* t = p->tuning) {
+    for (int c = 0; c < 3; ++c)
+      if (t->group_max[c] < 0 || t->group_max[c] > (8 << c))
+        return fail(GRNND_EINVAL, "tuning: need 0 <= group_max[c] <= 8 << c");
+    if (t->warp_ctas_per_sm < 0 || t->team_ctas_per_sm < 0)
+      return fail(GRNND_EINVAL, "tuning: CTAs per SM must be >= 0");
+  }
   return GRNND_OK;
 }
 
@@ -482,6 +491,11 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   P.d = d;
   P.metric = p->metric;
   P.vseg = vseg;
+  if (const grnnd_tuning* t = p->tuning) {
+    for (int c = 0; c < 3; ++c) P.group_max[c] = t->group_max[c];
+    P.warp_ctas = t->warp_ctas_per_sm;
+    P.team_ctas = t->team_ctas_per_sm;
+  }
   if (bf16) {
     P.precision = 1;
     P.Xb = qp;
@@ -663,6 +677,66 @@ int grnnd_build_batch(const float* points, const int64_t* offsets, int32_t nbuil
   }
   if (offsets[nbuild] > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "total points must be <= 2^31 - 2");
   return build_core(points, offsets[nbuild], d, p, offsets, nbuild, graphs_out);
+}
+
+int grnnd_autotune(const float* points, int64_t n, int32_t d, const int64_t* offsets, int32_t nbuild,
+                   const grnnd_params* p, grnnd_tuning* best) {
+  if (!best) return fail(GRNND_EINVAL, "best is NULL");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (offsets && (nbuild < 1 || offsets[nbuild] != n)) return fail(GRNND_EINVAL, "offsets must end at n");
+  grnnd_params q = *p;
+  std::vector<grnnd_graph*> gs(offsets ? (size_t)nbuild : 1, nullptr);
+  // one candidate: a build to settle allocations, then the best of two timed builds
+  auto trial = [&](const grnnd_tuning& t, float* ms) -> int {
+    q.tuning = &t;
+    float m = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      const auto t0 = std::chrono::steady_clock::now();
+      const int r = offsets ? grnnd_build_batch(points, offsets, nbuild, d, &q, gs.data())
+                            : grnnd_build_ex(points, n, d, &q, gs.data());
+      const auto t1 = std::chrono::steady_clock::now();
+      if (r != GRNND_OK) return r;
+      for (auto*& g : gs) {
+        grnnd_free(g);
+        g = nullptr;
+      }
+      if (rep > 0) m = std::min(m, std::chrono::duration<float, std::milli>(t1 - t0).count());
+    }
+    *ms = m;
+    return GRNND_OK;
+  };
+  grnnd_tuning cur{{8, 16, 32}, 0, 0, 0.0f};
+  float cur_ms = 0.0f;
+  if ((rc = trial(cur, &cur_ms))) return rc;
+  const int32_t routes[4][3] = {{0, 16, 32}, {0, 0, 32}, {8, 16, 16}, {0, 16, 16}};
+  grnnd_tuning base = cur;
+  for (const auto& r : routes) {
+    grnnd_tuning t = base;
+    for (int c = 0; c < 3; ++c) t.group_max[c] = r[c];
+    float ms;
+    if ((rc = trial(t, &ms))) return rc;
+    if (ms < cur_ms) cur = t, cur_ms = ms;
+  }
+  base = cur;
+  for (int w = 1; w <= 3; ++w) {
+    grnnd_tuning t = base;
+    t.warp_ctas_per_sm = w;
+    float ms;
+    if ((rc = trial(t, &ms))) return rc;
+    if (ms < cur_ms) cur = t, cur_ms = ms;
+  }
+  base = cur;
+  for (int w = 2; w <= 6; w += 2) {
+    grnnd_tuning t = base;
+    t.team_ctas_per_sm = w;
+    float ms;
+    if ((rc = trial(t, &ms))) return rc;
+    if (ms < cur_ms) cur = t, cur_ms = ms;
+  }
+  cur.ms = cur_ms;
+  *best = cur;
+  return GRNND_OK;
 }
 
 int grnnd_build(const float* points, int64_t n, int32_t d, int32_t metric, int32_t S, int32_t R,

@@ -41,6 +41,9 @@ struct PointsSet {
   // Batched builds: per vertex (first id, number of points) of the build it belongs to;
   // null for one build.  Random draws and visit orders use ids local to the build.
   const int2* vseg = nullptr;
+  // Join launch shape (grnnd_tuning): lane-group routing by pool size, CTAs per SM caps.
+  int group_max[3] = {8, 16, 32};
+  int warp_ctas = 0, team_ctas = 0;
 };
 
 size_t workspace_bytes(int64_t n, int R);

@@ -234,7 +234,7 @@ struct RecSet {
 
 __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
                             int64_t n, int R, uint8_t* __restrict__ active,
-                            int32_t* __restrict__ list_n, int warp_ok, RecSet rs,
+                            int32_t* __restrict__ list_n, int warp_ok, int3 gmax, RecSet rs,
                             const float2* __restrict__ aux, const int2* __restrict__ vseg,
                             int64_t* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
@@ -250,7 +250,7 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
       for (int j = 0; j < m && !act; ++j) act = !(keys[v * R + j] & 1ull);
       active[v] = act ? 1 : 0;
     }
-    const int cls = !warp_ok ? 3 : (m <= 8 ? 0 : (m <= 16 ? 1 : (m <= 32 ? 2 : 3)));
+    const int cls = !warp_ok ? 3 : (m <= gmax.x ? 0 : (m <= gmax.y ? 1 : (m <= gmax.z ? 2 : 3)));
     unsigned bc[4];
     int off[4];
 #pragma unroll
@@ -446,6 +446,7 @@ struct JoinArgs {
   int32_t* count;
   int64_t* stats;
   int32_t* err;
+  int warp_ctas, team_ctas;  // launch caps (host side only; 0: as many as fit)
 };
 
 __device__ __forceinline__ int tiles_of(int m, int k) {
@@ -1123,6 +1124,7 @@ constexpr int WW = 4;      // warps per CTA
 constexpr int WM = 32;     // pool entries a warp holds at a time
 constexpr int WRED = 256;  // redirect slots a warp reserves at a time
 constexpr int WDC = 128;   // dimensions per gathered chunk
+constexpr int WRQ = 128;   // re-decisions a warp queues per item (more are taken in place)
 
 template <int PREC>
 struct WPrec;
@@ -1151,6 +1153,8 @@ struct __align__(16) WarpSlot {
   uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
   uint8_t inv[WM];              // by storage slot (group base + slot): local position
   uint8_t F[WM][WM];            // F[p][q], q < p: pair (q, p) of a group fired (0 / 1)
+  uint16_t rq[WRQ];             // pairs (row i << 5 | row j) whose decision is re-taken in FP32
+  int32_t nrq;                  // queued re-decisions of the item
   int32_t gk[4], gm[4];         // per group: new entries, entries
   uint64_t bar;
   unsigned long long red_next, red_end;
@@ -1298,6 +1302,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       s.rnd[gb + row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)aux) : 0.0f, key_dist(key));
       if (PREC == 1) s.rdq[gb + row] = __uint_as_float((uint32_t)(aux >> 32));
     }
+    if (lane == 0) s.nrq = 0;
     if (gl == 0) {
       s.gk[g] = k;
       s.gm[g] = m;
@@ -1408,11 +1413,16 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
               const float eqi = s.rdq[i], eqj = s.rdq[j];
               const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
               if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
+                ++st_check;
+                const int slot = atomicAdd(&s.nrq, 1);
+                if (slot < WRQ) {
+                  s.rq[slot] = (uint16_t)((i << 5) | j);  // taken below, all together
+                  continue;
+                }
                 const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
                 const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
                 dab = row_dist<METRIC>(xa, xb, d);
                 fire = dab < mx;
-                ++st_check;
               }
             }
             s.pd[q[e]] = dab;
@@ -1451,6 +1461,21 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       if (a.emit_redirects)
         for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
       return;
+    }
+    // queued re-decisions, one per lane: the FP32 rows of every pair load at once
+    if (PREC == 1 && nch > 0) {
+      const int nq = min(s.nrq, WRQ);
+      for (int t = lane; t < nq; t += 32) {
+        const int i = s.rq[t] >> 5, j = s.rq[t] & 31;
+        const int ge = i >> lw, eb = ge << lw, li = i - eb, lj = j - eb;
+        const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+        const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
+        const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
+        const float dab = row_dist<METRIC>(xa, xb, d);
+        s.pd[ge * ((VW * (VW - 1)) >> 1) + s.roff[i] + (lj - li - 1)] = dab;
+        s.F[eb + max(pa2, pb2)][min(pa2, pb2)] = dab < fmaxf(s.rnd[i].y, s.rnd[j].y) ? 1 : 0;
+      }
+      __syncwarp();
     }
     // fire masks: position p gathers the bytes F[p][0..p-1] of the pairs it closes
     if (valid_p && nch > 0) {
@@ -1575,6 +1600,7 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
   int per_sm = 0;
   cudaError_t e = setup_kernel(ks, kern, WW * 32, smem, smem, &per_sm);
   if (e != cudaSuccess || setup_only) return e;
+  if (a.warp_ctas > 0) per_sm = std::min(per_sm, a.warp_ctas);
   if (per_sm < 1) per_sm = 1;
   const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
   ProfScope ps(name, st);
@@ -1603,6 +1629,7 @@ namespace {
 constexpr int TM = 64;     // pool entries per team
 constexpr int TRED = 512;  // redirect slots a team reserves at a time
 constexpr int TDC = 128;   // columns per gathered chunk
+constexpr int TRQ = 256;   // re-decisions a team queues per vertex (more are taken in place)
 
 template <int PREC>
 struct TPrec;
@@ -1637,6 +1664,8 @@ struct __align__(16) TeamSmem {
   int32_t pid[TM];                // by pi position
   int32_t roff[TM + 1];           // first pair index of new row i
   uint8_t rpos[TM], prow[TM], killer[TM];
+  uint16_t rq[TRQ];               // pairs (row i << 6 | row j) whose decision is re-taken in FP32
+  int32_t nrq;
   uint64_t newm, alive, wtot;
   uint32_t sm32[2];
   uint64_t bar[2];
@@ -1722,7 +1751,10 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       hk.pad = 0u;
       s.hk[tid] = hk;
     }
-    if (tid == 0) s.newm = 0ull;
+    if (tid == 0) {
+      s.newm = 0ull;
+      s.nrq = 0;
+    }
     __syncthreads();
     int pi = 0;
     if (has) {
@@ -1849,11 +1881,16 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
               const float eqi = s.rdq[i], eqj = s.rdq[j];
               const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
               if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
+                ++st_check;
+                const int slot = atomicAdd(&s.nrq, 1);
+                if (slot < TRQ) {
+                  s.rq[slot] = (uint16_t)((i << 6) | j);  // taken below, all together
+                  continue;
+                }
                 const float* xa = a.P.X + (int64_t)s.pid[s.rpos[i]] * a.P.ld;
                 const float* xb = a.P.X + (int64_t)s.pid[s.rpos[j]] * a.P.ld;
                 dab = row_dist<METRIC>(xa, xb, d);
                 fire = dab < mx;
-                ++st_check;
               }
             }
             s.pd[q[e]] = dab;
@@ -1897,6 +1934,20 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       return;
     }
 
+    // queued re-decisions, one per thread: the FP32 rows of every pair load at once
+    if (PREC == 1 && nch > 0 && s.nrq > 0) {
+      const int nq = min(s.nrq, TRQ);
+      for (int t = tid; t < nq; t += TM) {
+        const int i = s.rq[t] >> 6, j = s.rq[t] & 63;
+        const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+        const float* xa = a.P.X + (int64_t)s.pid[pa2] * a.P.ld;
+        const float* xb = a.P.X + (int64_t)s.pid[pb2] * a.P.ld;
+        const float dab = row_dist<METRIC>(xa, xb, d);
+        s.pd[s.roff[i] + (j - i - 1)] = dab;
+        s.F[max(pa2, pb2)][min(pa2, pb2)] = dab < fmaxf(s.rnd[i].y, s.rnd[j].y) ? 1 : 0;
+      }
+      __syncthreads();
+    }
     // fire masks: thread p gathers the bytes F[p][0..p-1] (the low bit of each: bytes that no
     // pair wrote may hold anything) and keeps the pairs that were evaluated
     if (tid < m) {
@@ -2020,6 +2071,7 @@ cudaError_t launch_join_team_t(const JoinArgs& a, cudaStream_t st, const char* n
   int per_sm = 0;
   cudaError_t e = setup_kernel(ks, kern, TM, smem_max, smem, &per_sm);
   if (e != cudaSuccess || setup_only) return e;
+  if (a.team_ctas > 0) per_sm = std::min(per_sm, a.team_ctas);
   if (per_sm < 1) per_sm = 1;
   const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, kMaxJoinGrid);
   ProfScope ps(name, st);
@@ -2417,8 +2469,9 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
     rs.w[c] = ws.rec_w[c];
     rs.cap[c] = ws.rec_cap[c];
   }
+  const int3 gmax = make_int3(P.group_max[0], P.group_max[1], P.group_max[2]);
   prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
-                                                rs, P.precision == 1 ? P.aux : nullptr, P.vseg, stats);
+                                                gmax, rs, P.precision == 1 ? P.aux : nullptr, P.vseg, stats);
   return cudaGetLastError();
 }
 
@@ -2457,6 +2510,8 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   a.count = ws.count;
   a.stats = stats;
   a.err = ws.err;
+  a.warp_ctas = P.warp_ctas;
+  a.team_ctas = P.team_ctas;
   return a;
 }
 

@@ -34,11 +34,29 @@ class GrnndError(RuntimeError):
         self.status = status
 
 
+class Tuning(ctypes.Structure):
+    """grnnd_tuning: lane-group routing by pool size and CTAs-per-SM caps of the join."""
+    _fields_ = [("group_max", ctypes.c_int32 * 3), ("warp_ctas_per_sm", ctypes.c_int32),
+                ("team_ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"group_max": list(self.group_max), "warp_ctas_per_sm": self.warp_ctas_per_sm,
+                "team_ctas_per_sm": self.team_ctas_per_sm, "ms": self.ms}
+
+
+def tuning(group_max=(8, 16, 32), warp_ctas_per_sm=0, team_ctas_per_sm=0) -> Tuning:
+    t = Tuning()
+    for c in range(3):
+        t.group_max[c] = group_max[c]
+    t.warp_ctas_per_sm, t.team_ctas_per_sm = warp_ctas_per_sm, team_ctas_per_sm
+    return t
+
+
 class Params(ctypes.Structure):
     _fields_ = [("S", ctypes.c_int32), ("R", ctypes.c_int32), ("T1", ctypes.c_int32), ("T2", ctypes.c_int32),
                 ("rho", ctypes.c_float), ("seed", ctypes.c_uint64), ("metric", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("order", ctypes.c_int32), ("final_prune", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_uint64)]
+                ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_uint64), ("tuning", ctypes.POINTER(Tuning))]
 
 
 class KernelTime(ctypes.Structure):
@@ -73,6 +91,8 @@ _SIGS = {
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.POINTER(Params), ctypes.POINTER(Tuning)]),
     "grnnd_build_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32,
@@ -221,18 +241,20 @@ class Graph:
 
 
 def params(S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,
-           final_prune=True, stream=None, hbm_budget=0) -> Params:
+           final_prune=True, stream=None, hbm_budget=0, tuning=None) -> Params:
     p = Params()
     lib().grnnd_params_default(ctypes.byref(p))
     p.S, p.R, p.T1, p.T2, p.rho, p.seed = S, R, T1, T2, rho, seed
     p.metric, p.precision, p.order, p.final_prune = metric, precision, order, int(bool(final_prune))
     p.stream = stream
     p.hbm_budget = hbm_budget
+    if tuning is not None:
+        p.tuning = ctypes.pointer(tuning)
     return p
 
 
 def build(points, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,
-          final_prune=True, stream=None, hbm_budget=0) -> Graph:
+          final_prune=True, stream=None, hbm_budget=0, tuning=None) -> Graph:
     """grnnd_build_ex on numpy (host) or torch (host or device) points of shape (n, d).
     With torch CUDA points the build runs on the current torch stream."""
     if isinstance(points, np.ndarray):
@@ -244,7 +266,7 @@ def build(points, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precisio
         ptr = ctypes.c_void_p(pts.data_ptr())
         st = _stream_ptr(stream).value if pts.is_cuda else None
     n, d = pts.shape
-    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, hbm_budget)
+    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, hbm_budget, tuning)
     h = ctypes.c_void_p()
     _check(lib().grnnd_build_ex(ptr, n, d, ctypes.byref(p), ctypes.byref(h)))
     n_, d_, R_, e_ = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -259,7 +281,7 @@ def _graph_of(h) -> Graph:
 
 
 def build_batch(points, offsets, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32,
-                order=ORDER_RANDOM, final_prune=True, stream=None, hbm_budget=0) -> list:
+                order=ORDER_RANDOM, final_prune=True, stream=None, hbm_budget=0, tuning=None) -> list:
     """grnnd_build_batch: independent builds of the row ranges [offsets[b], offsets[b+1]) of
     `points` (numpy or torch, shape (n, d)) in one pass; returns one Graph per build."""
     if isinstance(points, np.ndarray):
@@ -272,11 +294,32 @@ def build_batch(points, offsets, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric
         st = _stream_ptr(stream).value if pts.is_cuda else None
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     nb = len(off) - 1
-    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, hbm_budget)
+    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, hbm_budget, tuning)
     hs = (ctypes.c_void_p * nb)()
     _check(lib().grnnd_build_batch(ptr, off.ctypes.data_as(ctypes.c_void_p), nb, pts.shape[1], ctypes.byref(p),
                                    ctypes.cast(hs, ctypes.c_void_p)))
     return [_graph_of(ctypes.c_void_p(hs[b])) for b in range(nb)]
+
+
+def autotune(points, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,
+             final_prune=True, stream=None, offsets=None) -> Tuning:
+    """grnnd_autotune on a sample of the workload (numpy or torch rows; with offsets, a batch
+    of builds); returns the Tuning."""
+    if isinstance(points, np.ndarray):
+        pts = np.ascontiguousarray(points, dtype=np.float32)
+        ptr = pts.ctypes.data_as(ctypes.c_void_p)
+        st = None
+    else:
+        pts = points.contiguous()
+        ptr = ctypes.c_void_p(pts.data_ptr())
+        st = _stream_ptr(stream).value if pts.is_cuda else None
+    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st)
+    t = Tuning()
+    off = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(lib().grnnd_autotune(ptr, pts.shape[0], pts.shape[1],
+                                None if off is None else off.ctypes.data_as(ctypes.c_void_p),
+                                0 if off is None else len(off) - 1, ctypes.byref(p), ctypes.byref(t)))
+    return t
 
 
 def search(graph: Graph, queries, k: int = 10, beam: int = 64):

@@ -110,3 +110,14 @@ def test_build_batch_validates_before_any_launch(L):
     small = (ctypes.c_int64 * 4)(0, 10, 14, 30)  # S = 4 needs 5 points
     assert L.grnnd_build_batch(pts, small, 3, 4, ctypes.byref(p), hs) == G.EINVAL
     assert all(h is None for h in hs)
+
+
+def test_tuning_is_validated(L):
+    import ctypes
+    pts = ctypes.c_void_p(1 << 20)
+    h = ctypes.c_void_p()
+    for gm, w in [((9, 16, 32), 0), ((8, 17, 32), 0), ((8, 16, 33), 0), ((-1, 16, 32), 0), ((8, 16, 32), -1)]:
+        t = G.tuning(gm, w, 0)
+        p = G.params(S=4, R=8, tuning=t)
+        assert L.grnnd_build_ex(pts, 100, 4, ctypes.byref(p), ctypes.byref(h)) == G.EINVAL
+        assert b"tuning" in L.grnnd_last_error()

@@ -447,3 +447,28 @@ def test_build_batch_mixed_data_and_free_order(G):
     import gc
     gc.collect()
     assert (gs[0].to_numpy()[0] == gb.to_numpy()[0]).all()
+
+
+# ---------------------------------------------------------------------------------------
+# join launch shapes (grnnd_tuning) change speed only
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,metric", [("bf16", 0), ("fp32", 0), ("bf16", 1)])
+def test_tunings_give_the_same_graph(G, precision, metric):
+    X = synth.small_integers(3000, 40, -8, 8, seed=77)
+    prec = {"fp32": G.FP32, "bf16": G.BF16}[precision]
+    kw = dict(S=24, R=48, T1=2, T2=5, seed=2, metric=metric, precision=prec)
+    ref = G.build(X, **kw).to_numpy()
+    for gm, w, t in [((0, 16, 32), 0, 0), ((0, 0, 32), 1, 2), ((8, 16, 16), 2, 4), ((0, 16, 16), 0, 1),
+                     ((0, 0, 0), 0, 0)]:
+        got = G.build(X, tuning=G.tuning(gm, w, t), **kw).to_numpy()
+        for a, b in zip(got, ref):
+            assert (a == b).all(), (gm, w, t)
+
+
+def test_autotune_picks_a_candidate(G):
+    X = synth.small_integers(4000, 32, -8, 8, seed=8)
+    t = G.autotune(X, S=16, R=32, T1=2, T2=4, precision=G.BF16)
+    assert t.ms > 0
+    assert list(t.group_max) in ([8, 16, 32], [0, 16, 32], [0, 0, 32], [8, 16, 16], [0, 16, 16])
+    assert 0 <= t.warp_ctas_per_sm <= 3 and t.team_ctas_per_sm in (0, 2, 4, 6)
