@@ -432,10 +432,10 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   const size_t q_b = bf16 ? al256((size_t)n * ldb * 2) + al256((size_t)n * 8) + 256 : 0;
   const size_t pool_b = al256((size_t)n * R * 8), deg_b = al256((size_t)n * 4);
   const size_t ws_b = grnnd::workspace_bytes(n, R);
-  size_t ent_b = grnnd::entry_workspace_bytes(n, d);
+  const size_t ent_b = batched ? grnnd::entry_batch_workspace_bytes(nbuild, d) : grnnd::entry_workspace_bytes(n, d);
   const size_t graph_b = al256((size_t)n * R * 4) * 2 + deg_b;
   const size_t stats_b = 256 + al256((size_t)nbuild * 4);  // counters, then one entry per build
-  const size_t seg_b = batched ? al256((size_t)n * 8) : 0;
+  const size_t seg_b = batched ? al256((size_t)n * 8) + al256(((size_t)nbuild + 1) * 8) : 0;
   const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b + q_b + seg_b;
   if (p->hbm_budget && pts_b + graph_b + scratch_b > p->hbm_budget)
     return fail(GRNND_ENOMEM, "build needs " + std::to_string(pts_b + graph_b + scratch_b) +
@@ -462,6 +462,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   const size_t wsp_b = std::max(ws_b, ent_b);
   char* qp = sp + 2 * pool_b + 2 * deg_b + stats_b + al256(wsp_b);
   int2* vseg = batched ? reinterpret_cast<int2*>(qp + q_b) : nullptr;
+  int64_t* off_dev = batched ? reinterpret_cast<int64_t*>(qp + q_b + al256((size_t)n * 8)) : nullptr;
 
   // points -> padded device rows; the segment of every vertex
   const cudaMemcpyKind kind = is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -475,6 +476,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
       for (int64_t v = offsets[b]; v < offsets[b + 1]; ++v)
         hseg[(size_t)v] = make_int2((int)offsets[b], (int)(offsets[b + 1] - offsets[b]));
     GR_CU(cudaMemcpyAsync(vseg, hseg.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    GR_CU(cudaMemcpyAsync(off_dev, offsets, ((size_t)nbuild + 1) * 8, cudaMemcpyHostToDevice, st));
   }
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(wsp, wsp_b, n, R, &ws)) return fail(GRNND_EINVAL, "internal workspace");
@@ -600,10 +602,10 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   // the entry workspace reuses the (now idle) round workspace; the round status word
   // moves to the stats block first
   GR_CAP(cudaMemcpyAsync(stats + 8, ws.err, 4, cudaMemcpyDeviceToDevice, st));
-  for (int32_t b = 0; b < nbuild; ++b) {
-    const int64_t lo = batched ? offsets[b] : 0, nb = batched ? offsets[b + 1] - offsets[b] : n;
-    GR_CAP(grnnd::launch_entry(X + lo * ld, nb, d, ld, p->metric, d_entry + b, wsp, wsp_b, st));
-  }
+  if (batched)
+    GR_CAP(grnnd::launch_entry_batch(X, d, ld, p->metric, off_dev, nbuild, d_entry, wsp, wsp_b, st));
+  else
+    GR_CAP(grnnd::launch_entry(X, n, d, ld, p->metric, d_entry, wsp, wsp_b, st));
 #undef GR_CAP
   if (capture) {
     GR_CU(cudaStreamEndCapture(st, &graph));

@@ -89,6 +89,11 @@ cudaError_t launch_check_finite(const float* X, int64_t n, int d, int ld, int32_
                                 cudaStream_t st);
 
 size_t entry_workspace_bytes(int64_t n, int d);
+// Search entries of nbuild builds whose rows are [off[b], off[b+1]) of X (off: device
+// int64[nbuild + 1]); entries[b] = the entry launch_entry gives for build b alone (local id).
+size_t entry_batch_workspace_bytes(int32_t nbuild, int d);
+cudaError_t launch_entry_batch(const float* X, int d, int ld, int metric, const int64_t* off_dev, int32_t nbuild,
+                               int32_t* entries, void* ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_entry(const float* X, int64_t n, int d, int ld, int metric, int32_t* entry,
                          void* ws, size_t ws_bytes, cudaStream_t st);
 

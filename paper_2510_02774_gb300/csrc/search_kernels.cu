@@ -177,6 +177,105 @@ cudaError_t launch_entry(const float* X, int64_t n, int d, int ld, int metric, i
   return cudaGetLastError();
 }
 
+// ---- search entries of a batch of builds: the same arithmetic as launch_entry, per build --
+// Build b covers rows [off[b], off[b+1]); its column sums use the same row blocks as a
+// single build of those rows (rpb = ceil(n_b / 512) rows per block, blocks in order), so the
+// mean, and therefore the entry, is the one launch_entry computes for the build alone.
+__global__ void seg_colsum_kernel(const float* __restrict__ X, int ld, int d, const int64_t* __restrict__ off,
+                                  int nbuild, double* __restrict__ partial) {
+  const int64_t total = (int64_t)nbuild * kEntryBlocks * d;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % d);
+    const int64_t bj = t / d;
+    const int b = (int)(bj / kEntryBlocks), j = (int)(bj % kEntryBlocks);
+    const int64_t lo = off[b], nb = off[b + 1] - lo;
+    const int64_t rpb = (nb + kEntryBlocks - 1) / kEntryBlocks;
+    const int64_t r0 = lo + (int64_t)j * rpb, r1 = std::min<int64_t>(lo + nb, r0 + rpb);
+    if (r0 >= r1) continue;
+    double s = 0.0;
+    for (int64_t r = r0; r < r1; ++r) s = __dadd_rn(s, (double)X[r * ld + k]);
+    partial[bj * d + k] = s;
+  }
+}
+
+__global__ void seg_mean_kernel(const double* __restrict__ partial, int d, const int64_t* __restrict__ off,
+                                int nbuild, double* __restrict__ mu) {
+  const int64_t total = (int64_t)nbuild * d;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / d), k = (int)(t % d);
+    const int64_t nb = off[b + 1] - off[b];
+    const int64_t rpb = (nb + kEntryBlocks - 1) / kEntryBlocks;
+    const int blocks = (int)((nb + rpb - 1) / rpb);
+    double s = 0.0;
+    for (int j = 0; j < blocks; ++j) s = __dadd_rn(s, partial[((int64_t)b * kEntryBlocks + j) * d + k]);
+    mu[t] = __ddiv_rn(s, (double)nb);
+  }
+}
+
+template <int METRIC>
+__global__ void seg_nearest_kernel(const float* __restrict__ X, int ld, int d, const int64_t* __restrict__ off,
+                                   const double* __restrict__ mu, int32_t* __restrict__ entry) {
+  __shared__ double sd[256];
+  __shared__ int32_t si[256];
+  const int b = blockIdx.x;
+  const int64_t lo = off[b], nb = off[b + 1] - lo;
+  const double* m = mu + (int64_t)b * d;
+  double best = DBL_MAX;
+  int32_t bid = INT32_MAX;
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    const float* x = X + (lo + i) * ld;
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+      if (METRIC == 0) {
+        const double t = __dsub_rn((double)x[k], m[k]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+      } else {
+        s = __dadd_rn(s, __dmul_rn((double)x[k], m[k]));
+      }
+    }
+    if (METRIC != 0) s = __dsub_rn(1.0, s);
+    if (dl_less(s, (int32_t)i, best, bid)) {
+      best = s;
+      bid = (int32_t)i;
+    }
+  }
+  sd[threadIdx.x] = best;
+  si[threadIdx.x] = bid;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o && dl_less(sd[threadIdx.x + o], si[threadIdx.x + o], sd[threadIdx.x], si[threadIdx.x])) {
+      sd[threadIdx.x] = sd[threadIdx.x + o];
+      si[threadIdx.x] = si[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) entry[b] = si[0];
+}
+
+size_t entry_batch_workspace_bytes(int32_t nbuild, int d) {
+  return al256((size_t)nbuild * kEntryBlocks * d * 8) + al256((size_t)nbuild * d * 8);
+}
+
+cudaError_t launch_entry_batch(const float* X, int d, int ld, int metric, const int64_t* off_dev, int32_t nbuild,
+                               int32_t* entries, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (ws_bytes < entry_batch_workspace_bytes(nbuild, d)) return cudaErrorInvalidValue;
+  char* p = static_cast<char*>(ws);
+  double* partial = reinterpret_cast<double*>(p);
+  p += al256((size_t)nbuild * kEntryBlocks * d * 8);
+  double* mu = reinterpret_cast<double*>(p);
+  ProfScope ps("entry", st);
+  const int64_t t1 = (int64_t)nbuild * kEntryBlocks * d, t2 = (int64_t)nbuild * d;
+  seg_colsum_kernel<<<(unsigned)std::min<int64_t>(ceil_div(t1, 256), (int64_t)sm_count() * 32), 256, 0, st>>>(
+      X, ld, d, off_dev, nbuild, partial);
+  seg_mean_kernel<<<(unsigned)std::min<int64_t>(ceil_div(t2, 256), (int64_t)sm_count() * 8), 256, 0, st>>>(
+      partial, d, off_dev, nbuild, mu);
+  if (metric == 0)
+    seg_nearest_kernel<0><<<(unsigned)nbuild, 256, 0, st>>>(X, ld, d, off_dev, mu, entries);
+  else
+    seg_nearest_kernel<1><<<(unsigned)nbuild, 256, 0, st>>>(X, ld, d, off_dev, mu, entries);
+  return cudaGetLastError();
+}
+
 // ---- candidate-list search -----------------------------------------------------------------
 // One warp per query.  The candidate list C (ascending keys; bit 0 = expanded) lives in
 // shared memory.  A small direct-mapped cache of evaluated ids skips re-evaluations; a
