@@ -48,7 +48,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16 (the last one is the headline)")
+    ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16, fp8 (the last one is the headline)")
     ap.add_argument("--report", choices=["precision", "ablation", "batched"], default=None,
                     help="precision: per-form distance error against FP64 and recall loss on a "
                          "GIST-shaped (d=960, continuous) or DEEP-shaped (d=96, IP) set of --n points")
@@ -180,7 +180,7 @@ def _source_sha():
 def run_precision_report(args):
     """Each form's distance error against FP64 and its recall loss, on continuous data.
 
-    Builds the graph of the same points with the FP32 form and the BF16 form, then:
+    Builds the graph of the same points with the FP32, BF16 and FP8 forms, then:
       * recall@10 of a beam-64 search of 1000 held-out queries against exact k-NN (GPU brute
         force); the BF16 form's loss is FP32 recall - BF16 recall;
       * the recorded distance of every edge against the FP64 distance recomputed on the host
@@ -206,9 +206,9 @@ def run_precision_report(args):
     Qp, _ = grnnd.device_points(Q)
     gt, _ = grnnd.brute_knn(Xp, d, Qp, k, metric=metric)
     gt = gt.cpu().numpy()
-    X64 = X.astype(np.float64)
+    X64 = X.astype(np.float64) if n <= 200_000 else X  # rows are widened per chunk on large sets
     out = {"report": "precision", "workload": shape, "queries": nq, "k": k, "beam": beam, "forms": {}}
-    for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16)):
+    for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16), ("fp8", grnnd.FP8)):
         g = grnnd.build(Xd, precision=prec, metric=metric, **kw)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -220,13 +220,18 @@ def run_precision_report(args):
         found = g2.search(torch.from_numpy(Q).cuda(), k, beam).cpu().numpy()
         rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(found, gt)]))
         ids, dist, deg = g2.to_numpy()
-        rows = np.repeat(np.arange(n), deg)
-        cols = np.concatenate([ids[v, :deg[v]] for v in range(n)])
-        rec_d = np.concatenate([dist[v, :deg[v]] for v in range(n)]).astype(np.float64)
-        if metric == grnnd.L2SQ:
-            d64 = ((X64[rows] - X64[cols]) ** 2).sum(1)
-        else:
-            d64 = 1.0 - (X64[rows] * X64[cols]).sum(1)
+        mask = np.arange(ids.shape[1])[None, :] < deg[:, None]
+        rows = np.nonzero(mask)[0]
+        cols = ids[mask].astype(np.int64)
+        rec_d = dist[mask].astype(np.float64)
+        if len(rows) > 2_000_000:  # a seeded sample of the edges on large sets
+            pick = np.random.default_rng(1).choice(len(rows), 2_000_000, replace=False)
+            rows, cols, rec_d = rows[pick], cols[pick], rec_d[pick]
+        d64 = np.empty(len(rows))
+        for a in range(0, len(rows), 1 << 16):  # FP64 recomputation in chunks
+            xa = X64[rows[a:a + (1 << 16)]].astype(np.float64)
+            xb = X64[cols[a:a + (1 << 16)]].astype(np.float64)
+            d64[a:a + (1 << 16)] = ((xa - xb) ** 2).sum(1) if metric == grnnd.L2SQ else 1.0 - (xa * xb).sum(1)
         rel = np.abs(rec_d - d64) / np.maximum(np.abs(d64), 1e-30)
         st = g2.stats()
         out["forms"][name] = {"build_ms": t0.elapsed_time(t1), "recall@10": rec, "edges": int(deg.sum()),
@@ -234,8 +239,9 @@ def run_precision_report(args):
                               "dist_rel_err_p99": float(np.quantile(rel, 0.99)),
                               "rechecks": int(st["rechecks"]), "pair_distances": int(st["pair_distances"])}
         del g, g2
-    out["bf16_recall_loss"] = out["forms"]["fp32"]["recall@10"] - out["forms"]["bf16"]["recall@10"]
-    out["bf16_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"]["bf16"]["build_ms"]
+    for q in ("bf16", "fp8"):
+        out[q + "_recall_loss"] = out["forms"]["fp32"]["recall@10"] - out["forms"][q]["recall@10"]
+        out[q + "_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"][q]["build_ms"]
     print(json.dumps(out), flush=True)
 
 
@@ -447,7 +453,7 @@ def main():
     forms = {}
     names = [f.strip() for f in args.forms.split(",") if f.strip()]
     for name in names:
-        forms[name] = timed_form({"fp32": grnnd.FP32, "bf16": grnnd.BF16}[name])
+        forms[name] = timed_form({"fp32": grnnd.FP32, "bf16": grnnd.BF16, "fp8": grnnd.FP8}[name])
     head_name = names[-1]
     head = forms[head_name]
     total_ms, step_ms, stats, kern, clk, g = (head["total_ms"], head["step_ms"], head["stats"], head["kern"],
@@ -480,7 +486,7 @@ def main():
     L = grnnd.lib()
 
     def e2e_step():
-        p = grnnd.params(precision={"fp32": grnnd.FP32, "bf16": grnnd.BF16}[head_name], **kw)
+        p = grnnd.params(precision={"fp32": grnnd.FP32, "bf16": grnnd.BF16, "fp8": grnnd.FP8}[head_name], **kw)
         h = ctypes.c_void_p()
         grnnd._check(L.grnnd_build_ex(ctypes.c_void_p(Xh.data_ptr()), n, d, ctypes.byref(p), ctypes.byref(h)))
         grnnd._check(L.grnnd_graph_copy(h, ctypes.c_void_p(ids_h.data_ptr()), None, ctypes.c_void_p(deg_h.data_ptr())))
@@ -511,7 +517,7 @@ def main():
     dom_name, (dom_launches, dom_ms) = max(groups.items(), key=lambda kv: kv[1][1])
     agg = {k: sum(s[k] for s in stats) for k in stats[0]}
     rounds = agg["rounds"]
-    elem = 2 if head_name == "bf16" else 4
+    elem = {"fp32": 4, "bf16": 2, "fp8": 1}[head_name]
     units = dom_launches
     if dom_name == "rnd_join":
         # rows gathered (elem bytes per dimension); pool keys read once; survivors written;
@@ -555,10 +561,12 @@ def main():
         p99 = _pct(step_ms, 0.99)
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": head_name.replace("fp", "f"), "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[head_name], "data": "synthetic",
                 "config": {**{k: v for k, v in WORKLOAD.items()}, "n": n, "nq": args.nq,
-                           "precision": ("bf16 dist_tile (tensor cores, FP32 accumulate, FP32 re-decision)"
-                                         if head_name == "bf16" else "fp32 dist_tile (CUDA cores)"),
+                           "precision": {"bf16": "bf16 dist_tile (tensor cores, FP32 accumulate, FP32 re-decision)",
+                                         "fp8": "fp8-e4m3 dist_tile, per-row scales (tensor cores, FP32 accumulate, "
+                                                "FP32 re-decision)",
+                                         "fp32": "fp32 dist_tile (CUDA cores)"}[head_name],
                            "l2": "inputs larger than L2 (512 MB of points per replica)",
                            "parallelism": f"{world} independent replica(s)"},
                 "p50_ms": statistics.median(step_ms), "p99_ms": p99, "recall@10": recall.get(head_name),

@@ -62,11 +62,15 @@ typedef enum {
 
 typedef enum { GRNND_L2SQ = 0, GRNND_IP = 1 } grnnd_metric;
 
-/* Arithmetic of the pair-distance tiles (dist_tile).  FP32: direct differences
- * on CUDA cores (the canonical form).  BF16: Gram tiles of a bfloat16 copy on
- * the tensor cores with FP32 accumulation; decisions within the stated error
- * bound are re-decided in FP32. */
-typedef enum { GRNND_FP32 = 0, GRNND_BF16 = 1 } grnnd_precision;
+/* Arithmetic of the pair-distance tiles (dist_tile).  The paper states no
+ * precision (Sec 3.4 computes distances with FP32 warp arithmetic).  FP32:
+ * direct differences on CUDA cores (the canonical form).  BF16: Gram tiles of a
+ * bfloat16 copy on the tensor cores with FP32 accumulation.  FP8: Gram tiles of
+ * an e4m3 copy with one power-of-two scale per row, FP32 accumulation.  In both
+ * quantized forms a fire decision whose margin is within the per-pair error
+ * bound (quantization residuals of the two rows + accumulation) is re-decided
+ * with the canonical FP32 distance. */
+typedef enum { GRNND_FP32 = 0, GRNND_BF16 = 1, GRNND_FP8 = 2 } grnnd_precision;
 
 /* Visit order of a pool's pairs: disordered (Sec 3.3, the paper's method),
  * ascending (dist, id) (Alg 2's serial order), or descending (Sec 4.3 ablation). */

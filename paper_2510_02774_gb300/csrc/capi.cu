@@ -405,7 +405,7 @@ int check_params(const grnnd_params* p) {
   if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return fail(GRNND_EINVAL, "rho must be in [0, 1]");
   if (p->metric != GRNND_L2SQ && p->metric != GRNND_IP) return fail(GRNND_EINVAL, "unknown metric");
   if (p->order < 0 || p->order > 2) return fail(GRNND_EINVAL, "unknown order");
-  if (p->precision != GRNND_FP32 && p->precision != GRNND_BF16)
+  if (p->precision != GRNND_FP32 && p->precision != GRNND_BF16 && p->precision != GRNND_FP8)
     return fail(GRNND_EINVAL, "unknown precision");
   if (const grnnd_tuning* t = p->tuning) {
     for (int c = 0; c < 3; ++c)
@@ -424,12 +424,15 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
                int32_t nbuild, grnnd_graph** graphs_out) {
   const bool batched = offsets != nullptr;
   const int32_t R = p->R, ld = round4(d);
-  const bool bf16 = p->precision == GRNND_BF16;
-  const int32_t ldb = (d + 15) & ~15;
+  // quantized forms: a BF16 copy (rows of d rounded up to 16 elements) or an e4m3 copy
+  // (rows of d rounded up to 32 bytes), per-row terms and dataset flags
+  const bool quant = p->precision != GRNND_FP32;
+  const int32_t ldb = p->precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
+  const size_t qelem = p->precision == GRNND_FP8 ? 1 : 2;
   cudaStream_t st = (cudaStream_t)p->stream;
 
   const size_t pts_b = al256((size_t)n * ld * 4);
-  const size_t q_b = bf16 ? al256((size_t)n * ldb * 2) + al256((size_t)n * 8) + 256 : 0;
+  const size_t q_b = quant ? al256((size_t)n * ldb * qelem) + al256((size_t)n * 8) + 256 : 0;
   const size_t pool_b = al256((size_t)n * R * 8), deg_b = al256((size_t)n * 4);
   const size_t ws_b = grnnd::workspace_bytes(n, R);
   const size_t ent_b = batched ? grnnd::entry_batch_workspace_bytes(nbuild, d) : grnnd::entry_workspace_bytes(n, d);
@@ -498,12 +501,12 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
     P.warp_ctas = t->warp_ctas_per_sm;
     P.team_ctas = t->team_ctas_per_sm;
   }
-  if (bf16) {
-    P.precision = 1;
+  if (quant) {
+    P.precision = p->precision;
     P.Xb = qp;
     P.ldb = ldb;
-    P.aux = reinterpret_cast<const float2*>(qp + al256((size_t)n * ldb * 2));
-    P.qflags = reinterpret_cast<const unsigned*>(qp + al256((size_t)n * ldb * 2) + al256((size_t)n * 8));
+    P.aux = reinterpret_cast<const float2*>(qp + al256((size_t)n * ldb * qelem));
+    P.qflags = reinterpret_cast<const unsigned*>(qp + al256((size_t)n * ldb * qelem) + al256((size_t)n * 8));
   }
 
   // A batched pass runs every round (a round after one that left no new entry is an
@@ -546,9 +549,9 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
     }                                                                                          \
   } while (0)
 
-  if (bf16)
+  if (quant)
     GR_CAP(grnnd::launch_quantize(X, n, d, ld, qp, ldb, const_cast<float2*>(P.aux),
-                                  const_cast<unsigned*>(P.qflags), st));
+                                  const_cast<unsigned*>(P.qflags), p->precision, st));
   GR_CAP(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st, vseg));
   RoundProbe* probe = nullptr;
   cudaEvent_t rev[2] = {nullptr, nullptr};

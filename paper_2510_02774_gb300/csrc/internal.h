@@ -29,7 +29,9 @@ struct Workspace {
 };
 
 // The points as the pool kernels read them.  precision 0: FP32 rows only; 1: also a
-// BF16 copy (ldb = d rounded up to 16), per-row (norm^2, residual) and dataset flags.
+// BF16 copy (ldb = d rounded up to 16), per-row (norm^2, residual) and dataset flags;
+// 2: an FP8-e4m3 copy (ldb = d rounded up to 32) with the same per-row terms, the row's
+// scale exponent in the low byte of the residual.
 struct PointsSet {
   const float* X = nullptr;
   int ld = 0;
@@ -56,8 +58,10 @@ cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metri
 // Batched builds: subtracts each row's build base from its ids (-1 stays -1).
 cudaError_t launch_localize_ids(int64_t n, int R, int32_t* ids, const int2* vseg, cudaStream_t st);
 
+// precision 1: BF16 rows (ldb = d rounded up to 16 elements); 2: e4m3 rows with a
+// power-of-two scale per row (ldb = d rounded up to 32 bytes).
 cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xb, int ldb,
-                            float2* aux, unsigned* qflags, cudaStream_t st);
+                            float2* aux, unsigned* qflags, int precision, cudaStream_t st);
 
 // One-time launch set-up of the join kernels that points P will use (shared-memory opt-in,
 // occupancy); launches inside a stream capture rely on it having run.

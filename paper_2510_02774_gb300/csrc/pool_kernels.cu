@@ -9,6 +9,7 @@
 //   reverse       reverse-edge sampling (Sec 3.6) feeding the same merge
 //   quantize      BF16 copy of the points + per-row norm and residual for the BF16 form
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cstdio>
 
@@ -205,14 +206,78 @@ __global__ void quantize_kernel(const float* __restrict__ X, int64_t n, int d, i
   }
 }
 
+// =====================================================================================
+// quantize, FP8 form: e4m3 rows (ldb = d rounded up to 32 bytes, zero padded) with one
+// power-of-two scale per row, x_hat = 2^e q.  e = E - 8 for max |x| = f 2^E, f in [0.5, 1),
+// so every |x| 2^-e < 256 stays inside e4m3's finite range (448) and the scaling itself is
+// exact.  aux = (norm^2 of x_hat, ||x - x_hat|| rounded up); the low byte of the residual's
+// bits carries e + 127 (the residual is first rounded up to a multiple of 256 units in its
+// last place, so the stored value is still an upper bound).  qflags as for BF16, with
+// bit 1 = some value is not exact in the quantized row.
+// =====================================================================================
+__global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t n, int d, int ld,
+                                    uint8_t* __restrict__ Xq, int ldb, float2* __restrict__ aux,
+                                    unsigned* __restrict__ qflags) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned fl = 0, mx = 0;
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < n;
+       r += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+    float amax = 0.0f;
+    for (int k = lane; k < d; k += 32) amax = fmaxf(amax, fabsf(X[r * ld + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    int E = 0;
+    if (amax > 0.0f) frexpf(amax, &E);
+    const int e = amax > 0.0f ? min(127, max(-126, E - 8)) : 0;
+    const float inv = ldexpf(1.0f, -e), sc = ldexpf(1.0f, e);
+    float nrm = 0.0f;
+    double res = 0.0;
+    for (int k = lane; k < ldb; k += 32) {
+      const float x = k < d ? X[r * ld + k] : 0.0f;
+      const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3);
+      Xq[r * ldb + k] = (uint8_t)q;
+      const float xf = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;
+      nrm = __fmaf_rn(xf, xf, nrm);
+      const double dv = (double)x - (double)xf;
+      res += dv * dv;
+      fl |= (x != rintf(x)) ? 1u : 0u;
+      fl |= (xf != x) ? 2u : 0u;
+      mx = max(mx, __float_as_uint(fabsf(x)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+      res += __shfl_xor_sync(0xffffffffu, res, o);
+    }
+    if (lane == 0) {
+      uint32_t rb = __float_as_uint(__double2float_ru(sqrt(res) * (1.0 + 1e-12)));
+      rb = ((rb + 255u) & ~255u) | (uint32_t)(e + 127);
+      aux[r] = make_float2(nrm, __uint_as_float(rb));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    if (fl) atomicOr(&qflags[0], fl);
+    atomicMax(&qflags[1], mx);
+  }
+}
+
 cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv, int ldb,
-                            float2* aux, unsigned* qflags, cudaStream_t st) {
-  __nv_bfloat16* Xb = static_cast<__nv_bfloat16*>(Xbv);
+                            float2* aux, unsigned* qflags, int precision, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(qflags, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::min<int64_t>(ceil_div(n, 8), (int64_t)sm_count() * 16);
   ProfScope ps("quantize", st);
-  quantize_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, Xb, ldb, aux, qflags);
+  if (precision == 2)
+    quantize_fp8_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, static_cast<uint8_t*>(Xbv), ldb, aux,
+                                                          qflags);
+  else
+    quantize_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, static_cast<__nv_bfloat16*>(Xbv), ldb, aux,
+                                                      qflags);
   return cudaGetLastError();
 }
 
@@ -418,7 +483,7 @@ static_assert(sizeof(JoinSmem<0>) <= 115 * 1024 && sizeof(JoinSmem<1>) <= 115 * 
 struct PointsDev {
   const float* X;
   int ld;
-  const __nv_bfloat16* Xb;
+  const void* Xb;  // quantized rows: bfloat16 (BF16 form) or e4m3 bytes (FP8 form)
   int ldb;
   const float2* aux;
   const unsigned* qflags;
@@ -686,7 +751,7 @@ __device__ __forceinline__ void join_issue(JoinSmem<PREC>& s, const Batch& B, in
     if (B.np[B.rvb[r]] == 0) continue;
     const typename C::T* src =
         (PREC == 0) ? reinterpret_cast<const typename C::T*>(a.P.X + (int64_t)B.rid[r] * a.P.ld + c0)
-                    : reinterpret_cast<const typename C::T*>(a.P.Xb + (int64_t)B.rid[r] * a.P.ldb + c0);
+                    : reinterpret_cast<const typename C::T*>(a.P.Xb) + (int64_t)B.rid[r] * a.P.ldb + c0;
     bulk_g2s(&s.rows[buf][r][0], src, bytes, &s.bar[buf]);
   }
 }
@@ -710,6 +775,26 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
+
+__device__ __forceinline__ void mma_e4m3(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// One k-step of a quantized tile: m16n8k16 over BF16 rows, m16n8k32 over e4m3 rows.  Both
+// read 32 bytes of each row per step with the same fragment-to-byte layout, so ldmatrix
+// addresses are the same in bytes for the two forms.
+template <int PREC>
+__device__ __forceinline__ void mma_q(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  if constexpr (PREC == 2)
+    mma_e4m3(c, a, b);
+  else
+    mma_bf16(c, a, b);
+}
+// FP8 form: the power-of-two scale of a quantized row, from the low byte of its residual.
+__device__ __forceinline__ float q_scale(float rdq) { return __uint_as_float((__float_as_uint(rdq) & 0xffu) << 23); }
 
 // Bound on |D_tile(i,j) - D_fp32(i,j)| for the BF16 form (Higham-style: u = 2^-23 covers a
 // truncating accumulator; gamma_K = K u / (1 - K u)).  L2SQ:
@@ -1140,6 +1225,12 @@ struct WPrec<1> {
   static constexpr int RS = WDC + 8;
   static constexpr int VEC = 16;
 };
+template <>
+struct WPrec<2> {
+  using T = uint8_t;                  // e4m3 bytes
+  static constexpr int RS = WDC + 16; // 144-byte rows, as for BF16 in bytes per 64 columns
+  static constexpr int VEC = 32;      // whole k32 steps (32 bytes)
+};
 
 template <int PREC>
 struct __align__(16) WarpSlot {
@@ -1205,7 +1296,7 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
     x.m = (int)r[1];
     if (gl < x.m) {
       x.key = r[2 + gl];
-      if (PREC == 1) x.aux = r[2 + cap + gl];
+      if (PREC >= 1) x.aux = r[2 + cap + gl];
     }
   }
 }
@@ -1230,7 +1321,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   }
   __syncwarp();
   bool exact = false;
-  if (PREC == 1) {
+  if (PREC >= 1) {
     const unsigned fl = a.P.qflags[0];
     const float mxa = __uint_as_float(a.P.qflags[1]);
     exact = (fl == 0u) && ((double)d * (double)mxa * (double)mxa < 16777216.0);
@@ -1299,8 +1390,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       s.rpos[gb + row] = (uint8_t)gl;
       s.inv[hs] = (uint8_t)gl;  // storage slot -> pi position
       if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
-      s.rnd[gb + row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)aux) : 0.0f, key_dist(key));
-      if (PREC == 1) s.rdq[gb + row] = __uint_as_float((uint32_t)(aux >> 32));
+      s.rnd[gb + row] = make_float2(PREC >= 1 ? __uint_as_float((uint32_t)aux) : 0.0f, key_dist(key));
+      if (PREC >= 1) s.rdq[gb + row] = __uint_as_float((uint32_t)(aux >> 32));
     }
     if (lane == 0) s.nrq = 0;
     if (gl == 0) {
@@ -1340,18 +1431,19 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       __syncwarp();
       if (need) {
         const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id * a.P.ld + c0)
-                                   : reinterpret_cast<const T*>(a.P.Xb + (int64_t)id * a.P.ldb + c0);
+                                   : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)id * a.P.ldb + c0;
         bulk_g2s(&s.rows[gb + row][0], src, bytes, &s.bar);
       }
       ok = mbar_wait(&s.bar, phb, kWaitLimit);
       if (!__all_sync(0xffffffffu, ok)) break;
       phb ^= 1u;
       inflight = false;
-      if (PREC == 1) {
+      if (PREC >= 1) {
         // tiles one at a time; partial dot products wait in pd between chunks (d > 128),
         // and the last chunk takes the fire decisions straight from the accumulators
-        const __nv_bfloat16* rows = reinterpret_cast<const __nv_bfloat16*>(&s.rows[0][0]);
-        const int ksteps = (clen + 15) >> 4;
+        const T* rows = &s.rows[0][0];
+        constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
+        const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
         const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
         const bool first_c = (c == 0), last_c = (c + 1 == nch);
         const int g8 = lane >> 2, tg = lane & 3;
@@ -1379,13 +1471,13 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
           const int ra = I * 16 + (lane & 15);
           const int rb = J * 8 + (lane & 7);
-          const __nv_bfloat16* pa = rows + ra * C::RS + ((lane >> 4) << 3);
-          const __nv_bfloat16* pb = rows + rb * C::RS + (((lane >> 3) & 1) << 3);
+          const T* pa = rows + ra * C::RS + (lane >> 4) * KB;
+          const T* pb = rows + rb * C::RS + ((lane >> 3) & 1) * KB;
           for (int ks = 0; ks < ksteps; ++ks) {
             uint32_t fa[4], fb[2];
-            ldmatrix_x4(fa, pa + ks * 16);
-            ldmatrix_x2(fb, pb + ks * 16);
-            mma_bf16(acc, fa, fb);
+            ldmatrix_x4(fa, pa + ks * 2 * KB);
+            ldmatrix_x2(fb, pb + ks * 2 * KB);
+            mma_q<PREC>(acc, fa, fb);
           }
           if (!last_c) {
 #pragma unroll
@@ -1397,12 +1489,19 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
           const int pI[2] = {s.rpos[i0], s.rpos[i0 + 8]};
           const int pJ[2] = {s.rpos[j0], s.rpos[j0 + 1]};
+          float scI[2] = {1.0f, 1.0f}, scJ[2] = {1.0f, 1.0f};
+          if (PREC == 2) {  // the rows' power-of-two scales (exact products)
+            scI[0] = q_scale(s.rdq[i0]);
+            scI[1] = q_scale(s.rdq[i0 + 8]);
+            scJ[0] = q_scale(s.rdq[j0]);
+            scJ[1] = q_scale(s.rdq[j0 + 1]);
+          }
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             if (!ve[e]) continue;
             const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
             const int ge = i >> lw, eb = ge << lw;
-            const float gij = acc[e];
+            const float gij = (PREC == 2) ? acc[e] * scI[e >> 1] * scJ[e & 1] : acc[e];
             const float2 ri = rI[e >> 1], rj = rJ[e & 1];
             float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
                                       : __fsub_rn(1.0f, gij);
@@ -1463,7 +1562,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       return;
     }
     // queued re-decisions, one per lane: the FP32 rows of every pair load at once
-    if (PREC == 1 && nch > 0) {
+    if (PREC >= 1 && nch > 0) {
       const int nq = min(s.nrq, WRQ);
       for (int t = lane; t < nq; t += 32) {
         const int i = s.rq[t] >> 5, j = s.rq[t] & 31;
@@ -1586,7 +1685,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
-      if (PREC == 1 && st_check)
+      if (PREC >= 1 && st_check)
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[7]), (unsigned long long)st_check);
     }
   }
@@ -1644,6 +1743,12 @@ struct TPrec<1> {
   using T = __nv_bfloat16;
   static constexpr int RS = TDC + 8;  // 272 B: the 8 rows of an ldmatrix phase hit distinct banks
   static constexpr int VEC = 16;
+};
+template <>
+struct TPrec<2> {
+  using T = uint8_t;                  // e4m3 bytes
+  static constexpr int RS = TDC + 16; // 144 B: the 8 rows of an ldmatrix phase hit distinct banks
+  static constexpr int VEC = 32;
 };
 
 struct __align__(16) TeamKey {
@@ -1705,7 +1810,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   }
   __syncthreads();
   bool exact = false;
-  if (PREC == 1) {
+  if (PREC >= 1) {
     const unsigned fl = a.P.qflags[0];
     const float mxa = __uint_as_float(a.P.qflags[1]);
     exact = (fl == 0u) && ((double)d * (double)mxa * (double)mxa < 16777216.0);
@@ -1719,7 +1824,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   uint32_t nlo = (uint32_t)(r0[0] >> 32);
   int nm = (int)r0[1];
   uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
-  uint64_t naux = (PREC == 1 && tid < nm) ? r0[2 + R + tid] : 0ull;
+  uint64_t naux = (PREC >= 1 && tid < nm) ? r0[2 + R + tid] : 0ull;
 
   for (; p < cnt; p += gridDim.x) {
     const int64_t v = nv;
@@ -1733,7 +1838,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       nlo = (uint32_t)(rn[0] >> 32);
       nm = (int)rn[1];
       nkey = tid < nm ? rn[2 + tid] : kEmpty;
-      if (PREC == 1) naux = tid < nm ? rn[2 + R + tid] : 0ull;
+      if (PREC >= 1) naux = tid < nm ? rn[2 + R + tid] : 0ull;
     }
     // ---- visit order: rank of (h, id) among the m entries --------------------------------
     const uint32_t idl = key_id(keyl);
@@ -1789,8 +1894,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       s.prow[pi] = (uint8_t)row;
       s.rpos[row] = (uint8_t)pi;
       s.closer[pi] = pre ^ pbit;
-      s.rnd[row] = make_float2(PREC == 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
-      if (PREC == 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
+      s.rnd[row] = make_float2(PREC >= 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
+      if (PREC >= 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
     }
     if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
     __syncthreads();
@@ -1807,7 +1912,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       __syncthreads();
       if (has) {
         const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
-                                   : reinterpret_cast<const T*>(a.P.Xb + (int64_t)idl * a.P.ldb + c0);
+                                   : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)idl * a.P.ldb + c0;
         bulk_g2s(rowbase + ((size_t)st * TM + row) * C::RS, src, bytes, &s.bar[st]);
       }
     };
@@ -1825,9 +1930,9 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       infl &= ~(1u << st);
       const int clen = min(TDC, d - c * TDC);
       const T* rows = rowbase + (size_t)st * TM * C::RS;
-      if (PREC == 1) {
-        const __nv_bfloat16* rb16 = reinterpret_cast<const __nv_bfloat16*>(rows);
-        const int ksteps = (clen + 15) >> 4;
+      if (PREC >= 1) {
+        constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
+        const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
         const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
         const bool first_c = (c == 0), last_c = (c + 1 == nch);
         const int g = lane >> 2, tg = lane & 3;
@@ -1850,13 +1955,13 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
           const int ra = min(I * 16 + (lane & 15), TM - 1);
           const int rb = J * 8 + (lane & 7);
-          const __nv_bfloat16* pa = rb16 + ra * C::RS + ((lane >> 4) << 3);
-          const __nv_bfloat16* pb = rb16 + rb * C::RS + (((lane >> 3) & 1) << 3);
+          const T* pa = rows + ra * C::RS + (lane >> 4) * KB;
+          const T* pb = rows + rb * C::RS + ((lane >> 3) & 1) * KB;
           for (int ks = 0; ks < ksteps; ++ks) {
             uint32_t fa[4], fb[2];
-            ldmatrix_x4(fa, pa + ks * 16);
-            ldmatrix_x2(fb, pb + ks * 16);
-            mma_bf16(acc, fa, fb);
+            ldmatrix_x4(fa, pa + ks * 2 * KB);
+            ldmatrix_x2(fb, pb + ks * 2 * KB);
+            mma_q<PREC>(acc, fa, fb);
           }
           if (!last_c) {
 #pragma unroll
@@ -1867,12 +1972,19 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           // last chunk: distance and fire decision of each element
           const float2 rI[2] = {s.rnd[min(i0, TM - 1)], s.rnd[min(i0 + 8, TM - 1)]};
           const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
+          float scI[2] = {1.0f, 1.0f}, scJ[2] = {1.0f, 1.0f};
+          if (PREC == 2) {  // the rows' power-of-two scales (exact products)
+            scI[0] = q_scale(s.rdq[min(i0, TM - 1)]);
+            scI[1] = q_scale(s.rdq[min(i0 + 8, TM - 1)]);
+            scJ[0] = q_scale(s.rdq[j0]);
+            scJ[1] = q_scale(s.rdq[j0 + 1]);
+          }
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             if (!ve[e]) continue;
             const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
             const float2 ri = rI[e >> 1], rj = rJ[e & 1];
-            const float gij = acc[e];
+            const float gij = (PREC == 2) ? acc[e] * scI[e >> 1] * scJ[e & 1] : acc[e];
             float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
                                       : __fsub_rn(1.0f, gij);
             const float mx = fmaxf(ri.y, rj.y);
@@ -1935,7 +2047,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     }
 
     // queued re-decisions, one per thread: the FP32 rows of every pair load at once
-    if (PREC == 1 && nch > 0 && s.nrq > 0) {
+    if (PREC >= 1 && nch > 0 && s.nrq > 0) {
       const int nq = min(s.nrq, TRQ);
       for (int t = tid; t < nq; t += TM) {
         const int i = s.rq[t] >> 6, j = s.rq[t] & 63;
@@ -2051,7 +2163,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
     }
-    if (PREC == 1) {
+    if (PREC >= 1) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) st_check += __shfl_xor_sync(0xffffffffu, st_check, o);
       if (lane == 0 && st_check)
@@ -2471,7 +2583,7 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
   }
   const int3 gmax = make_int3(P.group_max[0], P.group_max[1], P.group_max[2]);
   prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
-                                                gmax, rs, P.precision == 1 ? P.aux : nullptr, P.vseg, stats);
+                                                gmax, rs, P.precision >= 1 ? P.aux : nullptr, P.vseg, stats);
   return cudaGetLastError();
 }
 
@@ -2482,7 +2594,7 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   JoinArgs a;
   a.P.X = P.X;
   a.P.ld = P.ld;
-  a.P.Xb = static_cast<const __nv_bfloat16*>(P.Xb);
+  a.P.Xb = P.Xb;
   a.P.ldb = P.ldb;
   a.P.aux = P.aux;
   a.P.qflags = P.qflags;
@@ -2515,24 +2627,33 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   return a;
 }
 
+template <int METRIC>
+cudaError_t launch_warp_p(int prec, const JoinArgs& a, cudaStream_t st, const char* name, bool so) {
+  if (prec == 2) return launch_join_warp_t<METRIC, 2>(a, st, name, so);
+  if (prec == 1) return launch_join_warp_t<METRIC, 1>(a, st, name, so);
+  return launch_join_warp_t<METRIC, 0>(a, st, name, so);
+}
+template <int METRIC>
+cudaError_t launch_team_p(int prec, const JoinArgs& a, cudaStream_t st, const char* name, bool so) {
+  if (prec == 2) return launch_join_team_t<METRIC, 2>(a, st, name, so);
+  if (prec == 1) return launch_join_team_t<METRIC, 1>(a, st, name, so);
+  return launch_join_team_t<METRIC, 0>(a, st, name, so);
+}
+
 cudaError_t dispatch_join(const PointsSet& P, const JoinArgs& a, cudaStream_t st, const char* name,
                           bool setup_only = false) {
-  if (P.precision == 1 && (!P.Xb || !P.aux || !P.qflags) && !setup_only) return cudaErrorInvalidValue;
+  if (P.precision >= 1 && (!P.Xb || !P.aux || !P.qflags) && !setup_only) return cudaErrorInvalidValue;
   cudaError_t e;
   // pools of up to 32 entries: one warp per vertex; 33..64 entries: a two-warp team per
   // vertex (batched CTAs with dimension chunks for FP32 rows longer than 128)
   const char* wname = (name[0] == 'r') ? "rnd_join_warp" : "final_prune_warp";
   const bool so = setup_only;
-  if (P.metric == 0)
-    e = P.precision == 1 ? launch_join_warp_t<0, 1>(a, st, wname, so) : launch_join_warp_t<0, 0>(a, st, wname, so);
-  else
-    e = P.precision == 1 ? launch_join_warp_t<1, 1>(a, st, wname, so) : launch_join_warp_t<1, 0>(a, st, wname, so);
+  e = P.metric == 0 ? launch_warp_p<0>(P.precision, a, st, wname, so) : launch_warp_p<1>(P.precision, a, st, wname, so);
   if (e != cudaSuccess) return e;
-  if (P.precision == 1 || P.d <= 128) {  // pools of 33..64 entries: a two-warp team per vertex
+  if (P.precision >= 1 || P.d <= 128) {  // pools of 33..64 entries: a two-warp team per vertex
     const char* tname = (name[0] == 'r') ? "rnd_join_team" : "final_prune_team";
-    if (P.metric == 0)
-      return P.precision == 1 ? launch_join_team_t<0, 1>(a, st, tname, so) : launch_join_team_t<0, 0>(a, st, tname, so);
-    return P.precision == 1 ? launch_join_team_t<1, 1>(a, st, tname, so) : launch_join_team_t<1, 0>(a, st, tname, so);
+    return P.metric == 0 ? launch_team_p<0>(P.precision, a, st, tname, so)
+                         : launch_team_p<1>(P.precision, a, st, tname, so);
   }
   // FP32 rows of more than 128 dimensions: batched CTAs with dimension chunks
   if (P.metric == 0) return launch_join_t<0, 0>(a, st, name, so);

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "grnnd.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
 L2SQ, IP = 0, 1
-FP32, BF16 = 0, 1
+FP32, BF16, FP8 = 0, 1, 2
 ORDER_RANDOM, ORDER_ASC, ORDER_DESC = 0, 1, 2
 EMPTY = 0xFFFFFFFFFFFFFFFF
 

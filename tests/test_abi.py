@@ -43,6 +43,7 @@ def test_defaults(L):
     (dict(S=2, R=4, rho=1.5), "rho"),
     (dict(S=2, R=4, metric=7), "metric"),
     (dict(S=2, R=4, order=9), "order"),
+    (dict(S=2, R=4, precision=3), "precision"),   # FP32, BF16 and FP8 only
 ])
 def test_build_rejects_bad_params_before_any_launch(L, kw, frag):
     X = np.zeros((10, 3), np.float32)

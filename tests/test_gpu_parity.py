@@ -388,6 +388,108 @@ def test_bf16_build_continuous_data(G, orc):
 
 
 # ---------------------------------------------------------------------------------------
+# FP8 form: e4m3 Gram tiles with a power-of-two scale per row, the same bound and
+# FP32 re-decisions
+# ---------------------------------------------------------------------------------------
+
+def _e4m3(a):
+    """Round-to-nearest-even float64 -> e4m3 (3 mantissa bits, smallest normal 2^-6,
+    subnormal step 2^-9, saturating at 448), returned as float64."""
+    a = np.asarray(a, np.float64)
+    m = np.abs(a)
+    E = np.floor(np.log2(np.where(m > 0, m, 1.0)))
+    step = 2.0 ** (np.maximum(E, -6.0) - 3.0)
+    q = np.minimum(np.rint(m / step) * step, 448.0)
+    return np.sign(a) * np.where(m > 0, q, 0.0)
+
+
+def _fp8_rows(X):
+    """The FP8 form's dequantised rows: per row the scale 2^e with e = E - 8 for
+    max|x| = f 2^E, f in [0.5, 1) (e = 0 for a zero row), then x_hat = 2^e e4m3(x 2^-e)."""
+    X = np.asarray(X, np.float64)
+    amax = np.abs(X).max(1)
+    _, E = np.frexp(amax)
+    e = np.where(amax > 0, np.clip(E - 8, -126, 127), 0).astype(np.float64)
+    sc = 2.0 ** e
+    return _e4m3(X / sc[:, None]) * sc[:, None]
+
+
+def test_e4m3_emulation_pins():
+    # the emulation against values fixed by the e4m3 format itself
+    assert list(_e4m3([0.0, 1.0, 1.0625, 1.125, 1.1875, 17.0, 448.0, 500.0, -3.3, 2.0 ** -9, 2.0 ** -10 * 1.5])) == \
+        [0.0, 1.0, 1.0, 1.125, 1.25, 16.0, 448.0, 448.0, -3.25, 2.0 ** -9, 2.0 ** -9]
+
+
+@pytest.mark.parametrize("n,d,S,R,metric", [(3000, 16, 8, 16, 0), (2500, 128, 32, 64, 0), (1800, 40, 16, 32, 1),
+                                            (1500, 200, 16, 32, 0), (1800, 40, 32, 64, 1), (2000, 100, 40, 64, 0)])
+def test_fp8_build_is_exact_on_integer_data(G, orc, n, d, S, R, metric):
+    # integers of magnitude <= 16 are exact in e4m3 at any power-of-two scale; with
+    # d * max|x|^2 < 2^24 every product and FP32 partial sum is exact, so the FP8 form must
+    # return the FP32 form's graph bit for bit (and the oracle's), with no re-decision.
+    X = synth.small_integers(n, d, -8, 8, seed=d + n + 1)
+    a = G.build(X, S=S, R=R, T1=2, T2=4, seed=3, metric=metric, precision=G.FP32).to_numpy()
+    gq = G.build(X, S=S, R=R, T1=2, T2=4, seed=3, metric=metric, precision=G.FP8)
+    b = gq.to_numpy()
+    for x, y in zip(a, b):
+        assert (x == y).all()
+    assert gq.stats()["rechecks"] == 0
+    wids, _, wdeg, _ = orc.build_graph(X, S, R, 2, 4, 0.6, 3, metric=metric)
+    assert (b[0] == wids).all() and (b[2] == wdeg).all()
+
+
+def test_fp8_exact_mode_needs_full_fp32_accumulation(G):
+    # integers in [-16, 16] over d = 1024: dot products reach 2^18 with every unit significant,
+    # so an accumulator that kept fewer than 19 significant bits would change distances and the
+    # graph; the FP8 form must still equal the FP32 form (its exact mode assumes FP32 sums).
+    X = synth.small_integers(1500, 1024, -16, 16, seed=21)
+    kw = dict(S=16, R=32, T1=2, T2=3, seed=4)
+    a = G.build(X, precision=G.FP32, **kw).to_numpy()
+    gq = G.build(X, precision=G.FP8, **kw)
+    for x, y in zip(a, gq.to_numpy()):
+        assert (x == y).all()
+    assert gq.stats()["rechecks"] == 0
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_fp8_build_continuous_data(G, orc, metric):
+    """Continuous data: e4m3 rows are far from exact, so many decisions are re-taken in
+    FP32.  Invariants hold, every recorded distance is within the stated bound (computed
+    from the emulated e4m3 rows) of FP64, and recall stays close to the FP32 form's."""
+    if metric == 0:
+        X, Q = synth.gaussian_mixture(6000, 48, 12, 6.0, 1.0, seed=5, nq=300)
+        kw = dict(S=16, R=32, T1=3, T2=6, seed=2)
+    else:
+        X, Q = synth.deep_like(6000, 300, d=64, seed=6)
+        kw = dict(S=16, R=32, T1=3, T2=6, seed=2, metric=1)
+    ga = G.build(X, precision=G.FP32, **kw)
+    gq = G.build(X, precision=G.FP8, **kw)
+    ids, dist, deg = gq.to_numpy()
+    assert gq.stats()["rechecks"] > 0
+    xq = _fp8_rows(X)
+    nrm = (xq ** 2).sum(1)
+    res = np.sqrt(((X.astype(np.float64) - xq) ** 2).sum(1))
+    d = X.shape[1]
+    for v in range(0, len(X), 7):
+        row = ids[v, :deg[v]]
+        assert v not in row and len(set(row.tolist())) == len(row) and (row >= 0).all()
+        for j, u in enumerate(row[:8]):
+            ref = orc.dist(X[v], X[u], metric=metric)
+            if metric == 0:
+                bound = _bf16_bound(ref, nrm[v], nrm[u], res[v], res[u], d)
+            else:
+                u_ = 2.0 ** -23
+                g = d * u_ / (1 - d * u_)
+                si, sj = np.sqrt(nrm[v]), np.sqrt(nrm[u])
+                tot = (g + 2 * u_) * si * sj + 2 * u_ * abs(ref) + res[v] * sj + res[u] * si + res[v] * res[u]
+                bound = (tot + (d + 3) * u_ * (abs(ref) + si * sj + tot)) * 1.0001
+            assert abs(dist[v, j] - ref) <= bound * 1.001 + 1e-30
+    gt, _ = orc.brute_knn(X, Q, 10, metric=metric)
+    ra = orc.recall_at_k(ga.search(Q, 10, 32), gt)
+    rq = orc.recall_at_k(gq.search(Q, 10, 32), gt)
+    assert rq >= ra - 0.02 and rq > 0.85
+
+
+# ---------------------------------------------------------------------------------------
 # in-place pool updates (the build's own mode)
 # ---------------------------------------------------------------------------------------
 
@@ -413,13 +515,13 @@ def test_join_round_in_place_matches_oracle(G, orc, n, d, S, R, hist):
 # batched builds: each build of a batch equals the same build alone
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision,metric", [("fp32", 0), ("bf16", 0), ("bf16", 1), ("fp32", 1)])
+@pytest.mark.parametrize("precision,metric", [("fp32", 0), ("bf16", 0), ("bf16", 1), ("fp32", 1), ("fp8", 0)])
 def test_build_batch_equals_single_builds(G, precision, metric):
     sizes = [300, 9, 1000, 57, 2000, 128]
     parts = [synth.small_integers(m, 24, -8, 8, seed=100 + i) for i, m in enumerate(sizes)]
     X = np.concatenate(parts)
     off = np.concatenate([[0], np.cumsum(sizes)])
-    prec = {"fp32": G.FP32, "bf16": G.BF16}[precision]
+    prec = {"fp32": G.FP32, "bf16": G.BF16, "fp8": G.FP8}[precision]
     kw = dict(S=8, R=16, T1=2, T2=4, rho=0.6, seed=11, metric=metric, precision=prec)
     gs = G.build_batch(torch.from_numpy(X).cuda(), off, **kw)
     Q = synth.small_integers(50, 24, -8, 8, seed=999)
@@ -453,10 +555,10 @@ def test_build_batch_mixed_data_and_free_order(G):
 # join launch shapes (grnnd_tuning) change speed only
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision,metric", [("bf16", 0), ("fp32", 0), ("bf16", 1)])
+@pytest.mark.parametrize("precision,metric", [("bf16", 0), ("fp32", 0), ("bf16", 1), ("fp8", 1)])
 def test_tunings_give_the_same_graph(G, precision, metric):
     X = synth.small_integers(3000, 40, -8, 8, seed=77)
-    prec = {"fp32": G.FP32, "bf16": G.BF16}[precision]
+    prec = {"fp32": G.FP32, "bf16": G.BF16, "fp8": G.FP8}[precision]
     kw = dict(S=24, R=48, T1=2, T2=5, seed=2, metric=metric, precision=prec)
     ref = G.build(X, **kw).to_numpy()
     for gm, w, t in [((0, 16, 32), 0, 0), ((0, 0, 32), 1, 2), ((8, 16, 16), 2, 4), ((0, 16, 16), 0, 1),
