@@ -49,10 +49,11 @@ def _args():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16, fp8 (the last one is the headline)")
-    ap.add_argument("--report", choices=["precision", "ablation", "batched"], default=None,
+    ap.add_argument("--report", choices=["precision", "ablation", "batched", "serve"], default=None,
                     help="precision: per-form distance error against FP64 and recall loss on a "
                          "GIST-shaped (d=960, continuous) or DEEP-shaped (d=96, IP) set of --n points")
     ap.add_argument("--shape", choices=["gist", "deep"], default="gist")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="serve report: length of the arrival stream")
     return ap.parse_args()
 
 
@@ -370,6 +371,110 @@ def run_batched_report(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve_report(args):
+    """Serving loop (grnnd_server_*): a Poisson stream of requests at 20 per second, each a
+    build (n log-uniform in [5k, 500k], d 128 SIFT-shaped L2 with S 32, R 64, T1 4, T2 15, or
+    d 96 DEEP-shaped inner product with S 16, R 32, T1 3, T2 10; BF16 tiles with FP32
+    re-decisions) or a search of 1..1024 queries (k 10, beam 64) against a resident index,
+    admitted under a 150 GB HBM budget on 4 slots.  Points and queries come from pinned host
+    memory (slices of two seeded 2M-point sets).  Reports p50/p99 latency per kind (submit to
+    done, the server's clock), then a burst of the stream's builds all submitted at once
+    against the same builds run one after another through grnnd_build_ex (FP32, the plain
+    per-request path, and BF16).  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd, synth
+    rng = np.random.default_rng(args.seed)
+    base = {128: synth.sift_like(2_000_000, 20000, seed=args.seed + 1),
+            96: synth.deep_like(2_000_000, 20000, seed=args.seed + 2)}
+    base = {d: (torch.from_numpy(X).pin_memory(), torch.from_numpy(Q).pin_memory()) for d, (X, Q) in base.items()}
+    cfg = {128: dict(S=32, R=64, T1=4, T2=15, rho=0.6, metric=grnnd.L2SQ),
+           96: dict(S=16, R=32, T1=3, T2=10, rho=0.6, metric=grnnd.IP)}
+    # the request stream: arrival times and contents, drawn up front
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / 20.0)
+        if t > args.serve_seconds:
+            break
+        if not reqs or rng.random() < 0.5:
+            n = int(np.exp(rng.uniform(np.log(5000), np.log(500000))))
+            d = int(rng.choice([96, 128]))
+            o = int(rng.integers(0, 2_000_000 - n))
+            reqs.append(("build", t, d, o, n))
+        else:
+            nq = int(rng.integers(1, 1025))
+            reqs.append(("search", t, None, int(rng.integers(0, 20000 - nq)), nq))
+    budget = 150 << 30
+    srv = grnnd.Server(slots=4, hbm_budget=budget)
+    # warm-up (kernel set-up, pool growth): one build of each shape, then released
+    for d in (96, 128):
+        srv.release(srv.wait(srv.submit_build(base[d][0][:20000], precision=grnnd.BF16, seed=1, **cfg[d]))["index"])
+    ids, built, kinds = [], [], []
+    t0 = time.perf_counter()
+    for kind, ta, d, o, n in reqs:
+        delay = ta - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        if kind == "build":
+            rid = srv.submit_build(base[d][0][o:o + n], precision=grnnd.BF16, seed=len(built), **cfg[d])
+            built.append((rid, d))
+        else:
+            idx, dq = built[int(rng.integers(0, len(built)))]
+            rid = srv.submit_search(idx, base[dq][1][o:o + n], 10, 64)
+        ids.append(rid)
+        kinds.append(kind)
+    infos = [srv.wait(r) for r in ids]
+    wall = time.perf_counter() - t0
+    st = srv.status()
+    lat = {k: sorted(1e3 * (i["t_done"] - i["t_submit"]) for i in infos if i["kind"] == k) for k in ("build", "search")}
+    pts = sum(i["units"] for i in infos if i["kind"] == "build")
+    nq_tot = sum(i["units"] for i in infos if i["kind"] == "search")
+    sb = [i["batch"] for i in infos if i["kind"] == "search"]
+    for rid, _ in built:
+        srv.release(rid)
+    # burst: the stream's builds all at once, against the same builds one after another
+    bl = [(d, o, n) for kind, _, d, o, n in reqs if kind == "build"]
+    t1 = time.perf_counter()
+    bids = [srv.submit_build(base[d][0][o:o + n], precision=grnnd.BF16, seed=i, **cfg[d]) for i, (d, o, n) in enumerate(bl)]
+    for r in bids:
+        srv.wait(r)
+    burst = time.perf_counter() - t1
+    for r in bids:
+        srv.release(r)
+    srv.close()
+    seq = {}
+    for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16)):
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for i, (d, o, n) in enumerate(bl):
+            g = grnnd.build(base[d][0][o:o + n], precision=prec, seed=i, **cfg[d])
+            del g
+        torch.cuda.synchronize()
+        seq[name] = time.perf_counter() - t2
+    bp = sum(n for _, _, n in bl)
+
+    def pct(xs, q):
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+    line = {"report": "serve",
+            "workload": "Poisson stream, 20 requests/s for %.0f s: builds (n log-uniform [5k, 500k]; d 128 SIFT-shaped "
+                        "L2 S32 R64 T1 4 T2 15, or d 96 DEEP-shaped IP S16 R32 T1 3 T2 10; BF16) and searches "
+                        "(1..1024 queries, k 10, beam 64) on resident indices; 150 GB budget, 4 slots" % args.serve_seconds,
+            "requests": len(infos), "builds": len(lat["build"]), "searches": len(lat["search"]),
+            "build_latency_ms": {"p50": pct(lat["build"], 0.5), "p99": pct(lat["build"], 0.99)},
+            "search_latency_ms": {"p50": pct(lat["search"], 0.5), "p99": pct(lat["search"], 0.99)},
+            "stream_points_per_s": pts / wall, "stream_queries_per_s": nq_tot / wall, "stream_wall_s": wall,
+            "search_batch_mean": float(np.mean(sb)) if sb else None, "search_batch_max": max(sb) if sb else None,
+            "peak_bytes": st["peak_bytes"],
+            "burst": {"builds": len(bl), "points": bp, "server_bf16_s": burst, "server_points_per_s": bp / burst,
+                      "sequential_fp32_s": seq["fp32"], "sequential_fp32_points_per_s": bp / seq["fp32"],
+                      "sequential_bf16_s": seq["bf16"], "sequential_bf16_points_per_s": bp / seq["bf16"],
+                      "speedup_vs_sequential_fp32": seq["fp32"] / burst}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist()
@@ -381,6 +486,9 @@ def main():
         return
     if args.report == "batched":
         run_batched_report(args)
+        return
+    if args.report == "serve":
+        run_serve_report(args)
         return
     if args.impl == "reference":
         if world > 1:

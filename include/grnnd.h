@@ -199,6 +199,96 @@ GRNND_API int grnnd_profile_begin(void);
 GRNND_API int grnnd_profile_end(grnnd_kernel_time *out, int32_t max_entries, int32_t *n_entries);
 
 /* ------------------------------------------------------------------------- */
+/* Serving loop (no counterpart in the paper, which builds one graph per run)  */
+/* ------------------------------------------------------------------------- */
+
+/* A request loop on the current device.  Build requests (each makes one resident
+ * index: a graph and its points) and search requests against resident indices are
+ * submitted from any host thread as they arrive.  `slots` worker threads each own a
+ * non-blocking CUDA stream, and every admitted request runs on a free slot, so requests
+ * that arrive while others run overlap with them on the device.
+ *   Admission: requests are considered in arrival order; one is admitted when a slot is
+ *   free and its device bytes fit the HBM budget beside the resident indices and the
+ *   requests in flight (a build: points, graph and scratch, as grnnd_build_ex allocates;
+ *   a search: its queries and results).  A request that does not fit yet, or a search
+ *   whose index is still being built, waits without holding back later requests.  A
+ *   build larger than the whole budget fails with GRNND_ENOMEM.
+ *   Continuous batching of searches: a slot that takes a search also takes every other
+ *   waiting search of the same index with the same k and beam (up to max_batch_queries
+ *   queries together) and serves them with one search launch.  Each query's result does
+ *   not depend on the other queries, so it is the same alone and in any mix.
+ *   Memory: builds and searches allocate from the server's own stream-ordered memory pool,
+ *   so one request's allocations and frees never wait on another request's kernels.
+ * Every entry point is thread-safe.  Buffers passed to a submit call (points, queries,
+ * ids_out; host or device memory) must stay valid until the request is done. */
+typedef struct grnnd_server grnnd_server; /* opaque */
+
+typedef struct grnnd_server_config {
+    int32_t slots;              /* requests on the device at once, 1..64 */
+    uint64_t hbm_budget;        /* device bytes for resident indices + requests in flight, > 0 */
+    int64_t max_batch_queries;  /* queries one search launch may merge; 0 = 65536 */
+} grnnd_server_config;
+
+typedef enum { GRNND_REQ_BUILD = 0, GRNND_REQ_SEARCH = 1 } grnnd_request_kind;
+typedef enum { GRNND_REQ_QUEUED = 0, GRNND_REQ_RUNNING = 1, GRNND_REQ_DONE = 2 } grnnd_request_state;
+
+typedef struct grnnd_request_info {
+    int64_t id;          /* request id; a build's id is also the id of the index it makes */
+    int32_t kind;        /* grnnd_request_kind */
+    int32_t state;       /* grnnd_request_state */
+    int32_t status;      /* grnnd_status of the request once done */
+    int32_t batch;       /* search: requests served by the same launch (1 = alone) */
+    int64_t index;       /* index built or searched */
+    int64_t units;       /* points (build) or queries (search) */
+    uint64_t bytes;      /* device bytes reserved while it ran */
+    double t_submit;     /* seconds on the server's steady clock: submitted, */
+    double t_admit;      /* admitted to a slot, */
+    double t_done;       /* done */
+    char message[128];   /* grnnd_last_error text of a failed request */
+} grnnd_request_info;
+
+/* Creates a server on the current device.  cfg: slots 1..64, hbm_budget > 0. */
+GRNND_API int grnnd_server_create(const grnnd_server_config *cfg, grnnd_server **out);
+
+/* Queues a build of n x d points (host or device) with params p (copied; p->stream and
+ * p->hbm_budget are ignored: the request runs on its slot's stream under the server's
+ * budget).  *id_out = the request id = the index id.  Arguments are validated as for
+ * grnnd_build_ex before anything is queued. */
+GRNND_API int grnnd_server_submit_build(grnnd_server *s, const float *points, int64_t n, int32_t d,
+                                        const grnnd_params *p, int64_t *id_out);
+
+/* Queues a search of nq queries (host or device rows of the index's d floats) on index
+ * `index` (a build request id, possibly still queued or running); ids_out (host or
+ * device, nq x k int32) receives what grnnd_search returns.  1 <= k <= beam <= 256.  A
+ * search of an index that failed or was released completes with GRNND_EINVAL. */
+GRNND_API int grnnd_server_submit_search(grnnd_server *s, int64_t index, const float *queries, int64_t nq,
+                                         int32_t k, int32_t beam, int32_t *ids_out, int64_t *id_out);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for request `id` and fills *info (may be
+ * NULL).  Returns the request's status once it is done (and then forgets the request), or
+ * GRNND_ETIMEOUT if it is still queued or running (info then holds its current state).
+ * An unknown id is GRNND_EINVAL. */
+GRNND_API int grnnd_server_wait(grnnd_server *s, int64_t id, double timeout_s, grnnd_request_info *info);
+
+/* The resident graph of a finished build (borrowed: valid until grnnd_server_release or
+ * grnnd_server_destroy; do not grnnd_free it).  GRNND_EBUSY while the build is queued or
+ * running, GRNND_EINVAL if it failed, was released or is unknown. */
+GRNND_API int grnnd_server_index(grnnd_server *s, int64_t index, const grnnd_graph **g);
+
+/* Frees a resident index.  GRNND_EBUSY while its build or a search of it is queued or
+ * running. */
+GRNND_API int grnnd_server_release(grnnd_server *s, int64_t index);
+
+/* Counters (any pointer may be NULL): device bytes reserved now and at most so far
+ * (resident indices + requests in flight), requests queued and running, resident indices. */
+GRNND_API int grnnd_server_status(grnnd_server *s, uint64_t *bytes_in_use, uint64_t *peak_bytes,
+                                  int32_t *queued, int32_t *running, int32_t *indices);
+
+/* Finishes the requests that are running, fails the queued ones (GRNND_EBUSY), frees
+ * every index and the server. */
+GRNND_API void grnnd_server_destroy(grnnd_server *s);
+
+/* ------------------------------------------------------------------------- */
 /* Step-level entry points on caller-owned device buffers                     */
 /* ------------------------------------------------------------------------- */
 

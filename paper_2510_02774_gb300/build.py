@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libgrnnd.so")
-UNITS = ["pool_kernels.cu", "search_kernels.cu", "capi.cu", "noalloc.cu"]
+UNITS = ["pool_kernels.cu", "search_kernels.cu", "capi.cu", "noalloc.cu", "server.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -16,28 +16,6 @@
 #include "grnnd.h"
 #include "internal.h"
 
-// Device memory of one build call; the graphs of a batched build share it, and it is freed
-// with the last of them.
-struct GraphBlock {
-  void* points = nullptr;
-  void* graph = nullptr;
-  ~GraphBlock() {
-    if (points) cudaFree(points);
-    if (graph) cudaFree(graph);
-  }
-};
-
-struct grnnd_graph {
-  int64_t n = 0;
-  int32_t d = 0, ld = 0, R = 0, metric = 0, entry = 0;
-  float* points = nullptr;   // n x ld, zero padded
-  int32_t* ids = nullptr;    // n x R
-  float* dists = nullptr;    // n x R
-  int32_t* deg = nullptr;    // n
-  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  std::shared_ptr<GraphBlock> mem;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -68,13 +46,26 @@ bool is_device_ptr(const void* p) {
 int32_t round4(int32_t d) { return (d + 3) & ~3; }
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Owned device allocation released on scope exit.
+// Owned device allocation released on scope exit: cudaMalloc / cudaFree, or stream-ordered
+// from a memory pool on the given stream.
 struct DevMem {
   void* p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t st = nullptr;
+  DevMem() = default;
+  DevMem(const grnnd::AllocMode& am, cudaStream_t s) : pool(am.pool), st(s) {}
   ~DevMem() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (pool)
+        cudaFreeAsync(p, st);
+      else
+        cudaFree(p);
+    }
   }
-  cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+  cudaError_t alloc(size_t bytes) {
+    if (!bytes) bytes = 16;
+    return pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMalloc(&p, bytes);
+  }
   void* release() {
     void* q = p;
     p = nullptr;
@@ -417,37 +408,62 @@ int check_params(const grnnd_params* p) {
   return GRNND_OK;
 }
 
-// One build call over n points: a single build (offsets == nullptr) or nbuild independent
-// builds of the rows [offsets[b], offsets[b+1]) (ids local to each build, one graph each).
-// A batched call records the whole pass in one CUDA graph and launches it once.
-int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p, const int64_t* offsets,
-               int32_t nbuild, grnnd_graph** graphs_out) {
-  const bool batched = offsets != nullptr;
+// Device bytes of one build call: what stays with the graphs (points + graph) and the
+// scratch released at the end (pools, round workspace, quantized rows, segments).
+struct BuildSizes {
+  size_t pts_b, q_b, pool_b, deg_b, ws_b, ent_b, graph_b, stats_b, seg_b, scratch_b;
+};
+BuildSizes build_sizes(int64_t n, int32_t d, const grnnd_params* p, bool batched, int32_t nbuild) {
+  BuildSizes z;
   const int32_t R = p->R, ld = round4(d);
   // quantized forms: a BF16 copy (rows of d rounded up to 16 elements) or an e4m3 copy
   // (rows of d rounded up to 32 bytes), per-row terms and dataset flags
   const bool quant = p->precision != GRNND_FP32;
   const int32_t ldb = p->precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
   const size_t qelem = p->precision == GRNND_FP8 ? 1 : 2;
+  z.pts_b = al256((size_t)n * ld * 4);
+  z.q_b = quant ? al256((size_t)n * ldb * qelem) + al256((size_t)n * 8) + 256 : 0;
+  z.pool_b = al256((size_t)n * R * 8);
+  z.deg_b = al256((size_t)n * 4);
+  z.ws_b = grnnd::workspace_bytes(n, R);
+  z.ent_b = batched ? grnnd::entry_batch_workspace_bytes(nbuild, d) : grnnd::entry_workspace_bytes(n, d);
+  z.graph_b = al256((size_t)n * R * 4) * 2 + z.deg_b;
+  z.stats_b = 256 + al256((size_t)nbuild * 4);  // counters, then one entry per build
+  z.seg_b = batched ? al256((size_t)n * 8) + al256(((size_t)nbuild + 1) * 8) : 0;
+  z.scratch_b = 2 * z.pool_b + 2 * z.deg_b + std::max(z.ws_b, z.ent_b) + z.stats_b + z.q_b + z.seg_b;
+  return z;
+}
+
+// One build call over n points: a single build (offsets == nullptr) or nbuild independent
+// builds of the rows [offsets[b], offsets[b+1]) (ids local to each build, one graph each).
+// A batched call records the whole pass in one CUDA graph and launches it once.
+int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p, const int64_t* offsets,
+               int32_t nbuild, grnnd_graph** graphs_out, const grnnd::AllocMode& am = grnnd::AllocMode()) {
+  const bool batched = offsets != nullptr;
+  const int32_t R = p->R, ld = round4(d);
+  const bool quant = p->precision != GRNND_FP32;
+  const int32_t ldb = p->precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
+  const size_t qelem = p->precision == GRNND_FP8 ? 1 : 2;
   cudaStream_t st = (cudaStream_t)p->stream;
 
-  const size_t pts_b = al256((size_t)n * ld * 4);
-  const size_t q_b = quant ? al256((size_t)n * ldb * qelem) + al256((size_t)n * 8) + 256 : 0;
-  const size_t pool_b = al256((size_t)n * R * 8), deg_b = al256((size_t)n * 4);
-  const size_t ws_b = grnnd::workspace_bytes(n, R);
-  const size_t ent_b = batched ? grnnd::entry_batch_workspace_bytes(nbuild, d) : grnnd::entry_workspace_bytes(n, d);
-  const size_t graph_b = al256((size_t)n * R * 4) * 2 + deg_b;
-  const size_t stats_b = 256 + al256((size_t)nbuild * 4);  // counters, then one entry per build
-  const size_t seg_b = batched ? al256((size_t)n * 8) + al256(((size_t)nbuild + 1) * 8) : 0;
-  const size_t scratch_b = 2 * pool_b + 2 * deg_b + std::max(ws_b, ent_b) + stats_b + q_b + seg_b;
+  const BuildSizes z = build_sizes(n, d, p, batched, nbuild);
+  const size_t pts_b = z.pts_b, q_b = z.q_b, pool_b = z.pool_b, deg_b = z.deg_b, ws_b = z.ws_b,
+               ent_b = z.ent_b, graph_b = z.graph_b, stats_b = z.stats_b, scratch_b = z.scratch_b;
   if (p->hbm_budget && pts_b + graph_b + scratch_b > p->hbm_budget)
     return fail(GRNND_ENOMEM, "build needs " + std::to_string(pts_b + graph_b + scratch_b) +
                                   " bytes, above hbm_budget " + std::to_string(p->hbm_budget));
 
   auto block = std::make_shared<GraphBlock>();
-  DevMem mscratch;
-  GR_CU(cudaMalloc(&block->points, pts_b));
-  GR_CU(cudaMalloc(&block->graph, graph_b));
+  DevMem mscratch(am, st);
+  if (am.pool) {
+    block->pooled = true;
+    block->free_stream = am.free_stream;
+    GR_CU(cudaMallocFromPoolAsync(&block->points, pts_b, am.pool, st));
+    GR_CU(cudaMallocFromPoolAsync(&block->graph, graph_b, am.pool, st));
+  } else {
+    GR_CU(cudaMalloc(&block->points, pts_b));
+    GR_CU(cudaMalloc(&block->graph, graph_b));
+  }
   GR_CU(mscratch.alloc(scratch_b));
   float* X = static_cast<float*>(block->points);
   char* gp = static_cast<char*>(block->graph);
@@ -654,15 +670,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
 
 int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
                    grnnd_graph** graph_out) {
-  if (graph_out) *graph_out = nullptr;
-  if (!graph_out) return fail(GRNND_EINVAL, "graph_out is NULL");
-  int rc = check_params(p);
-  if (rc) return rc;
-  if (!points) return fail(GRNND_EINVAL, "points is NULL");
-  if (n < 2 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n must be in [2, 2^31 - 2]");
-  if (d < 1) return fail(GRNND_EINVAL, "d must be >= 1");
-  if ((int64_t)p->S > n - 1) return fail(GRNND_EINVAL, "need 1 <= S <= min(R, n-1)");
-  return build_core(points, n, d, p, nullptr, 1, graph_out);
+  return grnnd::build_with(points, n, d, p, grnnd::AllocMode(), graph_out);
 }
 
 int grnnd_build_batch(const float* points, const int64_t* offsets, int32_t nbuild, int32_t d,
@@ -823,3 +831,30 @@ void grnnd_free(grnnd_graph* g) {
 }
 
 }  // extern "C"
+
+namespace grnnd {
+int validate_build(const float* points, int64_t n, int32_t d, const grnnd_params* p) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!points) return fail(GRNND_EINVAL, "points is NULL");
+  if (n < 2 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n must be in [2, 2^31 - 2]");
+  if (d < 1) return fail(GRNND_EINVAL, "d must be >= 1");
+  if ((int64_t)p->S > n - 1) return fail(GRNND_EINVAL, "need 1 <= S <= min(R, n-1)");
+  return GRNND_OK;
+}
+
+int build_with(const float* points, int64_t n, int32_t d, const grnnd_params* p, const AllocMode& am,
+               grnnd_graph** graph_out) {
+  if (graph_out) *graph_out = nullptr;
+  if (!graph_out) return fail(GRNND_EINVAL, "graph_out is NULL");
+  int rc = validate_build(points, n, d, p);
+  if (rc) return rc;
+  return build_core(points, n, d, p, nullptr, 1, graph_out, am);
+}
+
+size_t build_device_bytes(int64_t n, int32_t d, const grnnd_params* p, size_t* resident) {
+  const BuildSizes z = build_sizes(n, d, p, false, 1);
+  if (resident) *resident = z.pts_b + z.graph_b;
+  return z.pts_b + z.graph_b + z.scratch_b;
+}
+}  // namespace grnnd

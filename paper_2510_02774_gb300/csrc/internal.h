@@ -3,8 +3,11 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <cuda_runtime.h>
+
+#include "grnnd.h"
 
 namespace grnnd {
 
@@ -46,6 +49,15 @@ struct PointsSet {
   // Join launch shape (grnnd_tuning): lane-group routing by pool size, CTAs per SM caps.
   int group_max[3] = {8, 16, 32};
   int warp_ctas = 0, team_ctas = 0;
+};
+
+// Where a build's device memory comes from: cudaMalloc / cudaFree (pool == nullptr), or
+// stream-ordered allocations from `pool` on the build's stream, the graph's own memory being
+// released on `free_stream` (the serving loop: builds on different streams then never wait
+// on the implicit device synchronisation of cudaFree).
+struct AllocMode {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t free_stream = nullptr;
 };
 
 size_t workspace_bytes(int64_t n, int R);
@@ -126,4 +138,44 @@ struct ProfScope {
   ~ProfScope() { prof_stop(st); }
 };
 
+}  // namespace grnnd
+
+// Device memory of one build call; the graphs of a batched build share it, and it is freed
+// with the last of them (stream-ordered when it came from a memory pool).
+struct GraphBlock {
+  void* points = nullptr;
+  void* graph = nullptr;
+  bool pooled = false;
+  cudaStream_t free_stream = nullptr;
+  ~GraphBlock() {
+    for (void* q : {points, graph})
+      if (q) {
+        if (pooled)
+          cudaFreeAsync(q, free_stream);
+        else
+          cudaFree(q);
+      }
+  }
+};
+
+struct grnnd_graph {
+  int64_t n = 0;
+  int32_t d = 0, ld = 0, R = 0, metric = 0, entry = 0;
+  float* points = nullptr;   // n x ld, zero padded
+  int32_t* ids = nullptr;    // n x R
+  float* dists = nullptr;    // n x R
+  int32_t* deg = nullptr;    // n
+  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::shared_ptr<GraphBlock> mem;
+};
+
+namespace grnnd {
+// grnnd_build_ex's argument checks (GRNND_OK or GRNND_EINVAL with the message set).
+int validate_build(const float* points, int64_t n, int32_t d, const grnnd_params* p);
+// Whole build with the allocation mode of the caller (grnnd_build_ex's validation first).
+int build_with(const float* points, int64_t n, int32_t d, const grnnd_params* p, const AllocMode& am,
+               grnnd_graph** graph_out);
+// Device bytes a single build of n x d points with params p allocates: *resident of them stay
+// with the graph (points + rows), the rest is scratch released when the build returns.
+size_t build_device_bytes(int64_t n, int32_t d, const grnnd_params* p, size_t* resident);
 }  // namespace grnnd

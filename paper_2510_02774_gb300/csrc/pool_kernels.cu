@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include <atomic>
 #include <mutex>
 
 namespace grnnd {
@@ -67,14 +68,16 @@ __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x &
 }  // namespace
 
 int sm_count() {
-  static int cached = 0;
-  if (cached == 0) {
+  static std::atomic<int> cached{0};  // read by the worker threads of the serving loop too
+  int v = cached.load(std::memory_order_relaxed);
+  if (v == 0) {
     int dev = 0, c = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-    cached = c > 0 ? c : 152;
+    v = c > 0 ? c : 152;
+    cached.store(v, std::memory_order_relaxed);
   }
-  return cached;
+  return v;
 }
 
 // =====================================================================================

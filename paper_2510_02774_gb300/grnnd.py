@@ -63,6 +63,23 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64), ("max_batch_queries", ctypes.c_int64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("kind", ctypes.c_int32), ("state", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("batch", ctypes.c_int32), ("index", ctypes.c_int64),
+                ("units", ctypes.c_int64), ("bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("message", ctypes.c_char * 128)]
+
+    def as_dict(self):
+        return {"id": self.id, "kind": ("build", "search")[self.kind], "state": self.state, "status": self.status,
+                "batch": self.batch, "index": self.index, "units": self.units, "bytes": self.bytes,
+                "t_submit": self.t_submit, "t_admit": self.t_admit, "t_done": self.t_done,
+                "message": self.message.decode(errors="replace")}
+
+
 _SIGS = {
     "grnnd_profile_begin": (ctypes.c_int, []),
     "grnnd_profile_end": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -120,6 +137,20 @@ _SIGS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_keys_to_graph": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "grnnd_server_submit_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64)]),
+    "grnnd_server_submit_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                  ctypes.POINTER(ctypes.c_int64)]),
+    "grnnd_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                         ctypes.POINTER(RequestInfo)]),
+    "grnnd_server_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
+    "grnnd_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "grnnd_server_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "grnnd_server_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -488,3 +519,107 @@ def header_functions() -> list[str]:
     with open(HEADER) as f:
         txt = f.read()
     return sorted(set(re.findall(r"GRNND_API\s+[\w\s\*]*?\b(grnnd_\w+)\s*\(", txt)))
+
+
+# ---------------------------------------------------------------------------------------
+# Serving loop
+# ---------------------------------------------------------------------------------------
+
+class Server:
+    """grnnd_server_*: build and search requests served concurrently on `slots` streams under
+    an HBM budget.  Buffers handed to submit_* are kept alive here until their request is
+    waited for."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int = 8 << 30, max_batch_queries: int = 0):
+        cfg = ServerConfig(slots, hbm_budget, max_batch_queries)
+        self.handle = ctypes.c_void_p()
+        _check(lib().grnnd_server_create(ctypes.byref(cfg), ctypes.byref(self.handle)))
+        self._keep = {}
+        self._lock = threading.Lock()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().grnnd_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _rows(x):
+        if isinstance(x, np.ndarray):
+            a = np.ascontiguousarray(x, dtype=np.float32)
+            return a, a.ctypes.data_as(ctypes.c_void_p)
+        a = x.contiguous()
+        return a, ctypes.c_void_p(a.data_ptr())
+
+    def submit_build(self, points, **kw) -> int:
+        """Queues a build of points (numpy or torch, (n, d)); kw as for build().  Returns the
+        request id, which is also the index id."""
+        a, ptr = self._rows(points)
+        p = params(**kw)
+        rid = ctypes.c_int64()
+        _check(lib().grnnd_server_submit_build(self.handle, ptr, a.shape[0], a.shape[1], ctypes.byref(p),
+                                               ctypes.byref(rid)))
+        with self._lock:
+            self._keep[rid.value] = (a, p, kw.get("tuning"))
+        return rid.value
+
+    def submit_search(self, index: int, queries, k: int = 10, beam: int = 64, out=None) -> int:
+        """Queues a search of `queries` on index `index`; the result lands in `out` (numpy
+        int32 (nq, k) by default, or a torch tensor), returned by result()."""
+        a, ptr = self._rows(queries)
+        if out is None:
+            out = np.empty((a.shape[0], k), np.int32)
+        optr = out.ctypes.data_as(ctypes.c_void_p) if isinstance(out, np.ndarray) else ctypes.c_void_p(out.data_ptr())
+        rid = ctypes.c_int64()
+        _check(lib().grnnd_server_submit_search(self.handle, index, ptr, a.shape[0], k, beam, optr,
+                                                ctypes.byref(rid)))
+        with self._lock:
+            self._keep[rid.value] = (a, out)
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = -1.0) -> dict:
+        """Waits for request rid; returns its info dict (with 'out' for a search).  Raises
+        GrnndError if the request failed (or TimeoutError if it is not done in time)."""
+        info = RequestInfo()
+        rc = lib().grnnd_server_wait(self.handle, rid, timeout, ctypes.byref(info))
+        d = info.as_dict()
+        if rc == ETIMEOUT and d["state"] != 2:
+            raise TimeoutError(f"request {rid} not done")
+        with self._lock:
+            keep = self._keep.pop(rid, None)
+        if d["kind"] == "search" and keep is not None:
+            d["out"] = keep[1]
+        if rc != OK:
+            raise GrnndError(rc, d["message"])
+        return d
+
+    def graph(self, index: int):
+        """(ids, dists, deg) numpy copies and the entry of a resident index."""
+        h = ctypes.c_void_p()
+        _check(lib().grnnd_server_index(self.handle, index, ctypes.byref(h)))
+        n_, d_, R_, e_ = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().grnnd_graph_info(h, ctypes.byref(n_), ctypes.byref(d_), ctypes.byref(R_), ctypes.byref(e_)))
+        ids = np.empty((n_.value, R_.value), np.int32)
+        dists = np.empty((n_.value, R_.value), np.float32)
+        deg = np.empty(n_.value, np.int32)
+        _check(lib().grnnd_graph_copy(h, ids.ctypes.data_as(ctypes.c_void_p), dists.ctypes.data_as(ctypes.c_void_p),
+                                      deg.ctypes.data_as(ctypes.c_void_p)))
+        return ids, dists, deg, e_.value
+
+    def release(self, index: int):
+        _check(lib().grnnd_server_release(self.handle, index))
+
+    def status(self) -> dict:
+        u, pk = ctypes.c_uint64(), ctypes.c_uint64()
+        q, r, i = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().grnnd_server_status(self.handle, ctypes.byref(u), ctypes.byref(pk), ctypes.byref(q),
+                                         ctypes.byref(r), ctypes.byref(i)))
+        return {"bytes_in_use": u.value, "peak_bytes": pk.value, "queued": q.value, "running": r.value,
+                "indices": i.value}
+

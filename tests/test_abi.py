@@ -122,3 +122,20 @@ def test_tuning_is_validated(L):
         p = G.params(S=4, R=8, tuning=t)
         assert L.grnnd_build_ex(pts, 100, 4, ctypes.byref(p), ctypes.byref(h)) == G.EINVAL
         assert b"tuning" in L.grnnd_last_error()
+
+
+def test_server_validates_before_any_cuda_call(L):
+    import ctypes
+    h = ctypes.c_void_p()
+    for cfg in [G.ServerConfig(0, 1 << 30, 0), G.ServerConfig(65, 1 << 30, 0), G.ServerConfig(2, 0, 0),
+                G.ServerConfig(2, 1 << 30, -1)]:
+        assert L.grnnd_server_create(ctypes.byref(cfg), ctypes.byref(h)) == G.EINVAL
+        assert h.value is None
+    rid = ctypes.c_int64()
+    p = G.params(S=4, R=8)
+    assert L.grnnd_server_submit_build(None, ctypes.c_void_p(1 << 20), 100, 4, ctypes.byref(p),
+                                       ctypes.byref(rid)) == G.EINVAL
+    assert L.grnnd_server_submit_search(None, 1, ctypes.c_void_p(1 << 20), 1, 1, 1, ctypes.c_void_p(1 << 20),
+                                        ctypes.byref(rid)) == G.EINVAL
+    assert L.grnnd_server_wait(None, 1, 0.0, None) == G.EINVAL
+    assert L.grnnd_server_release(None, 1) == G.EINVAL
