@@ -590,7 +590,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
       // the round updates the pool in place: survivors are rewritten in their own row and
       // only rows that receive proposals are merged (the role of Sec 3.5's second buffer)
       GR_CAP(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
-                                 stats, st));
+                                 stats, st, rounds > 0));
       const int cur = (int)(rounds & 1);
       ++rounds;
       if (capture) continue;
@@ -611,7 +611,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   uint64_t* gkeys = poolA;
   int32_t* gdg = degA;
   if (p->final_prune) {
-    GR_CAP(grnnd::launch_final(P, n, R, poolA, degA, p->seed, p->T1 + 1, p->order, ws, poolB, degB, st));
+    GR_CAP(grnnd::launch_final(P, n, R, poolA, degA, p->seed, p->T1 + 1, p->order, ws, poolB, degB, st, true));
     gkeys = poolB;
     gdg = degB;
   }

@@ -22,6 +22,8 @@ struct Workspace {
   int64_t* off = nullptr;                  // n+1 exclusive prefix of count
   int64_t* bsum = nullptr;                 // scan block sums
   uint8_t* active = nullptr;               // n flags: the vertex is in the list
+  uint8_t* next_active = nullptr;          // n flags written by an in-place merge: the row holds
+                                           // a new entry (read by the next step's prep)
   uint64_t* rec[4] = {};                   // work records by pool-size class (entries <= 8,
   int rec_w[4] = {};                       // <= 16, <= 32, more): n records of rec_w[c]
   int rec_cap[4] = {};                     // words each, holding up to rec_cap[c] entries
@@ -79,16 +81,19 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xb, 
 // occupancy); launches inside a stream capture rely on it having run.
 cudaError_t prepare_join_kernels(const PointsSet& P);
 
-// One round of Alg 4: prep + rnd_join + scan + scatter + select (keys_out != keys_in).
+// One round of Alg 4: prep + rnd_join + scan + scatter + select (keys_out == keys_in: in
+// place).  use_hint: the last step on these pools was an in-place round or reverse step with
+// the same workspace, so its per-row new-entry flags replace prep's scan of the keys.
 cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int64_t* stats,
-                         cudaStream_t st);
+                         cudaStream_t st, bool use_hint = false);
 
-// Final prune-only pass: survivors only, no redirects.
+// Final prune-only pass: survivors only, no redirects (use_hint as for launch_round).
 cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int order,
-                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st);
+                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st,
+                         bool use_hint = false);
 
 // Reverse-edge sampling + merge.
 cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,

@@ -293,6 +293,8 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 //   word 0: v | (first id of v's build) << 32    word 1: m    words 2 .. 2+m: the pool keys
 //   (BF16 form) words 2+cap .. 2+cap+m: per entry (norm^2, residual) of the quantized row.
 // Also counts the entries of every pool (each one is proposed once, explicitly or in place).
+// With `hint` (the flags the last merge of the same pools wrote) no pool key is read for
+// the active test.
 // =====================================================================================
 struct RecSet {
   uint64_t* rec[4];
@@ -304,7 +306,7 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
                             int64_t n, int R, uint8_t* __restrict__ active,
                             int32_t* __restrict__ list_n, int warp_ok, int3 gmax, RecSet rs,
                             const float2* __restrict__ aux, const int2* __restrict__ vseg,
-                            int64_t* __restrict__ stats) {
+                            const uint8_t* __restrict__ hint, int64_t* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
   long long props = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -315,7 +317,10 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
     if (v < n) {
       m = deg[v];
       props += m;
-      for (int j = 0; j < m && !act; ++j) act = !(keys[v * R + j] & 1ull);
+      if (hint)  // the last merge of these pools recorded which rows hold a new entry
+        act = hint[v] != 0;
+      else
+        for (int j = 0; j < m && !act; ++j) act = !(keys[v * R + j] & 1ull);
       active[v] = act ? 1 : 0;
     }
     const int cls = !warp_ok ? 3 : (m <= gmax.x ? 0 : (m <= gmax.y ? 1 : (m <= gmax.z ? 2 : 3)));
@@ -2493,6 +2498,9 @@ struct SelectArgs {
   int64_t* round_new;
   int64_t* stats;
   const int32_t* err;      // nonzero: a wait of this round gave up, leave every pool as it is
+  uint8_t* next_active;    // per target: its output row holds a new entry (prep's hint), or null
+  int next_active_all;     // 1: write the flag of every target (a round: rows the merge leaves
+                           // alone hold no new entry); 0: only of merged targets (a reverse step)
 };
 
 __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
@@ -2504,44 +2512,63 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
   // in place (keys_out == keys_in): every row already holds the target's base pool
   const bool in_place = a.keys_out == a.keys_in;
   if (*a.err) return;
-  for (int64_t u = (int64_t)blockIdx.x * 8 + warp; u < a.n; u += (int64_t)gridDim.x * 8) {
-    int64_t b0 = 0, c = 0;
-    if (a.bucket) {
-      b0 = a.off[u];
-      c = a.off[u + 1] - b0;
-    }
-    const bool kept = in_place || (a.active && a.active[u]);
-    if (c == 0 && kept) continue;  // nothing proposed: the pool in place is final
-    const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
-    const int na = kept ? a.deg_out[u] : a.deg_in[u];
-    n_in += c;
-    uint64_t out0, out1;
-    if (c == 0) {
-      out0 = lane < na ? base[lane] : kEmpty;
-      out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
-    } else if (c <= 4) {  // a few proposals: insert them one by one into the sorted row
-      out0 = lane < na ? base[lane] : kEmpty;
-      out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
-      const uint64_t bl = lane < c ? a.bucket[b0 + lane] : kEmpty;
-      for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
-    } else {  // chunks of 32 proposals merged into the row
-      out0 = lane < na ? base[lane] : kEmpty;
-      out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
-      for (int64_t done = 0; done < c; done += 32) {
-        const uint64_t bl = done + lane < c ? a.bucket[b0 + done + lane] : kEmpty;
-        merge_chunk(out0, out1, bl, R, ms);
+  // a warp scans 32 consecutive targets at once (one per lane) and merges, one after the
+  // other, only those that received proposals or still need their base pool copied
+  for (int64_t u0 = ((int64_t)blockIdx.x * 8 + warp) * 32; u0 < a.n; u0 += (int64_t)gridDim.x * 8 * 32) {
+    const int64_t ul = u0 + lane;
+    int64_t b0l = 0, cl = 0;
+    bool keptl = true;
+    if (ul < a.n) {
+      if (a.bucket) {
+        b0l = a.off[ul];
+        cl = a.off[ul + 1] - b0l;
       }
+      keptl = in_place || (a.active && a.active[ul]);
     }
-    if (lane >= R) out0 = kEmpty;
-    if (lane + 32 >= R) out1 = kEmpty;
-    const unsigned v0 = __ballot_sync(0xffffffffu, out0 != kEmpty);
-    const unsigned v1 = __ballot_sync(0xffffffffu, out1 != kEmpty);
-    const unsigned w0 = __ballot_sync(0xffffffffu, out0 != kEmpty && !(out0 & 1ull));
-    const unsigned w1 = __ballot_sync(0xffffffffu, out1 != kEmpty && !(out1 & 1ull));
-    if (lane < R) a.keys_out[u * R + lane] = out0;
-    if (lane + 32 < R) a.keys_out[u * R + 32 + lane] = out1;
-    if (lane == 0) a.deg_out[u] = __popc(v0) + __popc(v1);
-    n_new += __popc(w0) + __popc(w1);
+    // a target with nothing proposed whose pool is in place is final already (and holds no
+    // new entry: the join rewrote every row it pruned as old)
+    unsigned work = __ballot_sync(0xffffffffu, ul < a.n && (cl != 0 || !keptl));
+    const bool merged_l = (work >> lane) & 1u;
+    bool mynew = false;
+    while (work) {
+      const int tl = __ffs(work) - 1;
+      work &= work - 1;
+      const int64_t u = u0 + tl;
+      const int64_t b0 = __shfl_sync(0xffffffffu, b0l, tl), c = __shfl_sync(0xffffffffu, cl, tl);
+      const bool kept = __shfl_sync(0xffffffffu, keptl ? 1 : 0, tl) != 0;
+      const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
+      const int na = kept ? a.deg_out[u] : a.deg_in[u];
+      n_in += c;
+      uint64_t out0, out1;
+      if (c == 0) {
+        out0 = lane < na ? base[lane] : kEmpty;
+        out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+      } else if (c <= 4) {  // a few proposals: insert them one by one into the sorted row
+        out0 = lane < na ? base[lane] : kEmpty;
+        out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+        const uint64_t bl = lane < c ? a.bucket[b0 + lane] : kEmpty;
+        for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
+      } else {  // chunks of 32 proposals merged into the row
+        out0 = lane < na ? base[lane] : kEmpty;
+        out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+        for (int64_t done = 0; done < c; done += 32) {
+          const uint64_t bl = done + lane < c ? a.bucket[b0 + done + lane] : kEmpty;
+          merge_chunk(out0, out1, bl, R, ms);
+        }
+      }
+      if (lane >= R) out0 = kEmpty;
+      if (lane + 32 >= R) out1 = kEmpty;
+      const unsigned v0 = __ballot_sync(0xffffffffu, out0 != kEmpty);
+      const unsigned v1 = __ballot_sync(0xffffffffu, out1 != kEmpty);
+      const unsigned w0 = __ballot_sync(0xffffffffu, out0 != kEmpty && !(out0 & 1ull));
+      const unsigned w1 = __ballot_sync(0xffffffffu, out1 != kEmpty && !(out1 & 1ull));
+      if (lane < R) a.keys_out[u * R + lane] = out0;
+      if (lane + 32 < R) a.keys_out[u * R + 32 + lane] = out1;
+      if (lane == 0) a.deg_out[u] = __popc(v0) + __popc(v1);
+      n_new += __popc(w0) + __popc(w1);
+      if (lane == tl) mynew = (w0 | w1) != 0u;
+    }
+    if (a.next_active && ul < a.n && (merged_l || a.next_active_all)) a.next_active[ul] = mynew ? 1 : 0;
   }
   if (lane == 0) {
     if (n_new) atomicAdd(reinterpret_cast<unsigned long long*>(a.round_new), (unsigned long long)n_new);
@@ -2566,14 +2593,14 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
     }
   }
   cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
-  const int64_t blocks = std::min<int64_t>(ceil_div(n, 8), (int64_t)sm_count() * 16);
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 16);
   ProfScope ps("select", st);
   select_kernel<<<(unsigned)blocks, 256, 0, st>>>(sa);
   return cudaGetLastError();
 }
 
 cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Workspace& ws,
-                     const PointsSet& P, int64_t* stats, cudaStream_t st) {
+                     const PointsSet& P, const uint8_t* hint, int64_t* stats, cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>(ceil_div(ws.n, 256), (int64_t)sm_count() * 8);
   ProfScope ps("prep", st);
   // the warp kernels take FP32 rows of up to 128 dimensions (BF16 rows of any length)
@@ -2586,7 +2613,8 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
   }
   const int3 gmax = make_int3(P.group_max[0], P.group_max[1], P.group_max[2]);
   prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
-                                                gmax, rs, P.precision >= 1 ? P.aux : nullptr, P.vseg, stats);
+                                                gmax, rs, P.precision >= 1 ? P.aux : nullptr, P.vseg, hint,
+                                                stats);
   return cudaGetLastError();
 }
 
@@ -2674,12 +2702,13 @@ cudaError_t prepare_join_kernels(const PointsSet& P) {
 cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int64_t* stats,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool use_hint) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;  // list_n and red_n
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
-  if ((e = run_prep(keys_in, deg_in, ws, P, stats, st)) != cudaSuccess) return e;
+  if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, stats, st)) != cudaSuccess)
+    return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out,
                                     deg_out, 1, stats);
   if ((e = dispatch_join(P, a, st, "rnd_join")) != cudaSuccess) return e;
@@ -2696,16 +2725,20 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.round_new = ws.round_new;
   sa.err = ws.err;
   sa.stats = stats;
+  sa.next_active = keys_out == keys_in ? ws.next_active : nullptr;
+  sa.next_active_all = 1;
   return merge_tail(ws, sa, st);
 }
 
 cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int order,
-                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st) {
+                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st,
+                         bool use_hint) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
-  if ((e = run_prep(keys_in, deg_in, ws, P, nullptr, st)) != cudaSuccess) return e;
+  if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, nullptr, st)) != cudaSuccess)
+    return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, 0, order, ws, keys_out,
                                     deg_out, 0, nullptr);
   if ((e = dispatch_join(P, a, st, "final_prune")) != cudaSuccess) return e;
@@ -2722,6 +2755,8 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.round_new = ws.round_new;
   sa.err = ws.err;
   sa.stats = nullptr;
+  sa.next_active = nullptr;
+  sa.next_active_all = 0;
   return merge_tail(ws, sa, st);
 }
 
@@ -2795,6 +2830,8 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
   sa.round_new = ws.round_new;
   sa.err = ws.err;
   sa.stats = stats;
+  sa.next_active = keys_out == keys_in ? ws.next_active : nullptr;  // rows not merged keep their flag
+  sa.next_active_all = 0;
   return merge_tail(ws, sa, st);
 }
 
@@ -2851,7 +2888,7 @@ size_t workspace_bytes(int64_t n, int R) {
   const size_t slots = red_slots(n, R);
   const size_t nb = (size_t)ceil_div(n, SCAN_TILE) + 1;
   return al256(slots * 4) + al256(slots * 8) + al256((size_t)n * R * 8) + al256((size_t)n * 4) +
-         al256(((size_t)n + 1) * 8) + al256(nb * 8) + al256((size_t)n) + rec_bytes(n, R) + al256(24) +
+         al256(((size_t)n + 1) * 8) + al256(nb * 8) + 2 * al256((size_t)n) + rec_bytes(n, R) + al256(24) +
          al256(4) + al256(8);
 }
 
@@ -2876,6 +2913,8 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   ws->bsum = reinterpret_cast<int64_t*>(p);
   p += al256(nb * 8);
   ws->active = reinterpret_cast<uint8_t*>(p);
+  p += al256((size_t)n);
+  ws->next_active = reinterpret_cast<uint8_t*>(p);
   p += al256((size_t)n);
   for (int c = 0; c < 4; ++c) {
     ws->rec_cap[c] = c == 3 ? R : rec_cap_of(R, c);
