@@ -27,6 +27,16 @@ __host__ __device__ __forceinline__ uint64_t counter_hash(uint64_t seed, uint64_
   return splitmix_step(h ^ x);
 }
 
+// The same hash in two parts: the first three steps depend only on (seed, t1, t2), so a
+// kernel computes them once, and hash_tail(hash_head(seed, t1, t2), v, x) equals
+// counter_hash(seed, t1, t2, v, x) bit for bit.
+__host__ __device__ __forceinline__ uint64_t hash_head(uint64_t seed, uint64_t t1, uint64_t t2) {
+  return splitmix_step(splitmix_step(splitmix_step(seed) ^ t1) ^ t2);
+}
+__host__ __device__ __forceinline__ uint64_t hash_tail(uint64_t head, uint64_t v, uint64_t x) {
+  return splitmix_step(splitmix_step(head ^ v) ^ x);
+}
+
 // ---- pool keys: (ordered float bits << 32) | (id << 1) | old -------------------------
 __device__ __forceinline__ uint32_t ordered_bits(float f) {
   uint32_t u = __float_as_uint(f);

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__
   __shared__ int32_t acc_ids[8][kMaxR];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* acc = acc_ids[warp];
+  const uint64_t head = hash_head(seed, 0, 0);
   const unsigned below = lanemask_lt();
   for (int64_t v = (int64_t)blockIdx.x * 8 + warp; v < n; v += (int64_t)gridDim.x * 8) {
     // the vertex's build: ids [lo, lo + nb); draws use the local id v - lo
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__
     int cnt = 0;
     // S <= nb - 1, so the draws cover enough distinct ids long before the bound.
     for (uint64_t base = 0; cnt < S && base < (1ull << 32); base += 32) {
-      const uint64_t r = counter_hash(seed, 0, 0, vl, base + lane) % nm1;
+      const uint64_t r = hash_tail(head, vl, base + lane) % nm1;
       const int32_t u = (int32_t)(lo + (int64_t)(r + (r >= vl ? 1u : 0u)));
       bool dup = false;
       for (int j = 0; j < cnt; ++j) dup |= (acc[j] == u);
@@ -648,6 +649,7 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
   }
   __syncthreads();
   const int nb = B.nb;
+  const uint64_t head = hash_head(a.seed, (uint64_t)a.t1, (uint64_t)a.t2);  // visit-order hash, uniform part
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int vb = warp + h * JW;
@@ -660,7 +662,7 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
     for (int j = 0; j < 2; ++j) {
       const int e = j * 32 + lane;
       id[j] = key_id(kx[h][j]);
-      hk[j] = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)(v - lox[h]),
+      hk[j] = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - lox[h]),
                                               (uint64_t)(id[j] - lox[h]))
               : (a.order == 1) ? (uint64_t)e
                                : (uint64_t)(m - 1 - e);
@@ -1322,6 +1324,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   if (gw >= items || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
   const int R = a.R, d = a.P.d;
   const int nchd = (d + WDC - 1) / WDC;
+  const uint64_t head = hash_head(a.seed, (uint64_t)a.t1, (uint64_t)a.t2);  // visit-order hash, uniform part
   if (lane == 0) {
     mbar_init(&s.bar, 1);
     fence_mbar_init();
@@ -1354,7 +1357,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     uint64_t h = ~0ull;
     uint32_t hid = 0xffffffffu, hs = (uint32_t)lane;
     if (gl < m) {
-      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)(v - cur.lo),
+      h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - cur.lo),
                                           (uint64_t)(idl - cur.lo))
           : (a.order == 1) ? (uint64_t)gl
                            : (uint64_t)(m - 1 - gl);
@@ -1603,11 +1606,14 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     int mykill = -1;
     {
       uint32_t cols = (__ballot_sync(0xffffffffu, valid_p && s.fire[P] != 0u) >> gb) & gmask;
+      int b = cols ? __ffs(cols) - 1 : 0;
+      uint32_t fb = s.fire[gb + b], cb = s.closer[gb + b];
       while (cols) {
-        const int b = __ffs(cols) - 1;
         cols &= cols - 1;
-        const uint32_t cand = s.fire[gb + b] & alive;
-        const uint32_t x = cand & s.closer[gb + b];
+        const int bn = cols ? __ffs(cols) - 1 : 0;
+        const uint32_t fn = s.fire[gb + bn], cn = s.closer[gb + bn];  // the next column, loaded early
+        const uint32_t cand = fb & alive;
+        const uint32_t x = cand & cb;
         uint32_t kill = cand;
         if (x) {
           const int f = __ffs(x) - 1;
@@ -1617,6 +1623,9 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
         }
         alive &= ~kill;
         if ((kill >> gl) & 1u) mykill = b;
+        b = bn;
+        fb = fn;
+        cb = cn;
       }
     }
     __syncwarp();
@@ -1809,6 +1818,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   if (p >= cnt || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
   const int R = a.R, W = a.rec_w[3], d = a.P.d;
   const int nchd = (d + TDC - 1) / TDC;  // chunks per row
+  const uint64_t head = hash_head(a.seed, (uint64_t)a.t1, (uint64_t)a.t2);  // visit-order hash, uniform part
   const int nst = nchd > 1 ? 2 : 1;      // stages
   if (tid == 0) {
     mbar_init(&s.bar[0], 1);
@@ -1853,7 +1863,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     const bool has = tid < m;
     uint64_t h = ~0ull;
     if (has)
-      h = (a.order == 0)   ? counter_hash(a.seed, (uint64_t)a.t1, (uint64_t)a.t2, (uint64_t)(v - lo),
+      h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - lo),
                                           (uint64_t)(idl - lo))
           : (a.order == 1) ? (uint64_t)tid
                            : (uint64_t)(m - 1 - tid);
