@@ -1612,16 +1612,14 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
         cols &= cols - 1;
         const int bn = cols ? __ffs(cols) - 1 : 0;
         const uint32_t fn = s.fire[gb + bn], cn = s.closer[gb + bn];  // the next column, loaded early
+        // the live partners of column b; when one of them is closer than b, those before the
+        // first such partner die (absorbed by b) and then b itself (absorbed by that partner)
         const uint32_t cand = fb & alive;
         const uint32_t x = cand & cb;
-        uint32_t kill = cand;
-        if (x) {
-          const int f = __ffs(x) - 1;
-          kill = cand & lanes_below32(f);
-          alive &= ~(1u << b);
-          if (gl == b) mykill = f;
-        }
-        alive &= ~kill;
+        const uint32_t low = x & (0u - x);  // first closer partner (0: none)
+        const uint32_t kill = x ? (cand & (low - 1u)) : cand;
+        alive &= ~(kill | (x ? (1u << b) : 0u));
+        if (x && gl == b) mykill = __ffs(x) - 1;
         if ((kill >> gl) & 1u) mykill = b;
         b = bn;
         fb = fn;
