@@ -31,9 +31,12 @@ METRIC = "build points/s at recall@10>=0.95 (BF16 vs FP32, 1 GB300); p50/p99 bui
 WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 1000-cluster mixture, "
                          "integers in [0,255]; S=32, R=64, T1=4, T2=15, rho=0.6; 10,000 queries, k=10, beam 64",
                 n=1_000_000, d=128, S=32, R=64, T1=4, T2=15, rho=0.6, nq=10_000, k=10, beam=64)
-# ncu DRAM bytes per rnd_join launch for the current kernel source (see profiles/);
-# reported only while the kernel source is unchanged since the capture.
-TRAFFIC = {"kernel": "rnd_join", "bytes_per_launch": None, "source_sha256": None}
+# ncu DRAM bytes (read + write) per unit of the join -- one round, i.e. its warp and team
+# launches -- averaged over the 60 rounds of one build of the workload above, from the
+# one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
+# the kernel source is unchanged since that capture.
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9073e9,
+           "source_sha256": "48e6d6bc5702da2cb1c5032132cc45ba6761d36db694e0b11563cdfe0059c626"}
 
 
 def _args():
@@ -648,7 +651,8 @@ def main():
     if algo is not None:
         achieved = algo / (dom_ms / 1e3) / 1e9
         traffic = None
-        if TRAFFIC["kernel"] == dom_name and TRAFFIC["source_sha256"] == _source_sha():
+        if (TRAFFIC["kernel"] == dom_name and TRAFFIC["form"] == head_name and TRAFFIC["n"] == n
+                and TRAFFIC["source_sha256"] == _source_sha()):
             traffic = TRAFFIC["bytes_per_launch"]
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": peak_src, "traffic": traffic,

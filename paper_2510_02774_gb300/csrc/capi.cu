@@ -13,12 +13,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "grnnd.h"
 #include "internal.h"
 
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range over a host scope (shown by profilers that attach; no cost otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -440,6 +448,7 @@ BuildSizes build_sizes(int64_t n, int32_t d, const grnnd_params* p, bool batched
 int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p, const int64_t* offsets,
                int32_t nbuild, grnnd_graph** graphs_out, const grnnd::AllocMode& am = grnnd::AllocMode()) {
   const bool batched = offsets != nullptr;
+  NvtxRange nvtx_build(batched ? "grnnd_build_batch" : "grnnd_build");
   const int32_t R = p->R, ld = round4(d);
   const bool quant = p->precision != GRNND_FP32;
   const int32_t ldb = p->precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
@@ -589,8 +598,11 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
     for (int32_t t2 = 1; t2 <= p->T2; ++t2) {
       // the round updates the pool in place: survivors are rewritten in their own row and
       // only rows that receive proposals are merged (the role of Sec 3.5's second buffer)
-      GR_CAP(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
-                                 stats, st, rounds > 0));
+      {
+        NvtxRange nvtx_round("round");
+        GR_CAP(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
+                                   stats, st, rounds > 0));
+      }
       const int cur = (int)(rounds & 1);
       ++rounds;
       if (capture) continue;
@@ -605,6 +617,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
       prev = cur;
     }
     if (t1 != p->T1) {
+      NvtxRange nvtx_rev("reverse_sample");
       GR_CAP(grnnd::launch_reverse(n, R, p->rho, poolA, degA, ws, poolA, degA, nullptr, st));
     }
   }

@@ -19,6 +19,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "grnnd.h"
 #include "internal.h"
 
@@ -189,6 +191,7 @@ bool pick_locked(grnnd_server* S, std::vector<Request*>& batch) {
 }
 
 void run_build(grnnd_server* S, Request* r, cudaStream_t st) {
+  nvtxRangePushA("serve build");
   grnnd_params p = r->p;
   p.stream = st;
   p.hbm_budget = 0;
@@ -198,6 +201,7 @@ void run_build(grnnd_server* S, Request* r, cudaStream_t st) {
   am.free_stream = S->free_stream;
   grnnd_graph* g = nullptr;
   const int rc = grnnd::build_with(r->points, r->units, r->d, &p, am, &g);
+  nvtxRangePop();
   const std::string msg = rc ? std::string(grnnd_last_error()) : std::string();
   std::lock_guard<std::mutex> lk(S->mu);
   Index& ix = S->indices[r->index];
@@ -258,7 +262,9 @@ void run_search(grnnd_server* S, const std::vector<Request*>& batch, cudaStream_
     std::lock_guard<std::mutex> lk(S->mu);
     g = S->indices[batch[0]->index].g;  // ready, and kept while its searches run
   }
+  nvtxRangePushA("serve search batch");
   const int rc = search_batch(g, batch, S->pool, st);
+  nvtxRangePop();
   const std::string msg = rc ? std::string(grnnd_last_error()) : std::string();
   std::lock_guard<std::mutex> lk(S->mu);
   for (Request* r : batch) {

@@ -574,3 +574,40 @@ def test_autotune_picks_a_candidate(G):
     assert t.ms > 0
     assert list(t.group_max) in ([8, 16, 32], [0, 16, 32], [0, 0, 32], [8, 16, 16], [0, 16, 16])
     assert 0 <= t.warp_ctas_per_sm <= 3 and t.team_ctas_per_sm in (0, 2, 4, 6)
+
+
+# ---------------------------------------------------------------------------------------
+# checkpoint / resume: the pool state (keys, degrees) between steps is the whole state of a
+# build (randomness is counter-based), so a build stopped after any round, saved to the
+# host and resumed in a new workspace ends with the graph of an uninterrupted build
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("stop_after", [1, 5, 9])
+def test_resume_from_host_checkpoint_equals_build(G, stop_after):
+    n, d, S, R, T1, T2, rho, seed = 3000, 24, 12, 24, 3, 4, 0.6, 17
+    X = synth.small_integers(n, d, -8, 8, seed=33)
+    want = G.build(X, S=S, R=R, T1=T1, T2=T2, rho=rho, seed=seed)
+    wids, wd, wdeg = want.to_numpy()
+    Xd, _ = G.device_points(X)
+    keys, deg = G.pool_init(Xd, d, S, R, seed)
+    ws = G.workspace(n, R)
+    rounds = 0
+    for t1 in range(1, T1 + 1):
+        for t2 in range(1, T2 + 1):
+            keys, deg = G.join_round(Xd, d, keys, deg, seed, t1, t2, ws=ws, inplace=True)
+            rounds += 1
+            if rounds == stop_after:  # checkpoint to the host, drop the device state, resume
+                hk, hd = keys.cpu().clone(), deg.cpu().clone()
+                del keys, deg, ws
+                torch.cuda.synchronize()
+                keys, deg = hk.cuda(), hd.cuda()
+                ws = G.workspace(n, R)
+        if t1 != T1:
+            keys, deg = G.reverse_sample(keys, deg, rho, ws=ws, inplace=True)
+    G.workspace_status(ws, n, R)
+    fk, fdeg = G.final_prune(Xd, d, keys, deg, seed, T1 + 1, ws=ws)
+    ids, dd = G.keys_to_graph(fk)
+    assert (fdeg.cpu().numpy() == wdeg).all()
+    assert (ids.cpu().numpy() == wids).all()
+    assert (dd.cpu().numpy()[wids >= 0] == wd[wids >= 0]).all()
+    assert G.entry_point(Xd, d) == want.entry
