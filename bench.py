@@ -39,6 +39,9 @@ TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_laun
            "source_sha256": "48e6d6bc5702da2cb1c5032132cc45ba6761d36db694e0b11563cdfe0059c626"}
 
 
+CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,6 +518,9 @@ def main():
         dist.barrier()
     from paper_2510_02774_gb300 import grnnd, synth
     grnnd.lib()
+    # builds keep their freed device memory for the next build (a caching allocator; the
+    # graphs are the same with or without it)
+    grnnd.set_memory_cache(CACHE_BYTES)
 
     w = WORKLOAD
     n, d = args.n, w["d"]
@@ -680,6 +686,7 @@ def main():
                                                 "FP32 re-decision)",
                                          "fp32": "fp32 dist_tile (CUDA cores)"}[head_name],
                            "l2": "inputs larger than L2 (512 MB of points per replica)",
+                           "allocator": f"library memory cache of {CACHE_BYTES >> 30} GiB (grnnd_set_memory_cache)",
                            "parallelism": f"{world} independent replica(s)"},
                 "p50_ms": statistics.median(step_ms), "p99_ms": p99, "recall@10": recall.get(head_name),
                 "beam": w["beam"],

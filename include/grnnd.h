@@ -121,6 +121,18 @@ GRNND_API void grnnd_params_default(grnnd_params *p);
 GRNND_API int grnnd_autotune(const float *points, int64_t n, int32_t d, const int64_t *offsets,
                              int32_t nbuild, const grnnd_params *p, grnnd_tuning *best);
 
+/* Memory cache of whole builds on the current device (no counterpart in the paper).  A build
+ * allocates its device memory (points, graph, pools, round workspace: about 4 GB for 1M x 128
+ * with R = 64) and frees the scratch part when it returns.  With bytes > 0, grnnd_build_ex and
+ * grnnd_build_batch take that memory from a stream-ordered pool owned by the library, which
+ * keeps up to `bytes` freed bytes for the next build instead of returning them to the driver
+ * (saving the cudaMalloc / cudaFree work of every build, a few ms at 1M points), like a
+ * framework's caching allocator.  The memory of a graph returns to the pool when the graph
+ * is freed (grnnd_free synchronises the device first, since the caller's own work may still
+ * read the graph).  bytes = 0 (the default) turns the cache off and releases what it holds.
+ * Graphs are the same either way. */
+GRNND_API int grnnd_set_memory_cache(uint64_t bytes);
+
 /* Builds a graph over n points of dimension d (Alg 3).  `points` is host or
  * device memory, n rows of d contiguous floats; every value must be finite.
  * Validation: n >= 2, d >= 1, 1 <= S <= min(R, n-1), 2 <= R <= 64, T1, T2 >= 1.

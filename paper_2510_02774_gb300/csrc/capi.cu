@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -369,6 +370,55 @@ int grnnd_keys_to_graph(int64_t n, int32_t R, const uint64_t* keys, int32_t* ids
 // ---------------------------------------------------------------------------------------
 
 namespace {
+// The memory cache of grnnd_set_memory_cache: one stream-ordered pool per device, keeping up
+// to the set number of freed bytes for the next build instead of returning them.
+constexpr int kMaxDevices = 64;
+std::mutex g_cache_mu;
+cudaMemPool_t g_cache_pool[kMaxDevices] = {};
+uint64_t g_cache_bytes[kMaxDevices] = {};
+
+grnnd::AllocMode cache_alloc_mode() {
+  grnnd::AllocMode am;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return am;
+  }
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  if (g_cache_bytes[dev] && g_cache_pool[dev]) {
+    am.pool = g_cache_pool[dev];
+    am.free_stream = nullptr;
+    am.sync_before_free = true;
+  }
+  return am;
+}
+}  // namespace
+
+int grnnd_set_memory_cache(uint64_t bytes) {
+  int dev = 0;
+  GR_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(GRNND_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  if (!g_cache_pool[dev]) {
+    if (!bytes) return GRNND_OK;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    GR_CU(cudaMemPoolCreate(&g_cache_pool[dev], &props));
+  }
+  uint64_t keep = bytes;
+  GR_CU(cudaMemPoolSetAttribute(g_cache_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+  g_cache_bytes[dev] = bytes;
+  if (!bytes) {  // off: return what the pool still keeps (graphs alive keep their memory)
+    GR_CU(cudaDeviceSynchronize());
+    GR_CU(cudaMemPoolTrimTo(g_cache_pool[dev], 0));
+  }
+  return GRNND_OK;
+}
+
+namespace {
 // Pinned host slots for the per-round probe of the build driver (one pair per host thread;
 // released at thread exit).
 struct RoundProbe {
@@ -466,6 +516,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   DevMem mscratch(am, st);
   if (am.pool) {
     block->pooled = true;
+    block->sync_before_free = am.sync_before_free;
     block->free_stream = am.free_stream;
     GR_CU(cudaMallocFromPoolAsync(&block->points, pts_b, am.pool, st));
     GR_CU(cudaMallocFromPoolAsync(&block->graph, graph_b, am.pool, st));
@@ -683,7 +734,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
 
 int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
                    grnnd_graph** graph_out) {
-  return grnnd::build_with(points, n, d, p, grnnd::AllocMode(), graph_out);
+  return grnnd::build_with(points, n, d, p, cache_alloc_mode(), graph_out);
 }
 
 int grnnd_build_batch(const float* points, const int64_t* offsets, int32_t nbuild, int32_t d,
@@ -702,7 +753,7 @@ int grnnd_build_batch(const float* points, const int64_t* offsets, int32_t nbuil
     if ((int64_t)p->S > nb - 1) return fail(GRNND_EINVAL, "need S <= (points of every build) - 1");
   }
   if (offsets[nbuild] > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "total points must be <= 2^31 - 2");
-  return build_core(points, offsets[nbuild], d, p, offsets, nbuild, graphs_out);
+  return build_core(points, offsets[nbuild], d, p, offsets, nbuild, graphs_out, cache_alloc_mode());
 }
 
 int grnnd_autotune(const float* points, int64_t n, int32_t d, const int64_t* offsets, int32_t nbuild,

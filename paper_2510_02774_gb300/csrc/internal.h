@@ -60,6 +60,9 @@ struct PointsSet {
 struct AllocMode {
   cudaMemPool_t pool = nullptr;
   cudaStream_t free_stream = nullptr;
+  // the graph's memory may still be read by the caller's own work on any stream when it is
+  // freed: synchronise the device first (the memory cache of grnnd_set_memory_cache)
+  bool sync_before_free = false;
 };
 
 size_t workspace_bytes(int64_t n, int R);
@@ -151,8 +154,10 @@ struct GraphBlock {
   void* points = nullptr;
   void* graph = nullptr;
   bool pooled = false;
+  bool sync_before_free = false;
   cudaStream_t free_stream = nullptr;
   ~GraphBlock() {
+    if (pooled && sync_before_free && (points || graph)) cudaDeviceSynchronize();
     for (void* q : {points, graph})
       if (q) {
         if (pooled)

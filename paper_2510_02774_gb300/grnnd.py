@@ -151,6 +151,7 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "grnnd_server_destroy": (None, [ctypes.c_void_p]),
+    "grnnd_set_memory_cache": (ctypes.c_int, [ctypes.c_uint64]),
 }
 
 
@@ -269,6 +270,12 @@ class Graph:
     def search(self, queries, k: int = 10, beam: int = 64):
         """Candidate-list search; queries numpy (host) or torch (host or device)."""
         return search(self, queries, k, beam)
+
+
+def set_memory_cache(nbytes: int) -> None:
+    """grnnd_set_memory_cache: keep up to nbytes of freed build memory on the current device
+    for the next build (0 turns the cache off and releases it)."""
+    _check(lib().grnnd_set_memory_cache(int(nbytes)))
 
 
 def params(S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,

@@ -611,3 +611,22 @@ def test_resume_from_host_checkpoint_equals_build(G, stop_after):
     assert (ids.cpu().numpy() == wids).all()
     assert (dd.cpu().numpy()[wids >= 0] == wd[wids >= 0]).all()
     assert G.entry_point(Xd, d) == want.entry
+
+
+def test_memory_cache_gives_the_same_graphs(G):
+    X = synth.small_integers(5000, 40, -8, 8, seed=44)
+    kw = dict(S=16, R=32, T1=2, T2=4, seed=5, precision=G.BF16)
+    want = G.build(X, **kw).to_numpy()
+    try:
+        G.set_memory_cache(1 << 30)
+        graphs = [G.build(X, **kw) for _ in range(3)]  # later builds reuse the cached memory
+        del graphs[0]
+        graphs.append(G.build(X, **kw))
+        batch = G.build_batch(X, [0, 2000, 5000], **kw)
+        for g in graphs:
+            for a, b in zip(g.to_numpy(), want):
+                assert (a == b).all()
+        assert (batch[1].to_numpy()[2] == G.build(X[2000:], **kw).to_numpy()[2]).all()
+    finally:
+        G.set_memory_cache(0)
+    assert (G.build(X, **kw).to_numpy()[0] == want[0]).all()
