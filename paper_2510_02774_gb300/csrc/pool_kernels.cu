@@ -87,18 +87,23 @@ int sm_count() {
 //   32 candidates are tested per step; a lane is rejected if its id matches an accepted
 //   id or an earlier lane of the same step.
 // =====================================================================================
+constexpr int IW = 4;   // warps per rnd_init CTA
+constexpr int IC = 16;  // dimensions per staged chunk
 template <int METRIC>
-__global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__ X, int64_t n,
-                                                        int d, int ld, int S, int R, uint64_t seed,
-                                                        uint64_t* __restrict__ keys,
-                                                        int32_t* __restrict__ deg,
-                                                        const int2* __restrict__ vseg) {
-  __shared__ int32_t acc_ids[8][kMaxR];
+__global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restrict__ X, int64_t n,
+                                                           int d, int ld, int S, int R, uint64_t seed,
+                                                           uint64_t* __restrict__ keys,
+                                                           int32_t* __restrict__ deg,
+                                                           const int2* __restrict__ vseg) {
+  __shared__ int32_t acc_ids[IW][kMaxR];
+  // the chunk of each drawn row (rows 0..S-1) and of v itself (row S), 16-byte granules
+  __shared__ __align__(16) float stage[IW][kMaxR + 1][IC + 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* acc = acc_ids[warp];
+  float(*rows)[IC + 4] = stage[warp];
   const uint64_t head = hash_head(seed, 0, 0);
   const unsigned below = lanemask_lt();
-  for (int64_t v = (int64_t)blockIdx.x * 8 + warp; v < n; v += (int64_t)gridDim.x * 8) {
+  for (int64_t v = (int64_t)blockIdx.x * IW + warp; v < n; v += (int64_t)gridDim.x * IW) {
     // the vertex's build: ids [lo, lo + nb); draws use the local id v - lo
     const int64_t lo = vseg ? vseg[v].x : 0;
     const uint64_t nm1 = (uint64_t)((vseg ? (int64_t)vseg[v].y : n) - 1);
@@ -118,16 +123,36 @@ __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__
       cnt = min(S, cnt + __popc(ok));
       __syncwarp();
     }
-    const float* xv = X + v * (int64_t)ld;
+    // canonical distances, lane e for entries e and e + 32: the rows are staged IC dimensions
+    // at a time with whole-row coalesced loads; each lane then advances its four partial sums
+    // over the chunk in ascending dimension order, exactly as row_dist does
+    float4 ps[2] = {make_float4(0.0f, 0.0f, 0.0f, 0.0f), make_float4(0.0f, 0.0f, 0.0f, 0.0f)};
+    for (int c0 = 0; c0 < d; c0 += IC) {
+      const int clen = min(IC, d - c0);
+      const int gr = (clen + 3) >> 2;  // granules per row
+      for (int t = lane; t < (S + 1) * gr; t += 32) {
+        const int r = t / gr, q = t - r * gr;
+        const int64_t src = r < S ? (int64_t)acc[r] : v;
+        float4 val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
+        if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
+        *reinterpret_cast<float4*>(&rows[r][4 * q]) = val;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int e = j * 32 + lane;
+        if (e < S)
+          for (int q = 0; q < gr; ++q)
+            dist_step4<METRIC>(ps[j], *reinterpret_cast<const float4*>(&rows[S][4 * q]),
+                               *reinterpret_cast<const float4*>(&rows[e][4 * q]));
+      }
+      __syncwarp();
+    }
     uint64_t kk[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int e = j * 32 + lane;
-      kk[j] = kEmpty;
-      if (e < S) {
-        const int32_t u = acc[e];
-        kk[j] = make_key(row_dist<METRIC>(xv, X + (int64_t)u * ld, d), (uint32_t)u, 0u);
-      }
+      kk[j] = e < S ? make_key(dist_finish4<METRIC>(ps[j]), (uint32_t)acc[e], 0u) : kEmpty;
     }
     warp_sort_u64<2>(kk);
 #pragma unroll
@@ -143,12 +168,12 @@ __global__ void __launch_bounds__(256) rnd_init_kernel(const float* __restrict__
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
                              uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st,
                              const int2* vseg) {
-  const int64_t blocks = std::min<int64_t>(ceil_div(n, 8), (int64_t)sm_count() * 16);
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
   ProfScope ps("rnd_init", st);
   if (metric == 0)
-    rnd_init_kernel<0><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
+    rnd_init_kernel<0><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
   else
-    rnd_init_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
+    rnd_init_kernel<1><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
   return cudaGetLastError();
 }
 
