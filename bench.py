@@ -35,8 +35,8 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # launches -- averaged over the 60 rounds of one build of the workload above, from the
 # one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
 # the kernel source is unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9073e9,
-           "source_sha256": "48e6d6bc5702da2cb1c5032132cc45ba6761d36db694e0b11563cdfe0059c626"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9069e9,
+           "source_sha256": "9e2aabad02143f3227221631d181f9bfb3990835b8d12b5e545979553bf12187"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
