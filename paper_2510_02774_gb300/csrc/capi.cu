@@ -34,6 +34,13 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+// The status word of a step: 1 = a bounded device wait gave up; 2 = an index outside its buffer
+// (only the checked build, -DGRNND_CHECKS=1, tests for it).
+int status_fail(int32_t word) {
+  if (word == 2) return fail(GRNND_ECUDA, "a device bounds check failed (checked build)");
+  return fail(GRNND_ETIMEOUT, "a device-side wait reached its iteration limit");
+}
+
 #define GR_CU(call)                                                                         \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
@@ -263,7 +270,7 @@ int grnnd_workspace_status(const void* workspace, size_t workspace_bytes, int64_
   int32_t h = 0;
   GR_CU(cudaMemcpyAsync(&h, ws.err, 4, cudaMemcpyDeviceToHost, st));
   GR_CU(cudaStreamSynchronize(st));
-  if (h) return fail(GRNND_ETIMEOUT, "a device-side wait of the last step reached its iteration limit");
+  if (h) return status_fail(h);
   return GRNND_OK;
 }
 
@@ -662,7 +669,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
       GR_CU(cudaEventRecord(rev[cur], st));
       if (prev >= 0) {  // the previous round's outcome, read while this one runs
         GR_CU(cudaEventSynchronize(rev[prev]));
-        if (probe[prev].err) return fail(GRNND_ETIMEOUT, "a device-side wait of a round reached its iteration limit");
+        if (probe[prev].err) return status_fail(probe[prev].err);
         if (probe[prev].fresh == 0) break;  // no new entry anywhere: the rest are identities
       }
       prev = cur;
@@ -701,7 +708,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   GR_CU(cudaMemcpyAsync(h_entry.data(), d_entry, (size_t)nbuild * 4, cudaMemcpyDeviceToHost, st));
   GR_CU(cudaMemcpyAsync(h_stats, stats, 72, cudaMemcpyDeviceToHost, st));
   GR_CU(cudaStreamSynchronize(st));
-  if ((int32_t)h_stats[8]) return fail(GRNND_ETIMEOUT, "a device-side wait reached its iteration limit");
+  if ((int32_t)h_stats[8]) return status_fail((int32_t)h_stats[8]);
 
   for (int32_t b = 0; b < nbuild; ++b) {
     const int64_t lo = batched ? offsets[b] : 0, nb = batched ? offsets[b + 1] - offsets[b] : n;

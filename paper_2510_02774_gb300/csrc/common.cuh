@@ -195,5 +195,18 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, u
 
 // Status word written by kernels whose bounded waits gave up.
 constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;
+
+// Bounds checks of the checked build (-DGRNND_CHECKS=1, the stand-in for a memory checker): an
+// index outside its buffer records kErrBounds in the step's status word (so the rest of the
+// step does nothing) and the access is skipped.  In the normal build they compile to nothing.
+#ifdef GRNND_CHECKS
+__device__ __forceinline__ bool in_bounds(bool ok, int32_t* err) {
+  if (!ok) atomicCAS(err, 0, kErrBounds);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(bool, int32_t*) { return true; }
+#endif
 
 }  // namespace grnnd

@@ -16,6 +16,7 @@ struct Workspace {
   int64_t n = 0;
   int R = 0;
   int32_t* red_tgt = nullptr;              // redirect / reverse-proposal targets (-1: unused)
+  int64_t red_cap = 0;                     // slots of red_tgt / red_key
   uint64_t* red_key = nullptr;             // n*R their keys
   uint64_t* bucket = nullptr;              // n*R keys bucketed by target
   int32_t* count = nullptr;                // n proposals per target (zeroed per step)

@@ -542,6 +542,7 @@ struct JoinArgs {
   int32_t* red_tgt;
   uint64_t* red_key;
   unsigned long long* red_n;
+  int64_t red_cap;          // redirect slots in red_tgt / red_key
   int32_t* count;
   int64_t* stats;
   int32_t* err;
@@ -1157,9 +1158,11 @@ __global__ void __launch_bounds__(JT) rnd_join_kernel(JoinArgs a) {
           const int g = s.deadrank[ev] + __popcll(~ealive & valid & bits_below(ep));
           const unsigned long long slot =
               g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
-          a.red_tgt[slot] = tgt;
-          a.red_key[slot] = make_key(dd, (uint32_t)B.pid[t], 0u);
-          atomicAdd(&a.count[tgt], 1);
+          if (in_bounds(slot < (unsigned long long)a.red_cap && (uint64_t)tgt < (uint64_t)a.n, a.err)) {
+            a.red_tgt[slot] = tgt;
+            a.red_key[slot] = make_key(dd, (uint32_t)B.pid[t], 0u);
+            atomicAdd(&a.count[tgt], 1);
+          }
         }
       }
       for (int u = tid; u < nb * R; u += JT) {
@@ -1452,7 +1455,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     }
 
     // ---- gather + tile ---------------------------------------------------------------
-    const bool need = valid_p && np > 0;  // rows of groups with pairs only
+    const bool need = valid_p && np > 0 &&  // rows of groups with pairs only
+                      in_bounds((uint64_t)(uint32_t)id < (uint64_t)a.n, a.err);
     const uint32_t needm = __ballot_sync(0xffffffffu, need);
     const int nch = needm ? nchd : 0;
     const int pdb = g * ((VW * (VW - 1)) >> 1);
@@ -1656,7 +1660,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const bool surv = valid_p && ((alive >> gl) & 1u);
     const uint32_t smask = (__reduce_or_sync(0xffffffffu, surv ? (1u << hs) : 0u) >> gb) & gmask;
     const int nkeep = __popc(alive & validm);
-    if (m > 0) {
+    if (m > 0 && in_bounds((uint64_t)v < (uint64_t)a.n, a.err)) {
       if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
       for (int t = nkeep + gl; t < R; t += VW) a.keys_out[v * R + t] = kEmpty;
       if (gl == 0) a.deg_out[v] = nkeep;
@@ -1694,9 +1698,11 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
         const int32_t tgt = s.pid[gb + mykill];
         const int rk = pre + __popc(~alive & validm & below);
         const unsigned long long sl = rk < avail ? base + (unsigned long long)rk : b1 + (unsigned long long)(rk - avail);
-        a.red_tgt[sl] = tgt;
-        a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
-        atomicAdd(&a.count[tgt], 1);
+        if (in_bounds(sl < (unsigned long long)a.red_cap && (uint64_t)(uint32_t)tgt < (uint64_t)a.n, a.err)) {
+          a.red_tgt[sl] = tgt;
+          a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
+          atomicAdd(&a.count[tgt], 1);
+        }
       }
     }
     if (gl == 0 && m > 0) {
@@ -1951,7 +1957,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
       infl |= 1u << st;
       __syncthreads();
-      if (has) {
+      // (checked build: a row id out of range is not copied; the stage's wait then gives up)
+      if (has && in_bounds((uint64_t)idl < (uint64_t)a.n, a.err)) {
         const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
                                    : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)idl * a.P.ldb + c0;
         bulk_g2s(rowbase + ((size_t)st * TM + row) * C::RS, src, bytes, &s.bar[st]);
@@ -2169,9 +2176,10 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     }
     __syncthreads();
     const uint64_t smask = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);  // survivors by slot
-    if (surv) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
-    for (int t = nkeep + tid; t < R; t += TM) a.keys_out[v * R + t] = kEmpty;
-    if (tid == 0) a.deg_out[v] = nkeep;
+    const bool vok = in_bounds((uint64_t)v < (uint64_t)a.n, a.err);
+    if (surv && vok) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
+    for (int t = nkeep + tid; vok && t < R; t += TM) a.keys_out[v * R + t] = kEmpty;
+    if (tid == 0 && vok) a.deg_out[v] = nkeep;
     if (a.emit_redirects && has && !surv) {
       const int kp = s.killer[pi];
       const int ri = s.prow[kp], rj = row;
@@ -2181,9 +2189,11 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       const int g = __popcll(~alive & valid & bits_below(pi));
       const unsigned long long sl =
           g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
-      a.red_tgt[sl] = tgt;
-      a.red_key[sl] = make_key(dd, idl, 0u);
-      atomicAdd(&a.count[tgt], 1);
+      if (in_bounds(sl < (unsigned long long)a.red_cap && (uint64_t)(uint32_t)tgt < (uint64_t)a.n, a.err)) {
+        a.red_tgt[sl] = tgt;
+        a.red_key[sl] = make_key(dd, idl, 0u);
+        atomicAdd(&a.count[tgt], 1);
+      }
     }
     if (tid == 0) {
       if (np > 0) {
@@ -2345,14 +2355,18 @@ __global__ void __launch_bounds__(SCAN_T) scan_apply_kernel(const int32_t* __res
 __global__ void scatter_kernel(const int32_t* __restrict__ tgt, const uint64_t* __restrict__ pk,
                                const unsigned long long* __restrict__ nred,
                                const int64_t* __restrict__ off, int32_t* __restrict__ count,
-                               uint64_t* __restrict__ bucket, const int32_t* __restrict__ err) {
+                               uint64_t* __restrict__ bucket, int32_t* __restrict__ err, int64_t n,
+                               int64_t red_cap, int64_t bucket_cap) {
   if (*err) return;  // a join wait gave up: the slots are incomplete, merge nothing
   const int64_t nslots = (int64_t)*nred;
+  if (!in_bounds(nslots <= red_cap, err)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t = tgt[i];
     if (t < 0) continue;  // unused tail of a reserved chunk
+    if (!in_bounds(t < n, err)) continue;
     const int pos = atomicSub(&count[t], 1) - 1;
+    if (!in_bounds(pos >= 0 && off[t] + pos < bucket_cap, err)) continue;
     bucket[off[t] + pos] = pk[i];
   }
 }
@@ -2530,7 +2544,7 @@ struct SelectArgs {
   int32_t* deg_out;
   int64_t* round_new;
   int64_t* stats;
-  const int32_t* err;      // nonzero: a wait of this round gave up, leave every pool as it is
+  int32_t* err;            // nonzero: a wait of this round gave up, leave every pool as it is
   uint8_t* next_active;    // per target: its output row holds a new entry (prep's hint), or null
   int next_active_all;     // 1: write the flag of every target (a round: rows the merge leaves
                            // alone hold no new entry); 0: only of merged targets (a reverse step)
@@ -2569,6 +2583,7 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
       const int64_t u = u0 + tl;
       const int64_t b0 = __shfl_sync(0xffffffffu, b0l, tl), c = __shfl_sync(0xffffffffu, cl, tl);
       const bool kept = __shfl_sync(0xffffffffu, keptl ? 1 : 0, tl) != 0;
+      if (!in_bounds(b0 >= 0 && c >= 0 && b0 + c <= a.n * R, a.err)) continue;
       const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
       const int na = kept ? a.deg_out[u] : a.deg_in[u];
       n_in += c;
@@ -2622,7 +2637,8 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
     {
       ProfScope ps("scatter", st);
       scatter_kernel<<<(unsigned)(sm_count() * 8), 256, 0, st>>>(ws.red_tgt, ws.red_key, ws.red_n, ws.off,
-                                                                 ws.count, ws.bucket, ws.err);
+                                                                 ws.count, ws.bucket, ws.err, n, ws.red_cap,
+                                                                 n * ws.R);
     }
   }
   cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
@@ -2683,6 +2699,7 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   a.red_tgt = ws.red_tgt;
   a.red_key = ws.red_key;
   a.red_n = ws.red_n;
+  a.red_cap = ws.red_cap;
   a.count = ws.count;
   a.stats = stats;
   a.err = ws.err;
@@ -2803,7 +2820,8 @@ __global__ void reverse_propose_kernel(int64_t n, int R, float rho,
                                        const int32_t* __restrict__ deg,
                                        int32_t* __restrict__ tgt, uint64_t* __restrict__ pk,
                                        unsigned long long* __restrict__ red_n,
-                                       int32_t* __restrict__ count) {
+                                       int32_t* __restrict__ count, int64_t red_cap,
+                                       int32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t total = n * R;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -2829,9 +2847,11 @@ __global__ void reverse_propose_kernel(int64_t n, int R, float rho,
     off = __shfl_sync(0xffffffffu, off, 0);
     if (emit) {
       const unsigned long long slot = off + __popc(b & lanemask_lt());
-      tgt[slot] = t;
-      pk[slot] = key;
-      atomicAdd(&count[t], 1);
+      if (in_bounds(slot < (unsigned long long)red_cap && (uint64_t)(uint32_t)t < (uint64_t)n, err)) {
+        tgt[slot] = t;
+        pk[slot] = key;
+        atomicAdd(&count[t], 1);
+      }
     }
   }
 }
@@ -2847,7 +2867,8 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
     const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
     ProfScope ps("reverse_propose", st);
     reverse_propose_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, R, rho, keys_in, deg_in, ws.red_tgt,
-                                                            ws.red_key, ws.red_n, ws.count);
+                                                            ws.red_key, ws.red_n, ws.count, ws.red_cap,
+                                                            ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   SelectArgs sa;
@@ -2934,6 +2955,7 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   ws->n = n;
   ws->R = R;
   ws->red_tgt = reinterpret_cast<int32_t*>(p);
+  ws->red_cap = (int64_t)slots;
   p += al256(slots * 4);
   ws->red_key = reinterpret_cast<uint64_t*>(p);
   p += al256(slots * 8);
