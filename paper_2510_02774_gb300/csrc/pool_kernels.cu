@@ -1774,7 +1774,7 @@ namespace {
 constexpr int TM = 64;     // pool entries per team
 constexpr int TRED = 512;  // redirect slots a team reserves at a time
 constexpr int TDC = 128;   // columns per gathered chunk
-constexpr int TRQ = 256;   // re-decisions a team queues per vertex (more are taken in place)
+constexpr int TRQ = 64;    // re-decisions a team queues per vertex (more are taken in place)
 
 template <int PREC>
 struct TPrec;
@@ -1804,16 +1804,15 @@ struct __align__(16) TeamKey {
 };
 
 struct __align__(16) TeamSmem {
-  float pd[TM * (TM - 1) / 2];    // per pair: its distance (partial dot product between chunks)
   union {
-    TeamKey hk[TM];               // order key by storage slot (visit order)
-    uint8_t F[TM][TM];            // F[p][q], q < p: pair (q, p) fired (0 / 1) (tile .. chain)
+    TeamKey hk[TM];                 // order key by storage slot (visit order), until the tiles
+    float pd[TM * (TM - 1) / 2];    // per pair: its distance (partial dot product between chunks)
   };
   uint64_t fire[TM], closer[TM];  // by pi position; bit a < b: pair (a, b) fired / a is closer
   float2 rnd[TM];                 // by row: (squared norm of the BF16 row, recorded dist to v)
   float rdq[TM];                  // by row: norm of the quantization residual
   int32_t pid[TM];                // by pi position
-  int32_t roff[TM + 1];           // first pair index of new row i
+  uint16_t roff[TM + 1];          // first pair index of new row i
   uint8_t rpos[TM], prow[TM], killer[TM];
   uint16_t rq[TRQ];               // pairs (row i << 6 | row j) whose decision is re-taken in FP32
   int32_t nrq;
@@ -1824,6 +1823,10 @@ struct __align__(16) TeamSmem {
   int32_t red_avail;
 };
 constexpr size_t kTeamRowsOff = (sizeof(TeamSmem) + 127) & ~(size_t)127;  // staged rows follow
+// BF16 rows of up to 128 dimensions: eight team CTAs fit one SM (233,472 bytes of shared
+// memory, 1,024 reserved per CTA), as many as the 128-register threads allow
+static_assert(8 * (kTeamRowsOff + (size_t)TM * (TDC + 8) * 2 + 1024) <= 233472,
+              "team shared memory must allow eight CTAs per SM");
 
 constexpr int kTeamTiles = 20;  // (I, J) with I < 4, J < 8 and J >= 2I (some j > i in the tile)
 
@@ -1945,6 +1948,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       if (PREC >= 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
     }
     if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
+    s.fire[tid] = 0ull;  // fire bits are set by the pairs that fire (shared atomics)
     __syncthreads();
 
     // ---- gather + tile -------------------------------------------------------------------
@@ -2055,7 +2059,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
             }
             s.pd[q[e]] = dab;
             const int pa2 = s.rpos[i], pb2 = s.rpos[j];
-            s.F[max(pa2, pb2)][min(pa2, pb2)] = fire ? 1 : 0;
+            if (fire)
+              atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa2, pb2)]), 1ull << min(pa2, pb2));
           }
         }
       } else {
@@ -2079,7 +2084,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           const float dab = dist_finish4<METRIC>(acc);
           s.pd[q] = dab;
           const int pa = s.rpos[i], pb = s.rpos[j];
-          s.F[max(pa, pb)][min(pa, pb)] = dab < fmaxf(s.rnd[i].y, s.rnd[j].y) ? 1 : 0;
+          if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y))
+            atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa, pb)]), 1ull << min(pa, pb));
         }
       }
       __syncthreads();
@@ -2104,23 +2110,11 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         const float* xb = a.P.X + (int64_t)s.pid[pb2] * a.P.ld;
         const float dab = row_dist<METRIC>(xa, xb, d);
         s.pd[s.roff[i] + (j - i - 1)] = dab;
-        s.F[max(pa2, pb2)][min(pa2, pb2)] = dab < fmaxf(s.rnd[i].y, s.rnd[j].y) ? 1 : 0;
+        if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y))
+          atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa2, pb2)]), 1ull << min(pa2, pb2));
       }
       __syncthreads();
     }
-    // fire masks: thread p gathers the bytes F[p][0..p-1] (the low bit of each: bytes that no
-    // pair wrote may hold anything) and keeps the pairs that were evaluated
-    if (tid < m) {
-      uint64_t fm = 0ull;
-      if (nch > 0) {
-        const uint32_t* fw = reinterpret_cast<const uint32_t*>(&s.F[tid][0]);
-        for (int w4 = 0; 4 * w4 < tid; ++w4)
-          fm |= (uint64_t)((((fw[w4] & 0x01010101u) * 0x10204080u) >> 28)) << (4 * w4);
-        fm &= bits_below(tid) & (((newm >> tid) & 1ull) ? valid : newm);
-      }
-      s.fire[tid] = fm;
-    }
-    __syncthreads();
     // ---- prune: warp 0 replays the chain over the columns with fire bits -----------------
     if (warp == 0) {
       uint64_t cl = (uint64_t)__ballot_sync(0xffffffffu, lane < m && s.fire[lane] != 0ull) |
