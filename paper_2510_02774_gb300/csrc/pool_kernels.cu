@@ -1281,7 +1281,6 @@ struct __align__(16) WarpSlot {
   int32_t roff[WM];             // by row: local index of the first pair of new row i
   uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
   uint8_t inv[WM];              // by storage slot (group base + slot): local position
-  uint8_t F[WM][WM];            // F[p][q], q < p: pair (q, p) of a group fired (0 / 1)
   uint16_t rq[WRQ];             // pairs (row i << 5 | row j) whose decision is re-taken in FP32
   int32_t nrq;                  // queued re-decisions of the item
   int32_t gk[4], gm[4];         // per group: new entries, entries
@@ -1437,6 +1436,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       s.gk[g] = k;
       s.gm[g] = m;
     }
+    s.fire[lane] = 0u;  // fire bits are set by the pairs that fire (shared atomics)
     __syncwarp();
     // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
     // closer mask of a position is the prefix OR, over the slots before its own, of the
@@ -1565,7 +1565,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
               }
             }
             s.pd[q[e]] = dab;
-            s.F[eb + max(pa2, pb2)][min(pa2, pb2)] = fire ? 1 : 0;
+            if (fire) atomicOr(&s.fire[eb + max(pa2, pb2)], 1u << min(pa2, pb2));
           }
         }
       } else {
@@ -1589,7 +1589,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           const float dab = dist_finish4<METRIC>(acc);
           s.pd[pdb + q] = dab;
           const int pa = s.rpos[gb + i], pb = s.rpos[gb + j];
-          s.F[gb + max(pa, pb)][min(pa, pb)] = dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y) ? 1 : 0;
+          if (dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y)) atomicOr(&s.fire[gb + max(pa, pb)], 1u << min(pa, pb));
         }
       }
       __syncwarp();
@@ -1612,20 +1612,9 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
         const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
         const float dab = row_dist<METRIC>(xa, xb, d);
         s.pd[ge * ((VW * (VW - 1)) >> 1) + s.roff[i] + (lj - li - 1)] = dab;
-        s.F[eb + max(pa2, pb2)][min(pa2, pb2)] = dab < fmaxf(s.rnd[i].y, s.rnd[j].y) ? 1 : 0;
+        if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y)) atomicOr(&s.fire[eb + max(pa2, pb2)], 1u << min(pa2, pb2));
       }
       __syncwarp();
-    }
-    // fire masks: position p gathers the bytes F[p][0..p-1] of the pairs it closes
-    if (valid_p && nch > 0) {
-      uint32_t fm = 0u;
-      const uint32_t* fw = reinterpret_cast<const uint32_t*>(&s.F[P][0]);
-      // the low bit of each byte (bytes never written may hold anything), four bits per word
-      for (int w4 = 0; 4 * w4 < gl; ++w4) fm |= (((fw[w4] & 0x01010101u) * 0x10204080u) >> 28) << (4 * w4);
-      const bool isnew = (newm >> gl) & 1u;
-      s.fire[P] = fm & below & (isnew ? validm : newm);  // evaluated pairs only
-    } else if (valid_p) {
-      s.fire[P] = 0u;
     }
     if (valid_p) s.closer[P] = closer_p;
     __syncwarp();
