@@ -359,14 +359,21 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
       if (lane == 0 && bc[c]) o = atomicAdd(&list_n[c], __popc(bc[c]));
       off[c] = __shfl_sync(0xffffffffu, o, 0);
     }
-    // the warp writes the records of its active vertices, one after the other
+    // the warp writes the records of its active vertices, four at a time (eight lanes each),
+    // so that four chains of dependent loads (key, then the row terms it names) overlap
     unsigned left = bc[0] | bc[1] | bc[2] | bc[3];
+    const int grp = lane >> 3, gln = lane & 7;
     while (left) {
-      const int l = __ffs(left) - 1;
-      left &= left - 1;
-      const int64_t u = base + l;
-      const int mu = __shfl_sync(0xffffffffu, m, l);
-      const int cu = __shfl_sync(0xffffffffu, cls, l);
+      unsigned mine = left;  // this group's vertex: the grp-th remaining one
+      for (int q = 0; q < grp; ++q) mine &= mine - 1;
+      const int l = mine ? __ffs(mine) - 1 : -1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) left &= left - 1;  // (clearing past the last bit is harmless)
+      const int ls = l < 0 ? 0 : l;
+      const int64_t u = base + ls;
+      const int mu = __shfl_sync(0xffffffffu, m, ls);
+      const int cu = __shfl_sync(0xffffffffu, cls, ls);
+      if (l < 0) continue;
       const unsigned below_l = (1u << l) - 1u;
       unsigned bcu = bc[0];
       int offu = off[0], W = rs.w[0], cap = rs.cap[0];
@@ -381,11 +388,11 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
           rg = rs.rec[c];
         }
       uint64_t* r = rg + (int64_t)(offu + __popc(bcu & below_l)) * W;
-      if (lane == 0) {
+      if (gln == 0) {
         r[0] = (uint64_t)u | ((uint64_t)(vseg ? vseg[u].x : 0) << 32);
         r[1] = (uint64_t)mu;
       }
-      for (int j = lane; j < mu; j += 32) {
+      for (int j = gln; j < mu; j += 8) {
         const uint64_t k = keys[u * R + j];
         r[2 + j] = k;
         if (aux) {
