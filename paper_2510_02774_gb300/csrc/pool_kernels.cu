@@ -2540,7 +2540,7 @@ struct SelectArgs {
                            // alone hold no new entry); 0: only of merged targets (a reverse step)
 };
 
-__global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
+__global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   __shared__ MergeScratch scratch[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   MergeScratch& ms = scratch[warp];
