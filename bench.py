@@ -35,8 +35,8 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # launches -- averaged over the 60 rounds of one build of the workload above, from the
 # one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
 # the kernel source is unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9069e9,
-           "source_sha256": "9e2aabad02143f3227221631d181f9bfb3990835b8d12b5e545979553bf12187"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9071e9,
+           "source_sha256": "9c75be028a1aab5a3d926d25540a8b4ad067d0e9b039c71acd4569e2a5d70c7e"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
