@@ -630,3 +630,18 @@ def test_memory_cache_gives_the_same_graphs(G):
     finally:
         G.set_memory_cache(0)
     assert (G.build(X, **kw).to_numpy()[0] == want[0]).all()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_build_high_dimension_matches_oracle(G, orc, precision):
+    # d = 960 (GIST's dimension): rows staged in eight chunks of 128 dimensions (partial sums
+    # carried between chunks in every join kernel; FP32 rows this long use the batched CTA
+    # join); integers keep every form exact, so the graph is the oracle's
+    X = synth.small_integers(1500, 960, -8, 8, seed=960)
+    prec = {"fp32": G.FP32, "bf16": G.BF16, "fp8": G.FP8}[precision]
+    g = G.build(X, S=16, R=48, T1=2, T2=3, rho=0.6, seed=5, precision=prec)
+    ids, dist, deg = g.to_numpy()
+    wids, wd, wdeg, _ = orc.build_graph(X, 16, 48, 2, 3, 0.6, 5)
+    assert (deg == wdeg).all() and (ids == wids).all()
+    assert (dist[wids >= 0] == wd[wids >= 0].astype(np.float32)).all()
+    assert g.stats()["rechecks"] == 0
