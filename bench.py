@@ -36,7 +36,7 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
 # the kernel source is unchanged since that capture.
 TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9071e9,
-           "source_sha256": "9c75be028a1aab5a3d926d25540a8b4ad067d0e9b039c71acd4569e2a5d70c7e"}
+           "source_sha256": "1d14de968d54abeb34ae595b565f53bd9cb01600fbbeed98d521f77324d15553"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
@@ -180,8 +180,13 @@ def _pct(xs, p):
 
 
 def _source_sha():
-    with open(os.path.join(ROOT, "paper_2510_02774_gb300", "csrc", "pool_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """sha256 of the pool kernels' code: comments and blank lines removed, so the figure
+    follows the code, not its commentary."""
+    import re
+    with open(os.path.join(ROOT, "paper_2510_02774_gb300", "csrc", "pool_kernels.cu")) as f:
+        text = f.read()
+    lines = [re.sub(r"\s*//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
 def run_precision_report(args):

@@ -1240,10 +1240,11 @@ cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name, 
 //            lane group -> pi
 //   gather   one bulk copy per row (lane p: the row of pi position p), new rows first,
 //            completing on the warp's own mbarrier, in chunks of 128 dimensions
-//   tile     BF16: mma.sync m16n8k16 tiles (six for one vertex, the four diagonal ones
-//            for lane groups), FP32 accumulators kept across chunks, fire decisions taken
-//            from the accumulators; FP32 (d <= 128): each group's lanes take its pairs
-//            one by one with the canonical four-accumulator distance
+//   tile     BF16 / FP8: mma.sync m16n8k16 / m16n8k32 tiles (six for one vertex, the four
+//            diagonal ones for lane groups), partial dot products kept between chunks,
+//            fire decisions taken from the accumulators; FP32 (d <= 128): each group's
+//            lanes take its pairs one by one with the canonical four-accumulator distance;
+//            a pair that fires sets its bit in the later position's mask (shared atomic)
 //   prune    every lane replays its group's mask chain (the data are broadcast), so each
 //            lane learns whether its entry survives and, if not, its absorber
 //   emit     survivors in key order in place; redirects into per-warp slot chunks
@@ -1757,10 +1758,11 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
 // vertex; thread t owns pool entry t (storage slot t).
 //   order   rank of (h, id) among the m entries (16-byte keys in shared memory);
 //   gather  one bulk copy per row and 128-column chunk (two stages when d > 128);
-//   tile    BF16: mma.sync m16n8k16 tiles over new rows x all rows, shared between the
-//           two warps and taken one at a time; partial dot products wait in shared memory
+//   tile    BF16 / FP8: mma.sync tiles over new rows x all rows, shared between the two
+//           warps and taken one at a time; partial dot products wait in shared memory
 //           between chunks, and the last chunk decides the fire bits straight from the
-//           accumulators.  FP32 (d <= 128): one thread per pair, canonical distance;
+//           accumulators (a pair that fires sets its bit in the later position's mask by
+//           a shared atomic).  FP32 (d <= 128): one thread per pair, canonical distance;
 //   chain   warp 0 replays the sequential outcome of the pair scan over the fire bits and
 //           records, for each entry made bottom, the entry that absorbed it;
 //   emit    survivors rewritten in place as old; redirects into reserved slots.
