@@ -297,7 +297,8 @@ GRNND_API int grnnd_server_status(grnnd_server *s, uint64_t *bytes_in_use, uint6
                                   int32_t *queued, int32_t *running, int32_t *indices);
 
 /* Finishes the requests that are running, fails the queued ones (GRNND_EBUSY), frees
- * every index and the server. */
+ * every index and the server.  No other call on this server may run concurrently with it
+ * or follow it (requests not yet collected by grnnd_server_wait go with the server). */
 GRNND_API void grnnd_server_destroy(grnnd_server *s);
 
 /* ------------------------------------------------------------------------- */
