@@ -166,3 +166,43 @@ def test_destroy_with_work_in_flight(G):
         srv.submit_build(synth.small_integers(30000, 32, -8, 8, seed=20 + i), S=8, R=16, T1=2, T2=3)
     time.sleep(0.01)
     srv.close()  # finishes what runs, fails what is queued, frees everything
+
+
+def test_submissions_from_several_host_threads(G):
+    # four host threads submit builds and searches at once (the binding releases the GIL in
+    # every call); each result equals the same request run alone
+    import threading
+    cases = []
+    for i in range(8):
+        X = synth.small_integers(1500 + 400 * i, 24 + 8 * (i % 3), -8, 8, seed=300 + i)
+        Q = synth.small_integers(40, X.shape[1], -8, 8, seed=400 + i)
+        kw = dict(S=8, R=16, T1=2, T2=3, seed=i, precision=i % 3)
+        g = G.build(X, **kw)
+        cases.append((X, Q, kw, g.to_numpy(), g.search(Q, 5, 16)))
+    srv = G.Server(slots=3, hbm_budget=4 << 30)
+    errors = []
+
+    def worker(idx):
+        try:
+            for X, Q, kw, want, wq in cases[idx::4]:
+                b = srv.submit_build(X, **kw)
+                s = srv.submit_search(b, Q, 5, 16)
+                srv.wait(b)
+                got = srv.graph(b)
+                assert (got[0] == want[0]).all() and (got[2] == want[2]).all()
+                assert (srv.wait(s)["out"] == wq).all()
+                srv.release(b)
+        except Exception as e:  # reported below, on the test's thread
+            errors.append(e)
+
+    try:
+        ts = [threading.Thread(target=worker, args=(i,)) for i in range(4)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        assert not errors, errors
+        st = srv.status()
+        assert st["indices"] == 0 and st["bytes_in_use"] == 0 and st["queued"] == 0
+    finally:
+        srv.close()
