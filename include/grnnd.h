@@ -363,6 +363,14 @@ GRNND_API int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64
 GRNND_API int grnnd_workspace_status(const void *workspace, size_t workspace_bytes, int64_t n,
                                      int32_t R, void *stream);
 
+/* Self-test of the device-side failure detection (no counterpart in the paper): one thread
+ * waits, with the bounded mbarrier wait of the join kernels, on a barrier that nothing
+ * completes; after `limit` tries (1 <= limit <= 2^20; each try is a hardware-timed
+ * try_wait) it gives up and records the timeout in a status word, which this call reads.
+ * Returns GRNND_ETIMEOUT (the expected outcome), never faults or hangs, copies nothing, and
+ * leaves the context usable.  Synchronises `stream`. */
+GRNND_API int grnnd_selftest_bounded_wait(uint32_t limit, void *stream);
+
 /* Final prune-only pass: the prune of a round with order key t1 (t2 = 0),
  * keeping only each vertex's survivors, in key order; no redirects.
  * keys_out: device n x R (written in full, must not alias keys_in), deg_out:

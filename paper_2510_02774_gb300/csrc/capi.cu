@@ -258,6 +258,15 @@ int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int3
   return GRNND_OK;
 }
 
+int grnnd_selftest_bounded_wait(uint32_t limit, void* stream) {
+  if (limit < 1 || limit > (1u << 20)) return fail(GRNND_EINVAL, "limit must be in [1, 2^20]");
+  int32_t status = -1;
+  GR_CU(grnnd::launch_wait_selftest(limit, &status, (cudaStream_t)stream));
+  if (status == 0) return GRNND_OK;
+  if (status == 1) return fail(GRNND_ETIMEOUT, "the self-test wait gave up after its iteration limit");
+  return fail(GRNND_ECUDA, "the self-test kernel did not report");
+}
+
 int grnnd_workspace_status(const void* workspace, size_t workspace_bytes, int64_t n, int32_t R,
                            void* stream) {
   if (n < 1 || n > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "n out of range");

@@ -131,6 +131,10 @@ cudaError_t launch_brute_knn(const float* X, int64_t n, int d, int ld, int metri
                              int64_t nq, int ldq, int k, int32_t* ids_out, float* dists_out,
                              cudaStream_t st);
 
+// Self-test of the bounded device waits: *status (host) = 1 when a wait that nothing
+// completes gave up after `limit` tries, 0 if it completed (never).  Synchronises `st`.
+cudaError_t launch_wait_selftest(uint32_t limit, int32_t* status, cudaStream_t st);
+
 int sm_count();
 
 // Sets the thread-local message returned by grnnd_last_error.

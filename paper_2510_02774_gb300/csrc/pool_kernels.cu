@@ -22,7 +22,7 @@ namespace grnnd {
 
 namespace {
 
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kWaitLimit = 1u << 18;  // mbarrier try_wait rounds before a wait gives up (about 1 s: a try that does not complete returns after about 3.8 us)
 constexpr int64_t kMaxJoinGrid = 2048;  // CTAs of the join at most (sizes the redirect slack)
 
 // Per-kernel launch set-up kept out of stream captures: the dynamic shared-memory opt-in

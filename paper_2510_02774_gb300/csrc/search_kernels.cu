@@ -520,4 +520,31 @@ cudaError_t launch_brute_knn(const float* X, int64_t n, int d, int ld, int metri
   return cudaGetLastError();
 }
 
+// ---- self-test of the bounded waits -------------------------------------------------------
+// One thread waits, with the same bounded mbarrier wait as the join kernels, on a barrier
+// that expects one arrival and gets none: the wait gives up after `limit` tries and the
+// outcome goes to the status word, as in a join.  Nothing is copied, so nothing is left in
+// flight when the thread returns.
+__device__ int32_t g_wait_selftest_status;
+
+__global__ void wait_selftest_kernel(uint32_t limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  const bool ok = mbar_wait(&bar, 0u, limit);
+  g_wait_selftest_status = ok ? 0 : kErrTimeout;
+}
+
+cudaError_t launch_wait_selftest(uint32_t limit, int32_t* status, cudaStream_t st) {
+  const int32_t unset = -1;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_wait_selftest_status, &unset, 4, 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  wait_selftest_kernel<<<1, 32, 0, st>>>(limit);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyFromSymbolAsync(status, g_wait_selftest_status, 4, 0, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  return cudaStreamSynchronize(st);
+}
+
 }  // namespace grnnd

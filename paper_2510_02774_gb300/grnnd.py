@@ -152,6 +152,7 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "grnnd_server_destroy": (None, [ctypes.c_void_p]),
     "grnnd_set_memory_cache": (ctypes.c_int, [ctypes.c_uint64]),
+    "grnnd_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_void_p]),
 }
 
 
