@@ -35,8 +35,8 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # launches -- averaged over the 60 rounds of one build of the workload above, from the
 # one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
 # the kernel source is unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9071e9,
-           "source_sha256": "1d14de968d54abeb34ae595b565f53bd9cb01600fbbeed98d521f77324d15553"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9070e9,
+           "source_sha256": "0d9dd18f4a54439f0fe9b4c0e4db3c9fd1d45c6a93fcf70f5c9c2cbf660432ee"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm

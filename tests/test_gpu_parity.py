@@ -655,12 +655,15 @@ def test_build_high_dimension_matches_oracle(G, orc, precision):
 def test_bounded_wait_gives_up_and_context_stays_usable(G):
     import time
     L = G.lib()
+    X = synth.small_integers(600, 8, -8, 8, seed=1)
+    before = G.build(X, S=4, R=8, T1=1, T2=2).to_numpy()
     t = time.perf_counter()
     rc = L.grnnd_selftest_bounded_wait(1 << 12, None)
     dt = time.perf_counter() - t
     assert rc == G.ETIMEOUT and b"gave up" in L.grnnd_last_error()
     assert dt < 10.0
     assert L.grnnd_selftest_bounded_wait(0, None) == G.EINVAL
-    X = synth.small_integers(600, 8, -8, 8, seed=1)
-    g = G.build(X, S=4, R=8, T1=1, T2=2)  # the next work on the device runs normally
-    assert g.to_numpy()[2].min() >= 1
+    after = G.build(X, S=4, R=8, T1=1, T2=2).to_numpy()  # later work on the context runs normally
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+    assert after[2].min() >= 1
