@@ -35,8 +35,8 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # launches -- averaged over the 60 rounds of one build of the workload above, from the
 # one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
 # the kernel source is unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9070e9,
-           "source_sha256": "0d9dd18f4a54439f0fe9b4c0e4db3c9fd1d45c6a93fcf70f5c9c2cbf660432ee"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9066e9,
+           "source_sha256": "aa4637b545f05aa3be3ac74e079e24ba7e5bdd3cd5f11fe868d93d4a15fd73b3"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
@@ -675,7 +675,7 @@ def main():
     # ---- CPU baseline (oracle) on a bounded sample --------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_s = min(20000, n)
+        n_s = min(50000, n)  # about 15 s of one host core
         rate, dt = oracle_build_rate(X, n_s)
         cpu = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
                "sample": f"first {n_s} points of the same dataset, same S/R/T1/T2/rho, FP64 single thread, {dt:.1f} s"}

@@ -1245,8 +1245,9 @@ cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name, 
 //            fire decisions taken from the accumulators; FP32 (d <= 128): each group's
 //            lanes take its pairs one by one with the canonical four-accumulator distance;
 //            a pair that fires sets its bit in the later position's mask (shared atomic)
-//   prune    every lane replays its group's mask chain (the data are broadcast), so each
-//            lane learns whether its entry survives and, if not, its absorber
+//   prune    the outcome of the group's sequential mask chain as a fixed point, one column
+//            (pi position) per lane: each lane learns whether its entry survives and, if
+//            not, its absorber
 //   emit     survivors in key order in place; redirects into per-warp slot chunks
 // =====================================================================================
 namespace {
@@ -1283,12 +1284,13 @@ struct __align__(16) WarpSlot {
   typename WPrec<PREC>::T rows[WM][WPrec<PREC>::RS];  // by row: group base + local row
   float pd[WM * (WM - 1) / 2];  // group g's pairs from g * VW (VW - 1) / 2
   int32_t pid[WM];              // by position: group base + local pi position
-  uint32_t fire[WM], closer[WM];  // by position; bits: earlier local positions
+  uint32_t fire[WM];            // by position; bits: earlier local positions that fired with it
   float2 rnd[WM];               // by row: (squared norm of the BF16 row, recorded dist to v)
   float rdq[WM];                // by row: norm of the quantization residual
   int32_t roff[WM];             // by row: local index of the first pair of new row i
   uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
   uint8_t inv[WM];              // by storage slot (group base + slot): local position
+  uint8_t kil[WM];              // by position: the column that absorbed it (chain rounds)
   uint16_t rq[WRQ];             // pairs (row i << 5 | row j) whose decision is re-taken in FP32
   int32_t nrq;                  // queued re-decisions of the item
   int32_t gk[4], gm[4];         // per group: new entries, entries
@@ -1624,33 +1626,46 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       }
       __syncwarp();
     }
-    if (valid_p) s.closer[P] = closer_p;
     __syncwarp();
 
-    // ---- prune: every lane replays its group's chain over the columns with fire bits ----
+    // ---- prune: the chain's outcome, one column (pi position) per lane of the group -------
+    // Column b of the sequential pair scan kills K_b: its live firing partners before the
+    // first closer one f, then b itself (absorbed by f); all of them when none is closer.
+    // Its live partners are the valid positions that no column c < b killed, so the scan's
+    // outcome is the fixed point of K_b = rule(fire[b] & valid & ~OR_{c<b} K_c).  Rounds
+    // that apply the rule to every column at once, from K = 0, reach it: after round r the
+    // columns 0..r hold their final value, so it takes at most m rounds; the first round
+    // whose K has the prefix it was computed from (in every group of the warp) is the fixed
+    // point and ends the loop.
     uint32_t alive = validm;
     int mykill = -1;
     {
-      uint32_t cols = (__ballot_sync(0xffffffffu, valid_p && s.fire[P] != 0u) >> gb) & gmask;
-      int b = cols ? __ffs(cols) - 1 : 0;
-      uint32_t fb = s.fire[gb + b], cb = s.closer[gb + b];
-      while (cols) {
-        cols &= cols - 1;
-        const int bn = cols ? __ffs(cols) - 1 : 0;
-        const uint32_t fn = s.fire[gb + bn], cn = s.closer[gb + bn];  // the next column, loaded early
-        // the live partners of column b; when one of them is closer than b, those before the
-        // first such partner die (absorbed by b) and then b itself (absorbed by that partner)
-        const uint32_t cand = fb & alive;
-        const uint32_t x = cand & cb;
+      const uint32_t fb = s.fire[P];
+      uint32_t K = 0u, before = 0u, inc = 0u;  // before: the OR of K over the earlier columns
+      int f = -1;
+      for (int r = 0;; ++r) {
+        const uint32_t cand = fb & validm & ~before;
+        const uint32_t x = cand & closer_p;
         const uint32_t low = x & (0u - x);  // first closer partner (0: none)
-        const uint32_t kill = x ? (cand & (low - 1u)) : cand;
-        alive &= ~(kill | (x ? (1u << b) : 0u));
-        if (x && gl == b) mykill = __ffs(x) - 1;
-        if ((kill >> gl) & 1u) mykill = b;
-        b = bn;
-        fb = fn;
-        cb = cn;
+        f = x ? __ffs(x) - 1 : -1;
+        K = x ? ((cand & (low - 1u)) | (1u << gl)) : cand;
+        inc = K;  // inclusive prefix OR over the group's columns
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          if (dd >= VW) break;
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, dd, VW);
+          if (gl >= dd) inc |= y;
+        }
+        uint32_t bn = __shfl_up_sync(0xffffffffu, inc, 1, VW);
+        if (gl == 0) bn = 0u;
+        // the new K has the prefix this round used: it is the fixed point
+        if (!__any_sync(0xffffffffu, bn != before) || r >= WM) break;
+        before = bn;
       }
+      alive = validm & ~__shfl_sync(0xffffffffu, inc, gb + VW - 1);
+      for (uint32_t ab = K & ~(1u << gl); ab; ab &= ab - 1) s.kil[gb + __ffs(ab) - 1] = (uint8_t)gl;
+      __syncwarp();
+      if (valid_p && !((alive >> gl) & 1u)) mykill = f >= 0 ? f : (int)s.kil[P];
     }
     __syncwarp();
     // ---- emit ----------------------------------------------------------------------------
@@ -1763,8 +1778,9 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
 //           between chunks, and the last chunk decides the fire bits straight from the
 //           accumulators (a pair that fires sets its bit in the later position's mask by
 //           a shared atomic).  FP32 (d <= 128): one thread per pair, canonical distance;
-//   chain   warp 0 replays the sequential outcome of the pair scan over the fire bits and
-//           records, for each entry made bottom, the entry that absorbed it;
+//   chain   the sequential outcome of the pair scan over the fire bits as a fixed point,
+//           one column (pi position) per thread; for each entry made bottom, the entry
+//           that absorbed it;
 //   emit    survivors rewritten in place as old; redirects into reserved slots.
 // =====================================================================================
 namespace {
@@ -1815,6 +1831,7 @@ struct __align__(16) TeamSmem {
   uint16_t rq[TRQ];               // pairs (row i << 6 | row j) whose decision is re-taken in FP32
   int32_t nrq;
   uint64_t newm, alive, wtot;
+  uint64_t kor[2][2];             // chain rounds: per warp, the OR of its columns' kill sets
   uint32_t sm32[2];
   uint64_t bar[2];
   unsigned long long red_next, red_end, red_b0, red_b1;
@@ -2113,34 +2130,43 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
       __syncthreads();
     }
-    // ---- prune: warp 0 replays the chain over the columns with fire bits -----------------
-    if (warp == 0) {
-      uint64_t cl = (uint64_t)__ballot_sync(0xffffffffu, lane < m && s.fire[lane] != 0ull) |
-                    ((uint64_t)__ballot_sync(0xffffffffu, lane + 32 < m && s.fire[lane + 32] != 0ull) << 32);
-      uint64_t alive = valid;
-      int b = cl ? __ffsll((long long)cl) - 1 : 0;
-      uint64_t fb = s.fire[b], cb = s.closer[b];
-      while (cl) {
-        cl &= cl - 1;
-        const int bn = cl ? __ffsll((long long)cl) - 1 : 0;
-        const uint64_t fn = s.fire[bn], cn = s.closer[bn];  // the next column, loaded early
-        const uint64_t cand = fb & alive;
+    // ---- prune: the chain's outcome, one column (pi position) per thread ------------------
+    // Column b of the sequential pair scan kills K_b: its live firing partners before the
+    // first closer one f, then b itself (absorbed by f); all of them when none is closer.
+    // Its live partners are the valid positions that no column c < b killed, so the scan's
+    // outcome is the fixed point of K_b = rule(fire[b] & valid & ~OR_{c<b} K_c).  Rounds
+    // that apply the rule to every column at once, from K = 0, reach it: after round r the
+    // columns 0..r hold their final value, so it takes at most m rounds; the first round
+    // whose K has the prefix it was computed from is the fixed point and ends the loop.
+    {
+      const uint64_t fb = s.fire[tid], cb = s.closer[tid];
+      // the OR of K over the earlier columns: bw of this warp's, t0 of warp 0's (for warp 1)
+      uint64_t K = 0ull, bw = 0ull, t0 = 0ull;
+      int f = -1, r = 0;
+      for (;; ++r) {
+        const uint64_t cand = fb & valid & ~(bw | (warp == 1 ? t0 : 0ull));
         const uint64_t x = cand & cb;
-        uint64_t kill = cand;
-        if (x) {  // b meets a closer partner first: entries fired before it die, then b itself
-          const int f = __ffsll((long long)x) - 1;
-          kill = cand & bits_below(f);
-          alive &= ~(1ull << b);
-          if (lane == 0) s.killer[b] = (uint8_t)f;
+        f = x ? __ffsll((long long)x) - 1 : -1;
+        K = x ? ((cand & bits_below(f)) | (1ull << tid)) : cand;
+        uint64_t inc = K;  // inclusive prefix OR over the warp's columns
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const uint64_t y = __shfl_up_sync(0xffffffffu, inc, dd);
+          if (lane >= dd) inc |= y;
         }
-        alive &= ~kill;
-        if ((kill >> lane) & 1ull) s.killer[lane] = (uint8_t)b;
-        if ((kill >> (lane + 32)) & 1ull) s.killer[lane + 32] = (uint8_t)b;
-        b = bn;
-        fb = fn;
-        cb = cn;
+        uint64_t bwn = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) bwn = 0ull;
+        if (lane == 31) s.kor[r & 1][warp] = inc;
+        // the new K has the prefix this round used: it is the fixed point
+        const bool moved = __syncthreads_or(bwn != bw || (warp == 0 && lane == 31 && inc != t0)) != 0;
+        if (!moved || r >= TM) break;
+        bw = bwn;
+        t0 = s.kor[r & 1][0];
       }
-      if (lane == 0) s.alive = alive;
+      // absorbers: b for the partners it kills, f for b itself
+      for (uint64_t ab = K & ~(1ull << tid); ab; ab &= ab - 1) s.killer[__ffsll((long long)ab) - 1] = (uint8_t)tid;
+      if (f >= 0) s.killer[tid] = (uint8_t)f;
+      if (tid == 0) s.alive = valid & ~(s.kor[r & 1][0] | s.kor[r & 1][1]);
     }
     __syncthreads();
     // ---- emit ------------------------------------------------------------------------------
@@ -2568,6 +2594,8 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
     // new entry: the join rewrote every row it pruned as old)
     unsigned work = __ballot_sync(0xffffffffu, ul < a.n && (cl != 0 || !keptl));
     const bool merged_l = (work >> lane) & 1u;
+    // the base pool sizes of the targets to merge, in one load
+    const int nal = merged_l ? (keptl ? a.deg_out[ul] : a.deg_in[ul]) : 0;
     bool mynew = false;
     while (work) {
       const int tl = __ffs(work) - 1;
@@ -2577,7 +2605,7 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
       const bool kept = __shfl_sync(0xffffffffu, keptl ? 1 : 0, tl) != 0;
       if (!in_bounds(b0 >= 0 && c >= 0 && b0 + c <= a.n * R, a.err)) continue;
       const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
-      const int na = kept ? a.deg_out[u] : a.deg_in[u];
+      const int na = __shfl_sync(0xffffffffu, nal, tl);
       n_in += c;
       uint64_t out0, out1;
       if (c == 0) {
