@@ -392,12 +392,28 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
         r[0] = (uint64_t)u | ((uint64_t)(vseg ? vseg[u].x : 0) << 32);
         r[1] = (uint64_t)mu;
       }
-      for (int j = gln; j < mu; j += 8) {
-        const uint64_t k = keys[u * R + j];
-        r[2 + j] = k;
-        if (aux) {
-          const float2 q = aux[key_id(k)];
-          r[2 + cap + j] = ((uint64_t)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
+      // up to 8 entries per lane at a time: every key load, then every row-term load it names,
+      // are in flight together
+      for (int j0 = 0; j0 < mu; j0 += 64) {
+        uint64_t kk[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = j0 + gln + 8 * t;
+          kk[t] = j < mu ? keys[u * R + j] : kEmpty;
+        }
+        float2 qq[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = j0 + gln + 8 * t;
+          qq[t] = (aux && j < mu) ? aux[key_id(kk[t])] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = j0 + gln + 8 * t;
+          if (j < mu) {
+            r[2 + j] = kk[t];
+            if (aux) r[2 + cap + j] = ((uint64_t)__float_as_uint(qq[t].y) << 32) | __float_as_uint(qq[t].x);
+          }
         }
       }
     }
@@ -2440,6 +2456,7 @@ struct __align__(16) MergeScratch {
   uint8_t hix[128];   // ... and their row indices
   uint8_t rrm[64];    // row entry replaced by a nearer proposal
   uint8_t rold[64];   // row entry kept, with the old bit of a proposal
+  uint32_t oid[128];  // hash of the ids the target's row held as old before its first chunk
 };
 
 __device__ __forceinline__ uint32_t id_slot(uint32_t id) { return (id * 0x9E3779B1u) >> 25; }
@@ -2566,6 +2583,14 @@ struct SelectArgs {
   uint8_t* next_active;    // per target: its output row holds a new entry (prep's hint), or null
   int next_active_all;     // 1: write the flag of every target (a round: rows the merge leaves
                            // alone hold no new entry); 0: only of merged targets (a reverse step)
+  // Copies of one id proposed to one target can differ in distance only when the recorded
+  // distances are not canonical FP32 (quantized tiles outside their exact mode); then the
+  // merge first gives each proposal the old bit its id has in the row.  old_pass 1: always;
+  // 0: when qflags (the quantized rows' dataset flags, null for FP32 rows) show that the
+  // tiles of d-dimensional rows are not exact.
+  int old_pass;
+  const unsigned* qflags;
+  int d;
 };
 
 __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
@@ -2577,6 +2602,11 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   // in place (keys_out == keys_in): every row already holds the target's base pool
   const bool in_place = a.keys_out == a.keys_in;
   if (*a.err) return;
+  bool old_pass = a.old_pass != 0;
+  if (!old_pass && a.qflags) {
+    const float mxa = __uint_as_float(a.qflags[1]);
+    old_pass = !(a.qflags[0] == 0u && (double)a.d * (double)mxa * (double)mxa < 16777216.0);
+  }
   // a warp scans 32 consecutive targets at once (one per lane) and merges, one after the
   // other, only those that received proposals or still need their base pool copied
   for (int64_t u0 = ((int64_t)blockIdx.x * 8 + warp) * 32; u0 < a.n; u0 += (int64_t)gridDim.x * 8 * 32) {
@@ -2614,13 +2644,58 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
       } else if (c <= 4) {  // a few proposals: insert them one by one into the sorted row
         out0 = lane < na ? base[lane] : kEmpty;
         out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
-        const uint64_t bl = lane < c ? a.bucket[b0 + lane] : kEmpty;
+        uint64_t bl = lane < c ? a.bucket[b0 + lane] : kEmpty;
+        // Proposals are new; an id is old in the result iff the row held it as old.  An insert
+        // can push that row entry out before a nearer copy of the same id arrives (copies can
+        // differ in distance when the tiles are not exact), so proposals take the row's old
+        // bit first.
+        for (int t = 0; old_pass && t < (int)c; ++t) {
+          const uint32_t idt = key_id(__shfl_sync(0xffffffffu, bl, t));
+          const bool held = (out0 != kEmpty && (out0 & 1ull) && key_id(out0) == idt) ||
+                            (out1 != kEmpty && (out1 & 1ull) && key_id(out1) == idt);
+          if (__any_sync(0xffffffffu, held) && lane == t) bl |= 1ull;
+        }
         for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
       } else {  // chunks of 32 proposals merged into the row
         out0 = lane < na ? base[lane] : kEmpty;
         out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
+        // over several chunks, an earlier chunk can push an old row entry out before a later
+        // one brings a nearer copy of its id: the ids the row holds as old are hashed first,
+        // and each later proposal takes the old bit of its id
+        const bool multi = old_pass && c > 32;
+        if (multi) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ms.oid[lane + 32 * q] = 0xffffffffu;
+          __syncwarp();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t xk = h ? out1 : out0;
+            if (xk != kEmpty && (xk & 1ull)) {  // the row's ids are distinct: a free slot is found
+              const uint32_t id = key_id(xk);
+              uint32_t sl = id_slot(id);
+              for (int probe = 0; probe < 128; ++probe) {
+                if (atomicCAS(&ms.oid[sl], 0xffffffffu, id) == 0xffffffffu) break;
+                sl = (sl + 1) & 127u;
+              }
+            }
+          }
+          __syncwarp();
+        }
         for (int64_t done = 0; done < c; done += 32) {
-          const uint64_t bl = done + lane < c ? a.bucket[b0 + done + lane] : kEmpty;
+          uint64_t bl = done + lane < c ? a.bucket[b0 + done + lane] : kEmpty;
+          if (multi && done > 0 && bl != kEmpty && !(bl & 1ull)) {
+            const uint32_t idb = key_id(bl);
+            uint32_t sl = id_slot(idb);
+            for (int probe = 0; probe < 128; ++probe) {
+              const uint32_t hv = ms.oid[sl];
+              if (hv == idb) {
+                bl |= 1ull;
+                break;
+              }
+              if (hv == 0xffffffffu) break;
+              sl = (sl + 1) & 127u;
+            }
+          }
           merge_chunk(out0, out1, bl, R, ms);
         }
       }
@@ -2797,6 +2872,9 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.stats = stats;
   sa.next_active = keys_out == keys_in ? ws.next_active : nullptr;
   sa.next_active_all = 1;
+  sa.old_pass = 0;
+  sa.qflags = P.precision >= 1 ? P.qflags : nullptr;
+  sa.d = P.d;
   return merge_tail(ws, sa, st);
 }
 
@@ -2827,6 +2905,9 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.stats = nullptr;
   sa.next_active = nullptr;
   sa.next_active_all = 0;
+  sa.old_pass = 0;  // no proposals
+  sa.qflags = nullptr;
+  sa.d = P.d;
   return merge_tail(ws, sa, st);
 }
 
@@ -2906,6 +2987,9 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
   sa.stats = stats;
   sa.next_active = keys_out == keys_in ? ws.next_active : nullptr;  // rows not merged keep their flag
   sa.next_active_all = 0;
+  sa.old_pass = 1;  // the points (and so the exactness of the recorded distances) are not known here
+  sa.qflags = nullptr;
+  sa.d = 0;
   return merge_tail(ws, sa, st);
 }
 

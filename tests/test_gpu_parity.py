@@ -667,3 +667,21 @@ def test_bounded_wait_gives_up_and_context_stays_usable(G):
     for a, b in zip(before, after):
         np.testing.assert_array_equal(a, b)
     assert after[2].min() >= 1
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_continuous_builds_repeat_exactly(G, precision):
+    """On continuous data the tiles are not exact, so two copies of one id proposed to one
+    target can carry different distances (a tile distance and a re-decided FP32 one), and the
+    order of a target's proposals in its bucket varies between runs.  The merge's result must
+    not depend on that order (an id is old iff some copy is old, whichever copy is kept), so
+    repeated builds evaluate the same pairs and return the same graph."""
+    X = synth.deep_like(50000, seed=5)
+    kw = dict(S=16, R=32, T1=3, T2=10, metric=1, precision=precision)
+    first = G.build(X, **kw)
+    want, want_stats = first.to_numpy(), first.stats()
+    for _ in range(3):
+        g = G.build(X, **kw)
+        assert g.stats() == want_stats
+        for a, b in zip(g.to_numpy(), want):
+            np.testing.assert_array_equal(a, b)
