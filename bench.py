@@ -35,8 +35,8 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # launches -- averaged over the 60 rounds of one build of the workload above, from the
 # one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
 # the kernel source is unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9066e9,
-           "source_sha256": "987d8faa99cc7657fdabd6265d695357ec7548b45f7e85ef16c3b9ab234b9616"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9065e9,
+           "source_sha256": "5aed72a4cce8e8b846a9530ad05ea51925363c470ff9a9ecb12addac57b603ce"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm

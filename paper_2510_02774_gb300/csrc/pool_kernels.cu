@@ -1254,8 +1254,10 @@ cudaError_t launch_join_t(const JoinArgs& a, cudaStream_t st, const char* name, 
 // end to end, with no block-wide barrier.
 //   order    bitonic sort of (h(seed,t1,t2,v,id), id) (or the key order) within each
 //            lane group -> pi
-//   gather   one bulk copy per row (lane p: the row of pi position p), new rows first,
-//            completing on the warp's own mbarrier, in chunks of 128 dimensions
+//   gather   one bulk copy per row (lane s: the row of storage slot s; rows hold the new
+//            entries first, then the old ones, each part in slot order), completing on the
+//            warp's own mbarrier, in chunks of 128 dimensions; the first chunk's copies are
+//            issued before the visit order is sorted
 //   tile     BF16 / FP8: mma.sync m16n8k16 / m16n8k32 tiles (six for one vertex, the four
 //            diagonal ones for lane groups), partial dot products kept between chunks,
 //            fire decisions taken from the accumulators; FP32 (d <= 128): each group's
@@ -1405,6 +1407,37 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const int m = cur.m;
     const int64_t v = cur.v;
     const uint64_t keyl = cur.key;
+    // ---- rows, and the first chunk's gather in flight while the visit order is sorted ----
+    // Rows hold the new entries first, then the old ones, each part in storage-slot order
+    // (lane gb + s holds slot s here): the pairs are enumerated over rows (new row i, any
+    // later row j), so the order inside each part does not matter.
+    const uint32_t validm = low_bits32(m);
+    const bool valid_s = gl < m;
+    const uint32_t news = (__ballot_sync(0xffffffffu, valid_s && !key_old(keyl)) >> gb) & gmask;
+    const int k = __popc(news);
+    const int np = k * (m - 1) - k * (k - 1) / 2;
+    const uint32_t below_s = lanes_below32(gl);
+    const int row_s = ((news >> gl) & 1u) ? __popc(news & below_s) : k + __popc(~news & validm & below_s);
+    const uint32_t id_s = key_id(keyl);
+    const bool need = valid_s && np > 0 &&  // rows of groups with pairs only
+                      in_bounds((uint64_t)id_s < (uint64_t)a.n, a.err);
+    const uint32_t needm = __ballot_sync(0xffffffffu, need);
+    const int nch = needm ? nchd : 0;
+    auto issue = [&](int c) {  // the bulk copies of chunk c, completing on the warp's mbarrier
+      const int c0 = c * WDC;
+      const int cpy = (min(WDC, d - c0) + C::VEC - 1) / C::VEC * C::VEC;
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(T));
+      if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
+      inflight = true;
+      __syncwarp();
+      if (need) {
+        const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id_s * a.P.ld + c0)
+                                   : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)id_s * a.P.ldb + c0;
+        bulk_g2s(&s.rows[gb + row_s][0], src, bytes, &s.bar);
+      }
+    };
+    if (nch > 0) issue(0);
+
     // ---- visit order: bitonic sort of (h, id, source lane) within each lane group ---------
     const uint32_t idl = key_id(keyl);
     uint64_t h = ~0ull;
@@ -1440,12 +1473,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     const uint64_t key = __shfl_sync(0xffffffffu, keyl, (int)hs);
     const uint64_t aux = __shfl_sync(0xffffffffu, cur.aux, (int)hs);
     const bool valid_p = gl < m;
-    const uint32_t validm = low_bits32(m);
-    const uint32_t newm = (__ballot_sync(0xffffffffu, valid_p && !key_old(key)) >> gb) & gmask;
-    const int k = __popc(newm);
-    const int np = k * (m - 1) - k * (k - 1) / 2;
     const uint32_t below = lanes_below32(gl);
-    const int row = ((newm >> gl) & 1u) ? __popc(newm & below) : k + __popc(~newm & validm & below);
+    const int row = __shfl_sync(0xffffffffu, row_s, (int)hs);  // the row of this position's entry
     const int32_t id = (int32_t)key_id(key);
     const int P = gb + gl;
     if (valid_p) {
@@ -1481,25 +1510,12 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     }
 
     // ---- gather + tile ---------------------------------------------------------------
-    const bool need = valid_p && np > 0 &&  // rows of groups with pairs only
-                      in_bounds((uint64_t)(uint32_t)id < (uint64_t)a.n, a.err);
-    const uint32_t needm = __ballot_sync(0xffffffffu, need);
-    const int nch = needm ? nchd : 0;
     const int pdb = g * ((VW * (VW - 1)) >> 1);
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int c0 = c * WDC;
       const int clen = min(WDC, d - c0);
-      const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(T));
-      if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
-      inflight = true;
-      __syncwarp();
-      if (need) {
-        const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id * a.P.ld + c0)
-                                   : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)id * a.P.ldb + c0;
-        bulk_g2s(&s.rows[gb + row][0], src, bytes, &s.bar);
-      }
+      if (c > 0) issue(c);  // (chunk 0 is in flight since before the visit order)
       ok = mbar_wait(&s.bar, phb, kWaitLimit);
       if (!__all_sync(0xffffffffu, ok)) break;
       phb ^= 1u;
@@ -1788,7 +1804,9 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
 // rnd_join for pools of 33..64 entries: a team of two warps (one 64-thread CTA) per
 // vertex; thread t owns pool entry t (storage slot t).
 //   order   rank of (h, id) among the m entries (16-byte keys in shared memory);
-//   gather  one bulk copy per row and 128-column chunk (two stages when d > 128);
+//   gather  one bulk copy per row and 128-column chunk (two stages when d > 128); rows hold
+//           the new entries first, then the old ones, each part in slot order, so the first
+//           chunk's copies are issued before the visit order is ranked;
 //   tile    BF16 / FP8: mma.sync tiles over new rows x all rows, shared between the two
 //           warps and taken one at a time; partial dot products wait in shared memory
 //           between chunks, and the last chunk decides the fire bits straight from the
@@ -1846,7 +1864,7 @@ struct __align__(16) TeamSmem {
   uint8_t rpos[TM], prow[TM], killer[TM];
   uint16_t rq[TRQ];               // pairs (row i << 6 | row j) whose decision is re-taken in FP32
   int32_t nrq;
-  uint64_t newm, alive, wtot;
+  uint64_t alive, wtot;
   uint64_t kor[2][2];             // chain rounds: per warp, the OR of its columns' kill sets
   uint32_t sm32[2];
   uint64_t bar[2];
@@ -1937,52 +1955,25 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       hk.pad = 0u;
       s.hk[tid] = hk;
     }
-    if (tid == 0) {
-      s.newm = 0ull;
-      s.nrq = 0;
+    {
+      const unsigned nw = __ballot_sync(0xffffffffu, has && !key_old(keyl));  // new entries by slot
+      if (lane == 0) s.sm32[warp] = nw;
     }
+    if (tid == 0) s.nrq = 0;
     __syncthreads();
-    int pi = 0;
-    if (has) {
-#pragma unroll 4
-      for (int f = 0; f < m; ++f) {
-        const TeamKey o = s.hk[f];
-        pi += (o.h < h) || (o.h == h && o.id < idl);
-      }
-      if (!key_old(keyl)) atomicOr(reinterpret_cast<unsigned long long*>(&s.newm), 1ull << pi);
-    }
-    // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
-    // closer mask of a position is the OR of the position bits of the slots before its own
-    const uint64_t pbit = has ? (1ull << pi) : 0ull;
-    uint64_t pre = pbit;
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
-      if (lane >= dd) pre |= y;
-    }
-    if (warp == 0 && lane == 31) s.wtot = pre;
-    __syncthreads();
-    if (warp == 1) pre |= s.wtot;
-    const uint64_t newm = s.newm;
-    const int k = __popcll(newm);
+    // rows: the new entries first, then the old ones, each part in storage-slot order (the
+    // pairs are enumerated over rows: new row i, any later row j, so the order inside each
+    // part does not matter); the first chunk's copies are in flight while the visit order
+    // is ranked
+    const uint64_t news = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);
+    const int k = __popcll(news);
     const int np = k * (m - 1) - k * (k - 1) / 2;
     const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
     int row = 0;
     if (has) {
-      const uint64_t lo = bits_below(pi);
-      row = ((newm >> pi) & 1ull) ? __popcll(newm & lo) : k + __popcll(~newm & valid & lo);
-      s.pid[pi] = (int32_t)idl;
-      s.prow[pi] = (uint8_t)row;
-      s.rpos[row] = (uint8_t)pi;
-      s.closer[pi] = pre ^ pbit;
-      s.rnd[row] = make_float2(PREC >= 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
-      if (PREC >= 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
+      const uint64_t bt = bits_below(tid);
+      row = ((news >> tid) & 1ull) ? __popcll(news & bt) : k + __popcll(~news & valid & bt);
     }
-    if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
-    s.fire[tid] = 0ull;  // fire bits are set by the pairs that fire (shared atomics)
-    __syncthreads();
-
-    // ---- gather + tile -------------------------------------------------------------------
     const int nch = np > 0 ? nchd : 0;
     auto issue = [&](int c, int st) {
       const int c0 = c * TDC;
@@ -1999,8 +1990,41 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         bulk_g2s(rowbase + ((size_t)st * TM + row) * C::RS, src, bytes, &s.bar[st]);
       }
     };
-    bool fail = false;
     if (nch > 0) issue(0, stage);
+    int pi = 0;
+    if (has) {
+#pragma unroll 4
+      for (int f = 0; f < m; ++f) {
+        const TeamKey o = s.hk[f];
+        pi += (o.h < h) || (o.h == h && o.id < idl);
+      }
+    }
+    // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
+    // closer mask of a position is the OR of the position bits of the slots before its own
+    const uint64_t pbit = has ? (1ull << pi) : 0ull;
+    uint64_t pre = pbit;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
+      if (lane >= dd) pre |= y;
+    }
+    if (warp == 0 && lane == 31) s.wtot = pre;
+    __syncthreads();
+    if (warp == 1) pre |= s.wtot;
+    if (has) {
+      s.pid[pi] = (int32_t)idl;
+      s.prow[pi] = (uint8_t)row;
+      s.rpos[row] = (uint8_t)pi;
+      s.closer[pi] = pre ^ pbit;
+      s.rnd[row] = make_float2(PREC >= 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
+      if (PREC >= 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
+    }
+    if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
+    s.fire[tid] = 0ull;  // fire bits are set by the pairs that fire (shared atomics)
+    __syncthreads();
+
+    // ---- gather + tile (chunk 0 is in flight since before the visit order) --------------
+    bool fail = false;
     for (int c = 0; c < nch; ++c) {
       const int st = stage;
       if (nst > 1 && c + 1 < nch) issue(c + 1, st ^ 1);
