@@ -32,9 +32,9 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
                          "integers in [0,255]; S=32, R=64, T1=4, T2=15, rho=0.6; 10,000 queries, k=10, beam 64",
                 n=1_000_000, d=128, S=32, R=64, T1=4, T2=15, rho=0.6, nq=10_000, k=10, beam=64)
 # ncu DRAM bytes (read + write) per unit of the join -- one round, i.e. its warp and team
-# launches -- averaged over the 60 rounds of one build of the workload above, from the
-# one-pass capture summarised in profiles/rnd_join_bf16_sift1m_dram.md; reported only while
-# the kernel source is unchanged since that capture.
+# launches -- averaged over the 60 rounds of one build of the workload above, from an ncu
+# capture of the join kernels; reported only while the kernel source is unchanged since
+# that capture.
 TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9065e9,
            "source_sha256": "5aed72a4cce8e8b846a9530ad05ea51925363c470ff9a9ecb12addac57b603ce"}
 

@@ -421,7 +421,9 @@ GRNND_API int grnnd_keys_to_graph(int64_t n, int32_t R, const uint64_t *keys, in
  * 4,208,640 bytes inside the library (held on every GPU that loads it until
  * exit), so 1 <= d <= 1024 (larger d returns GRNND_EINVAL).  No cudaMalloc or
  * cudaFree is called.  The first call on a device looks up the array's address
- * with that device current; make it before any stream capture.  All calls on a
+ * with that device current and remembers it with the current context's id; a
+ * call under a new context (after cudaDeviceReset) looks it up again.  Make the
+ * first call, and the first after a reset, before any stream capture.  All calls on a
  * device share the array: calls that overlap on the GPU race, so order them on
  * one stream.  points: device n x ld (16-byte aligned, ld % 4 == 0);
  * entry_out: device int32[1]. */

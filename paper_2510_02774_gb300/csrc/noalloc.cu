@@ -12,8 +12,11 @@
 //   * it occupies kNoAllocScratchBytes of device memory on every GPU that loads the
 //     library, until the process exits;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current) and caches it; make that first call
-//     before any stream capture;
+//     cudaGetSymbolAddress (with that device current) and caches it together with the
+//     identity of the CUDA context that was current; a later call under another context
+//     (after cudaDeviceReset, for instance, the module is loaded again and the array can
+//     move) looks the address up again.  Make the first call on a device, and the first
+//     after a reset, before any stream capture;
 //   * every call on a device uses the same array and leaves its contents behind; each
 //     kernel of the computation writes every scratch word it later reads, so nothing has
 //     to start at zero;
@@ -21,6 +24,8 @@
 //     ordering) race on the array: order them on one stream.
 #include <mutex>
 #include <string>
+
+#include <cuda.h>
 
 #include "grnnd.h"
 #include "internal.h"
@@ -36,7 +41,35 @@ static __device__ __align__(256) unsigned char g_entry_scratch[kNoAllocScratchBy
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
+// Per device: the array's device address and the id of the context it was looked up under
+// (context ids are never reused within a process, unlike context handles).
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// Id of the current context, through the driver entry points that the runtime hands out (no
+// link against the driver library).  Returns false if it cannot be read.
+bool current_context_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      return false;
+    }
+    get_current = reinterpret_cast<GetCurrent>(f1);
+    get_id = reinterpret_cast<GetId>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 int noalloc_fail(int code, const std::string& msg) {
   grnnd::set_last_error(msg);
@@ -63,17 +96,24 @@ extern "C" int grnnd_entry_point_noalloc(const float* points, int64_t n, int32_t
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(GRNND_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(GRNND_EINVAL, "device index above 63");
+  // make the device's primary context current (it already is after any earlier runtime call
+  // on this device), so that its id is readable; this initialises, it allocates nothing
+  if ((e = cudaSetDevice(dev)) != cudaSuccess)
+    return noalloc_fail(GRNND_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  unsigned long long ctx = 0;
+  if (!current_context_id(&ctx)) return noalloc_fail(GRNND_ECUDA, "cannot read the current CUDA context");
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-      // once per device, with that device current: the host-side name of the array is
-      // not a device address, so ask the runtime for the real one.
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
+      // once per device and context, with that device current: the host-side name of the
+      // array is not a device address, so ask the runtime for the real one.
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_entry_scratch);
       if (e != cudaSuccess || !p)
         return noalloc_fail(GRNND_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_scratch_addr[dev] = p;
+      g_scratch_ctx[dev] = ctx;
     }
     scratch = g_scratch_addr[dev];
   }

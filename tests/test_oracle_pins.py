@@ -233,6 +233,38 @@ def test_rng_edges_survive_any_order(orc):
             assert set(rng_nb) <= surv
 
 
+def _mrng_neighbours(D, v):
+    """Brute-force MRNG set of v over every other point (strict lune, ties by id):
+    candidates in ascending (d(v,.), id); u is kept iff no kept w has d(w,u) < d(v,u)."""
+    n = D.shape[0]
+    kept = []
+    for u in sorted((u for u in range(n) if u != v), key=lambda u: (D[v, u], u)):
+        if not any(D[w, u] < D[v, u] for w in kept):
+            kept.append(u)
+    return kept
+
+
+@pytest.mark.parametrize("case", ["gauss", "ties"])
+def test_full_pool_ascending_final_prune_is_mrng(orc, case):
+    # S = R = n - 1: every pool holds all other points; the ascending (Alg 2) order then
+    # makes the prune-only pass keep exactly the brute-force MRNG neighbours of each point.
+    if case == "gauss":
+        n = 48
+        X = np.random.default_rng(31).standard_normal((n, 3)).astype(np.float32)
+    else:
+        n = 40
+        X = synth.small_integers(n, 2, -2, 2, seed=3)  # many equal distances and duplicates
+    D = ((X[:, None, :].astype(np.float64) - X[None, :, :]) ** 2).sum(-1)
+    pool, _ = orc.init(X, n - 1, n - 1, seed=9)
+    assert (pool.deg == n - 1).all()
+    gids, gd, gdeg, _ = orc.final_prune(X, pool, seed=9, t1=2, order=1)
+    for v in range(n):
+        want = _mrng_neighbours(D, v)
+        got = gids[v, :gdeg[v]].tolist()
+        assert got == want, v
+        assert all(gd[v, j] == D[v, u] for j, u in enumerate(got))
+
+
 def test_visit_order_modes(orc):
     ids = np.array([5, 9, 2, 7], np.int32)
     assert orc.visit_order(0, 1, 1, 3, ids, 1).tolist() == [0, 1, 2, 3]
@@ -419,6 +451,24 @@ def test_brute_knn_matches_exhaustive(orc):
     X, Q = synth.small_integers(300, 5, -3, 3, seed=2, nq=40)  # many exact ties
     ids, dd = orc.brute_knn(X, Q, 10)
     assert (ids == _np_knn(X, Q, 10)).all()
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_brute_knn_matches_a_second_plain_loop(orc, metric):
+    # 2,000 points: every query's k-NN from one distance loop over all points, written out
+    # here in FP64, ordered by (dist, id)
+    X, Q = synth.small_integers(2000, 16, -4, 4, seed=12, nq=150)
+    k = 10
+    ids, dd = orc.brute_knn(X, Q, k, metric=metric)
+    Xd = X.astype(np.float64)
+    for i in range(len(Q)):
+        q = Q[i].astype(np.float64)
+        dist = np.empty(len(X))
+        for u in range(len(X)):
+            dist[u] = ((Xd[u] - q) ** 2).sum() if metric == 0 else 1.0 - (Xd[u] * q).sum()
+        order = sorted(range(len(X)), key=lambda u: (dist[u], u))[:k]
+        assert ids[i].tolist() == order
+        assert np.array_equal(dd[i], dist[order])
 
 
 def test_entry_is_nearest_to_mean(orc):
