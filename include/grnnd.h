@@ -20,7 +20,10 @@
  *     and the base address 16-byte aligned (rows are moved with bulk copies).
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  Step-level calls are asynchronous on that stream; grnnd_build*,
- *     grnnd_search and grnnd_graph_copy are synchronous on return.
+ *     grnnd_search and grnnd_graph_copy are synchronous on return.  Calls that
+ *     take no stream argument (grnnd_build, grnnd_search, grnnd_graph_copy), and
+ *     grnnd_build_ex / grnnd_build_batch given p->stream == NULL, run on the
+ *     calling thread's current stream (grnnd_set_stream).
  *   - Pool layout (step-level calls): a pool is n rows of R slots of uint64
  *     keys plus an int32 degree per row.  A key packs one entry as
  *         key = (ordered_bits(dist) << 32) | (id << 1) | old
@@ -94,7 +97,7 @@ typedef struct grnnd_tuning {
 /* Parameters of a build (Table 1: S, R, T1, T2, rho). */
 typedef struct grnnd_params {
     int32_t S;            /* initial random neighbours per vertex, 1 <= S <= min(R, n-1) */
-    int32_t R;            /* pool capacity = maximum out-degree, 2 <= R <= 64 */
+    int32_t R;            /* pool capacity = maximum out-degree, 2 <= R <= 256 (Sec 3.5) */
     int32_t T1;           /* outer iterations, >= 1 */
     int32_t T2;           /* inner iterations (rounds) per outer iteration, >= 1 */
     float rho;            /* reverse-edge sampling ratio in [0, 1] (Sec 3.6); default 0.6 */
@@ -103,7 +106,8 @@ typedef struct grnnd_params {
     int32_t precision;    /* grnnd_precision */
     int32_t order;        /* grnnd_order */
     int32_t final_prune;  /* 1: return the survivors of one more prune pass; 0: the last pool */
-    void *stream;         /* cudaStream_t for all work of the build; NULL = legacy default */
+    void *stream;         /* cudaStream_t for all work of the build; NULL = the calling
+                             thread's current stream (grnnd_set_stream) */
     uint64_t hbm_budget;  /* bytes the build may allocate; 0 = no limit */
     const grnnd_tuning *tuning; /* join launch shape; NULL = defaults */
 } grnnd_params;
@@ -135,11 +139,19 @@ GRNND_API int grnnd_set_memory_cache(uint64_t bytes);
 
 /* Builds a graph over n points of dimension d (Alg 3).  `points` is host or
  * device memory, n rows of d contiguous floats; every value must be finite.
- * Validation: n >= 2, d >= 1, 1 <= S <= min(R, n-1), 2 <= R <= 64, T1, T2 >= 1.
+ * Validation: n >= 2, d >= 1, 1 <= S <= min(R, n-1), 2 <= R <= 256, T1, T2 >= 1.
  * On success *graph_out owns a device copy of the points and the graph; free it
- * with grnnd_free.  Runs on the legacy default stream. */
+ * with grnnd_free.  Runs on the calling thread's current stream (grnnd_set_stream). */
 GRNND_API int grnnd_build(const float *points, int64_t n, int32_t d, int32_t metric, int32_t S,
                 int32_t R, int32_t T1, int32_t T2, uint64_t seed, grnnd_graph **graph_out);
+
+/* The calling thread's current stream (no counterpart in the paper, which runs one build at a
+ * time): the stream of every call that takes no stream argument and of builds whose
+ * p->stream is NULL.  A framework binding sets it to its own current stream before a call
+ * (the Python binding passes PyTorch's).  Initially NULL, the legacy default stream; the
+ * setting is per host thread. */
+GRNND_API void grnnd_set_stream(void *stream);
+GRNND_API void *grnnd_get_stream(void);
 
 /* Same as grnnd_build with every parameter of grnnd_params. */
 GRNND_API int grnnd_build_ex(const float *points, int64_t n, int32_t d, const grnnd_params *p,
@@ -343,6 +355,37 @@ GRNND_API int grnnd_join_round(const float *points, int64_t n, int32_t d, int32_
                      int32_t t1, int32_t t2, int32_t order, uint64_t *keys_out, int32_t *deg_out,
                      void *workspace, size_t workspace_bytes, int64_t *stats, void *stream);
 
+/* Quantized copy of the points for the precision forms of the step calls (the
+ * build calls make their own).  The paper states no precision (Sec 3.4 computes
+ * FP32 distances); these are the BF16 / FP8 forms of the dist_tile step of
+ * Alg 5 / Eq 2 that grnnd_precision describes.  grnnd_quantized_size returns
+ * the bytes of the copy of n x d points in `precision` (GRNND_BF16 or
+ * GRNND_FP8; 0 for anything else): rows rounded once to bfloat16 (round to
+ * nearest even) or to e4m3 with one power-of-two scale per row, per-row
+ * (squared norm of the rounded row, norm of the rounding residual) terms and
+ * two dataset flags; the layout is private to the library.  grnnd_quantize
+ * writes it from `points` (device n x ld floats, as for grnnd_join_round) into
+ * `qpoints` (device, 256-byte aligned, >= grnnd_quantized_size bytes), which
+ * the caller owns; asynchronous on `stream`.  GRNND_EINVAL for a bad
+ * precision, size or alignment. */
+GRNND_API size_t grnnd_quantized_size(int64_t n, int32_t d, int32_t precision);
+GRNND_API int grnnd_quantize(const float *points, int64_t n, int32_t d, int32_t ld, int32_t precision,
+                             void *qpoints, size_t qpoints_bytes, void *stream);
+
+/* grnnd_join_round in a precision form: the pair distances of the prune (Eq 2)
+ * come from the quantized tiles of `qpoints` (written by grnnd_quantize for
+ * the same points and precision), with every decision inside the tiles' error
+ * bound re-taken with the canonical FP32 distance of `points`, as in the
+ * builds.  precision GRNND_FP32 ignores qpoints (NULL allowed) and equals
+ * grnnd_join_round.  Other arguments, results and errors as for
+ * grnnd_join_round. */
+GRNND_API int grnnd_join_round_q(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                                 int32_t precision, const void *qpoints, size_t qpoints_bytes, int32_t R,
+                                 const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
+                                 int32_t t1, int32_t t2, int32_t order, uint64_t *keys_out,
+                                 int32_t *deg_out, void *workspace, size_t workspace_bytes,
+                                 int64_t *stats, void *stream);
+
 /* Reverse-edge sampling (Sec 3.6): for each v with k = deg_in[v], the first
  * floor((double)rho * k) entries n of its row propose (v, d(v,n), new) to n;
  * pool_out[u] = merge of pool_in[u] with the proposals to u (same rule as the
@@ -379,6 +422,14 @@ GRNND_API int grnnd_final_prune(const float *points, int64_t n, int32_t d, int32
                       int32_t R, const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
                       int32_t t1, int32_t order, uint64_t *keys_out, int32_t *deg_out,
                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* grnnd_final_prune in a precision form (qpoints and precision as for
+ * grnnd_join_round_q). */
+GRNND_API int grnnd_final_prune_q(const float *points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                                  int32_t precision, const void *qpoints, size_t qpoints_bytes, int32_t R,
+                                  const uint64_t *keys_in, const int32_t *deg_in, uint64_t seed,
+                                  int32_t t1, int32_t order, uint64_t *keys_out, int32_t *deg_out,
+                                  void *workspace, size_t workspace_bytes, void *stream);
 
 /* Canonical FP32 distances of np point pairs: out[i] = d(points[pairs[2i]],
  * points[pairs[2i+1]]) exactly as the pool kernels compute it.  pairs: device

@@ -20,8 +20,8 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libgrnnd.so")
 OUT_CHECKS = os.path.join(PKG, "_build_checks")
 LIB_CHECKS = os.path.join(OUT_CHECKS, "libgrnnd.so")
-UNITS = ["pool_kernels.cu", "search_kernels.cu", "capi.cu", "noalloc.cu", "server.cu"]
-HEADERS = ["common.cuh", "internal.h"]
+UNITS = ["pool_kernels.cu", "wide_kernels.cu", "search_kernels.cu", "capi.cu", "noalloc.cu", "server.cu"]
+HEADERS = ["common.cuh", "internal.h", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", SRC]

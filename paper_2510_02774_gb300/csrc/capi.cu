@@ -22,6 +22,8 @@
 namespace {
 
 thread_local std::string g_err;
+// The calling thread's current stream (grnnd_set_stream); null = the legacy default stream.
+thread_local cudaStream_t g_stream = nullptr;
 
 // NVTX range over a host scope (shown by profilers that attach; no cost otherwise).
 struct NvtxRange {
@@ -62,6 +64,44 @@ bool is_device_ptr(const void* p) {
 int32_t round4(int32_t d) { return (d + 3) & ~3; }
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Layout of the quantized copy of n x d points (BF16 or FP8 form), shared by the builds and
+// grnnd_quantize: rows of ldb elements of qelem bytes, then the per-row (norm^2, residual)
+// terms, then the two dataset flags; each region 256-byte aligned.
+struct QLayout {
+  int32_t ldb = 0;
+  size_t qelem = 0, rows_b = 0, aux_b = 0, total = 0;
+};
+QLayout q_layout(int64_t n, int32_t d, int32_t precision) {
+  QLayout q;
+  if (precision != GRNND_BF16 && precision != GRNND_FP8) return q;
+  q.ldb = precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
+  q.qelem = precision == GRNND_FP8 ? 1 : 2;
+  q.rows_b = al256((size_t)n * q.ldb * q.qelem);
+  q.aux_b = al256((size_t)n * 8);
+  q.total = q.rows_b + q.aux_b + 256;
+  return q;
+}
+// The point set of a step call: FP32 rows, plus the quantized copy in a precision form.
+int step_points(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric, int32_t precision,
+                const void* qpoints, size_t qbytes, grnnd::PointsSet* P) {
+  P->X = points;
+  P->ld = ld;
+  P->d = d;
+  P->metric = metric;
+  if (precision == GRNND_FP32) return GRNND_OK;
+  if (precision != GRNND_BF16 && precision != GRNND_FP8) return fail(GRNND_EINVAL, "unknown precision");
+  const QLayout q = q_layout(n, d, precision);
+  if (!qpoints || ((uintptr_t)qpoints & 255u) != 0 || qbytes < q.total)
+    return fail(GRNND_EINVAL, "quantized points: need a 256-byte aligned buffer of grnnd_quantized_size bytes");
+  const char* b = static_cast<const char*>(qpoints);
+  P->precision = precision;
+  P->Xb = b;
+  P->ldb = q.ldb;
+  P->aux = reinterpret_cast<const float2*>(b + q.rows_b);
+  P->qflags = reinterpret_cast<const unsigned*>(b + q.rows_b + q.aux_b);
+  return GRNND_OK;
+}
+
 // Owned device allocation released on scope exit: cudaMalloc / cudaFree, or stream-ordered
 // from a memory pool on the given stream.
 struct DevMem {
@@ -99,7 +139,7 @@ int check_step_points(const float* points, int64_t n, int32_t d, int32_t ld, int
 }
 
 int check_R(int32_t R) {
-  if (R < 2 || R > 64) return fail(GRNND_EINVAL, "R must be in [2, 64]");
+  if (R < 2 || R > 256) return fail(GRNND_EINVAL, "R must be in [2, 256]");
   return GRNND_OK;
 }
 
@@ -151,6 +191,9 @@ void prof_stop(cudaStream_t st) {
 extern "C" {
 
 const char* grnnd_last_error(void) { return g_err.c_str(); }
+
+void grnnd_set_stream(void* stream) { g_stream = (cudaStream_t)stream; }
+void* grnnd_get_stream(void) { return (void*)g_stream; }
 
 int grnnd_profile_begin(void) {
   for (auto& r : g_prof.recs) {
@@ -232,10 +275,11 @@ int grnnd_pool_init(const float* points, int64_t n, int32_t d, int32_t ld, int32
   return GRNND_OK;
 }
 
-int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
-                     int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
-                     int32_t t1, int32_t t2, int32_t order, uint64_t* keys_out, int32_t* deg_out,
-                     void* workspace, size_t workspace_bytes, int64_t* stats, void* stream) {
+int grnnd_join_round_q(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                       int32_t precision, const void* qpoints, size_t qpoints_bytes, int32_t R,
+                       const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed, int32_t t1,
+                       int32_t t2, int32_t order, uint64_t* keys_out, int32_t* deg_out, void* workspace,
+                       size_t workspace_bytes, int64_t* stats, void* stream) {
   int rc = check_step_points(points, n, d, ld, metric);
   if (rc) return rc;
   if ((rc = check_R(R))) return rc;
@@ -243,18 +287,41 @@ int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int3
   if ((keys_in == keys_out) != (deg_in == deg_out))
     return fail(GRNND_EINVAL, "keys and degrees must both be in place or both separate");
   if (order < 0 || order > 2) return fail(GRNND_EINVAL, "unknown order");
+  grnnd::PointsSet P;
+  if ((rc = step_points(points, n, d, ld, metric, precision, qpoints, qpoints_bytes, &P))) return rc;
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
     return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  grnnd::PointsSet P;
-  P.X = points;
-  P.ld = ld;
-  P.d = d;
-  P.metric = metric;
   GR_CU(grnnd::launch_round(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out, deg_out,
                             stats, st));
   if (stats) GR_CU(cudaMemcpyAsync(stats + 5, ws.round_new, 8, cudaMemcpyDeviceToDevice, st));
+  return GRNND_OK;
+}
+
+int grnnd_join_round(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                     int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
+                     int32_t t1, int32_t t2, int32_t order, uint64_t* keys_out, int32_t* deg_out,
+                     void* workspace, size_t workspace_bytes, int64_t* stats, void* stream) {
+  return grnnd_join_round_q(points, n, d, ld, metric, GRNND_FP32, nullptr, 0, R, keys_in, deg_in, seed, t1,
+                            t2, order, keys_out, deg_out, workspace, workspace_bytes, stats, stream);
+}
+
+size_t grnnd_quantized_size(int64_t n, int32_t d, int32_t precision) {
+  if (n < 1 || d < 1) return 0;
+  return q_layout(n, d, precision).total;
+}
+
+int grnnd_quantize(const float* points, int64_t n, int32_t d, int32_t ld, int32_t precision, void* qpoints,
+                   size_t qpoints_bytes, void* stream) {
+  int rc = check_step_points(points, n, d, ld, GRNND_L2SQ);
+  if (rc) return rc;
+  if (precision != GRNND_BF16 && precision != GRNND_FP8)
+    return fail(GRNND_EINVAL, "precision must be GRNND_BF16 or GRNND_FP8");
+  grnnd::PointsSet P;
+  if ((rc = step_points(points, n, d, ld, GRNND_L2SQ, precision, qpoints, qpoints_bytes, &P))) return rc;
+  GR_CU(grnnd::launch_quantize(points, n, d, ld, const_cast<void*>(P.Xb), P.ldb, const_cast<float2*>(P.aux),
+                               const_cast<unsigned*>(P.qflags), precision, (cudaStream_t)stream));
   return GRNND_OK;
 }
 
@@ -301,10 +368,11 @@ int grnnd_reverse_sample(int64_t n, int32_t R, float rho, const uint64_t* keys_i
   return GRNND_OK;
 }
 
-int grnnd_final_prune(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
-                      int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
-                      int32_t t1, int32_t order, uint64_t* keys_out, int32_t* deg_out,
-                      void* workspace, size_t workspace_bytes, void* stream) {
+int grnnd_final_prune_q(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                        int32_t precision, const void* qpoints, size_t qpoints_bytes, int32_t R,
+                        const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed, int32_t t1,
+                        int32_t order, uint64_t* keys_out, int32_t* deg_out, void* workspace,
+                        size_t workspace_bytes, void* stream) {
   int rc = check_step_points(points, n, d, ld, metric);
   if (rc) return rc;
   if ((rc = check_R(R))) return rc;
@@ -312,17 +380,22 @@ int grnnd_final_prune(const float* points, int64_t n, int32_t d, int32_t ld, int
   if (keys_in == keys_out || deg_in == deg_out)
     return fail(GRNND_EINVAL, "output pool must not alias the input pool");
   if (order < 0 || order > 2) return fail(GRNND_EINVAL, "unknown order");
+  grnnd::PointsSet P;
+  if ((rc = step_points(points, n, d, ld, metric, precision, qpoints, qpoints_bytes, &P))) return rc;
   grnnd::Workspace ws;
   if (!grnnd::carve_workspace(workspace, workspace_bytes, n, R, &ws))
     return fail(GRNND_EINVAL, "workspace too small or not 256-byte aligned");
-  grnnd::PointsSet P;
-  P.X = points;
-  P.ld = ld;
-  P.d = d;
-  P.metric = metric;
   GR_CU(grnnd::launch_final(P, n, R, keys_in, deg_in, seed, t1, order, ws, keys_out, deg_out,
                             (cudaStream_t)stream));
   return GRNND_OK;
+}
+
+int grnnd_final_prune(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
+                      int32_t R, const uint64_t* keys_in, const int32_t* deg_in, uint64_t seed,
+                      int32_t t1, int32_t order, uint64_t* keys_out, int32_t* deg_out,
+                      void* workspace, size_t workspace_bytes, void* stream) {
+  return grnnd_final_prune_q(points, n, d, ld, metric, GRNND_FP32, nullptr, 0, R, keys_in, deg_in, seed, t1,
+                             order, keys_out, deg_out, workspace, workspace_bytes, stream);
 }
 
 int grnnd_pair_dist(const float* points, int64_t n, int32_t d, int32_t ld, int32_t metric,
@@ -492,11 +565,8 @@ BuildSizes build_sizes(int64_t n, int32_t d, const grnnd_params* p, bool batched
   const int32_t R = p->R, ld = round4(d);
   // quantized forms: a BF16 copy (rows of d rounded up to 16 elements) or an e4m3 copy
   // (rows of d rounded up to 32 bytes), per-row terms and dataset flags
-  const bool quant = p->precision != GRNND_FP32;
-  const int32_t ldb = p->precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
-  const size_t qelem = p->precision == GRNND_FP8 ? 1 : 2;
   z.pts_b = al256((size_t)n * ld * 4);
-  z.q_b = quant ? al256((size_t)n * ldb * qelem) + al256((size_t)n * 8) + 256 : 0;
+  z.q_b = q_layout(n, d, p->precision).total;
   z.pool_b = al256((size_t)n * R * 8);
   z.deg_b = al256((size_t)n * 4);
   z.ws_b = grnnd::workspace_bytes(n, R);
@@ -517,8 +587,6 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   NvtxRange nvtx_build(batched ? "grnnd_build_batch" : "grnnd_build");
   const int32_t R = p->R, ld = round4(d);
   const bool quant = p->precision != GRNND_FP32;
-  const int32_t ldb = p->precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
-  const size_t qelem = p->precision == GRNND_FP8 ? 1 : 2;
   cudaStream_t st = (cudaStream_t)p->stream;
 
   const BuildSizes z = build_sizes(n, d, p, batched, nbuild);
@@ -593,13 +661,8 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
     P.warp_ctas = t->warp_ctas_per_sm;
     P.team_ctas = t->team_ctas_per_sm;
   }
-  if (quant) {
-    P.precision = p->precision;
-    P.Xb = qp;
-    P.ldb = ldb;
-    P.aux = reinterpret_cast<const float2*>(qp + al256((size_t)n * ldb * qelem));
-    P.qflags = reinterpret_cast<const unsigned*>(qp + al256((size_t)n * ldb * qelem) + al256((size_t)n * 8));
-  }
+  if (quant && step_points(X, n, d, ld, p->metric, p->precision, qp, q_b, &P) != GRNND_OK)
+    return fail(GRNND_EINVAL, "internal quantized layout");
 
   // A batched pass runs every round (a round after one that left no new entry is an
   // identity) and is recorded as one CUDA graph; a single build reads each round's
@@ -642,9 +705,13 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   } while (0)
 
   if (quant)
-    GR_CAP(grnnd::launch_quantize(X, n, d, ld, qp, ldb, const_cast<float2*>(P.aux),
+    GR_CAP(grnnd::launch_quantize(X, n, d, ld, qp, P.ldb, const_cast<float2*>(P.aux),
                                   const_cast<unsigned*>(P.qflags), p->precision, st));
-  GR_CAP(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st, vseg));
+  if (p->precision == GRNND_BF16)  // the drawn rows from the BF16 copy when it is exact
+    GR_CAP(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st, vseg, P.Xb, P.ldb,
+                                   P.qflags));
+  else
+    GR_CAP(grnnd::launch_pool_init(X, n, d, ld, p->metric, p->S, R, p->seed, poolA, degA, st, vseg));
   RoundProbe* probe = nullptr;
   cudaEvent_t rev[2] = {nullptr, nullptr};
   struct EvGuard {
@@ -750,6 +817,11 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
 
 int grnnd_build_ex(const float* points, int64_t n, int32_t d, const grnnd_params* p,
                    grnnd_graph** graph_out) {
+  if (p && !p->stream && g_stream) {  // no stream given: the thread's current stream
+    grnnd_params q = *p;
+    q.stream = (void*)g_stream;
+    return grnnd::build_with(points, n, d, &q, cache_alloc_mode(), graph_out);
+  }
   return grnnd::build_with(points, n, d, p, cache_alloc_mode(), graph_out);
 }
 
@@ -769,7 +841,9 @@ int grnnd_build_batch(const float* points, const int64_t* offsets, int32_t nbuil
     if ((int64_t)p->S > nb - 1) return fail(GRNND_EINVAL, "need S <= (points of every build) - 1");
   }
   if (offsets[nbuild] > 0x7FFFFFFELL) return fail(GRNND_EINVAL, "total points must be <= 2^31 - 2");
-  return build_core(points, offsets[nbuild], d, p, offsets, nbuild, graphs_out, cache_alloc_mode());
+  grnnd_params q = *p;
+  if (!q.stream) q.stream = (void*)g_stream;  // no stream given: the thread's current stream
+  return build_core(points, offsets[nbuild], d, &q, offsets, nbuild, graphs_out, cache_alloc_mode());
 }
 
 int grnnd_autotune(const float* points, int64_t n, int32_t d, const int64_t* offsets, int32_t nbuild,
@@ -853,6 +927,7 @@ int grnnd_search(const grnnd_graph* g, const float* queries, int64_t nq, int32_t
   if (g->d > 1024) return fail(GRNND_EINVAL, "search supports d <= 1024");
   if (nq == 0) return GRNND_OK;
   const int32_t ldq = g->ld;
+  const cudaStream_t st = g_stream;  // the thread's current stream
   DevMem mq, mo;
   GR_CU(mq.alloc((size_t)nq * ldq * 4));
   const bool out_dev = is_device_ptr(ids_out);
@@ -863,12 +938,12 @@ int grnnd_search(const grnnd_graph* g, const float* queries, int64_t nq, int32_t
   }
   float* dq = static_cast<float*>(mq.p);
   const cudaMemcpyKind kind = is_device_ptr(queries) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (ldq != g->d) GR_CU(cudaMemset(dq, 0, (size_t)nq * ldq * 4));
-  GR_CU(cudaMemcpy2D(dq, (size_t)ldq * 4, queries, (size_t)g->d * 4, (size_t)g->d * 4, (size_t)nq, kind));
+  if (ldq != g->d) GR_CU(cudaMemsetAsync(dq, 0, (size_t)nq * ldq * 4, st));
+  GR_CU(cudaMemcpy2DAsync(dq, (size_t)ldq * 4, queries, (size_t)g->d * 4, (size_t)g->d * 4, (size_t)nq, kind, st));
   GR_CU(grnnd::launch_search(g->points, g->n, g->d, g->ld, g->metric, g->ids, g->deg, g->R, g->entry,
-                             dq, nq, ldq, k, beam, dids, nullptr, 0));
-  if (!out_dev) GR_CU(cudaMemcpy(ids_out, dids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost));
-  GR_CU(cudaDeviceSynchronize());
+                             dq, nq, ldq, k, beam, dids, nullptr, st));
+  if (!out_dev) GR_CU(cudaMemcpyAsync(ids_out, dids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaStreamSynchronize(st));
   return GRNND_OK;
 }
 
@@ -893,9 +968,11 @@ int grnnd_graph_view(const grnnd_graph* g, const int32_t** ids, const float** di
 int grnnd_graph_copy(const grnnd_graph* g, int32_t* ids, float* dists, int32_t* deg) {
   if (!g) return fail(GRNND_EINVAL, "graph is NULL");
   const size_t nr = (size_t)g->n * g->R;
-  if (ids) GR_CU(cudaMemcpy(ids, g->ids, nr * 4, cudaMemcpyDefault));
-  if (dists) GR_CU(cudaMemcpy(dists, g->dists, nr * 4, cudaMemcpyDefault));
-  if (deg) GR_CU(cudaMemcpy(deg, g->deg, (size_t)g->n * 4, cudaMemcpyDefault));
+  const cudaStream_t st = g_stream;  // the thread's current stream
+  if (ids) GR_CU(cudaMemcpyAsync(ids, g->ids, nr * 4, cudaMemcpyDefault, st));
+  if (dists) GR_CU(cudaMemcpyAsync(dists, g->dists, nr * 4, cudaMemcpyDefault, st));
+  if (deg) GR_CU(cudaMemcpyAsync(deg, g->deg, (size_t)g->n * 4, cudaMemcpyDefault, st));
+  GR_CU(cudaStreamSynchronize(st));
   return GRNND_OK;
 }
 

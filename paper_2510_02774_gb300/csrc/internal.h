@@ -25,10 +25,11 @@ struct Workspace {
   uint8_t* active = nullptr;               // n flags: the vertex is in the list
   uint8_t* next_active = nullptr;          // n flags written by an in-place merge: the row holds
                                            // a new entry (read by the next step's prep)
-  uint64_t* rec[4] = {};                   // work records by pool-size class (entries <= 8,
-  int rec_w[4] = {};                       // <= 16, <= 32, more): n records of rec_w[c]
-  int rec_cap[4] = {};                     // words each, holding up to rec_cap[c] entries
-  int32_t* list_n = nullptr;               // [4] records per class
+  uint64_t* rec[5] = {};                   // work records by pool-size class (entries <= 8,
+  int rec_w[5] = {};                       // <= 16, <= 32, <= 64, more): n records of rec_w[c]
+  int rec_cap[5] = {};                     // words each, holding up to rec_cap[c] entries (the
+                                           // last class exists only when R > 64)
+  int32_t* list_n = nullptr;               // [5] records per class
   unsigned long long* red_n = nullptr;     // number of redirects / reverse proposals
   int32_t* err = nullptr;                  // device status word (bounded waits)
   int64_t* round_new = nullptr;            // new entries written by the last merge
@@ -69,9 +70,12 @@ struct AllocMode {
 size_t workspace_bytes(int64_t n, int R);
 bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws);
 
+// Xb16 / ldb / qflags (optional): the BF16 copy of the rows and its dataset flags; when every
+// value is exact in BF16 the drawn rows are read from it (same values, half the bytes).
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
                              uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st,
-                             const int2* vseg = nullptr);
+                             const int2* vseg = nullptr, const void* Xb16 = nullptr, int ldb = 0,
+                             const unsigned* qflags = nullptr);
 
 // Batched builds: subtracts each row's build base from its ids (-1 stays -1).
 cudaError_t launch_localize_ids(int64_t n, int R, int32_t* ids, const int2* vseg, cudaStream_t st);

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "kernels.cuh"
 #include <atomic>
 #include <mutex>
 
@@ -23,7 +24,6 @@ namespace grnnd {
 namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 18;  // mbarrier try_wait rounds before a wait gives up (about 1 s: a try that does not complete returns after about 3.8 us)
-constexpr int64_t kMaxJoinGrid = 2048;  // CTAs of the join at most (sizes the redirect slack)
 
 // Per-kernel launch set-up kept out of stream captures: the dynamic shared-memory opt-in
 // (once) and the resident blocks per SM (cached per shared-memory size).  Shared by host
@@ -87,22 +87,28 @@ int sm_count() {
 //   32 candidates are tested per step; a lane is rejected if its id matches an accepted
 //   id or an earlier lane of the same step.
 // =====================================================================================
-constexpr int IW = 4;   // warps per rnd_init CTA
 constexpr int IC = 16;  // dimensions per staged chunk
-template <int METRIC>
+// E: pool entries per lane (32 E >= R); IW: warps per CTA (E = 2: 4 warps; E = 8, pools of
+// up to 256 entries: 2 warps, so that the staged rows stay within the static shared memory)
+// Xb (may be null): a BF16 copy of the rows (ldb elements per row); when qflags say that every
+// value is exact in BF16, the drawn rows are read from it -- the same values in half the bytes.
+template <int METRIC, int E, int IW>
 __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restrict__ X, int64_t n,
                                                            int d, int ld, int S, int R, uint64_t seed,
                                                            uint64_t* __restrict__ keys,
                                                            int32_t* __restrict__ deg,
-                                                           const int2* __restrict__ vseg) {
-  __shared__ int32_t acc_ids[IW][kMaxR];
+                                                           const int2* __restrict__ vseg,
+                                                           const __nv_bfloat16* __restrict__ Xb, int ldb,
+                                                           const unsigned* __restrict__ qflags) {
+  __shared__ int32_t acc_ids[IW][32 * E];
   // the chunk of each drawn row (rows 0..S-1) and of v itself (row S), 16-byte granules
-  __shared__ __align__(16) float stage[IW][kMaxR + 1][IC + 4];
+  __shared__ __align__(16) float stage[IW][32 * E + 1][IC + 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* acc = acc_ids[warp];
   float(*rows)[IC + 4] = stage[warp];
   const uint64_t head = hash_head(seed, 0, 0);
   const unsigned below = lanemask_lt();
+  const bool use_b = Xb != nullptr && (qflags[0] & 2u) == 0u;  // every value exact in BF16
   for (int64_t v = (int64_t)blockIdx.x * IW + warp; v < n; v += (int64_t)gridDim.x * IW) {
     // the vertex's build: ids [lo, lo + nb); draws use the local id v - lo
     const int64_t lo = vseg ? vseg[v].x : 0;
@@ -126,20 +132,29 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
     // canonical distances, lane e for entries e and e + 32: the rows are staged IC dimensions
     // at a time with whole-row coalesced loads; each lane then advances its four partial sums
     // over the chunk in ascending dimension order, exactly as row_dist does
-    float4 ps[2] = {make_float4(0.0f, 0.0f, 0.0f, 0.0f), make_float4(0.0f, 0.0f, 0.0f, 0.0f)};
+    float4 ps[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) ps[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int c0 = 0; c0 < d; c0 += IC) {
       const int clen = min(IC, d - c0);
       const int gr = (clen + 3) >> 2;  // granules per row
       for (int t = lane; t < (S + 1) * gr; t += 32) {
         const int r = t / gr, q = t - r * gr;
         const int64_t src = r < S ? (int64_t)acc[r] : v;
-        float4 val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
+        float4 val;
+        if (use_b) {  // four BF16 values, widened exactly
+          const uint2 u = *reinterpret_cast<const uint2*>(Xb + src * ldb + c0 + 4 * q);
+          val = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                            __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+        } else {
+          val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
+        }
         if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
         *reinterpret_cast<float4*>(&rows[r][4 * q]) = val;
       }
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < E; ++j) {
         const int e = j * 32 + lane;
         if (e < S)
           for (int q = 0; q < gr; ++q)
@@ -148,15 +163,15 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
       }
       __syncwarp();
     }
-    uint64_t kk[2];
+    uint64_t kk[E];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < E; ++j) {
       const int e = j * 32 + lane;
       kk[j] = e < S ? make_key(dist_finish4<METRIC>(ps[j]), (uint32_t)acc[e], 0u) : kEmpty;
     }
-    warp_sort_u64<2>(kk);
+    warp_sort_u64<E>(kk);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < E; ++j) {
       const int e = j * 32 + lane;
       if (e < R) keys[v * R + e] = kk[j];
     }
@@ -167,13 +182,24 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
 
 cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metric, int S, int R,
                              uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st,
-                             const int2* vseg) {
-  const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
+                             const int2* vseg, const void* Xb16, int ldb, const unsigned* qflags) {
+  const __nv_bfloat16* Xb = (Xb16 && qflags) ? static_cast<const __nv_bfloat16*>(Xb16) : nullptr;
   ProfScope ps("rnd_init", st);
-  if (metric == 0)
-    rnd_init_kernel<0><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
-  else
-    rnd_init_kernel<1><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg);
+  if (R <= kTeamMaxM) {
+    constexpr int IW = 4;
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
+    if (metric == 0)
+      rnd_init_kernel<0, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+    else
+      rnd_init_kernel<1, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+  } else {  // pools of up to 256 entries
+    constexpr int IW = 2;
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 32);
+    if (metric == 0)
+      rnd_init_kernel<0, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+    else
+      rnd_init_kernel<1, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+  }
   return cudaGetLastError();
 }
 
@@ -203,16 +229,17 @@ __global__ void quantize_kernel(const float* __restrict__ X, int64_t n, int d, i
   unsigned fl = 0, mx = 0;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < n;
        r += (int64_t)gridDim.x * (blockDim.x >> 5)) {
-    float nrm = 0.0f;
-    double res = 0.0;
+    float nrm = 0.0f, res = 0.0f;
     for (int k = lane; k < ldb; k += 32) {
       const float x = k < d ? X[r * ld + k] : 0.0f;
       const __nv_bfloat16 b = __float2bfloat16_rn(x);
       Xb[r * ldb + k] = b;
       const float xf = __bfloat162float(b);
       nrm = __fmaf_rn(xf, xf, nrm);
-      const double e = (double)x - (double)xf;
-      res += e * e;
+      // |x - xf|, its square and the running sum rounded upward: res stays an upper bound
+      // of the squared residual norm
+      const float e = x >= xf ? __fsub_ru(x, xf) : __fsub_ru(xf, x);
+      res = __fmaf_ru(e, e, res);
       fl |= (x != rintf(x)) ? 1u : 0u;
       fl |= (xf != x) ? 2u : 0u;
       mx = max(mx, __float_as_uint(fabsf(x)));
@@ -220,9 +247,9 @@ __global__ void quantize_kernel(const float* __restrict__ X, int64_t n, int d, i
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-      res += __shfl_xor_sync(0xffffffffu, res, o);
+      res = __fadd_ru(res, __shfl_xor_sync(0xffffffffu, res, o));
     }
-    if (lane == 0) aux[r] = make_float2(nrm, __double2float_ru(sqrt(res) * (1.0 + 1e-12)));
+    if (lane == 0) aux[r] = make_float2(nrm, __fsqrt_ru(res));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -259,16 +286,17 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t n, int 
     if (amax > 0.0f) frexpf(amax, &E);
     const int e = amax > 0.0f ? min(127, max(-126, E - 8)) : 0;
     const float inv = ldexpf(1.0f, -e), sc = ldexpf(1.0f, e);
-    float nrm = 0.0f;
-    double res = 0.0;
+    float nrm = 0.0f, res = 0.0f;
     for (int k = lane; k < ldb; k += 32) {
       const float x = k < d ? X[r * ld + k] : 0.0f;
       const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3);
       Xq[r * ldb + k] = (uint8_t)q;
       const float xf = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;
       nrm = __fmaf_rn(xf, xf, nrm);
-      const double dv = (double)x - (double)xf;
-      res += dv * dv;
+      // |x - xf|, its square and the running sum rounded upward: res stays an upper bound
+      // of the squared residual norm
+      const float e = x >= xf ? __fsub_ru(x, xf) : __fsub_ru(xf, x);
+      res = __fmaf_ru(e, e, res);
       fl |= (x != rintf(x)) ? 1u : 0u;
       fl |= (xf != x) ? 2u : 0u;
       mx = max(mx, __float_as_uint(fabsf(x)));
@@ -276,10 +304,10 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t n, int 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-      res += __shfl_xor_sync(0xffffffffu, res, o);
+      res = __fadd_ru(res, __shfl_xor_sync(0xffffffffu, res, o));
     }
     if (lane == 0) {
-      uint32_t rb = __float_as_uint(__double2float_ru(sqrt(res) * (1.0 + 1e-12)));
+      uint32_t rb = __float_as_uint(__fsqrt_ru(res));
       rb = ((rb + 255u) & ~255u) | (uint32_t)(e + 127);
       aux[r] = make_float2(nrm, __uint_as_float(rb));
     }
@@ -312,26 +340,25 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 
 // =====================================================================================
 // prep: active flag of the vertices whose pool holds a new entry, and for each of them a
-// contiguous work record that the join prefetches in one piece.  Records go to one of four
-// regions by pool size (entries <= 8, <= 16, <= 32, more; everything to the last region
-// when the warp kernels cannot take the rows), so that a warp can take several small pools
-// at once.  A record of a region holding up to cap entries:
-//   word 0: v | (first id of v's build) << 32    word 1: m    words 2 .. 2+m: the pool keys
-//   (BF16 form) words 2+cap .. 2+cap+m: per entry (norm^2, residual) of the quantized row.
+// contiguous work record that the join prefetches in one piece.  Records go to one of five
+// regions by pool size (entries <= 8, <= 16, <= 32, <= 64, more; pools of up to 64 entries
+// all to the fourth region when the warp kernels cannot take the rows), so that a warp can
+// take several small pools at once.  A record of a region holding up to cap entries:
+//   word 0: v | (first id of v's build) << 32    word 1: m    words 2 .. 2+m: the pool keys.
 // Also counts the entries of every pool (each one is proposed once, explicitly or in place).
 // With `hint` (the flags the last merge of the same pools wrote) no pool key is read for
 // the active test.
 // =====================================================================================
 struct RecSet {
-  uint64_t* rec[4];
-  int w[4];
-  int cap[4];
+  uint64_t* rec[kNumClasses];
+  int w[kNumClasses];
+  int cap[kNumClasses];
 };
 
 __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
                             int64_t n, int R, uint8_t* __restrict__ active,
                             int32_t* __restrict__ list_n, int warp_ok, int3 gmax, RecSet rs,
-                            const float2* __restrict__ aux, const int2* __restrict__ vseg,
+                            const int2* __restrict__ vseg,
                             const uint8_t* __restrict__ hint, int64_t* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
   long long props = 0;
@@ -349,11 +376,11 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
         for (int j = 0; j < m && !act; ++j) act = !(keys[v * R + j] & 1ull);
       active[v] = act ? 1 : 0;
     }
-    const int cls = !warp_ok ? 3 : (m <= gmax.x ? 0 : (m <= gmax.y ? 1 : (m <= gmax.z ? 2 : 3)));
-    unsigned bc[4];
-    int off[4];
+    const int cls = m > kTeamMaxM ? 4 : !warp_ok ? 3 : (m <= gmax.x ? 0 : (m <= gmax.y ? 1 : (m <= gmax.z ? 2 : 3)));
+    unsigned bc[kNumClasses];
+    int off[kNumClasses];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kNumClasses; ++c) {
       bc[c] = __ballot_sync(0xffffffffu, act && cls == c);
       int o = 0;
       if (lane == 0 && bc[c]) o = atomicAdd(&list_n[c], __popc(bc[c]));
@@ -361,7 +388,7 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
     }
     // the warp writes the records of its active vertices, four at a time (eight lanes each),
     // so that four chains of dependent loads (key, then the row terms it names) overlap
-    unsigned left = bc[0] | bc[1] | bc[2] | bc[3];
+    unsigned left = bc[0] | bc[1] | bc[2] | bc[3] | bc[4];
     const int grp = lane >> 3, gln = lane & 7;
     while (left) {
       unsigned mine = left;  // this group's vertex: the grp-th remaining one
@@ -376,15 +403,14 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
       if (l < 0) continue;
       const unsigned below_l = (1u << l) - 1u;
       unsigned bcu = bc[0];
-      int offu = off[0], W = rs.w[0], cap = rs.cap[0];
+      int offu = off[0], W = rs.w[0];
       uint64_t* rg = rs.rec[0];
 #pragma unroll
-      for (int c = 1; c < 4; ++c)
+      for (int c = 1; c < kNumClasses; ++c)
         if (cu == c) {
           bcu = bc[c];
           offu = off[c];
           W = rs.w[c];
-          cap = rs.cap[c];
           rg = rs.rec[c];
         }
       uint64_t* r = rg + (int64_t)(offu + __popc(bcu & below_l)) * W;
@@ -392,8 +418,7 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
         r[0] = (uint64_t)u | ((uint64_t)(vseg ? vseg[u].x : 0) << 32);
         r[1] = (uint64_t)mu;
       }
-      // up to 8 entries per lane at a time: every key load, then every row-term load it names,
-      // are in flight together
+      // up to 8 entries per lane at a time: their key loads are in flight together
       for (int j0 = 0; j0 < mu; j0 += 64) {
         uint64_t kk[8];
 #pragma unroll
@@ -401,19 +426,10 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
           const int j = j0 + gln + 8 * t;
           kk[t] = j < mu ? keys[u * R + j] : kEmpty;
         }
-        float2 qq[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int j = j0 + gln + 8 * t;
-          qq[t] = (aux && j < mu) ? aux[key_id(kk[t])] : make_float2(0.0f, 0.0f);
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int j = j0 + gln + 8 * t;
-          if (j < mu) {
-            r[2 + j] = kk[t];
-            if (aux) r[2 + cap + j] = ((uint64_t)__float_as_uint(qq[t].y) << 32) | __float_as_uint(qq[t].x);
-          }
+          if (j < mu) r[2 + j] = kk[t];
         }
       }
     }
@@ -462,8 +478,8 @@ constexpr int SPW = 12;                        // FP32 tile: row segments per wa
 constexpr int BSEG = 288;                      // row segments per batch at most
 constexpr int BT = 64;                         // mma output tiles per batch at most
 constexpr int TPW = BT / JW;                   // mma tiles per warp
-constexpr int RECW_MAX = 2 + 2 * kMaxR;        // work-record words (R = 64, BF16 form)
-constexpr int RED_CHUNK = 1024;                // redirect slots reserved per CTA at a time
+constexpr int RECW_MAX = 2 + kMaxR;            // work-record words (R = 64)
+constexpr int RED_CHUNK = kRedChunk;           // redirect slots reserved per CTA at a time
 
 // A row segment is up to 32 consecutive pairs (i, j0..j0+31) of one new row i: one warp
 // takes a segment, one lane a partner j.
@@ -537,41 +553,6 @@ struct __align__(16) JoinSmem {
 static_assert(sizeof(JoinSmem<0>) <= 115 * 1024 && sizeof(JoinSmem<1>) <= 115 * 1024,
               "join shared memory must allow two CTAs per SM");
 
-struct PointsDev {
-  const float* X;
-  int ld;
-  const void* Xb;  // quantized rows: bfloat16 (BF16 form) or e4m3 bytes (FP8 form)
-  int ldb;
-  const float2* aux;
-  const unsigned* qflags;
-  int d;
-};
-
-struct JoinArgs {
-  PointsDev P;
-  int64_t n;
-  int R;
-  const uint64_t* keys_in;
-  const int32_t* deg_in;
-  const int32_t* list_n;    // records per pool-size class
-  const uint64_t* rec[4];   // work records by class (entries <= 8, <= 16, <= 32, more)
-  int rec_w[4];             // words per record
-  int rec_cap[4];           // entries a record holds (the last class: R)
-  uint64_t seed;
-  int t1, t2, order;
-  uint64_t* keys_out;  // survivors (in place for the round, final graph for the last pass)
-  int32_t* deg_out;
-  int emit_redirects;
-  int32_t* red_tgt;
-  uint64_t* red_key;
-  unsigned long long* red_n;
-  int64_t red_cap;          // redirect slots in red_tgt / red_key
-  int32_t* count;
-  int64_t* stats;
-  int32_t* err;
-  int warp_ctas, team_ctas;  // launch caps (host side only; 0: as many as fit)
-};
-
 __device__ __forceinline__ int tiles_of(int m, int k) {
   int nt = 0;
   const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
@@ -629,10 +610,7 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
       for (int j = 0; j < 2; ++j) {
         const int e = j * 32 + lane;
         if (e < m) kx[h][j] = r[2 + e];
-        if (PREC == 1 && e < m) {
-          const uint64_t q = r[2 + R + e];
-          ax[h][j] = make_float2(__uint_as_float((uint32_t)q), __uint_as_float((uint32_t)(q >> 32)));
-        }
+        if (PREC == 1 && e < m) ax[h][j] = a.P.aux[key_id(kx[h][j])];
       }
       const int k = __popc(__ballot_sync(0xffffffffu, lane < m && !key_old(kx[h][0]))) +
                     __popc(__ballot_sync(0xffffffffu, lane + 32 < m && !key_old(kx[h][1])));
@@ -1354,14 +1332,15 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
   x.key = kEmpty;
   x.aux = 0ull;
   if (rr < (int64_t)a.list_n[cls]) {
-    const int cap = a.rec_cap[cls];
     const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
     x.v = (int64_t)(r[0] & 0xffffffffull);
     x.lo = (uint32_t)(r[0] >> 32);
     x.m = (int)r[1];
     if (gl < x.m) {
       x.key = r[2 + gl];
-      if (PREC >= 1) x.aux = r[2 + cap + gl];
+      // the quantized row's (norm^2, residual), read here a whole item ahead of its use
+      if (PREC >= 1 && in_bounds((uint64_t)key_id(x.key) < (uint64_t)a.n, a.err))
+        x.aux = __ldg(reinterpret_cast<const unsigned long long*>(a.P.aux) + key_id(x.key));
     }
   }
 }
@@ -1923,7 +1902,12 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   uint32_t nlo = (uint32_t)(r0[0] >> 32);
   int nm = (int)r0[1];
   uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
-  uint64_t naux = (PREC >= 1 && tid < nm) ? r0[2 + R + tid] : 0ull;
+  // the quantized rows' (norm^2, residual) of the entries, read a vertex ahead of their use
+  auto row_terms = [&](uint64_t k) -> uint64_t {
+    if (PREC == 0 || !in_bounds((uint64_t)key_id(k) < (uint64_t)a.n, a.err)) return 0ull;
+    return __ldg(reinterpret_cast<const unsigned long long*>(a.P.aux) + key_id(k));
+  };
+  uint64_t naux = (PREC >= 1 && tid < nm) ? row_terms(nkey) : 0ull;
 
   for (; p < cnt; p += gridDim.x) {
     const int64_t v = nv;
@@ -1937,7 +1921,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       nlo = (uint32_t)(rn[0] >> 32);
       nm = (int)rn[1];
       nkey = tid < nm ? rn[2 + tid] : kEmpty;
-      if (PREC >= 1) naux = tid < nm ? rn[2 + R + tid] : 0ull;
+      if (PREC >= 1) naux = tid < nm ? row_terms(nkey) : 0ull;
     }
     // ---- visit order: rank of (h, id) among the m entries --------------------------------
     const uint32_t idl = key_id(keyl);
@@ -2591,32 +2575,6 @@ __device__ __forceinline__ void merge_chunk(uint64_t& x0, uint64_t& x1, uint64_t
   __syncwarp();
 }
 
-struct SelectArgs {
-  int64_t n;
-  int R;
-  const uint64_t* bucket;  // null: no bucket (every target keeps its base pool)
-  const int64_t* off;
-  const uint8_t* active;   // null: the base pool of every target is keys_in
-  const uint64_t* keys_in;
-  const int32_t* deg_in;
-  uint64_t* keys_out;      // holds the kept survivors of active targets on entry
-  int32_t* deg_out;
-  int64_t* round_new;
-  int64_t* stats;
-  int32_t* err;            // nonzero: a wait of this round gave up, leave every pool as it is
-  uint8_t* next_active;    // per target: its output row holds a new entry (prep's hint), or null
-  int next_active_all;     // 1: write the flag of every target (a round: rows the merge leaves
-                           // alone hold no new entry); 0: only of merged targets (a reverse step)
-  // Copies of one id proposed to one target can differ in distance only when the recorded
-  // distances are not canonical FP32 (quantized tiles outside their exact mode); then the
-  // merge first gives each proposal the old bit its id has in the row.  old_pass 1: always;
-  // 0: when qflags (the quantized rows' dataset flags, null for FP32 rows) show that the
-  // tiles of d-dimensional rows are not exact.
-  int old_pass;
-  const unsigned* qflags;
-  int d;
-};
-
 __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   __shared__ MergeScratch scratch[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2761,6 +2719,7 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
     }
   }
   cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
+  if (sa.R > kTeamMaxM) return launch_select_wide(sa, st);  // rows of more than 64 entries
   const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 16);
   ProfScope ps("select", st);
   select_kernel<<<(unsigned)blocks, 256, 0, st>>>(sa);
@@ -2774,15 +2733,15 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
   // the warp kernels take FP32 rows of up to 128 dimensions (BF16 rows of any length)
   const int warp_ok = (P.precision == 0 && P.d > 128) ? 0 : 1;
   RecSet rs;
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < kNumClasses; ++c) {
     rs.rec[c] = ws.rec[c];
     rs.w[c] = ws.rec_w[c];
     rs.cap[c] = ws.rec_cap[c];
   }
   const int3 gmax = make_int3(P.group_max[0], P.group_max[1], P.group_max[2]);
+  // (the join kernels read the quantized rows' terms themselves, a vertex ahead of their use)
   prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
-                                                gmax, rs, P.precision >= 1 ? P.aux : nullptr, P.vseg, hint,
-                                                stats);
+                                                gmax, rs, P.vseg, hint, stats);
   return cudaGetLastError();
 }
 
@@ -2803,7 +2762,7 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   a.keys_in = keys_in;
   a.deg_in = deg_in;
   a.list_n = ws.list_n;
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < kNumClasses; ++c) {
     a.rec[c] = ws.rec[c];
     a.rec_w[c] = ws.rec_w[c];
     a.rec_cap[c] = ws.rec_cap[c];
@@ -2852,12 +2811,14 @@ cudaError_t dispatch_join(const PointsSet& P, const JoinArgs& a, cudaStream_t st
   if (e != cudaSuccess) return e;
   if (P.precision >= 1 || P.d <= 128) {  // pools of 33..64 entries: a two-warp team per vertex
     const char* tname = (name[0] == 'r') ? "rnd_join_team" : "final_prune_team";
-    return P.metric == 0 ? launch_team_p<0>(P.precision, a, st, tname, so)
-                         : launch_team_p<1>(P.precision, a, st, tname, so);
+    e = P.metric == 0 ? launch_team_p<0>(P.precision, a, st, tname, so)
+                      : launch_team_p<1>(P.precision, a, st, tname, so);
+  } else {  // FP32 rows of more than 128 dimensions: batched CTAs with dimension chunks
+    e = P.metric == 0 ? launch_join_t<0, 0>(a, st, name, so) : launch_join_t<1, 0>(a, st, name, so);
   }
-  // FP32 rows of more than 128 dimensions: batched CTAs with dimension chunks
-  if (P.metric == 0) return launch_join_t<0, 0>(a, st, name, so);
-  return launch_join_t<1, 0>(a, st, name, so);
+  if (e != cudaSuccess || so || a.R <= kTeamMaxM) return e;
+  // pools of 65..R entries: the wide join, one CTA per vertex
+  return launch_join_wide(a, P.metric, st, (name[0] == 'r') ? "rnd_join_wide" : "final_prune_wide");
 }
 
 }  // namespace
@@ -2874,7 +2835,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          cudaStream_t st, bool use_hint) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;  // list_n and red_n
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;  // list_n and red_n
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, stats, st)) != cudaSuccess)
     return e;
@@ -2907,7 +2868,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st,
                          bool use_hint) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, nullptr, st)) != cudaSuccess)
     return e;
@@ -2986,7 +2947,7 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
                            int32_t* deg_out, int64_t* stats, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 24, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   {
     const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
@@ -3050,11 +3011,16 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 namespace {
 // work records of a size class holding up to cap entries: v, m, cap keys, cap (norm^2,
 // residual) pairs of the BF16 rows (an even number of words: 16-byte aligned records)
-inline int rec_cap_of(int R, int c) { return std::min(R, 8 << c); }
-inline int rec_words(int cap) { return 2 + 2 * cap; }
+// (classes 0..3 hold up to min(R, 8 << c) entries; class 4, only when R > 64, up to R)
+inline int rec_cap_of(int R, int c) { return c < 4 ? std::min(R, 8 << c) : (R > kTeamMaxM ? R : 0); }
+inline int rec_words(int cap) { return 2 + ((cap + 1) & ~1); }
+inline size_t rec_region_bytes(int64_t n, int R, int c) {
+  const int cap = rec_cap_of(R, c);
+  return cap > 0 ? al256((size_t)n * rec_words(cap) * 8) : 0;
+}
 inline size_t rec_bytes(int64_t n, int R) {
   size_t b = 0;
-  for (int c = 0; c < 4; ++c) b += al256((size_t)n * rec_words(c == 3 ? R : rec_cap_of(R, c)) * 8);
+  for (int c = 0; c < kNumClasses; ++c) b += rec_region_bytes(n, R, c);
   return b;
 }
 // Redirect slots: a vertex loses at most m - 1 <= R - 1 entries (the one with the smallest
@@ -3063,7 +3029,10 @@ inline size_t rec_bytes(int64_t n, int R) {
 // kernel leaves at most (its units x its chunk) <= kMaxJoinGrid x RED_CHUNK slots unused.
 static_assert(WW * WRED <= RED_CHUNK && TRED <= RED_CHUNK, "per-CTA redirect reservation above the slack");
 static_assert(BV * 63 <= RED_CHUNK && WM <= WRED && TM <= TRED, "a batch or vertex must fit one fresh chunk");
-inline size_t red_slots(int64_t n, int R) { return (size_t)n * R + 2 * (size_t)kMaxJoinGrid * RED_CHUNK; }
+// (a third join kernel, the wide one, runs when R > 64)
+inline size_t red_slots(int64_t n, int R) {
+  return (size_t)n * R + (R > kTeamMaxM ? 3 : 2) * (size_t)kMaxJoinGrid * RED_CHUNK;
+}
 }  // namespace
 
 size_t workspace_bytes(int64_t n, int R) {
@@ -3099,14 +3068,14 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   p += al256((size_t)n);
   ws->next_active = reinterpret_cast<uint8_t*>(p);
   p += al256((size_t)n);
-  for (int c = 0; c < 4; ++c) {
-    ws->rec_cap[c] = c == 3 ? R : rec_cap_of(R, c);
+  for (int c = 0; c < kNumClasses; ++c) {
+    ws->rec_cap[c] = rec_cap_of(R, c);
     ws->rec_w[c] = rec_words(ws->rec_cap[c]);
-    ws->rec[c] = reinterpret_cast<uint64_t*>(p);
-    p += al256((size_t)n * ws->rec_w[c] * 8);
+    ws->rec[c] = ws->rec_cap[c] > 0 ? reinterpret_cast<uint64_t*>(p) : nullptr;
+    p += rec_region_bytes(n, R, c);
   }
-  ws->list_n = reinterpret_cast<int32_t*>(p);  // [4] records per class, then the redirect count
-  ws->red_n = reinterpret_cast<unsigned long long*>(p + 16);
+  ws->list_n = reinterpret_cast<int32_t*>(p);  // [5] records per class, then the redirect count
+  ws->red_n = reinterpret_cast<unsigned long long*>(p + 24);
   p += al256(24);
   ws->err = reinterpret_cast<int32_t*>(p);
   p += al256(4);

@@ -108,6 +108,21 @@ _SIGS = {
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_quantized_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+    "grnnd_quantize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "grnnd_join_round_q": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "grnnd_final_prune_q": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p]),
+    "grnnd_set_stream": (None, [ctypes.c_void_p]),
+    "grnnd_get_stream": (ctypes.c_void_p, []),
     "grnnd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int32, ctypes.POINTER(Params), ctypes.POINTER(Tuning)]),
     "grnnd_build_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -371,7 +386,14 @@ def search(graph: Graph, queries, k: int = 10, beam: int = 64):
     torch = _torch()
     q = queries.contiguous().to(torch.float32)
     out = torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device)
-    _check(lib().grnnd_search(graph.handle, _ptr(q), q.shape[0], k, beam, _ptr(out)))
+    L = lib()
+    prev = L.grnnd_get_stream()
+    if q.is_cuda:  # the search runs on the current torch stream
+        L.grnnd_set_stream(_stream_ptr())
+    try:
+        _check(L.grnnd_search(graph.handle, _ptr(q), q.shape[0], k, beam, _ptr(out)))
+    finally:
+        L.grnnd_set_stream(prev)
     return out
 
 
@@ -388,17 +410,34 @@ def pool_init(X, d: int, S: int, R: int, seed: int, metric: int = L2SQ, stream=N
     return keys, deg
 
 
+def quantize(X, d: int, precision: int, stream=None):
+    """Quantized copy of device points X (n x ld) for the BF16 / FP8 step calls (a uint8 tensor)."""
+    torch = _torch()
+    n, ld = X.shape
+    nb = lib().grnnd_quantized_size(n, d, precision)
+    if nb == 0:
+        raise GrnndError(EINVAL, "precision must be BF16 or FP8")
+    q = torch.empty(nb + 256, dtype=torch.uint8, device=X.device)
+    off = (-q.data_ptr()) % 256
+    q = q[off:off + nb]
+    _check(lib().grnnd_quantize(_ptr(X), n, d, ld, precision, _ptr(q), nb, _stream_ptr(stream)))
+    return q
+
+
 def join_round(X, d: int, keys, deg, seed: int, t1: int, t2: int, order: int = ORDER_RANDOM, metric: int = L2SQ,
-               ws=None, stats=None, stream=None, inplace: bool = False):
-    """One round; with inplace=True the pool tensors are updated and returned."""
+               ws=None, stats=None, stream=None, inplace: bool = False, precision: int = FP32, qpoints=None):
+    """One round; with inplace=True the pool tensors are updated and returned.  In the BF16 /
+    FP8 forms `qpoints` is the copy from quantize(X, d, precision)."""
     torch = _torch()
     n, ld = X.shape
     R = keys.shape[1]
     ws = workspace(n, R, X.device) if ws is None else ws
     k2 = keys if inplace else torch.empty_like(keys)
     d2 = deg if inplace else torch.empty_like(deg)
-    _check(lib().grnnd_join_round(_ptr(X), n, d, ld, metric, R, _ptr(keys), _ptr(deg), seed, t1, t2, order,
-                                  _ptr(k2), _ptr(d2), _ptr(ws), ws.numel(), _ptr(stats), _stream_ptr(stream)))
+    qn = 0 if qpoints is None else qpoints.numel()
+    _check(lib().grnnd_join_round_q(_ptr(X), n, d, ld, metric, precision, _ptr(qpoints), qn, R, _ptr(keys), _ptr(deg),
+                                    seed, t1, t2, order, _ptr(k2), _ptr(d2), _ptr(ws), ws.numel(), _ptr(stats),
+                                    _stream_ptr(stream)))
     return k2, d2
 
 
@@ -419,15 +458,17 @@ def workspace_status(ws, n: int, R: int, stream=None) -> None:
 
 
 def final_prune(X, d: int, keys, deg, seed: int, t1: int, order: int = ORDER_RANDOM, metric: int = L2SQ, ws=None,
-                stream=None):
+                stream=None, precision: int = FP32, qpoints=None):
     torch = _torch()
     n, ld = X.shape
     R = keys.shape[1]
     ws = workspace(n, R, X.device) if ws is None else ws
     k2 = torch.empty_like(keys)
     d2 = torch.empty_like(deg)
-    _check(lib().grnnd_final_prune(_ptr(X), n, d, ld, metric, R, _ptr(keys), _ptr(deg), seed, t1, order, _ptr(k2),
-                                   _ptr(d2), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    qn = 0 if qpoints is None else qpoints.numel()
+    _check(lib().grnnd_final_prune_q(_ptr(X), n, d, ld, metric, precision, _ptr(qpoints), qn, R, _ptr(keys),
+                                     _ptr(deg), seed, t1, order, _ptr(k2), _ptr(d2), _ptr(ws), ws.numel(),
+                                     _stream_ptr(stream)))
     return k2, d2
 
 

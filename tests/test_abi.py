@@ -37,7 +37,7 @@ def test_defaults(L):
 
 @pytest.mark.parametrize("kw,frag", [
     (dict(S=8, R=4), "S"),          # S > R
-    (dict(S=2, R=65), "R"),         # R above the 64-slot masks
+    (dict(S=2, R=257), "R"),        # R above the largest pool (256)
     (dict(S=2, R=1), "R"),
     (dict(S=2, R=4, T1=0), "T1"),
     (dict(S=2, R=4, rho=1.5), "rho"),
@@ -139,3 +139,33 @@ def test_server_validates_before_any_cuda_call(L):
                                         ctypes.byref(rid)) == G.EINVAL
     assert L.grnnd_server_wait(None, 1, 0.0, None) == G.EINVAL
     assert L.grnnd_server_release(None, 1) == G.EINVAL
+
+
+def test_current_stream_is_per_thread(L):
+    import threading
+    assert L.grnnd_get_stream() is None
+    L.grnnd_set_stream(ctypes.c_void_p(0x1234))
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(L.grnnd_get_stream()))
+    t.start()
+    t.join()
+    try:
+        assert seen == [None]                 # another thread keeps its own (NULL) stream
+        assert L.grnnd_get_stream() == 0x1234
+    finally:
+        L.grnnd_set_stream(None)
+    assert L.grnnd_get_stream() is None
+
+
+def test_quantized_step_calls_validate(L):
+    assert L.grnnd_quantized_size(100, 33, G.BF16) >= 100 * 48 * 2 + 100 * 8  # rows of 48 BF16, row terms
+    assert L.grnnd_quantized_size(100, 33, G.FP8) >= 100 * 64 + 100 * 8       # rows of 64 e4m3 bytes
+    assert L.grnnd_quantized_size(100, 33, G.FP32) == 0
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = L.grnnd_quantize(ctypes.c_void_p(256), 100, 33, 36, G.FP32, buf, len(buf), None)
+    assert rc == G.EINVAL and b"precision" in L.grnnd_last_error()
+    # a precision form without its quantized rows is rejected before any launch
+    rc = L.grnnd_join_round_q(ctypes.c_void_p(256), 100, 33, 36, 0, G.BF16, None, 0, 16, ctypes.c_void_p(256),
+                              ctypes.c_void_p(256), 1, 1, 1, 0, ctypes.c_void_p(256), ctypes.c_void_p(256),
+                              ctypes.c_void_p(256), 1 << 30, None, None)
+    assert rc == G.EINVAL and b"quantized" in L.grnnd_last_error()

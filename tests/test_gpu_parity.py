@@ -84,7 +84,8 @@ def test_pair_dist_fp32_within_1e5_of_fp64(G, orc):
 # rnd_init
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n,d,S,R", [(3000, 33, 16, 32), (700, 8, 64, 64), (2, 3, 1, 2), (65, 5, 64, 64)])
+@pytest.mark.parametrize("n,d,S,R", [(3000, 33, 16, 32), (700, 8, 64, 64), (2, 3, 1, 2), (65, 5, 64, 64),
+                                     (900, 9, 200, 256), (300, 20, 64, 128), (257, 3, 256, 256)])
 def test_pool_init_matches_oracle(G, orc, n, d, S, R):
     X = synth.small_integers(n, d, -8, 8, seed=n + d)
     Xd, _ = G.device_points(X)
@@ -110,6 +111,13 @@ CASES = [
     (1200, 128, 48, 64, 0, 0, 1),    # pools of 33..64 entries, rows of exactly 128 floats
     (1200, 37, 40, 64, 0, 1, 1),     # pools of 33..64 entries, inner product, ragged rows
     (1200, 11, 40, 64, 2, 0, 2),     # pools of 33..64 entries, descending order
+    # wide pools (65..256 entries): multi-word fire and closer masks, the wide merge
+    (1000, 12, 80, 96, 0, 0, 1),     # R = 96, pools of every size class
+    (800, 10, 128, 128, 0, 0, 0),    # R = 128, every pool starts full
+    (700, 9, 200, 256, 0, 0, 1),     # R = 256: four mask words
+    (700, 40, 150, 256, 1, 0, 1),    # R = 256, ascending order, two tile chunks of dimensions
+    (600, 7, 100, 128, 0, 1, 2),     # R = 128, inner product
+    (600, 150, 90, 128, 2, 0, 1),    # R = 128, descending order, FP32 rows longer than 128
 ]
 
 
@@ -177,20 +185,20 @@ def test_join_round_gaussian_config1(G, orc):
 # reverse sampling, final prune
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("rho", [0.0, 0.6, 1.0])
-def test_reverse_sample_matches_oracle(G, orc, rho):
-    X = synth.small_integers(3000, 9, -8, 8, seed=11)
-    p = oracle_state(orc, X, 16, 32, 5, 6)
+@pytest.mark.parametrize("rho,R", [(0.0, 32), (0.6, 32), (1.0, 32), (0.6, 128), (1.0, 256)])
+def test_reverse_sample_matches_oracle(G, orc, rho, R):
+    X = synth.small_integers(3000 if R <= 64 else 800, 9, -8, 8, seed=11)
+    p = oracle_state(orc, X, R // 2, R, 5, 6 if R <= 64 else 2)
     want, _ = orc.reverse(p, rho)
     keys, deg = G.reverse_sample(to_keys(G, p), torch.from_numpy(p.deg).cuda(), rho)
     assert_pool_equal(G, keys, deg, want)
 
 
-@pytest.mark.parametrize("order", [0, 1])
-def test_final_prune_matches_oracle(G, orc, order):
-    X = synth.small_integers(2500, 20, -8, 8, seed=13)
+@pytest.mark.parametrize("order,R", [(0, 32), (1, 32), (0, 200)])
+def test_final_prune_matches_oracle(G, orc, order, R):
+    X = synth.small_integers(2500 if R <= 64 else 700, 20, -8, 8, seed=13)
     Xd, _ = G.device_points(X)
-    p = oracle_state(orc, X, 16, 32, 8, 2)
+    p = oracle_state(orc, X, R // 2, R, 8, 2)
     gids, gd, gdeg, _ = orc.final_prune(X, p, 8, 9, order=order)
     keys, deg = G.final_prune(Xd, 20, to_keys(G, p), torch.from_numpy(p.deg).cuda(), 8, 9, order)
     ids, dist, _, dg = from_gpu(G, keys, deg)
@@ -221,6 +229,58 @@ def test_build_matches_oracle(G, orc, n, d, S, R, T1, T2, metric, order, final):
     assert g.entry == orc.entry(X, metric)
     st = g.stats()
     assert st["rounds"] >= 1 and st["pair_distances"] > 0
+
+
+@pytest.mark.parametrize("R,S,precision,metric", [(96, 48, 0, 0), (128, 100, 1, 0), (256, 64, 0, 1),
+                                                   (256, 200, 2, 0), (160, 160, 1, 1)])
+def test_build_wide_pools_matches_oracle(G, orc, R, S, precision, metric):
+    # pools of up to 256 entries (Sec 3.5's fixed capacity): init, rounds with the wide join
+    # and merge, reverse sampling, final prune, search; integer data keeps every form exact
+    X, Q = synth.small_integers(1200, 16, -8, 8, seed=R + S, nq=50)
+    g = G.build(X, S=S, R=R, T1=2, T2=3, rho=0.6, seed=21, metric=metric, precision=precision)
+    ids, dist, deg = g.to_numpy()
+    wids, wd, wdeg, _ = orc.build_graph(X, S, R, 2, 3, 0.6, 21, metric=metric)
+    assert (deg == wdeg).all() and (ids == wids).all()
+    assert (dist[wids >= 0] == wd[wids >= 0].astype(np.float32)).all()
+    assert g.stats()["rechecks"] == 0
+    want, _, _ = orc.search(wids, wdeg, X, Q, 10, 64, orc.entry(X, metric), metric=metric)
+    assert (g.search(Q, 10, 64) == want).all()
+
+
+def test_build_wide_pools_keep_the_last_pool(G, orc):
+    # without the final prune the graph is the last pool: rows of up to R = 256 entries
+    X = synth.small_integers(900, 6, -4, 4, seed=3)
+    g = G.build(X, S=128, R=256, T1=2, T2=2, seed=2, final_prune=False)
+    ids, dist, deg = g.to_numpy()
+    wids, wd, wdeg, _ = orc.build_graph(X, 128, 256, 2, 2, 0.6, 2, final_prune=False)
+    assert (deg == wdeg).all() and (ids == wids).all()
+    assert deg.max() > 64
+
+
+def test_plain_calls_run_on_the_current_stream(G):
+    # grnnd_build / grnnd_search / grnnd_graph_copy take no stream: they run on the calling
+    # thread's current stream (here a side stream), with the same results
+    import ctypes
+    X, Q = synth.small_integers(3000, 16, -8, 8, seed=4, nq=64)
+    ref = G.build(X, S=8, R=16, T1=2, T2=3, seed=3)
+    want, want_q = ref.to_numpy(), ref.search(Q, 10, 32)
+    L = G.lib()
+    side = torch.cuda.Stream()
+    L.grnnd_set_stream(ctypes.c_void_p(side.cuda_stream))
+    try:
+        assert L.grnnd_get_stream() == side.cuda_stream
+        h = ctypes.c_void_p()
+        assert L.grnnd_build(X.ctypes.data_as(ctypes.c_void_p), 3000, 16, 0, 8, 16, 2, 3, 3, ctypes.byref(h)) == G.OK
+        g = G._graph_of(h)
+        got = g.to_numpy()
+        out = np.empty((64, 10), np.int32)
+        assert L.grnnd_search(h, Q.ctypes.data_as(ctypes.c_void_p), 64, 10, 32,
+                              out.ctypes.data_as(ctypes.c_void_p)) == G.OK
+    finally:
+        L.grnnd_set_stream(None)
+    for a, b in zip(got, want):
+        assert (a == b).all()
+    assert (out == want_q).all()
 
 
 def test_build_device_input_equals_host_input(G):
@@ -490,6 +550,121 @@ def test_fp8_build_continuous_data(G, orc, metric):
 
 
 # ---------------------------------------------------------------------------------------
+# one step of the BF16 / FP8 forms from an oracle state on continuous data
+# ---------------------------------------------------------------------------------------
+
+def _q_rows(X, precision):
+    """Dequantised rows of a precision form (emulated in numpy), their squared norms and
+    residual norms: the terms the stated error bound is made of."""
+    xq = _bf16(X).astype(np.float64) if precision == 1 else _fp8_rows(X)
+    return (xq ** 2).sum(1), np.sqrt(((X.astype(np.float64) - xq) ** 2).sum(1))
+
+
+def _q_bound(metric, D, ni, nj, ei, ej, d):
+    """The stated per-pair bound on |tile distance - FP32 distance| (BF16 and FP8 forms)."""
+    if metric == 0:
+        return _bf16_bound(D, ni, nj, ei, ej, d)
+    u = 2.0 ** -23
+    g = d * u / (1 - d * u)
+    si, sj = np.sqrt(ni), np.sqrt(nj)
+    tot = (g + 2 * u) * si * sj + 2 * u * abs(D) + ei * sj + ej * si + ei * ej
+    return (tot + (d + 3) * u * (abs(D) + si * sj + tot)) * 1.0001
+
+
+def _continuous_case(shape):
+    if shape == "gauss":  # the 10k x 32 mixture, L2
+        return synth.gaussian_mixture(10000, 32, 20, 10.0, 1.0, seed=0), 0, 16, 32
+    X = synth.deep_like(8000, d=96, seed=3)  # DEEP-shaped unit vectors, inner product
+    return X, 1, 16, 32
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("shape", ["gauss", "deep"])
+def test_precision_prune_matches_oracle_on_continuous_data(G, orc, shape, precision):
+    """Every fire decision of the BF16 / FP8 tiles either clears the stated bound or is
+    re-taken in FP32, so each vertex's survivors are the oracle's except where the oracle
+    itself flags a decision as within FP32 rounding.  The prune-only pass shows the decisions
+    alone (no merge): unflagged rows must equal the oracle's bit for bit."""
+    X, metric, S, R = _continuous_case(shape)
+    n, d = X.shape
+    Xd, _ = G.device_points(X)
+    qp = G.quantize(Xd, d, precision)
+    tol = 2 * (d + 2) * 2.0 ** -24 * 2
+    p = oracle_state(orc, X, S, R, 7, 2, metric)
+    gids, gd, gdeg, flags = orc.final_prune(X, p, 7, 5, metric=metric, tol=tol)
+    keys, deg = G.final_prune(Xd, d, to_keys(G, p), torch.from_numpy(p.deg).cuda(), 7, 5, metric=metric,
+                              precision=precision, qpoints=qp)
+    ids, dist, _, dg = from_gpu(G, keys, deg)
+    ok = flags == 0
+    assert ok.mean() > 0.99
+    assert (dg[ok] == gdeg[ok]).all()
+    assert (ids[ok] == gids[ok]).all()
+    m = (gids >= 0) & ok[:, None]
+    assert (dist[m] == gd[m].astype(np.float32)).all()  # survivors keep their recorded distances
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("shape", ["gauss", "deep"])
+def test_precision_round_matches_oracle_on_continuous_data(G, orc, shape, precision, record_property):
+    """One join round in the BF16 / FP8 forms from an oracle state.  The decisions are the
+    oracle's (test above); a redirect records the tile distance, which may differ from FP64
+    by the stated bound, so a target's R-entry cut may swap entries whose distances are within
+    their bounds of each other.  Every unflagged target must hold the oracle's id set, or a set
+    that differs only by such swaps; every recorded distance must be within its bound of FP64."""
+    X, metric, S, R = _continuous_case(shape)
+    n, d = X.shape
+    Xd, _ = G.device_points(X)
+    qp = G.quantize(Xd, d, precision)
+    nrm, res = _q_rows(X, precision)
+    tol = 2 * (d + 2) * 2.0 ** -24 * 2
+    p = oracle_state(orc, X, S, R, 7, 2, metric)
+    want, flags, _ = orc.round_(X, p, 7, 1, 3, metric=metric, tol=tol)
+    keys, deg = G.join_round(Xd, d, to_keys(G, p), torch.from_numpy(p.deg).cuda(), 7, 1, 3, metric=metric,
+                             precision=precision, qpoints=qp)
+    ids, dist, _, dg = from_gpu(G, keys, deg)
+    unsure = np.zeros(n, bool)
+    for v in np.nonzero(flags & 1)[0]:  # a flagged prune reaches v and every member of its pool
+        unsure[v] = True
+        unsure[p.ids[v, :p.deg[v]]] = True
+    assert unsure.mean() < 0.5  # most targets are reached by unflagged prunes only
+
+    X64 = X.astype(np.float64)
+
+    def d64(u, xs):  # FP64 distances from u to the ids xs
+        xs = np.asarray(xs, np.int64)
+        if metric == 0:
+            return ((X64[xs] - X64[u]) ** 2).sum(1)
+        return 1.0 - X64[xs] @ X64[u]
+
+    def bnd(u, xs, D):
+        return np.array([_q_bound(metric, Dk, nrm[u], nrm[x], res[u], res[x], d) for x, Dk in zip(xs, D)])
+
+    exact = swapped = 0
+    for u in np.nonzero(~unsure)[0]:
+        a = ids[u, :dg[u]]
+        b = want.ids[u, :want.deg[u]]
+        assert dg[u] == want.deg[u], u  # the same candidates, hence the same count
+        ref = d64(u, a)                 # recorded distances within their bound of FP64
+        slack = 1e-6 * np.maximum(1.0, np.abs(ref))
+        assert (np.abs(dist[u, :dg[u]] - ref) <= bnd(u, a, ref) * 1.001 + slack).all(), u
+        if set(a.tolist()) == set(b.tolist()):
+            exact += 1
+            continue
+        swapped += 1
+        only_gpu = np.array(sorted(set(a.tolist()) - set(b.tolist())), np.int64)
+        only_orc = np.array(sorted(set(b.tolist()) - set(a.tolist())), np.int64)
+        dy, dx = d64(u, only_gpu), d64(u, only_orc)
+        by, bx = bnd(u, only_gpu, dy), bnd(u, only_orc, dx)
+        # every entry only the GPU kept is at most as far as every entry only the oracle kept,
+        # up to the two bounds
+        assert (dy[:, None] <= dx[None, :] + bx[None, :] + by[:, None] +
+                1e-6 * np.maximum(1.0, np.abs(dx))[None, :]).all(), (u, only_gpu, only_orc)
+    record_property("exact_targets", exact)
+    record_property("swapped_targets", swapped)
+    assert exact >= 0.5 * (exact + swapped)
+
+
+# ---------------------------------------------------------------------------------------
 # in-place pool updates (the build's own mode)
 # ---------------------------------------------------------------------------------------
 
@@ -516,7 +691,7 @@ def test_join_round_in_place_matches_oracle(G, orc, n, d, S, R, hist):
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("precision,metric", [("fp32", 0), ("bf16", 0), ("bf16", 1), ("fp32", 1), ("fp8", 0)])
-def test_build_batch_equals_single_builds(G, precision, metric):
+def test_build_batch_equals_single_builds(G, orc, precision, metric):
     sizes = [300, 9, 1000, 57, 2000, 128]
     parts = [synth.small_integers(m, 24, -8, 8, seed=100 + i) for i, m in enumerate(sizes)]
     X = np.concatenate(parts)
@@ -533,6 +708,16 @@ def test_build_batch_equals_single_builds(G, precision, metric):
         qa = gs[b].search(torch.from_numpy(Q).cuda(), 5, 16).cpu().numpy()
         qo = one.search(torch.from_numpy(Q).cuda(), 5, 16).cpu().numpy()
         assert (qa == qo).all()
+        # and each build of the batch is the oracle's build of its rows (integer data: every
+        # form is exact), with the oracle's entry and search results
+        wids, wd, wdeg, _ = orc.build_graph(part, 8, 16, 2, 4, 0.6, 11, metric=metric)
+        assert (a[0] == wids).all() and (a[2] == wdeg).all()
+        assert (a[1][wids >= 0] == wd[wids >= 0].astype(np.float32)).all()
+        went = orc.entry(part, metric)
+        assert gs[b].entry == went
+        if len(part) > 16:
+            wq, _, _ = orc.search(wids, wdeg, part, Q, 5, 16, went, metric=metric)
+            assert (qa == wq).all()
 
 
 def test_build_batch_mixed_data_and_free_order(G):

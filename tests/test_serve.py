@@ -49,9 +49,26 @@ def _mix(seed):
     return cases
 
 
-def test_results_in_the_mix_equal_results_alone(G):
+def _oracle_leg(orc, X, kw, queries):
+    """The oracle's graph, entry and search results for a request on integer data (exact in
+    every form: |x| <= 8 and d * 64 < 2^24)."""
+    m = kw.get("metric", 0)
+    wids, wd, wdeg, _ = orc.build_graph(X, kw["S"], kw["R"], kw["T1"], kw["T2"], 0.6, kw["seed"], metric=m)
+    e = orc.entry(X, m)
+    found = [orc.search(wids, wdeg, X, Q, k, beam, e, metric=m)[0] for Q, k, beam in queries]
+    return (wids, wd, wdeg), e, found
+
+
+def test_results_in_the_mix_equal_results_alone(G, orc):
     cases = _mix(1)
     want = [_alone(G, X, kw, q) for X, kw, q in cases]
+    # the requests on integer data, alone, are the oracle's builds and searches
+    for (X, kw, queries), ((ids, dists, deg), entry, found) in zip(cases[:5], want[:5]):
+        (wids, wd, wdeg), went, wfound = _oracle_leg(orc, X, kw, queries)
+        assert (ids == wids).all() and (deg == wdeg).all() and entry == went
+        assert (dists[wids >= 0] == wd[wids >= 0].astype(np.float32)).all()
+        for a, b in zip(found, wfound):
+            assert (a == b).all()
     srv = G.Server(slots=3, hbm_budget=4 << 30)
     try:
         builds, searches = [], []
