@@ -55,11 +55,12 @@ def _args():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16, fp8 (the last one is the headline)")
-    ap.add_argument("--report", choices=["precision", "ablation", "batched", "serve"], default=None,
+    ap.add_argument("--report", choices=["precision", "ablation", "batched", "serve", "rounds"], default=None,
                     help="precision: per-form distance error against FP64 and recall loss on a "
                          "GIST-shaped (d=960, continuous) or DEEP-shaped (d=96, IP) set of --n points")
     ap.add_argument("--shape", choices=["gist", "deep"], default="gist")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="serve report: length of the arrival stream")
+    ap.add_argument("--rounds", type=int, default=2, help="rounds report: rounds of the first outer iteration")
     return ap.parse_args()
 
 
@@ -170,7 +171,7 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------------------
 
-KERNELS_PER_GROUP = {"scan": 3, "entry": 4}
+KERNELS_PER_GROUP = {"scan": 3, "entry": 6}
 JOIN_KERNELS = ("rnd_join_warp", "rnd_join_team", "rnd_join")
 
 
@@ -255,6 +256,41 @@ def run_precision_report(args):
         out[q + "_recall_loss"] = out["forms"]["fp32"]["recall@10"] - out["forms"][q]["recall@10"]
         out[q + "_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"][q]["build_ms"]
     print(json.dumps(out), flush=True)
+
+
+def join_algorithmic_bytes(rows, n, proposals, fired, rechecks, d, elem):
+    """Algorithmic bytes of the join over some rounds: rows gathered (elem bytes per
+    dimension), pool degrees read once per round, every entry proposed (kept in place or
+    written) once, each redirect written (target + key) and counted, and the FP32 rows of
+    every re-decided pair (three rows: the pair and the row it is decided against)."""
+    return rows * d * elem + n * 4 + proposals * 8 + fired * (12 + 4) + rechecks * 3 * d * 4
+
+
+def run_rounds_report(args):
+    """The first --rounds rounds of the bench workload's build (BF16 form) through the step
+    calls, one JSON line per round with its counters and the join's algorithmic bytes: the
+    reference figures for a DRAM capture of the same rounds' join launches."""
+    import torch
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd, synth
+    w = WORKLOAD
+    n, d = args.n, w["d"]
+    X = synth.sift_like(n, 0, seed=args.seed)
+    Xd, _ = grnnd.device_points(X)
+    qp = grnnd.quantize(Xd, d, grnnd.BF16)
+    keys, deg = grnnd.pool_init(Xd, d, w["S"], w["R"], args.seed)
+    ws = grnnd.workspace(n, w["R"])
+    for t2 in range(1, args.rounds + 1):
+        st = torch.zeros(8, dtype=torch.int64, device="cuda")
+        keys, deg = grnnd.join_round(Xd, d, keys, deg, args.seed, 1, t2, ws=ws, stats=st, inplace=True,
+                                     precision=grnnd.BF16, qpoints=qp)
+        grnnd.workspace_status(ws, n, w["R"])
+        s = st.cpu().tolist()
+        algo = join_algorithmic_bytes(s[1], n, s[4], s[3], 0, d, 2)
+        print(json.dumps({"report": "rounds", "n": n, "t1": 1, "t2": t2, "vertices_with_new": s[0],
+                          "rows_gathered": s[1], "pair_distances": s[2], "pairs_fired": s[3], "proposals": s[4],
+                          "join_algorithmic_bytes": algo}), flush=True)
 
 
 def run_ablation_report(args):
@@ -501,6 +537,9 @@ def main():
     if args.report == "serve":
         run_serve_report(args)
         return
+    if args.report == "rounds":
+        run_rounds_report(args)
+        return
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist
@@ -644,8 +683,8 @@ def main():
     if dom_name == "rnd_join":
         # rows gathered (elem bytes per dimension); pool keys read once; survivors written;
         # redirects out (target + key); FP32 rows of the rechecked pairs
-        algo = (agg["rows_gathered"] * d * elem + rounds * n * 4 + agg["proposals"] * 8
-                + agg["pairs_fired"] * (12 + 4) + agg["rechecks"] * 3 * d * 4)
+        algo = (join_algorithmic_bytes(agg["rows_gathered"], n, agg["proposals"], agg["pairs_fired"],
+                                       agg["rechecks"], d, elem) + (rounds - 1) * n * 4)
         units = rounds
     elif dom_name == "select":
         algo = agg["merged"] * 8 + agg["proposals"] * 8 * 2

@@ -21,22 +21,34 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "grnnd_oracle.c")
+_SRC_MT = os.path.join(_HERE, "grnnd_oracle_mt.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libgrnnd_oracle.so")
+_LIB_MT_PATH = os.path.join(_OUT_DIR, "libgrnnd_oracle_mt.so")
 _lock = threading.Lock()
 _lib = None
+_lib_mt = None
 
 # -ffp-contract=off: no fused multiply-add, so x86 and Arm hosts agree bit for bit.
 _CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
 
+def _stale(lib, srcs):
+    return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(s) for s in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into ``oracle/_build`` (idempotent)."""
+    """Compile the oracle with gcc into ``oracle/_build`` (idempotent), and the library of
+    its multi-threaded build driver (the oracle's source plus ``grnnd_oracle_mt.c``)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    if force or _stale(_LIB_PATH, [_SRC]):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.run(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
+    if force or _stale(_LIB_MT_PATH, [_SRC, _SRC_MT]):
+        tmp = _LIB_MT_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *_CFLAGS, "-pthread", "-o", tmp, _SRC, _SRC_MT, "-lm"], check=True)
+        os.replace(tmp, _LIB_MT_PATH)
     return _LIB_PATH
 
 
@@ -246,6 +258,38 @@ def build_graph(X, S: int, R: int, T1: int, T2: int, rho: float = 0.6, seed: int
                            order, int(skip_old), int(final_prune), _ptr(gids, ctypes.c_int32),
                            _ptr(gd, ctypes.c_double), _ptr(gdeg, ctypes.c_int32), _ptr(stats, ctypes.c_int64)),
            "build")
+    return gids, gd, gdeg, stats
+
+
+def lib_mt():
+    global _lib_mt
+    with _lock:
+        if _lib_mt is not None:
+            return _lib_mt
+        build()
+        L = ctypes.CDLL(_LIB_MT_PATH)
+        i32, i64, u64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+        L.orc_build_mt.argtypes = [_p(f32), i64, i32, i32, i32, i32, i32, i32, f32, u64, i32, i32, i32, i32,
+                                   _p(i32), _p(ctypes.c_double), _p(i32), _p(i64)]
+        L.orc_build_mt.restype = ctypes.c_int
+        _lib_mt = L
+        return L
+
+
+def build_graph_mt(X, S: int, R: int, T1: int, T2: int, rho: float = 0.6, seed: int = 0, metric: int = 0,
+                   order: int = 0, skip_old: bool = False, final_prune: bool = True, threads: int = 1):
+    """build_graph with the per-vertex prunes and the per-target merges split over `threads`
+    host threads (grnnd_oracle_mt.c); the same results at any thread count."""
+    X = _f32(X)
+    n, d = X.shape
+    gids = np.full((n, R), -1, np.int32)
+    gd = np.full((n, R), np.inf)
+    gdeg = np.zeros(n, np.int32)
+    stats = np.zeros(3, np.int64)
+    _check(lib_mt().orc_build_mt(_ptr(X, ctypes.c_float), n, d, metric, S, R, T1, T2, ctypes.c_float(rho), seed,
+                                 order, int(skip_old), int(final_prune), int(threads), _ptr(gids, ctypes.c_int32),
+                                 _ptr(gd, ctypes.c_double), _ptr(gdeg, ctypes.c_int32), _ptr(stats, ctypes.c_int64)),
+           "build_mt")
     return gids, gd, gdeg, stats
 
 

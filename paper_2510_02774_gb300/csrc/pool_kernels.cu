@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
                                                            int32_t* __restrict__ deg,
                                                            const int2* __restrict__ vseg,
                                                            const __nv_bfloat16* __restrict__ Xb, int ldb,
-                                                           const unsigned* __restrict__ qflags) {
+                                                           const unsigned* __restrict__ qflags,
+                                                           uint64_t magic) {
   __shared__ int32_t acc_ids[IW][32 * E];
   // the chunk of each drawn row (rows 0..S-1) and of v itself (row S), 16-byte granules
   __shared__ __align__(16) float stage[IW][32 * E + 1][IC + 4];
@@ -114,10 +115,15 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
     const int64_t lo = vseg ? vseg[v].x : 0;
     const uint64_t nm1 = (uint64_t)((vseg ? (int64_t)vseg[v].y : n) - 1);
     const uint64_t vl = (uint64_t)(v - lo);
+    // h mod nm1 without a division: q = high 64 bits of h * floor((2^64 - 1) / nm1) is
+    // h / nm1 rounded down, or one less, so one correction gives the exact remainder
+    const uint64_t mg = vseg ? (~0ull / nm1) : magic;
     int cnt = 0;
     // S <= nb - 1, so the draws cover enough distinct ids long before the bound.
     for (uint64_t base = 0; cnt < S && base < (1ull << 32); base += 32) {
-      const uint64_t r = hash_tail(head, vl, base + lane) % nm1;
+      const uint64_t hv = hash_tail(head, vl, base + lane);
+      uint64_t r = hv - __umul64hi(hv, mg) * nm1;
+      if (r >= nm1) r -= nm1;
       const int32_t u = (int32_t)(lo + (int64_t)(r + (r >= vl ? 1u : 0u)));
       bool dup = false;
       for (int j = 0; j < cnt; ++j) dup |= (acc[j] == u);
@@ -138,18 +144,21 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
     for (int c0 = 0; c0 < d; c0 += IC) {
       const int clen = min(IC, d - c0);
       const int gr = (clen + 3) >> 2;  // granules per row
-      for (int t = lane; t < (S + 1) * gr; t += 32) {
-        const int r = t / gr, q = t - r * gr;
+      // row t / 4, granule t % 4 (IC / 4 = 4 granules per row; those past d are zero)
+      for (int t = lane; t < (S + 1) * (IC / 4); t += 32) {
+        const int r = t >> 2, q = t & 3;
         const int64_t src = r < S ? (int64_t)acc[r] : v;
-        float4 val;
-        if (use_b) {  // four BF16 values, widened exactly
-          const uint2 u = *reinterpret_cast<const uint2*>(Xb + src * ldb + c0 + 4 * q);
-          val = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                            __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-        } else {
-          val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
+        float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (q < gr) {
+          if (use_b) {  // four BF16 values, widened exactly
+            const uint2 u = *reinterpret_cast<const uint2*>(Xb + src * ldb + c0 + 4 * q);
+            val = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                              __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+          } else {
+            val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
+          }
+          if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
         }
-        if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
         *reinterpret_cast<float4*>(&rows[r][4 * q]) = val;
       }
       __syncwarp();
@@ -169,7 +178,19 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
       const int e = j * 32 + lane;
       kk[j] = e < S ? make_key(dist_finish4<METRIC>(ps[j]), (uint32_t)acc[e], 0u) : kEmpty;
     }
-    warp_sort_u64<E>(kk);
+    // sort the registers that hold entries (the others hold only empty keys, which are last)
+    if (S <= 32) {
+      uint64_t k1[1] = {kk[0]};
+      warp_sort_u64<1>(k1);
+      kk[0] = k1[0];
+    } else if (E == 2 || S <= 64) {
+      uint64_t k2[2] = {kk[0], kk[1]};
+      warp_sort_u64<2>(k2);
+      kk[0] = k2[0];
+      kk[1] = k2[1];
+    } else {
+      warp_sort_u64<E>(kk);
+    }
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int e = j * 32 + lane;
@@ -184,21 +205,22 @@ cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metri
                              uint64_t seed, uint64_t* keys, int32_t* deg, cudaStream_t st,
                              const int2* vseg, const void* Xb16, int ldb, const unsigned* qflags) {
   const __nv_bfloat16* Xb = (Xb16 && qflags) ? static_cast<const __nv_bfloat16*>(Xb16) : nullptr;
+  const uint64_t magic = ~0ull / (uint64_t)(n - 1);  // the draws' modulus of a single build (n >= 2)
   ProfScope ps("rnd_init", st);
   if (R <= kTeamMaxM) {
     constexpr int IW = 4;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
     if (metric == 0)
-      rnd_init_kernel<0, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+      rnd_init_kernel<0, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
     else
-      rnd_init_kernel<1, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+      rnd_init_kernel<1, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
   } else {  // pools of up to 256 entries
     constexpr int IW = 2;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 32);
     if (metric == 0)
-      rnd_init_kernel<0, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+      rnd_init_kernel<0, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
     else
-      rnd_init_kernel<1, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags);
+      rnd_init_kernel<1, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
   }
   return cudaGetLastError();
 }

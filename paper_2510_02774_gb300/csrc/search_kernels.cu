@@ -90,31 +90,151 @@ __device__ __forceinline__ bool dl_less(double da, int32_t ia, double db, int32_
   return da < db || (da == db && ia < ib);
 }
 
+// FP32 pre-filter of the nearest point.  For every point, a warp computes the FP32 distance
+// d32 to the FP32-rounded mean and a rigorous bound B on |d32 - d64|, where d64 is the FP64
+// value that nearest_kernel computes (ascending dimensions, unfused).  Any point whose d64
+// can be the minimum satisfies d32 - B <= min_j (d32_j + B_j), so only those candidates need
+// the FP64 evaluation; ties among them are still settled by id.
+//   L2:  e1 = (2d + 16) u d32                   FP32 rounding of t = x - mu32, t^2, the sum
+//        e2 = delta (2 sqrt(d32 + e1) + 3 delta) mu32 instead of mu, delta = ||mu - mu32||_2
+//        e3 = (d + 4) 2^-52 (d32 + e1 + e2)     the FP64 evaluation itself
+//   IP:  e1 = (d + 4) u 1.01 a + u (1 + |s|)    a = sum |x mu32|, s = sum x mu32
+//        e2 = 1.00001 ||x|| delta
+//        e3 = (d + 4) 2^-52 (a + ||x|| delta + 1) + 2^-53 (1 + |s|)
+//   B = 1.1 (e1 + e2 + e3) + 1e-30, u = 2^-24, and the bound itself rounded upward.
+template <int METRIC>
+__device__ __forceinline__ void entry_d32(const float* __restrict__ x, int d, const float* __restrict__ mu32,
+                                          float delta, float& lo, float& hi) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.0f, a = 0.0f, xx = 0.0f;
+  for (int k = lane; k < d; k += 32) {
+    const float xv = x[k], m = mu32[k];
+    if (METRIC == 0) {
+      const float t = xv - m;
+      s = fmaf(t, t, s);
+    } else {
+      s = fmaf(xv, m, s);
+      a = fmaf(fabsf(xv), fabsf(m), a);
+      xx = fmaf(xv, xv, xx);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (METRIC != 0) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+  }
+  const float u = 5.9604645e-08f;  // 2^-24
+  float d32, B;
+  if (METRIC == 0) {
+    d32 = fmaxf(s, 0.0f);
+    const float e1 = __fmul_ru(__fmul_ru((float)(2 * d + 16), u), d32);
+    const float e2 = __fmul_ru(delta, __fadd_ru(__fmul_ru(2.0f, __fsqrt_ru(__fadd_ru(d32, e1))), __fmul_ru(3.0f, delta)));
+    const float e3 = __fmul_ru(__fmul_ru((float)(d + 4), 2.220446e-16f), __fadd_ru(__fadd_ru(d32, e1), e2));
+    B = __fadd_ru(__fmul_ru(1.1f, __fadd_ru(__fadd_ru(e1, e2), e3)), 1e-30f);
+  } else {
+    d32 = 1.0f - s;
+    const float as = fabsf(s);
+    const float e1 = __fadd_ru(__fmul_ru(__fmul_ru((float)(d + 4) * 1.01f, u), a), __fmul_ru(u, __fadd_ru(1.0f, as)));
+    const float xn = __fmul_ru(__fsqrt_ru(xx), 1.00001f);
+    const float e2 = __fmul_ru(xn, delta);
+    const float e3 = __fadd_ru(__fmul_ru(__fmul_ru((float)(d + 4), 2.220446e-16f), __fadd_ru(__fadd_ru(a, e2), 1.0f)),
+                               __fmul_ru(1.110223e-16f, __fadd_ru(1.0f, as)));
+    B = __fadd_ru(__fmul_ru(1.1f, __fadd_ru(__fadd_ru(e1, e2), e3)), 1e-30f);
+  }
+  lo = __fsub_rd(d32, B);
+  hi = __fadd_ru(d32, B);
+}
+
+// mu32 = FP32 rounding of the FP64 mean and delta = ||mu - mu32||_2 rounded upward (one block).
+__global__ void mean32_kernel(const double* __restrict__ mu, int d, float* __restrict__ mu32,
+                              float* __restrict__ delta) {
+  __shared__ double red[256];
+  double e = 0.0;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    const float m = __double2float_rn(mu[k]);
+    mu32[k] = m;
+    const double t = mu[k] - (double)m;
+    e += t * t;
+  }
+  red[threadIdx.x] = e;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *delta = __double2float_ru(sqrt(red[0] * (1.0 + 1e-12)) * (1.0 + 1e-12));
+}
+
+// Per block: the smallest upper end d32 + B of its points (warp per point).
+template <int METRIC>
+__global__ void __launch_bounds__(256) entry_upper_kernel(const float* __restrict__ X, int64_t n, int d, int ld,
+                                                          const float* __restrict__ mu32,
+                                                          const float* __restrict__ delta,
+                                                          float* __restrict__ bmin) {
+  __shared__ float wmin[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float dl = *delta;
+  float best = FLT_MAX;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < n; i += (int64_t)gridDim.x * 8) {
+    float lo, hi;
+    entry_d32<METRIC>(X + i * ld, d, mu32, dl, lo, hi);
+    best = fminf(best, hi);
+  }
+  if (lane == 0) wmin[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = wmin[0];
+    for (int w = 1; w < 8; ++w) b = fminf(b, wmin[w]);
+    bmin[blockIdx.x] = b;
+  }
+}
+
+// Per block: (FP64 distance, id) minimum over the candidate points only: those whose lower
+// end d32 - B is at most the smallest upper end over all points.
 template <int METRIC>
 __global__ void __launch_bounds__(256) nearest_kernel(const float* __restrict__ X, int64_t n, int d,
                                                       int ld, const double* __restrict__ mu,
+                                                      const float* __restrict__ mu32,
+                                                      const float* __restrict__ delta,
+                                                      const float* __restrict__ bmin, int nbmin,
                                                       double* __restrict__ bd,
                                                       int32_t* __restrict__ bi) {
   __shared__ double sd[256];
   __shared__ int32_t si[256];
+  __shared__ float s_up;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    float u = FLT_MAX;
+    for (int b = 0; b < nbmin; ++b) u = fminf(u, bmin[b]);
+    s_up = u;
+  }
+  __syncthreads();
+  const float up = s_up, dl = *delta;
   double best = DBL_MAX;
   int32_t bid = INT32_MAX;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < n; i += (int64_t)gridDim.x * 8) {
     const float* x = X + i * ld;
-    double s = 0.0;
-    for (int k = 0; k < d; ++k) {
-      if (METRIC == 0) {
-        const double t = __dsub_rn((double)x[k], mu[k]);
-        s = __dadd_rn(s, __dmul_rn(t, t));
-      } else {
-        s = __dadd_rn(s, __dmul_rn((double)x[k], mu[k]));
+    float lo, hi;
+    entry_d32<METRIC>(x, d, mu32, dl, lo, hi);
+    if (lo > up) continue;  // cannot be the nearest point (warp-uniform)
+    if (lane == 0) {  // the FP64 value, exactly as defined: ascending dimensions, unfused
+      double s = 0.0;
+      for (int k = 0; k < d; ++k) {
+        if (METRIC == 0) {
+          const double t = __dsub_rn((double)x[k], mu[k]);
+          s = __dadd_rn(s, __dmul_rn(t, t));
+        } else {
+          s = __dadd_rn(s, __dmul_rn((double)x[k], mu[k]));
+        }
       }
-    }
-    if (METRIC != 0) s = __dsub_rn(1.0, s);
-    if (dl_less(s, (int32_t)i, best, bid)) {
-      best = s;
-      bid = (int32_t)i;
+      if (METRIC != 0) s = __dsub_rn(1.0, s);
+      if (dl_less(s, (int32_t)i, best, bid)) {
+        best = s;
+        bid = (int32_t)i;
+      }
     }
   }
   sd[threadIdx.x] = best;
@@ -163,16 +283,25 @@ cudaError_t launch_entry(const float* X, int64_t n, int d, int ld, int metric, i
   double* bd = reinterpret_cast<double*>(p);
   p += al256(kEntryBlocks * 8);
   int32_t* bi = reinterpret_cast<int32_t*>(p);
+  // once the mean is formed, the column sums' region holds the FP32 mean, its distance to the
+  // FP64 mean and the per-block upper ends (d + 256 + 512 floats <= 512 d doubles)
+  float* mu32 = reinterpret_cast<float*>(partial);
+  float* delta = mu32 + al256((size_t)d * 4) / 4;
+  float* bmin = delta + 64;
   const int64_t rpb = ceil_div(n, kEntryBlocks);
   const int nb = (int)ceil_div(n, rpb);
+  const int nb2 = (int)std::min<int64_t>(kEntryBlocks, ceil_div(n, 8));
   ProfScope ps("entry", st);
   colsum_kernel<<<nb, 256, 0, st>>>(X, n, d, ld, rpb, partial);
   mean_kernel<<<(unsigned)ceil_div(d, 256), 256, 0, st>>>(partial, nb, d, n, mu);
-  const int nb2 = (int)std::min<int64_t>(kEntryBlocks, ceil_div(n, 256));
-  if (metric == 0)
-    nearest_kernel<0><<<nb2, 256, 0, st>>>(X, n, d, ld, mu, bd, bi);
-  else
-    nearest_kernel<1><<<nb2, 256, 0, st>>>(X, n, d, ld, mu, bd, bi);
+  mean32_kernel<<<1, 256, 0, st>>>(mu, d, mu32, delta);
+  if (metric == 0) {
+    entry_upper_kernel<0><<<nb2, 256, 0, st>>>(X, n, d, ld, mu32, delta, bmin);
+    nearest_kernel<0><<<nb2, 256, 0, st>>>(X, n, d, ld, mu, mu32, delta, bmin, nb2, bd, bi);
+  } else {
+    entry_upper_kernel<1><<<nb2, 256, 0, st>>>(X, n, d, ld, mu32, delta, bmin);
+    nearest_kernel<1><<<nb2, 256, 0, st>>>(X, n, d, ld, mu, mu32, delta, bmin, nb2, bd, bi);
+  }
   nearest_final_kernel<<<1, 32, 0, st>>>(bd, bi, nb2, entry);
   return cudaGetLastError();
 }

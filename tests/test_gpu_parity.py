@@ -332,10 +332,21 @@ def test_hbm_budget_is_checked_before_allocation(G):
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("metric", [0, 1])
-def test_entry_point_matches_oracle(G, orc, metric):
-    X = synth.small_integers(5000, 13, -8, 8, seed=3)
+@pytest.mark.parametrize("case", ["integers", "gauss", "deep", "ties"])
+def test_entry_point_matches_oracle(G, orc, metric, case):
+    # the FP32 pre-filter must never drop the FP64 nearest point, ties included
+    if case == "integers":
+        X = synth.small_integers(5000, 13, -8, 8, seed=3)
+    elif case == "gauss":
+        X = synth.gaussian_mixture(20000, 40, 10, 5.0, 1.0, seed=8)
+    elif case == "deep":
+        X = synth.deep_like(20000, d=96, seed=9)
+    else:  # +-e_k and copies: every point at the same distance from the mean (0)
+        E = np.eye(12, dtype=np.float32)
+        X = np.concatenate([E, -E, E, -E, 3 * E, -3 * E])
+    d = X.shape[1]
     Xd, _ = G.device_points(X)
-    assert G.entry_point(Xd, 13, metric) == orc.entry(X, metric)
+    assert G.entry_point(Xd, d, metric) == orc.entry(X, metric)
 
 
 @pytest.mark.parametrize("beam", [10, 32, 64, 200])

@@ -506,3 +506,16 @@ def test_oracle_graph_search_recall(orc, small_mix):
     ids, _, _ = orc.search(gids, gdeg, X, Q, 10, 64, orc.entry(X))
     gt, _ = orc.brute_knn(X, Q, 10)
     assert orc.recall_at_k(ids, gt) >= 0.95
+
+
+@pytest.mark.parametrize("threads", [1, 2, 7])
+@pytest.mark.parametrize("final_prune", [True, False])
+def test_threaded_oracle_driver_equals_oracle_build(orc, threads, final_prune):
+    # the CPU baseline's multi-threaded driver calls the oracle's own steps over vertex and
+    # target ranges: the graph and counters must be orc_build's at any thread count
+    X = synth.small_integers(1500, 10, -8, 8, seed=6)
+    kw = dict(S=12, R=24, T1=2, T2=3, rho=0.6, seed=5, final_prune=final_prune)
+    want = orc.build_graph(X, **kw)
+    got = orc.build_graph_mt(X, threads=threads, **kw)
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
