@@ -65,8 +65,9 @@ int32_t round4(int32_t d) { return (d + 3) & ~3; }
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Layout of the quantized copy of n x d points (BF16 or FP8 form), shared by the builds and
-// grnnd_quantize: rows of ldb elements of qelem bytes, then the per-row (norm^2, residual)
-// terms, then the two dataset flags; each region 256-byte aligned.
+// grnnd_quantize: rows of ldb elements of qelem bytes (each ending in its (norm^2, residual)
+// tail), then the per-row terms once more as an array, then the two dataset flags; each
+// region 256-byte aligned.
 struct QLayout {
   int32_t ldb = 0;
   size_t qelem = 0, rows_b = 0, aux_b = 0, total = 0;
@@ -74,7 +75,8 @@ struct QLayout {
 QLayout q_layout(int64_t n, int32_t d, int32_t precision) {
   QLayout q;
   if (precision != GRNND_BF16 && precision != GRNND_FP8) return q;
-  q.ldb = precision == GRNND_FP8 ? ((d + 31) & ~31) : ((d + 15) & ~15);
+  // padded dimensions, then the row's 16-byte tail of (norm^2, residual)
+  q.ldb = precision == GRNND_FP8 ? ((d + 31) & ~31) + grnnd::kRowTail8 : ((d + 15) & ~15) + grnnd::kRowTail16;
   q.qelem = precision == GRNND_FP8 ? 1 : 2;
   q.rows_b = al256((size_t)n * q.ldb * q.qelem);
   q.aux_b = al256((size_t)n * 8);

@@ -35,10 +35,18 @@ struct Workspace {
   int64_t* round_new = nullptr;            // new entries written by the last merge
 };
 
+// Each quantized row ends in a 32-byte tail holding (norm^2 of the quantized row, residual
+// norm) as two floats, then zeros: 16 BF16 elements or 32 e4m3 bytes, which keeps every row
+// on a 32-byte sector boundary.  The row stride is the padded dimension count (16 BF16 / 32
+// e4m3 elements) plus the tail; the joins copy the tail's first kTailCopy bytes with a row.
+constexpr int kRowTail16 = 16;
+constexpr int kRowTail8 = 32;
+constexpr int kTailCopy = 16;
+
 // The points as the pool kernels read them.  precision 0: FP32 rows only; 1: also a
-// BF16 copy (ldb = d rounded up to 16), per-row (norm^2, residual) and dataset flags;
-// 2: an FP8-e4m3 copy (ldb = d rounded up to 32) with the same per-row terms, the row's
-// scale exponent in the low byte of the residual.
+// BF16 copy (row stride ldb = d rounded up to 16, plus the tail), per-row (norm^2, residual)
+// and dataset flags; 2: an FP8-e4m3 copy (ldb = d rounded up to 32, plus the tail) with the
+// same per-row terms, the row's scale exponent in the low byte of the residual.
 struct PointsSet {
   const float* X = nullptr;
   int ld = 0;
@@ -80,8 +88,8 @@ cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metri
 // Batched builds: subtracts each row's build base from its ids (-1 stays -1).
 cudaError_t launch_localize_ids(int64_t n, int R, int32_t* ids, const int2* vseg, cudaStream_t st);
 
-// precision 1: BF16 rows (ldb = d rounded up to 16 elements); 2: e4m3 rows with a
-// power-of-two scale per row (ldb = d rounded up to 32 bytes).
+// precision 1: BF16 rows (ldb = d rounded up to 16 elements, plus the tail); 2: e4m3 rows
+// with a power-of-two scale per row (ldb = d rounded up to 32 bytes, plus the tail).
 cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xb, int ldb,
                             float2* aux, unsigned* qflags, int precision, cudaStream_t st);
 

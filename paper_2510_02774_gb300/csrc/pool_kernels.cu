@@ -240,19 +240,22 @@ cudaError_t launch_localize_ids(int64_t n, int R, int32_t* ids, const int2* vseg
 }
 
 // =====================================================================================
-// quantize: BF16 rows (ldb = d rounded up to 16, zero padded), aux = (norm^2 of the BF16
-// row, ||x - bf16(x)|| rounded up), and dataset flags: qflags[0] bit 0 = some value is
-// not an integer, bit 1 = some value is not exact in BF16; qflags[1] = max |x| (bits).
+// quantize: BF16 rows (dp = d rounded up to 16 elements, zero padded) followed by a 32-byte
+// tail (norm^2 of the BF16 row, ||x - bf16(x)|| rounded up, then zeros), so that a row's bulk
+// copy brings its terms along; ldb = dp + 16 elements is the row stride.  The same terms go to
+// aux, and the dataset flags: qflags[0] bit 0 = some value is not an integer, bit 1 = some
+// value is not exact in BF16; qflags[1] = max |x| (bits).
 // =====================================================================================
 __global__ void quantize_kernel(const float* __restrict__ X, int64_t n, int d, int ld,
                                 __nv_bfloat16* __restrict__ Xb, int ldb, float2* __restrict__ aux,
                                 unsigned* __restrict__ qflags) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dp = ldb - kRowTail16;  // padded dimensions of a row
   unsigned fl = 0, mx = 0;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < n;
        r += (int64_t)gridDim.x * (blockDim.x >> 5)) {
     float nrm = 0.0f, res = 0.0f;
-    for (int k = lane; k < ldb; k += 32) {
+    for (int k = lane; k < dp; k += 32) {
       const float x = k < d ? X[r * ld + k] : 0.0f;
       const __nv_bfloat16 b = __float2bfloat16_rn(x);
       Xb[r * ldb + k] = b;
@@ -271,7 +274,12 @@ __global__ void quantize_kernel(const float* __restrict__ X, int64_t n, int d, i
       nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
       res = __fadd_ru(res, __shfl_xor_sync(0xffffffffu, res, o));
     }
-    if (lane == 0) aux[r] = make_float2(nrm, __fsqrt_ru(res));
+    if (lane == 0) {
+      const float2 t = make_float2(nrm, __fsqrt_ru(res));
+      aux[r] = t;
+      *reinterpret_cast<float4*>(Xb + r * ldb + dp) = make_float4(t.x, t.y, 0.0f, 0.0f);
+      *reinterpret_cast<float4*>(Xb + r * ldb + dp + 8) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -285,8 +293,9 @@ __global__ void quantize_kernel(const float* __restrict__ X, int64_t n, int d, i
 }
 
 // =====================================================================================
-// quantize, FP8 form: e4m3 rows (ldb = d rounded up to 32 bytes, zero padded) with one
-// power-of-two scale per row, x_hat = 2^e q.  e = E - 8 for max |x| = f 2^E, f in [0.5, 1),
+// quantize, FP8 form: e4m3 rows (dp = d rounded up to 32 bytes, zero padded, then the same
+// 32-byte tail as the BF16 rows; ldb = dp + 32) with one power-of-two scale per row,
+// x_hat = 2^e q.  e = E - 8 for max |x| = f 2^E, f in [0.5, 1),
 // so every |x| 2^-e < 256 stays inside e4m3's finite range (448) and the scaling itself is
 // exact.  aux = (norm^2 of x_hat, ||x - x_hat|| rounded up); the low byte of the residual's
 // bits carries e + 127 (the residual is first rounded up to a multiple of 256 units in its
@@ -308,8 +317,9 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t n, int 
     if (amax > 0.0f) frexpf(amax, &E);
     const int e = amax > 0.0f ? min(127, max(-126, E - 8)) : 0;
     const float inv = ldexpf(1.0f, -e), sc = ldexpf(1.0f, e);
+    const int dp = ldb - kRowTail8;  // padded dimensions of a row
     float nrm = 0.0f, res = 0.0f;
-    for (int k = lane; k < ldb; k += 32) {
+    for (int k = lane; k < dp; k += 32) {
       const float x = k < d ? X[r * ld + k] : 0.0f;
       const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3);
       Xq[r * ldb + k] = (uint8_t)q;
@@ -332,6 +342,8 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t n, int 
       uint32_t rb = __float_as_uint(__fsqrt_ru(res));
       rb = ((rb + 255u) & ~255u) | (uint32_t)(e + 127);
       aux[r] = make_float2(nrm, __uint_as_float(rb));
+      *reinterpret_cast<float4*>(Xq + r * ldb + dp) = make_float4(nrm, __uint_as_float(rb), 0.0f, 0.0f);
+      *reinterpret_cast<float4*>(Xq + r * ldb + dp + 16) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
   }
 #pragma unroll
@@ -1326,7 +1338,7 @@ struct WItem {
   int m;
   uint32_t lo;  // first id of the vertex's build
   int64_t v;
-  uint64_t key, aux;
+  uint64_t key;
 };
 
 template <int PREC>
@@ -1352,18 +1364,13 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
   x.lo = 0u;
   x.v = -1;
   x.key = kEmpty;
-  x.aux = 0ull;
+
   if (rr < (int64_t)a.list_n[cls]) {
     const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
     x.v = (int64_t)(r[0] & 0xffffffffull);
     x.lo = (uint32_t)(r[0] >> 32);
     x.m = (int)r[1];
-    if (gl < x.m) {
-      x.key = r[2 + gl];
-      // the quantized row's (norm^2, residual), read here a whole item ahead of its use
-      if (PREC >= 1 && in_bounds((uint64_t)key_id(x.key) < (uint64_t)a.n, a.err))
-        x.aux = __ldg(reinterpret_cast<const unsigned long long*>(a.P.aux) + key_id(x.key));
-    }
+    if (gl < x.m) x.key = r[2 + gl];
   }
 }
 
@@ -1427,7 +1434,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     auto issue = [&](int c) {  // the bulk copies of chunk c, completing on the warp's mbarrier
       const int c0 = c * WDC;
       const int cpy = (min(WDC, d - c0) + C::VEC - 1) / C::VEC * C::VEC;
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(T));
+      // a quantized row's last chunk brings the row's terms (norm^2, residual) along
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
       if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
       inflight = true;
       __syncwarp();
@@ -1472,7 +1480,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     // lane gb + p now holds local pi position p: its source lane hs (storage slot hs - gb)
     const int slot = (int)hs - gb;
     const uint64_t key = __shfl_sync(0xffffffffu, keyl, (int)hs);
-    const uint64_t aux = __shfl_sync(0xffffffffu, cur.aux, (int)hs);
     const bool valid_p = gl < m;
     const uint32_t below = lanes_below32(gl);
     const int row = __shfl_sync(0xffffffffu, row_s, (int)hs);  // the row of this position's entry
@@ -1484,8 +1491,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       s.rpos[gb + row] = (uint8_t)gl;
       s.inv[hs] = (uint8_t)gl;  // storage slot -> pi position
       if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
-      s.rnd[gb + row] = make_float2(PREC >= 1 ? __uint_as_float((uint32_t)aux) : 0.0f, key_dist(key));
-      if (PREC >= 1) s.rdq[gb + row] = __uint_as_float((uint32_t)(aux >> 32));
+      // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
+      s.rnd[gb + row] = make_float2(0.0f, key_dist(key));
     }
     if (lane == 0) s.nrq = 0;
     if (gl == 0) {
@@ -1521,6 +1528,15 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       if (!__all_sync(0xffffffffu, ok)) break;
       phb ^= 1u;
       inflight = false;
+      if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
+        if (need) {
+          const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+          const float2 t = *reinterpret_cast<const float2*>(&s.rows[gb + row_s][cpy]);
+          s.rnd[gb + row_s].x = t.x;
+          s.rdq[gb + row_s] = t.y;
+        }
+        __syncwarp();
+      }
       if (PREC >= 1) {
         // tiles one at a time; partial dot products wait in pd between chunks (d > 128),
         // and the last chunk takes the fire decisions straight from the accumulators
@@ -1924,26 +1940,19 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   uint32_t nlo = (uint32_t)(r0[0] >> 32);
   int nm = (int)r0[1];
   uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
-  // the quantized rows' (norm^2, residual) of the entries, read a vertex ahead of their use
-  auto row_terms = [&](uint64_t k) -> uint64_t {
-    if (PREC == 0 || !in_bounds((uint64_t)key_id(k) < (uint64_t)a.n, a.err)) return 0ull;
-    return __ldg(reinterpret_cast<const unsigned long long*>(a.P.aux) + key_id(k));
-  };
-  uint64_t naux = (PREC >= 1 && tid < nm) ? row_terms(nkey) : 0ull;
+
 
   for (; p < cnt; p += gridDim.x) {
     const int64_t v = nv;
     const uint32_t lo = nlo;  // first id of the vertex's build
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
-    const uint64_t auxl = naux;
     if (p + gridDim.x < cnt) {
       const uint64_t* rn = a.rec[3] + (p + gridDim.x) * W;
       nv = (int64_t)(rn[0] & 0xffffffffull);
       nlo = (uint32_t)(rn[0] >> 32);
       nm = (int)rn[1];
       nkey = tid < nm ? rn[2 + tid] : kEmpty;
-      if (PREC >= 1) naux = tid < nm ? row_terms(nkey) : 0ull;
     }
     // ---- visit order: rank of (h, id) among the m entries --------------------------------
     const uint32_t idl = key_id(keyl);
@@ -1985,7 +1994,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       const int c0 = c * TDC;
       const int clen = min(TDC, d - c0);
       const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(T));
+      // a quantized row's last chunk brings the row's terms (norm^2, residual) along
+      const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
       if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
       infl |= 1u << st;
       __syncthreads();
@@ -2022,8 +2032,8 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       s.prow[pi] = (uint8_t)row;
       s.rpos[row] = (uint8_t)pi;
       s.closer[pi] = pre ^ pbit;
-      s.rnd[row] = make_float2(PREC >= 1 ? __uint_as_float((uint32_t)auxl) : 0.0f, key_dist(keyl));
-      if (PREC >= 1) s.rdq[row] = __uint_as_float((uint32_t)(auxl >> 32));
+      // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
+      s.rnd[row] = make_float2(0.0f, key_dist(keyl));
     }
     if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
     s.fire[tid] = 0ull;  // fire bits are set by the pairs that fire (shared atomics)
@@ -2043,6 +2053,15 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       infl &= ~(1u << st);
       const int clen = min(TDC, d - c * TDC);
       const T* rows = rowbase + (size_t)st * TM * C::RS;
+      if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
+        if (has) {
+          const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+          const float2 t = *reinterpret_cast<const float2*>(rows + (size_t)row * C::RS + cpy);
+          s.rnd[row].x = t.x;
+          s.rdq[row] = t.y;
+        }
+        __syncthreads();
+      }
       if (PREC >= 1) {
         constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
         const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
