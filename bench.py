@@ -32,11 +32,13 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
                          "integers in [0,255]; S=32, R=64, T1=4, T2=15, rho=0.6; 10,000 queries, k=10, beam 64",
                 n=1_000_000, d=128, S=32, R=64, T1=4, T2=15, rho=0.6, nq=10_000, k=10, beam=64)
 # ncu DRAM bytes (read + write) per unit of the join -- one round, i.e. its warp and team
-# launches -- averaged over the 60 rounds of one build of the workload above, from an ncu
-# capture of the join kernels; reported only while the kernel source is unchanged since
-# that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 1.9065e9,
-           "source_sha256": "5aed72a4cce8e8b846a9530ad05ea51925363c470ff9a9ecb12addac57b603ce"}
+# launches -- for the workload above: DRAM bytes per algorithmic byte of the join, measured by
+# an ncu capture of rounds 1 and 2 of a 600,000-point build of the same generator (BF16 rows
+# of 173 MB, larger than L2; 0.8653 = 8.469 GB / 9.787 GB), times the full workload's
+# algorithmic bytes per round (2.2025e9); reported only while the join kernels' code is
+# unchanged since that capture.
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 0.8653 * 2.2025e9,
+           "source_sha256": "64f411b1c481049c41b70340c104bbea910d55d241f881ab5f418e8977d1a452"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
@@ -199,81 +201,21 @@ def _pct(xs, p):
 
 
 def _source_sha():
-    """sha256 of the pool kernels' code: comments and blank lines removed, so the figure
-    follows the code, not its commentary."""
+    """sha256 of the code of the join kernels that the traffic figure was taken on (the warp
+    and team joins of pool_kernels.cu, with common.cuh and kernels.cuh): comments and blank
+    lines removed, so the figure follows the code, not its commentary."""
     import re
-    with open(os.path.join(ROOT, "paper_2510_02774_gb300", "csrc", "pool_kernels.cu")) as f:
+    csrc = os.path.join(ROOT, "paper_2510_02774_gb300", "csrc")
+    with open(os.path.join(csrc, "pool_kernels.cu")) as f:
         text = f.read()
-    lines = [re.sub(r"\s*//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    a = text.index("// rnd_join for pools of at most 32 entries")
+    b = text.index("// rev_merge: exclusive scan")
+    parts = [text[a:b]]
+    for h in ("common.cuh", "kernels.cuh"):
+        with open(os.path.join(csrc, h)) as f:
+            parts.append(f.read())
+    lines = [re.sub(r"\s*//.*$", "", ln).rstrip() for ln in "\n".join(parts).splitlines()]
     return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
-
-
-def run_precision_report(args):
-    """Each form's distance error against FP64 and its recall loss, on continuous data.
-
-    Builds the graph of the same points with the FP32, BF16 and FP8 forms, then:
-      * recall@10 of a beam-64 search of 1000 held-out queries against exact k-NN (GPU brute
-        force); the BF16 form's loss is FP32 recall - BF16 recall;
-      * the recorded distance of every edge against the FP64 distance recomputed on the host
-        (relative error |d_rec - d_64| / max(d_64, tiny)), and how many prune decisions the
-        BF16 form re-took in FP32."""
-    import numpy as np
-    import torch
-    from paper_2510_02774_gb300 import build as B
-    B.build()
-    from paper_2510_02774_gb300 import grnnd, synth
-    n, nq, k, beam = args.n, 1000, 10, 64
-    if args.shape == "gist":
-        X, Q = synth.gist_like(n, nq, seed=args.seed)
-        metric, kw = grnnd.L2SQ, dict(S=32, R=64, T1=4, T2=15, rho=0.6, seed=args.seed)
-        shape = f"GIST1M-shaped synthetic: n={n}, d=960, 500-cluster mixture, per-dimension scales log-uniform in [0.1, 10]; S 32, R 64, T1 4, T2 15"
-    else:
-        X, Q = synth.deep_like(n, nq, seed=args.seed)
-        metric, kw = grnnd.IP, dict(S=16, R=32, T1=3, T2=10, rho=0.6, seed=args.seed)
-        shape = f"DEEP-shaped synthetic: n={n}, d=96, unit vectors, 50-cluster vMF-like mixture, inner product; S 16, R 32, T1 3, T2 10"
-    d = X.shape[1]
-    Xd = torch.from_numpy(X).cuda()
-    Xp, _ = grnnd.device_points(X)
-    Qp, _ = grnnd.device_points(Q)
-    gt, _ = grnnd.brute_knn(Xp, d, Qp, k, metric=metric)
-    gt = gt.cpu().numpy()
-    X64 = X.astype(np.float64) if n <= 200_000 else X  # rows are widened per chunk on large sets
-    out = {"report": "precision", "workload": shape, "queries": nq, "k": k, "beam": beam, "forms": {}}
-    for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16), ("fp8", grnnd.FP8)):
-        g = grnnd.build(Xd, precision=prec, metric=metric, **kw)
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        g2 = grnnd.build(Xd, precision=prec, metric=metric, **kw)
-        t1.record()
-        torch.cuda.synchronize()
-        found = g2.search(torch.from_numpy(Q).cuda(), k, beam).cpu().numpy()
-        rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(found, gt)]))
-        ids, dist, deg = g2.to_numpy()
-        mask = np.arange(ids.shape[1])[None, :] < deg[:, None]
-        rows = np.nonzero(mask)[0]
-        cols = ids[mask].astype(np.int64)
-        rec_d = dist[mask].astype(np.float64)
-        if len(rows) > 2_000_000:  # a seeded sample of the edges on large sets
-            pick = np.random.default_rng(1).choice(len(rows), 2_000_000, replace=False)
-            rows, cols, rec_d = rows[pick], cols[pick], rec_d[pick]
-        d64 = np.empty(len(rows))
-        for a in range(0, len(rows), 1 << 16):  # FP64 recomputation in chunks
-            xa = X64[rows[a:a + (1 << 16)]].astype(np.float64)
-            xb = X64[cols[a:a + (1 << 16)]].astype(np.float64)
-            d64[a:a + (1 << 16)] = ((xa - xb) ** 2).sum(1) if metric == grnnd.L2SQ else 1.0 - (xa * xb).sum(1)
-        rel = np.abs(rec_d - d64) / np.maximum(np.abs(d64), 1e-30)
-        st = g2.stats()
-        out["forms"][name] = {"build_ms": t0.elapsed_time(t1), "recall@10": rec, "edges": int(deg.sum()),
-                              "dist_rel_err_max": float(rel.max()), "dist_rel_err_mean": float(rel.mean()),
-                              "dist_rel_err_p99": float(np.quantile(rel, 0.99)),
-                              "rechecks": int(st["rechecks"]), "pair_distances": int(st["pair_distances"])}
-        del g, g2
-    for q in ("bf16", "fp8"):
-        out[q + "_recall_loss"] = out["forms"]["fp32"]["recall@10"] - out["forms"][q]["recall@10"]
-        out[q + "_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"][q]["build_ms"]
-    print(json.dumps(out), flush=True)
 
 
 def join_algorithmic_bytes(rows, n, proposals, fired, rechecks, d, elem):

@@ -737,7 +737,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
       {
         NvtxRange nvtx_round("round");
         GR_CAP(grnnd::launch_round(P, n, R, poolA, degA, p->seed, t1, t2, p->order, ws, poolA, degA,
-                                   stats, st, rounds > 0));
+                                   stats, st, rounds > 0, /*keys_canonical=*/true));
       }
       const int cur = (int)(rounds & 1);
       ++rounds;

@@ -100,10 +100,12 @@ cudaError_t prepare_join_kernels(const PointsSet& P);
 // One round of Alg 4: prep + rnd_join + scan + scatter + select (keys_out == keys_in: in
 // place).  use_hint: the last step on these pools was an in-place round or reverse step with
 // the same workspace, so its per-row new-entry flags replace prep's scan of the keys.
+// keys_canonical: every distance in the pools came from the library's own arithmetic (a
+// whole build), so the merge may find duplicate ids by their keys.
 cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int64_t* stats,
-                         cudaStream_t st, bool use_hint = false);
+                         cudaStream_t st, bool use_hint = false, bool keys_canonical = false);
 
 // Final prune-only pass: survivors only, no redirects (use_hint as for launch_round).
 cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,

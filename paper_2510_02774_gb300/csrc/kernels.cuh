@@ -74,6 +74,10 @@ struct SelectArgs {
   int old_pass;
   const unsigned* qflags;
   int d;
+  // 1: every distance recorded in the pools came from this library's own canonical arithmetic
+  // (a whole build), so copies of one id carry equal keys up to the old bit and duplicates
+  // can be found by comparing keys; 0 (step calls on caller-supplied pools): by id
+  int keys_canonical;
 };
 
 // The join of pools of 65..R entries (records of class 4), every precision form, and the

@@ -87,12 +87,15 @@ int sm_count() {
 //   32 candidates are tested per step; a lane is rejected if its id matches an accepted
 //   id or an earlier lane of the same step.
 // =====================================================================================
-constexpr int IC = 16;  // dimensions per staged chunk
-// E: pool entries per lane (32 E >= R); IW: warps per CTA (E = 2: 4 warps; E = 8, pools of
-// up to 256 entries: 2 warps, so that the staged rows stay within the static shared memory)
+// E: pool entries per lane (32 E >= R); IW: warps per CTA (E = 2, pools of up to 64 entries:
+// 4 warps; E = 8, up to 256 entries: 2 warps, so that the staged rows stay within the static
+// shared memory); IC: FP32 dimensions per staged chunk (64 bytes of each row per round trip).
+// A BF16 source is staged in the same bytes as bfloat16 values, 2 IC dimensions per chunk.
+// (Larger chunks cut round trips but the bigger buffer halves the resident warps: 32-dimension
+// FP32 chunks made the 1M-point init 1.9x slower.)
 // Xb (may be null): a BF16 copy of the rows (ldb elements per row); when qflags say that every
 // value is exact in BF16, the drawn rows are read from it -- the same values in half the bytes.
-template <int METRIC, int E, int IW>
+template <int METRIC, int E, int IW, int IC>
 __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restrict__ X, int64_t n,
                                                            int d, int ld, int S, int R, uint64_t seed,
                                                            uint64_t* __restrict__ keys,
@@ -101,15 +104,21 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
                                                            const __nv_bfloat16* __restrict__ Xb, int ldb,
                                                            const unsigned* __restrict__ qflags,
                                                            uint64_t magic) {
+  constexpr int RSF = IC + 4;       // staged row stride in floats (16-byte granules)
+  constexpr int RSB = 2 * RSF;      // ... in bfloat16 values
+  constexpr int GF = IC / 4;        // FP32 granules (4 dimensions) per staged row chunk
+  constexpr int GB = IC / 4;        // BF16 granules (8 dimensions) per staged row chunk
   __shared__ int32_t acc_ids[IW][32 * E];
   // the chunk of each drawn row (rows 0..S-1) and of v itself (row S), 16-byte granules
-  __shared__ __align__(16) float stage[IW][32 * E + 1][IC + 4];
+  __shared__ __align__(16) float stage[IW][32 * E + 1][RSF];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* acc = acc_ids[warp];
-  float(*rows)[IC + 4] = stage[warp];
+  float(*rows)[RSF] = stage[warp];
+  uint16_t* rows_b = reinterpret_cast<uint16_t*>(&stage[warp][0][0]);
   const uint64_t head = hash_head(seed, 0, 0);
   const unsigned below = lanemask_lt();
   const bool use_b = Xb != nullptr && (qflags[0] & 2u) == 0u;  // every value exact in BF16
+  const uint16_t* Xbs = reinterpret_cast<const uint16_t*>(Xb);
   for (int64_t v = (int64_t)blockIdx.x * IW + warp; v < n; v += (int64_t)gridDim.x * IW) {
     // the vertex's build: ids [lo, lo + nb); draws use the local id v - lo
     const int64_t lo = vseg ? vseg[v].x : 0;
@@ -135,40 +144,70 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
       cnt = min(S, cnt + __popc(ok));
       __syncwarp();
     }
-    // canonical distances, lane e for entries e and e + 32: the rows are staged IC dimensions
-    // at a time with whole-row coalesced loads; each lane then advances its four partial sums
-    // over the chunk in ascending dimension order, exactly as row_dist does
+    // canonical distances, lane e for entries e, e + 32, ...: the rows are staged a chunk of
+    // dimensions at a time with coalesced 16-byte loads; each lane then advances its four
+    // partial sums over the chunk in ascending dimension order, exactly as row_dist does
     float4 ps[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) ps[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int c0 = 0; c0 < d; c0 += IC) {
-      const int clen = min(IC, d - c0);
-      const int gr = (clen + 3) >> 2;  // granules per row
-      // row t / 4, granule t % 4 (IC / 4 = 4 granules per row; those past d are zero)
-      for (int t = lane; t < (S + 1) * (IC / 4); t += 32) {
-        const int r = t >> 2, q = t & 3;
-        const int64_t src = r < S ? (int64_t)acc[r] : v;
-        float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (q < gr) {
-          if (use_b) {  // four BF16 values, widened exactly
-            const uint2 u = *reinterpret_cast<const uint2*>(Xb + src * ldb + c0 + 4 * q);
-            val = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                              __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-          } else {
-            val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
-          }
-          if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
+    const int CH = use_b ? 2 * IC : IC;  // dimensions per chunk
+    for (int c0 = 0; c0 < d; c0 += CH) {
+      const int clen = min(CH, d - c0);
+      if (use_b) {
+        // row t / GB, granule t % GB of 8 BF16 values (those past d are zero)
+        for (int t = lane; t < (S + 1) * GB; t += 32) {
+          const int r = t / GB, q = t % GB;  // (GB is a power of two)
+          const int64_t src = r < S ? (int64_t)acc[r] : v;
+          uint4 u = make_uint4(0u, 0u, 0u, 0u);
+          if (8 * q < clen) u = *reinterpret_cast<const uint4*>(Xbs + src * ldb + c0 + 8 * q);
+          *reinterpret_cast<uint4*>(rows_b + r * RSB + 8 * q) = u;
         }
-        *reinterpret_cast<float4*>(&rows[r][4 * q]) = val;
+      } else {
+        // row t / GF, granule t % GF of 4 FP32 values (those past d are zero)
+        for (int t = lane; t < (S + 1) * GF; t += 32) {
+          const int r = t / GF, q = t % GF;  // (GF is a power of two)
+          const int64_t src = r < S ? (int64_t)acc[r] : v;
+          float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (4 * q < clen) {
+            val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
+            if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
+          }
+          *reinterpret_cast<float4*>(&rows[r][4 * q]) = val;
+        }
       }
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const int e = j * 32 + lane;
-        if (e < S)
+        if (e >= S) continue;
+        if (use_b) {
+          for (int q = 0; 8 * q < clen; ++q) {  // eight BF16 values, widened exactly
+            const uint4 a = *reinterpret_cast<const uint4*>(rows_b + S * RSB + 8 * q);
+            const uint4 b = *reinterpret_cast<const uint4*>(rows_b + e * RSB + 8 * q);
+            float4 a0 = make_float4(__uint_as_float(a.x << 16), __uint_as_float(a.x & 0xffff0000u),
+                                    __uint_as_float(a.y << 16), __uint_as_float(a.y & 0xffff0000u));
+            float4 a1 = make_float4(__uint_as_float(a.z << 16), __uint_as_float(a.z & 0xffff0000u),
+                                    __uint_as_float(a.w << 16), __uint_as_float(a.w & 0xffff0000u));
+            float4 b0 = make_float4(__uint_as_float(b.x << 16), __uint_as_float(b.x & 0xffff0000u),
+                                    __uint_as_float(b.y << 16), __uint_as_float(b.y & 0xffff0000u));
+            float4 b1 = make_float4(__uint_as_float(b.z << 16), __uint_as_float(b.z & 0xffff0000u),
+                                    __uint_as_float(b.w << 16), __uint_as_float(b.w & 0xffff0000u));
+            const int rem = clen - 8 * q;  // past d: zero, as row_dist's tail
+            if (rem < 8) {
+              a0 = mask4(a0, rem);
+              b0 = mask4(b0, rem);
+              a1 = mask4(a1, rem - 4);
+              b1 = mask4(b1, rem - 4);
+            }
+            dist_step4<METRIC>(ps[j], a0, b0);
+            if (rem > 4) dist_step4<METRIC>(ps[j], a1, b1);
+          }
+        } else {
+          const int gr = (clen + 3) >> 2;  // granules of the chunk
           for (int q = 0; q < gr; ++q)
             dist_step4<METRIC>(ps[j], *reinterpret_cast<const float4*>(&rows[S][4 * q]),
                                *reinterpret_cast<const float4*>(&rows[e][4 * q]));
+        }
       }
       __syncwarp();
     }
@@ -211,16 +250,16 @@ cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metri
     constexpr int IW = 4;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
     if (metric == 0)
-      rnd_init_kernel<0, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<0, 2, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
     else
-      rnd_init_kernel<1, 2, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<1, 2, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
   } else {  // pools of up to 256 entries
     constexpr int IW = 2;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 32);
     if (metric == 0)
-      rnd_init_kernel<0, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<0, 8, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
     else
-      rnd_init_kernel<1, 8, IW><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<1, 8, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
   }
   return cudaGetLastError();
 }
@@ -1879,6 +1918,7 @@ struct __align__(16) TeamSmem {
   int32_t pid[TM];                // by pi position
   uint16_t roff[TM + 1];          // first pair index of new row i
   uint8_t rpos[TM], prow[TM], killer[TM];
+  uint8_t spos[TM];               // by storage slot: its pi position (the sort's result)
   uint16_t rq[TRQ];               // pairs (row i << 6 | row j) whose decision is re-taken in FP32
   int32_t nrq;
   uint64_t alive, wtot;
@@ -1964,13 +2004,6 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           : (a.order == 1) ? (uint64_t)tid
                            : (uint64_t)(m - 1 - tid);
     {
-      TeamKey hk;
-      hk.h = h;
-      hk.id = has ? idl : 0xffffffffu;
-      hk.pad = 0u;
-      s.hk[tid] = hk;
-    }
-    {
       const unsigned nw = __ballot_sync(0xffffffffu, has && !key_old(keyl));  // new entries by slot
       if (lane == 0) s.sm32[warp] = nw;
     }
@@ -2007,13 +2040,51 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
     };
     if (nch > 0) issue(0, stage);
+    // ---- visit order: bitonic sort of (h, id) over the team's 64 threads (empty slots last),
+    // carrying each entry's storage slot; thread p then holds the entry of pi position p
     int pi = 0;
-    if (has) {
-#pragma unroll 4
-      for (int f = 0; f < m; ++f) {
-        const TeamKey o = s.hk[f];
-        pi += (o.h < h) || (o.h == h && o.id < idl);
+    {
+      uint64_t sh = h;
+      uint32_t sid = has ? idl : 0xffffffffu, ss = (uint32_t)tid;
+      auto cmpx = [&](uint64_t oh, uint32_t oid, uint32_t os, bool up, bool lower) {
+        // (the slot breaks the ties of the empty slots: a strict order, every slot sorted once)
+        const bool other_less = (oh < sh) || (oh == sh && (oid < sid || (oid == sid && os < ss)));
+        if ((lower == up) ? other_less : !other_less) {
+          sh = oh;
+          sid = oid;
+          ss = os;
+        }
+      };
+#pragma unroll
+      for (int kk = 2; kk <= 32; kk <<= 1) {  // within each warp: warp 0 ascending, warp 1 descending
+#pragma unroll
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+          const uint64_t oh = __shfl_xor_sync(0xffffffffu, sh, jj);
+          const uint32_t oid = __shfl_xor_sync(0xffffffffu, sid, jj);
+          const uint32_t os = __shfl_xor_sync(0xffffffffu, ss, jj);
+          cmpx(oh, oid, os, (tid & kk) == 0, (lane & jj) == 0);
+        }
       }
+      {  // the 64-element merge: distance 32 across the two warps, through shared memory
+        TeamKey mine;
+        mine.h = sh;
+        mine.id = sid;
+        mine.pad = ss;
+        s.hk[tid] = mine;
+        __syncthreads();
+        const TeamKey o = s.hk[tid ^ 32];
+        cmpx(o.h, o.id, o.pad, true, (tid & 32) == 0);
+      }
+#pragma unroll
+      for (int jj = 16; jj > 0; jj >>= 1) {
+        const uint64_t oh = __shfl_xor_sync(0xffffffffu, sh, jj);
+        const uint32_t oid = __shfl_xor_sync(0xffffffffu, sid, jj);
+        const uint32_t os = __shfl_xor_sync(0xffffffffu, ss, jj);
+        cmpx(oh, oid, os, true, (lane & jj) == 0);
+      }
+      s.spos[ss] = (uint8_t)tid;
+      __syncthreads();
+      pi = s.spos[tid];
     }
     // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
     // closer mask of a position is the OR of the position bits of the slots before its own
@@ -2616,6 +2687,65 @@ __device__ __forceinline__ void merge_chunk(uint64_t& x0, uint64_t& x1, uint64_t
   __syncwarp();
 }
 
+// merge_chunk when every copy of an id proposed to the target carries the same distance (the
+// pools' distances all come from the library's canonical FP32 arithmetic or exact tiles, as
+// in a whole build) and the proposals are new: copies of
+// one id then have equal keys up to the old bit, so duplicates are found by comparing keys --
+// adjacent proposals after the sort, and a proposal against its lower bound in the row (the
+// row's copy, old or not, is the one kept) -- with no id hash.  Then, as in merge_chunk, each
+// kept element's rank in the merged row is its index in its own sorted list plus the number
+// of smaller keys in the other list.
+__device__ __forceinline__ void merge_chunk_exact(uint64_t& x0, uint64_t& x1, uint64_t b, int R, MergeScratch& ms) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t below = lane == 0 ? 0u : (0xffffffffu >> (32 - lane));
+  {
+    uint64_t t[1] = {b};
+    warp_sort_u64<1>(t);
+    b = t[0];
+  }
+  const uint64_t bk = b >> 1;  // (dist, id)
+  const uint64_t prev = __shfl_up_sync(0xffffffffu, bk, 1);
+  bool keep = b != kEmpty && (lane == 0 || prev != bk);  // the first of each run of copies
+  ms.row[lane] = x0;
+  ms.row[lane + 32] = x1;
+  const int nr = __popc(__ballot_sync(0xffffffffu, x0 != kEmpty)) + __popc(__ballot_sync(0xffffffffu, x1 != kEmpty));
+  __syncwarp();
+  int lo = 0;  // row entries with a smaller key
+  if (keep) {
+    int hi = nr;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((ms.row[mid] >> 1) < bk) lo = mid + 1; else hi = mid;
+    }
+    if (lo < nr && (ms.row[lo] >> 1) == bk) keep = false;  // the row holds this copy already
+  }
+  const unsigned kb = __ballot_sync(0xffffffffu, keep);
+  const int nb = __popc(kb), ib = __popc(kb & below);
+  if (keep) {
+    ms.prop[ib] = b;
+    ms.out[ib + lo] = b;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint64_t xk = h ? x1 : x0;
+    if (xk != kEmpty) {
+      const uint64_t xkk = xk >> 1;
+      int l2 = 0, h2 = nb;  // kept proposals with a smaller key
+      while (l2 < h2) {
+        const int mid = (l2 + h2) >> 1;
+        if ((ms.prop[mid] >> 1) < xkk) l2 = mid + 1; else h2 = mid;
+      }
+      ms.out[lane + 32 * h + l2] = xk;
+    }
+  }
+  __syncwarp();
+  const int tot = min(nb + nr, R);
+  x0 = lane < tot ? ms.out[lane] : kEmpty;
+  x1 = lane + 32 < tot ? ms.out[lane + 32] : kEmpty;
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   __shared__ MergeScratch scratch[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2719,7 +2849,10 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
               sl = (sl + 1) & 127u;
             }
           }
-          merge_chunk(out0, out1, bl, R, ms);
+          if (old_pass || !a.keys_canonical)
+            merge_chunk(out0, out1, bl, R, ms);
+          else
+            merge_chunk_exact(out0, out1, bl, R, ms);
         }
       }
       if (lane >= R) out0 = kEmpty;
@@ -2873,7 +3006,7 @@ cudaError_t prepare_join_kernels(const PointsSet& P) {
 cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                          const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int64_t* stats,
-                         cudaStream_t st, bool use_hint) {
+                         cudaStream_t st, bool use_hint, bool keys_canonical) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;  // list_n and red_n
@@ -2901,6 +3034,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.old_pass = 0;
   sa.qflags = P.precision >= 1 ? P.qflags : nullptr;
   sa.d = P.d;
+  sa.keys_canonical = keys_canonical ? 1 : 0;
   return merge_tail(ws, sa, st);
 }
 
@@ -2934,6 +3068,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.old_pass = 0;  // no proposals
   sa.qflags = nullptr;
   sa.d = P.d;
+  sa.keys_canonical = 0;
   return merge_tail(ws, sa, st);
 }
 
@@ -3014,6 +3149,7 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
   sa.next_active = keys_out == keys_in ? ws.next_active : nullptr;  // rows not merged keep their flag
   sa.next_active_all = 0;
   sa.old_pass = 1;  // the points (and so the exactness of the recorded distances) are not known here
+  sa.keys_canonical = 0;
   sa.qflags = nullptr;
   sa.d = 0;
   return merge_tail(ws, sa, st);
