@@ -191,7 +191,7 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------------------
 
-KERNELS_PER_GROUP = {"scan": 3, "entry": 6}
+KERNELS_PER_GROUP = {"scan": 2, "entry": 6}
 JOIN_KERNELS = ("rnd_join_warp", "rnd_join_team", "rnd_join")
 
 
@@ -224,6 +224,85 @@ def join_algorithmic_bytes(rows, n, proposals, fired, rechecks, d, elem):
     written) once, each redirect written (target + key) and counted, and the FP32 rows of
     every re-decided pair (three rows: the pair and the row it is decided against)."""
     return rows * d * elem + n * 4 + proposals * 8 + fired * (12 + 4) + rechecks * 3 * d * 4
+
+
+def run_precision_report(args):
+    """Each form's distance error against FP64 and its recall loss, on continuous data.
+
+    Builds the graph of the same points with the FP32, BF16 and FP8 forms, then:
+      * recall@10 of a beam-64 search of 1000 held-out queries against exact k-NN (GPU brute
+        force); the BF16 form's loss is FP32 recall - BF16 recall;
+      * the recorded distance of every edge against the FP64 distance recomputed on the host
+        (relative error |d_rec - d_64| / max(d_64, tiny)), and how many prune decisions the
+        BF16 form re-took in FP32."""
+    import numpy as np
+    import torch
+    from paper_2510_02774_gb300 import build as B
+    B.build()
+    from paper_2510_02774_gb300 import grnnd, synth
+    n, nq, k, beam = args.n, 1000, 10, 64
+    if args.shape == "gist":
+        X, Q = synth.gist_like(n, nq, seed=args.seed)
+        metric, kw = grnnd.L2SQ, dict(S=32, R=64, T1=4, T2=15, rho=0.6, seed=args.seed)
+        shape = f"GIST1M-shaped synthetic: n={n}, d=960, 500-cluster mixture, per-dimension scales log-uniform in [0.1, 10]; S 32, R 64, T1 4, T2 15"
+    else:
+        X, Q = synth.deep_like(n, nq, seed=args.seed)
+        metric, kw = grnnd.IP, dict(S=16, R=32, T1=3, T2=10, rho=0.6, seed=args.seed)
+        shape = f"DEEP-shaped synthetic: n={n}, d=96, unit vectors, 50-cluster vMF-like mixture, inner product; S 16, R 32, T1 3, T2 10"
+    d = X.shape[1]
+    Xd = torch.from_numpy(X).cuda()
+    Xp, _ = grnnd.device_points(X)
+    Qp, _ = grnnd.device_points(Q)
+    gt, _ = grnnd.brute_knn(Xp, d, Qp, k, metric=metric)
+    gt = gt.cpu().numpy()
+    X64 = X.astype(np.float64) if n <= 200_000 else X  # rows are widened per chunk on large sets
+    out = {"report": "precision", "workload": shape, "queries": nq, "k": k, "beam": beam, "forms": {}}
+    for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16), ("fp8", grnnd.FP8)):
+        g = grnnd.build(Xd, precision=prec, metric=metric, **kw)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        g2 = grnnd.build(Xd, precision=prec, metric=metric, **kw)
+        t1.record()
+        torch.cuda.synchronize()
+        Qt = torch.from_numpy(Q).cuda()
+
+        def recall_at(bm):
+            found = g2.search(Qt, k, bm).cpu().numpy()
+            return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(found, gt)]))
+
+        rec = recall_at(beam)
+        # the smallest candidate list of these that reaches recall@10 >= 0.95
+        beams = {bm: (rec if bm == beam else recall_at(bm)) for bm in (48, 64, 80, 96, 128, 192, 256)}
+        min_beam = min((bm for bm, r in beams.items() if r >= 0.95), default=None)
+        ids, dist, deg = g2.to_numpy()
+        mask = np.arange(ids.shape[1])[None, :] < deg[:, None]
+        rows = np.nonzero(mask)[0]
+        cols = ids[mask].astype(np.int64)
+        rec_d = dist[mask].astype(np.float64)
+        if len(rows) > 2_000_000:  # a seeded sample of the edges on large sets
+            pick = np.random.default_rng(1).choice(len(rows), 2_000_000, replace=False)
+            rows, cols, rec_d = rows[pick], cols[pick], rec_d[pick]
+        d64 = np.empty(len(rows))
+        for a in range(0, len(rows), 1 << 16):  # FP64 recomputation in chunks
+            xa = X64[rows[a:a + (1 << 16)]].astype(np.float64)
+            xb = X64[cols[a:a + (1 << 16)]].astype(np.float64)
+            d64[a:a + (1 << 16)] = ((xa - xb) ** 2).sum(1) if metric == grnnd.L2SQ else 1.0 - (xa * xb).sum(1)
+        rel = np.abs(rec_d - d64) / np.maximum(np.abs(d64), 1e-30)
+        st = g2.stats()
+        out["forms"][name] = {"build_ms": t0.elapsed_time(t1), "recall@10": rec, "edges": int(deg.sum()),
+                              "recall@10_by_beam": beams, "smallest_beam_recall_0.95": min_beam,
+                              "dist_rel_err_max": float(rel.max()), "dist_rel_err_mean": float(rel.mean()),
+                              "dist_rel_err_p99": float(np.quantile(rel, 0.99)),
+                              "rechecks": int(st["rechecks"]), "pair_distances": int(st["pair_distances"])}
+        del g, g2
+    for q in ("bf16", "fp8"):
+        out[q + "_recall_loss"] = out["forms"]["fp32"]["recall@10"] - out["forms"][q]["recall@10"]
+        out[q + "_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"][q]["build_ms"]
+    print(json.dumps(out), flush=True)
+
+
 
 
 def run_rounds_report(args):
@@ -450,7 +529,31 @@ def run_serve_report(args):
     burst = time.perf_counter() - t1
     for r in bids:
         srv.release(r)
+    # search burst: 2,000 search requests (1..1024 queries each) submitted at once against one
+    # resident 500k-point index: waiting searches of the same index are served together
+    # (continuous batching); against the same searches one after another through grnnd_search
+    idx = srv.wait(srv.submit_build(base[128][0][:500000], precision=grnnd.BF16, seed=7, **cfg[128]))["index"]
+    qreq = []
+    for _ in range(2000):
+        nq = int(rng.integers(1, 1025))
+        qreq.append((int(rng.integers(0, 20000 - nq)), nq))
+    t3 = time.perf_counter()
+    sids = [srv.submit_search(idx, base[128][1][o:o + nq], 10, 64) for o, nq in qreq]
+    sinfo = [srv.wait(r) for r in sids]
+    sburst = time.perf_counter() - t3
+    srv.release(idx)
     srv.close()
+    gref = grnnd.build(base[128][0][:500000].numpy(), precision=grnnd.BF16, seed=7, **cfg[128])
+    qnp = base[128][1].numpy()
+    t4 = time.perf_counter()
+    same = True
+    for (o, nq), inf in zip(qreq, sinfo):
+        same &= bool((gref.search(qnp[o:o + nq], 10, 64) == inf["out"]).all())
+    sseq = time.perf_counter() - t4
+    del gref
+    qtot = sum(nq for _, nq in qreq)
+    slat = sorted(1e3 * (i["t_done"] - i["t_submit"]) for i in sinfo)
+    sbat = [i["batch"] for i in sinfo]
     seq = {}
     for name, prec in (("fp32", grnnd.FP32), ("bf16", grnnd.BF16)):
         torch.cuda.synchronize()
@@ -475,6 +578,11 @@ def run_serve_report(args):
             "stream_points_per_s": pts / wall, "stream_queries_per_s": nq_tot / wall, "stream_wall_s": wall,
             "search_batch_mean": float(np.mean(sb)) if sb else None, "search_batch_max": max(sb) if sb else None,
             "peak_bytes": st["peak_bytes"],
+            "search_burst": {"requests": len(qreq), "queries": qtot, "server_s": sburst,
+                             "server_queries_per_s": qtot / sburst, "batch_mean": float(np.mean(sbat)),
+                             "batch_max": max(sbat), "latency_ms": {"p50": pct(slat, 0.5), "p99": pct(slat, 0.99)},
+                             "sequential_s": sseq, "sequential_queries_per_s": qtot / sseq,
+                             "results_equal_to_sequential": same},
             "burst": {"builds": len(bl), "points": bp, "server_bf16_s": burst, "server_points_per_s": bp / burst,
                       "sequential_fp32_s": seq["fp32"], "sequential_fp32_points_per_s": bp / seq["fp32"],
                       "sequential_bf16_s": seq["bf16"], "sequential_bf16_points_per_s": bp / seq["bf16"],

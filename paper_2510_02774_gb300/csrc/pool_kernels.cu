@@ -1918,7 +1918,6 @@ struct __align__(16) TeamSmem {
   int32_t pid[TM];                // by pi position
   uint16_t roff[TM + 1];          // first pair index of new row i
   uint8_t rpos[TM], prow[TM], killer[TM];
-  uint8_t spos[TM];               // by storage slot: its pi position (the sort's result)
   uint16_t rq[TRQ];               // pairs (row i << 6 | row j) whose decision is re-taken in FP32
   int32_t nrq;
   uint64_t alive, wtot;
@@ -2004,6 +2003,13 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           : (a.order == 1) ? (uint64_t)tid
                            : (uint64_t)(m - 1 - tid);
     {
+      TeamKey hk;
+      hk.h = h;
+      hk.id = has ? idl : 0xffffffffu;
+      hk.pad = 0u;
+      s.hk[tid] = hk;
+    }
+    {
       const unsigned nw = __ballot_sync(0xffffffffu, has && !key_old(keyl));  // new entries by slot
       if (lane == 0) s.sm32[warp] = nw;
     }
@@ -2040,51 +2046,13 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
     };
     if (nch > 0) issue(0, stage);
-    // ---- visit order: bitonic sort of (h, id) over the team's 64 threads (empty slots last),
-    // carrying each entry's storage slot; thread p then holds the entry of pi position p
     int pi = 0;
-    {
-      uint64_t sh = h;
-      uint32_t sid = has ? idl : 0xffffffffu, ss = (uint32_t)tid;
-      auto cmpx = [&](uint64_t oh, uint32_t oid, uint32_t os, bool up, bool lower) {
-        // (the slot breaks the ties of the empty slots: a strict order, every slot sorted once)
-        const bool other_less = (oh < sh) || (oh == sh && (oid < sid || (oid == sid && os < ss)));
-        if ((lower == up) ? other_less : !other_less) {
-          sh = oh;
-          sid = oid;
-          ss = os;
-        }
-      };
-#pragma unroll
-      for (int kk = 2; kk <= 32; kk <<= 1) {  // within each warp: warp 0 ascending, warp 1 descending
-#pragma unroll
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-          const uint64_t oh = __shfl_xor_sync(0xffffffffu, sh, jj);
-          const uint32_t oid = __shfl_xor_sync(0xffffffffu, sid, jj);
-          const uint32_t os = __shfl_xor_sync(0xffffffffu, ss, jj);
-          cmpx(oh, oid, os, (tid & kk) == 0, (lane & jj) == 0);
-        }
+    if (has) {
+#pragma unroll 4
+      for (int f = 0; f < m; ++f) {
+        const TeamKey o = s.hk[f];
+        pi += (o.h < h) || (o.h == h && o.id < idl);
       }
-      {  // the 64-element merge: distance 32 across the two warps, through shared memory
-        TeamKey mine;
-        mine.h = sh;
-        mine.id = sid;
-        mine.pad = ss;
-        s.hk[tid] = mine;
-        __syncthreads();
-        const TeamKey o = s.hk[tid ^ 32];
-        cmpx(o.h, o.id, o.pad, true, (tid & 32) == 0);
-      }
-#pragma unroll
-      for (int jj = 16; jj > 0; jj >>= 1) {
-        const uint64_t oh = __shfl_xor_sync(0xffffffffu, sh, jj);
-        const uint32_t oid = __shfl_xor_sync(0xffffffffu, sid, jj);
-        const uint32_t os = __shfl_xor_sync(0xffffffffu, ss, jj);
-        cmpx(oh, oid, os, true, (lane & jj) == 0);
-      }
-      s.spos[ss] = (uint8_t)tid;
-      __syncthreads();
-      pi = s.spos[tid];
     }
     // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
     // closer mask of a position is the OR of the position bits of the slots before its own
@@ -2435,50 +2403,28 @@ __global__ void __launch_bounds__(SCAN_T) scan_reduce_kernel(const int32_t* __re
   }
 }
 
-// Single block: exclusive scan of nb block sums in place, total to off[n].
-__global__ void __launch_bounds__(1024) scan_blocks_kernel(int64_t* __restrict__ bsum, int64_t nb,
-                                                           int64_t* __restrict__ off_total) {
-  __shared__ int64_t wsum[32];
-  __shared__ int64_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t base = 0; base < nb; base += 1024) {
-    const int64_t idx = base + threadIdx.x;
-    const int64_t x = idx < nb ? bsum[idx] : 0;
-    int64_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-      int64_t w = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      wsum[lane] = w;
-    }
-    __syncthreads();
-    const int64_t wpre = warp > 0 ? wsum[warp - 1] : 0;
-    const int64_t c = carry;
-    if (idx < nb) bsum[idx] = c + wpre + inc - x;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = c + wpre + inc;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *off_total = carry;
-}
-
+// Each block first adds up the sums of the blocks before it (a few thousand int64 at most,
+// from L2), then scans its own tile; the last block also writes the total to off[n].
 __global__ void __launch_bounds__(SCAN_T) scan_apply_kernel(const int32_t* __restrict__ cnt,
                                                             int64_t n,
-                                                            const int64_t* __restrict__ bpre,
+                                                            const int64_t* __restrict__ bsum,
                                                             int64_t* __restrict__ off) {
   __shared__ int64_t wsum[SCAN_T / 32];
+  __shared__ int64_t bpre_s;
+  {
+    int64_t x = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_T) x += bsum[b];
+    x = warp_sum64(x);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t t = 0;
+      for (int w = 0; w < SCAN_T / 32; ++w) t += wsum[w];
+      bpre_s = t;
+    }
+    __syncthreads();
+  }
+  const int64_t bpre = bpre_s;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
   int32_t v[SCAN_IPT];
   int64_t tsum = 0;
@@ -2494,16 +2440,18 @@ __global__ void __launch_bounds__(SCAN_T) scan_apply_kernel(const int32_t* __res
     const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += y;
   }
+  __syncthreads();  // (wsum is reused)
   if (lane == 31) wsum[warp] = inc;
   __syncthreads();
   int64_t wpre = 0;
   for (int w = 0; w < warp; ++w) wpre += wsum[w];
-  int64_t run = bpre[blockIdx.x] + wpre + inc - tsum;
+  int64_t run = bpre + wpre + inc - tsum;
 #pragma unroll
   for (int i = 0; i < SCAN_IPT; ++i) {
     if (base + i < n) off[base + i] = run;
     run += v[i];
   }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_T - 1) off[n] = run;  // the total
 }
 
 __global__ void scatter_kernel(const int32_t* __restrict__ tgt, const uint64_t* __restrict__ pk,
@@ -2882,7 +2830,6 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
     {
       ProfScope ps("scan", st);
       scan_reduce_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(ws.count, n, ws.bsum);
-      scan_blocks_kernel<<<1, 1024, 0, st>>>(ws.bsum, nb, ws.off + n);
       scan_apply_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(ws.count, n, ws.bsum, ws.off);
     }
     {
