@@ -31,6 +31,7 @@ struct Workspace {
                                            // last class exists only when R > 64)
   int32_t* list_n = nullptr;               // [5] records per class
   unsigned long long* red_n = nullptr;     // number of redirects / reverse proposals
+  unsigned int* work_q = nullptr;          // [3] next work item of the warp and team joins (third word spare)
   int32_t* err = nullptr;                  // device status word (bounded waits)
   int64_t* round_new = nullptr;            // new entries written by the last merge
 };

@@ -47,6 +47,7 @@ struct JoinArgs {
   int32_t* count;
   int64_t* stats;
   int32_t* err;
+  unsigned int* work_q;      // [3] device work queues of the warp and team joins, one spare (zeroed per step)
   int warp_ctas, team_ctas;  // launch caps (host side only; 0: as many as fit)
 };
 

@@ -412,12 +412,13 @@ cudaError_t launch_quantize(const float* X, int64_t n, int d, int ld, void* Xbv,
 }
 
 // =====================================================================================
-// prep: active flag of the vertices whose pool holds a new entry, and for each of them a
-// contiguous work record that the join prefetches in one piece.  Records go to one of five
+// prep: active flag of the vertices whose pool holds a new entry, and for each of them a work
+// record in the list of its pool-size class.  Records go to one of five
 // regions by pool size (entries <= 8, <= 16, <= 32, <= 64, more; pools of up to 64 entries
 // all to the fourth region when the warp kernels cannot take the rows), so that a warp can
 // take several small pools at once.  A record of a region holding up to cap entries:
-//   word 0: v | (first id of v's build) << 32    word 1: m    words 2 .. 2+m: the pool keys.
+//   word 0: v | (first id of v's build) << 32    word 1: m
+// (the joins read the m pool keys from v's own row).
 // Also counts the entries of every pool (each one is proposed once, explicitly or in place).
 // With `hint` (the flags the last merge of the same pools wrote) no pool key is read for
 // the active test.
@@ -459,52 +460,15 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
       if (lane == 0 && bc[c]) o = atomicAdd(&list_n[c], __popc(bc[c]));
       off[c] = __shfl_sync(0xffffffffu, o, 0);
     }
-    // the warp writes the records of its active vertices, four at a time (eight lanes each),
-    // so that four chains of dependent loads (key, then the row terms it names) overlap
-    unsigned left = bc[0] | bc[1] | bc[2] | bc[3] | bc[4];
-    const int grp = lane >> 3, gln = lane & 7;
-    while (left) {
-      unsigned mine = left;  // this group's vertex: the grp-th remaining one
-      for (int q = 0; q < grp; ++q) mine &= mine - 1;
-      const int l = mine ? __ffs(mine) - 1 : -1;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) left &= left - 1;  // (clearing past the last bit is harmless)
-      const int ls = l < 0 ? 0 : l;
-      const int64_t u = base + ls;
-      const int mu = __shfl_sync(0xffffffffu, m, ls);
-      const int cu = __shfl_sync(0xffffffffu, cls, ls);
-      if (l < 0) continue;
-      const unsigned below_l = (1u << l) - 1u;
-      unsigned bcu = bc[0];
-      int offu = off[0], W = rs.w[0];
-      uint64_t* rg = rs.rec[0];
+    // each active vertex writes its record: v and its build's first id, and m (the join reads
+    // the pool keys from the vertex's own row, which nothing else writes before its join)
+    if (act) {
+      uint64_t* r = rs.rec[0] + (int64_t)(off[0] + __popc(bc[0] & lanemask_lt())) * rs.w[0];
 #pragma unroll
       for (int c = 1; c < kNumClasses; ++c)
-        if (cu == c) {
-          bcu = bc[c];
-          offu = off[c];
-          W = rs.w[c];
-          rg = rs.rec[c];
-        }
-      uint64_t* r = rg + (int64_t)(offu + __popc(bcu & below_l)) * W;
-      if (gln == 0) {
-        r[0] = (uint64_t)u | ((uint64_t)(vseg ? vseg[u].x : 0) << 32);
-        r[1] = (uint64_t)mu;
-      }
-      // up to 8 entries per lane at a time: their key loads are in flight together
-      for (int j0 = 0; j0 < mu; j0 += 64) {
-        uint64_t kk[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int j = j0 + gln + 8 * t;
-          kk[t] = j < mu ? keys[u * R + j] : kEmpty;
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int j = j0 + gln + 8 * t;
-          if (j < mu) r[2 + j] = kk[t];
-        }
-      }
+        if (cls == c) r = rs.rec[c] + (int64_t)(off[c] + __popc(bc[c] & lanemask_lt())) * rs.w[c];
+      r[0] = (uint64_t)v | ((uint64_t)(vseg ? vseg[v].x : 0) << 32);
+      r[1] = (uint64_t)m;
     }
   }
   if (stats) {
@@ -551,7 +515,7 @@ constexpr int SPW = 12;                        // FP32 tile: row segments per wa
 constexpr int BSEG = 288;                      // row segments per batch at most
 constexpr int BT = 64;                         // mma output tiles per batch at most
 constexpr int TPW = BT / JW;                   // mma tiles per warp
-constexpr int RECW_MAX = 2 + kMaxR;            // work-record words (R = 64)
+constexpr int RECW_MAX = 2;                    // work-record words
 constexpr int RED_CHUNK = kRedChunk;           // redirect slots reserved per CTA at a time
 
 // A row segment is up to 32 consecutive pairs (i, j0..j0+31) of one new row i: one warp
@@ -682,7 +646,7 @@ __device__ int join_form_batch(JoinSmem<PREC>& s, Batch& B, int64_t pos, int64_t
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int e = j * 32 + lane;
-        if (e < m) kx[h][j] = r[2 + e];
+        if (e < m && in_bounds((uint64_t)v < (uint64_t)a.n, a.err)) kx[h][j] = a.keys_in[v * a.R + e];
         if (PREC == 1 && e < m) ax[h][j] = a.P.aux[key_id(kx[h][j])];
       }
       const int k = __popc(__ballot_sync(0xffffffffu, lane < m && !key_old(kx[h][0]))) +
@@ -1409,7 +1373,7 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
     x.v = (int64_t)(r[0] & 0xffffffffull);
     x.lo = (uint32_t)(r[0] >> 32);
     x.m = (int)r[1];
-    if (gl < x.m) x.key = r[2 + gl];
+    if (gl < x.m && in_bounds((uint64_t)x.v < (uint64_t)a.n, a.err)) x.key = a.keys_in[x.v * a.R + gl];
   }
 }
 
@@ -1443,11 +1407,20 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   bool inflight = false;
   int st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;  // per lane; summed at the end
 
+  // the first item of each warp is gw; the later ones come from a device work queue (items
+  // GW, GW + 1, ... in the order warps ask), which evens out items of uneven cost; each warp
+  // holds its next item's ticket and record one item ahead
+  auto ticket = [&]() -> int64_t {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.work_q, 1u);
+    return GW + (int64_t)__shfl_sync(0xffffffffu, t, 0);
+  };
   WItem nx;
   warp_item_load<PREC>(a, gw, n2, n1, lane, nx);
-  for (int64_t w = gw; w < items; w += GW) {
+  int64_t wnext = ticket();
+  for (int64_t w = gw; w < items;) {
     const WItem cur = nx;
-    if (w + GW < items) warp_item_load<PREC>(a, w + GW, n2, n1, lane, nx);
+    if (wnext < items) warp_item_load<PREC>(a, wnext, n2, n1, lane, nx);
     const int cls = cur.cls, lw = 3 + cls, VW = 1 << lw, G = 32 >> lw;
     const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
     const uint32_t gmask = low_bits32(VW);
@@ -1814,6 +1787,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       st_fired += ndead;
     }
     __syncwarp();
+    w = wnext;
+    if (w < items) wnext = ticket();
   }
   if (a.emit_redirects)
     for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
@@ -1926,6 +1901,7 @@ struct __align__(16) TeamSmem {
   uint64_t bar[2];
   unsigned long long red_next, red_end, red_b0, red_b1;
   int32_t red_avail;
+  int64_t next_p;                 // the team's next record (device work queue)
 };
 constexpr size_t kTeamRowsOff = (sizeof(TeamSmem) + 127) & ~(size_t)127;  // staged rows follow
 // BF16 rows of up to 128 dimensions: eight team CTAs fit one SM (233,472 bytes of shared
@@ -1978,20 +1954,24 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   int64_t nv = (int64_t)(r0[0] & 0xffffffffull);
   uint32_t nlo = (uint32_t)(r0[0] >> 32);
   int nm = (int)r0[1];
-  uint64_t nkey = tid < nm ? r0[2 + tid] : kEmpty;
+  uint64_t nkey = (tid < nm && in_bounds((uint64_t)nv < (uint64_t)a.n, a.err)) ? a.keys_in[nv * R + tid] : kEmpty;
+  // the first record of each team is its block index; the later ones come from a device work
+  // queue (records gridDim.x, gridDim.x + 1, ... in the order teams ask), one record ahead
+  if (tid == 0) s.next_p = (int64_t)gridDim.x + (int64_t)atomicAdd(a.work_q + 1, 1u);
+  __syncthreads();
+  int64_t pnext = s.next_p;
 
-
-  for (; p < cnt; p += gridDim.x) {
+  while (p < cnt) {
     const int64_t v = nv;
     const uint32_t lo = nlo;  // first id of the vertex's build
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
-    if (p + gridDim.x < cnt) {
-      const uint64_t* rn = a.rec[3] + (p + gridDim.x) * W;
+    if (pnext < cnt) {
+      const uint64_t* rn = a.rec[3] + pnext * W;
       nv = (int64_t)(rn[0] & 0xffffffffull);
       nlo = (uint32_t)(rn[0] >> 32);
       nm = (int)rn[1];
-      nkey = tid < nm ? rn[2 + tid] : kEmpty;
+      nkey = (tid < nm && in_bounds((uint64_t)nv < (uint64_t)a.n, a.err)) ? a.keys_in[nv * R + tid] : kEmpty;
     }
     // ---- visit order: rank of (h, id) among the m entries --------------------------------
     const uint32_t idl = key_id(keyl);
@@ -2324,8 +2304,11 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         st_pairs += np;
       }
       st_fired += ndead;
+      if (pnext < cnt) s.next_p = (int64_t)gridDim.x + (int64_t)atomicAdd(a.work_q + 1, 1u);
     }
     __syncthreads();
+    p = pnext;
+    pnext = s.next_p;
   }
   if (a.emit_redirects)
     for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
@@ -2902,6 +2885,7 @@ JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* ke
   a.count = ws.count;
   a.stats = stats;
   a.err = ws.err;
+  a.work_q = ws.work_q;
   a.warp_ctas = P.warp_ctas;
   a.team_ctas = P.team_ctas;
   return a;
@@ -2956,7 +2940,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          cudaStream_t st, bool use_hint, bool keys_canonical) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;  // list_n and red_n
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 48, st)) != cudaSuccess) return e;  // list_n, red_n, work queues
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, stats, st)) != cudaSuccess)
     return e;
@@ -2990,7 +2974,7 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, cudaStream_t st,
                          bool use_hint) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 48, st)) != cudaSuccess) return e;  // list_n, red_n, work queues
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, nullptr, st)) != cudaSuccess)
     return e;
@@ -3070,7 +3054,7 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
                            int32_t* deg_out, int64_t* stats, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 32, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.list_n, 0, 48, st)) != cudaSuccess) return e;  // list_n, red_n, work queues
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   {
     const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
@@ -3133,11 +3117,10 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }
 
 namespace {
-// work records of a size class holding up to cap entries: v, m, cap keys, cap (norm^2,
-// residual) pairs of the BF16 rows (an even number of words: 16-byte aligned records)
-// (classes 0..3 hold up to min(R, 8 << c) entries; class 4, only when R > 64, up to R)
+// work records of a size class: two words (v and its build's first id, m) per active vertex
+// (classes 0..3 hold pools of up to min(R, 8 << c) entries; class 4, only when R > 64, up to R)
 inline int rec_cap_of(int R, int c) { return c < 4 ? std::min(R, 8 << c) : (R > kTeamMaxM ? R : 0); }
-inline int rec_words(int cap) { return 2 + ((cap + 1) & ~1); }
+inline int rec_words(int cap) { return cap > 0 ? 2 : 0; }  // v | build's first id, m
 inline size_t rec_region_bytes(int64_t n, int R, int c) {
   const int cap = rec_cap_of(R, c);
   return cap > 0 ? al256((size_t)n * rec_words(cap) * 8) : 0;
@@ -3163,7 +3146,7 @@ size_t workspace_bytes(int64_t n, int R) {
   const size_t slots = red_slots(n, R);
   const size_t nb = (size_t)ceil_div(n, SCAN_TILE) + 1;
   return al256(slots * 4) + al256(slots * 8) + al256((size_t)n * R * 8) + al256((size_t)n * 4) +
-         al256(((size_t)n + 1) * 8) + al256(nb * 8) + 2 * al256((size_t)n) + rec_bytes(n, R) + al256(24) +
+         al256(((size_t)n + 1) * 8) + al256(nb * 8) + 2 * al256((size_t)n) + rec_bytes(n, R) + al256(48) +
          al256(4) + al256(8);
 }
 
@@ -3200,7 +3183,8 @@ bool carve_workspace(void* base, size_t bytes, int64_t n, int R, Workspace* ws) 
   }
   ws->list_n = reinterpret_cast<int32_t*>(p);  // [5] records per class, then the redirect count
   ws->red_n = reinterpret_cast<unsigned long long*>(p + 24);
-  p += al256(24);
+  ws->work_q = reinterpret_cast<unsigned int*>(p + 32);  // [3] work queues of the warp and team joins, one spare
+  p += al256(48);
   ws->err = reinterpret_cast<int32_t*>(p);
   p += al256(4);
   ws->round_new = reinterpret_cast<int64_t*>(p);

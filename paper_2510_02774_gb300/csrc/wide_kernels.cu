@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(XW) rnd_join_wide_kernel(JoinArgs a) {
     const uint32_t lo = (uint32_t)(rec[0] >> 32);  // first id of the vertex's build
     const int m = (int)rec[1];
     const bool has = tid < m;
-    const uint64_t key = has ? rec[2 + tid] : kEmpty;
+    const uint64_t key = (has && in_bounds((uint64_t)v < (uint64_t)a.n, a.err)) ? a.keys_in[v * R + tid] : kEmpty;
     const uint32_t idl = key_id(key);
     // ---- visit order and local rows ---------------------------------------------------
     uint64_t h = ~0ull;
