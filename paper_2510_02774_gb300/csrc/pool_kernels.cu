@@ -1408,19 +1408,20 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   int st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;  // per lane; summed at the end
 
   // the first item of each warp is gw; the later ones come from a device work queue (items
-  // GW, GW + 1, ... in the order warps ask), which evens out items of uneven cost; each warp
-  // holds its next item's ticket and record one item ahead
-  auto ticket = [&]() -> int64_t {
-    unsigned int t = 0;
-    if (lane == 0) t = atomicAdd(a.work_q, 1u);
-    return GW + (int64_t)__shfl_sync(0xffffffffu, t, 0);
-  };
+  // GW, GW + 1, ... in the order warps ask), which evens out items of uneven cost.  A warp
+  // holds its next item's record one item ahead, and asks for the item after that when the
+  // current one starts (the answer is read when it ends, so the atomic's latency is hidden)
   WItem nx;
   warp_item_load<PREC>(a, gw, n2, n1, lane, nx);
-  int64_t wnext = ticket();
+  unsigned int tq = 0;
+  if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+  int64_t wnext = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
   for (int64_t w = gw; w < items;) {
     const WItem cur = nx;
-    if (wnext < items) warp_item_load<PREC>(a, wnext, n2, n1, lane, nx);
+    if (wnext < items) {
+      warp_item_load<PREC>(a, wnext, n2, n1, lane, nx);
+      if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+    }
     const int cls = cur.cls, lw = 3 + cls, VW = 1 << lw, G = 32 >> lw;
     const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
     const uint32_t gmask = low_bits32(VW);
@@ -1788,7 +1789,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     }
     __syncwarp();
     w = wnext;
-    if (w < items) wnext = ticket();
+    if (w < items) wnext = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
   }
   if (a.emit_redirects)
     for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
@@ -1961,12 +1962,14 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   __syncthreads();
   int64_t pnext = s.next_p;
 
+  unsigned int tq = 0;  // thread 0: the ticket asked when a record starts, published when it ends
   while (p < cnt) {
     const int64_t v = nv;
     const uint32_t lo = nlo;  // first id of the vertex's build
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
     if (pnext < cnt) {
+      if (tid == 0) tq = atomicAdd(a.work_q + 1, 1u);
       const uint64_t* rn = a.rec[3] + pnext * W;
       nv = (int64_t)(rn[0] & 0xffffffffull);
       nlo = (uint32_t)(rn[0] >> 32);
@@ -2304,7 +2307,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         st_pairs += np;
       }
       st_fired += ndead;
-      if (pnext < cnt) s.next_p = (int64_t)gridDim.x + (int64_t)atomicAdd(a.work_q + 1, 1u);
+      if (pnext < cnt) s.next_p = (int64_t)gridDim.x + (int64_t)tq;
     }
     __syncthreads();
     p = pnext;
