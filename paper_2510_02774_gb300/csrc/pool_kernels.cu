@@ -1344,9 +1344,15 @@ struct WItem {
   uint64_t key;
 };
 
-template <int PREC>
-__device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int64_t n2, int64_t n1, int lane,
-                                               WItem& x) {
+// The work record of item w for this lane's group: the vertex word and m (m = 0: the group
+// has no vertex).  cnt: records per class 0..2.
+struct WRec {
+  uint64_t r0;
+  int m;
+  int cls;
+};
+__device__ __forceinline__ void warp_rec_load(const JoinArgs& a, int64_t w, int64_t n2, int64_t n1, const int cnt[3],
+                                              int lane, WRec& x) {
   int cls;
   int64_t it;
   if (w < n2) {
@@ -1360,21 +1366,25 @@ __device__ __forceinline__ void warp_item_load(const JoinArgs& a, int64_t w, int
     it = w - n2 - n1;
   }
   const int lw = 3 + cls;  // log2 of the group width
-  const int g = lane >> lw, gl = lane & ((1 << lw) - 1);
-  const int64_t rr = it * (32 >> lw) + g;
+  const int64_t rr = it * (32 >> lw) + (lane >> lw);
   x.cls = cls;
   x.m = 0;
-  x.lo = 0u;
-  x.v = -1;
-  x.key = kEmpty;
-
-  if (rr < (int64_t)a.list_n[cls]) {
+  x.r0 = 0;
+  if (rr < (int64_t)(cls == 2 ? cnt[2] : cls == 1 ? cnt[1] : cnt[0])) {
     const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
-    x.v = (int64_t)(r[0] & 0xffffffffull);
-    x.lo = (uint32_t)(r[0] >> 32);
+    x.r0 = r[0];
     x.m = (int)r[1];
-    if (gl < x.m && in_bounds((uint64_t)x.v < (uint64_t)a.n, a.err)) x.key = a.keys_in[x.v * a.R + gl];
   }
+}
+// The item of a loaded record: this lane's pool key (storage slot lane % group width).
+__device__ __forceinline__ void warp_item_of(const JoinArgs& a, const WRec& r, int lane, WItem& x) {
+  x.cls = r.cls;
+  x.m = r.m;
+  x.v = r.m > 0 ? (int64_t)(r.r0 & 0xffffffffull) : -1;
+  x.lo = (uint32_t)(r.r0 >> 32);
+  x.key = kEmpty;
+  const int gl = lane & ((8 << r.cls) - 1);
+  if (gl < x.m && in_bounds((uint64_t)x.v < (uint64_t)a.n, a.err)) x.key = a.keys_in[x.v * a.R + gl];
 }
 
 template <int METRIC, int PREC>
@@ -1384,7 +1394,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   using T = typename C::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSlot<PREC>& s = reinterpret_cast<WarpSlot<PREC>*>(smem_raw)[wid];
-  const int64_t n2 = a.list_n[2], n1 = (a.list_n[1] + 1) / 2, n0 = (a.list_n[0] + 3) / 4;
+  const int cnt[3] = {a.list_n[0], a.list_n[1], a.list_n[2]};
+  const int64_t n2 = cnt[2], n1 = (cnt[1] + 1) / 2, n0 = (cnt[0] + 3) / 4;
   const int64_t items = n2 + n1 + n0;
   const int64_t gw = (int64_t)blockIdx.x * WW + wid, GW = (int64_t)gridDim.x * WW;
   if (gw >= items || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
@@ -1407,20 +1418,32 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   bool inflight = false;
   int st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;  // per lane; summed at the end
 
-  // the first item of each warp is gw; the later ones come from a device work queue (items
-  // GW, GW + 1, ... in the order warps ask), which evens out items of uneven cost.  A warp
-  // holds its next item's record one item ahead, and asks for the item after that when the
-  // current one starts (the answer is read when it ends, so the atomic's latency is hidden)
+  // The first item of each warp is gw; the later ones come from a device work queue (items
+  // GW, GW + 1, ... in the order warps ask), which evens out items of uneven cost.  Loads are
+  // pipelined so that no item waits for memory: when item w starts, the pool keys of the next
+  // item w1 (whose record arrived during item w - 1) and the record of the item after, w2
+  // (whose ticket arrived during item w - 1), are requested, and the ticket after w2 is asked.
   WItem nx;
-  warp_item_load<PREC>(a, gw, n2, n1, lane, nx);
+  WRec nrec;
+  warp_rec_load(a, gw, n2, n1, cnt, lane, nrec);
+  warp_item_of(a, nrec, lane, nx);
   unsigned int tq = 0;
   if (lane == 0) tq = atomicAdd(a.work_q, 1u);
   int64_t wnext = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
+  if (wnext < items) {
+    warp_rec_load(a, wnext, n2, n1, cnt, lane, nrec);
+    if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+  }
   for (int64_t w = gw; w < items;) {
     const WItem cur = nx;
+    int64_t w2 = items;
     if (wnext < items) {
-      warp_item_load<PREC>(a, wnext, n2, n1, lane, nx);
-      if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+      warp_item_of(a, nrec, lane, nx);
+      w2 = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
+      if (w2 < items) {
+        warp_rec_load(a, w2, n2, n1, cnt, lane, nrec);
+        if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+      }
     }
     const int cls = cur.cls, lw = 3 + cls, VW = 1 << lw, G = 32 >> lw;
     const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
@@ -1789,7 +1812,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     }
     __syncwarp();
     w = wnext;
-    if (w < items) wnext = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
+    wnext = w2;
   }
   if (a.emit_redirects)
     for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
@@ -1956,25 +1979,36 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   uint32_t nlo = (uint32_t)(r0[0] >> 32);
   int nm = (int)r0[1];
   uint64_t nkey = (tid < nm && in_bounds((uint64_t)nv < (uint64_t)a.n, a.err)) ? a.keys_in[nv * R + tid] : kEmpty;
-  // the first record of each team is its block index; the later ones come from a device work
-  // queue (records gridDim.x, gridDim.x + 1, ... in the order teams ask), one record ahead
+  // The first record of each team is its block index; the later ones come from a device work
+  // queue (records gridDim.x, gridDim.x + 1, ... in the order teams ask).  Loads are pipelined
+  // so that no record waits for memory: when record p starts, the pool keys of the next record
+  // (whose words arrived during the record before) are requested, the ticket asked then is
+  // published, and the words of the record it names are requested.
   if (tid == 0) s.next_p = (int64_t)gridDim.x + (int64_t)atomicAdd(a.work_q + 1, 1u);
   __syncthreads();
   int64_t pnext = s.next_p;
+  __syncthreads();  // (thread 0 writes the next ticket there when the first record starts)
+  uint64_t qr0 = 0;  // the words of record pnext
+  int qm = 0;
+  unsigned int tq = 0;  // thread 0: the ticket of the record after pnext
+  if (pnext < cnt) {
+    const uint64_t* rn = a.rec[3] + pnext * W;
+    qr0 = rn[0];
+    qm = (int)rn[1];
+    if (tid == 0) tq = atomicAdd(a.work_q + 1, 1u);
+  }
 
-  unsigned int tq = 0;  // thread 0: the ticket asked when a record starts, published when it ends
   while (p < cnt) {
     const int64_t v = nv;
     const uint32_t lo = nlo;  // first id of the vertex's build
     const int m = nm;
     const uint64_t keyl = tid < m ? nkey : kEmpty;
     if (pnext < cnt) {
-      if (tid == 0) tq = atomicAdd(a.work_q + 1, 1u);
-      const uint64_t* rn = a.rec[3] + pnext * W;
-      nv = (int64_t)(rn[0] & 0xffffffffull);
-      nlo = (uint32_t)(rn[0] >> 32);
-      nm = (int)rn[1];
+      nv = (int64_t)(qr0 & 0xffffffffull);
+      nlo = (uint32_t)(qr0 >> 32);
+      nm = qm;
       nkey = (tid < nm && in_bounds((uint64_t)nv < (uint64_t)a.n, a.err)) ? a.keys_in[nv * R + tid] : kEmpty;
+      if (tid == 0) s.next_p = (int64_t)gridDim.x + (int64_t)tq;
     }
     // ---- visit order: rank of (h, id) among the m entries --------------------------------
     const uint32_t idl = key_id(keyl);
@@ -1998,6 +2032,13 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     }
     if (tid == 0) s.nrq = 0;
     __syncthreads();
+    const int64_t p2 = pnext < cnt ? s.next_p : cnt;  // the record after pnext
+    if (p2 < cnt) {
+      const uint64_t* rn = a.rec[3] + p2 * W;
+      qr0 = rn[0];
+      qm = (int)rn[1];
+      if (tid == 0) tq = atomicAdd(a.work_q + 1, 1u);
+    }
     // rows: the new entries first, then the old ones, each part in storage-slot order (the
     // pairs are enumerated over rows: new row i, any later row j, so the order inside each
     // part does not matter); the first chunk's copies are in flight while the visit order
@@ -2307,11 +2348,10 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         st_pairs += np;
       }
       st_fired += ndead;
-      if (pnext < cnt) s.next_p = (int64_t)gridDim.x + (int64_t)tq;
     }
     __syncthreads();
     p = pnext;
-    pnext = s.next_p;
+    pnext = p2;
   }
   if (a.emit_redirects)
     for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
