@@ -85,12 +85,17 @@ typedef struct grnnd_graph grnnd_graph; /* opaque, library-owned */
  * by a lane group of 8 lanes (four pools per warp) if m <= group_max[0], else of 16 lanes
  * (two per warp) if m <= group_max[1], else of 32 lanes if m <= group_max[2], else by a
  * 64-thread CTA; 0 <= group_max[c] <= 8 << c.  warp_ctas_per_sm / team_ctas_per_sm cap the
- * resident CTAs per SM of the two join kernels (0: as many as fit).  Only speed depends on
- * it: every tuning gives the same graph.  Defaults {8, 16, 32}, 0, 0. */
+ * resident CTAs per SM of the two join kernels (0: as many as fit); row_copies picks how the
+ * warp join stages quantized rows in shared memory.  Only speed depends on it: every tuning
+ * gives the same graph.  Defaults {8, 16, 32}, 0, 0, 0. */
 typedef struct grnnd_tuning {
     int32_t group_max[3];
     int32_t warp_ctas_per_sm;
     int32_t team_ctas_per_sm;
+    int32_t row_copies;   /* BF16 / FP8 rows of the warp join: 1 = one bulk copy per row,
+                             2 = TMA gather4 copies of four rows each (where the rows' layout
+                             allows: fewer copy instructions, 2-way bank conflicts in the tiles),
+                             0 = gather4 for BF16 rows of at most 128 dimensions, else 1 */
     float ms;             /* grnnd_autotune: build time of the chosen tuning on the sample */
 } grnnd_tuning;
 
@@ -121,7 +126,8 @@ GRNND_API void grnnd_params_default(grnnd_params *p);
  * grnnd_build_batch) once per candidate tuning and writes the fastest to *best (with its
  * time in best->ms).  Candidates: the lane-group routing {8,16,32}, {0,16,32}, {0,0,32},
  * {8,16,16} and {0,16,16}, then 1..3 warp-kernel CTAs and 2, 4 or 6 team CTAs per SM around
- * the best, one axis at a time.  p->tuning is ignored.  Synchronous. */
+ * the best, one axis at a time, then (BF16 / FP8) row_copies 1 and 2.  p->tuning is ignored.
+ * Synchronous. */
 GRNND_API int grnnd_autotune(const float *points, int64_t n, int32_t d, const int64_t *offsets,
                              int32_t nbuild, const grnnd_params *p, grnnd_tuning *best);
 

@@ -553,6 +553,7 @@ int check_params(const grnnd_params* p) {
         return fail(GRNND_EINVAL, "tuning: need 0 <= group_max[c] <= 8 << c");
     if (t->warp_ctas_per_sm < 0 || t->team_ctas_per_sm < 0)
       return fail(GRNND_EINVAL, "tuning: CTAs per SM must be >= 0");
+    if (t->row_copies < 0 || t->row_copies > 2) return fail(GRNND_EINVAL, "tuning: row_copies must be 0, 1 or 2");
   }
   return GRNND_OK;
 }
@@ -662,6 +663,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
     for (int c = 0; c < 3; ++c) P.group_max[c] = t->group_max[c];
     P.warp_ctas = t->warp_ctas_per_sm;
     P.team_ctas = t->team_ctas_per_sm;
+    P.row_copies = t->row_copies;
   }
   if (quant && step_points(X, n, d, ld, p->metric, p->precision, qp, q_b, &P) != GRNND_OK)
     return fail(GRNND_EINVAL, "internal quantized layout");
@@ -875,7 +877,7 @@ int grnnd_autotune(const float* points, int64_t n, int32_t d, const int64_t* off
     *ms = m;
     return GRNND_OK;
   };
-  grnnd_tuning cur{{8, 16, 32}, 0, 0, 0.0f};
+  grnnd_tuning cur{{8, 16, 32}, 0, 0, 0, 0.0f};
   float cur_ms = 0.0f;
   if ((rc = trial(cur, &cur_ms))) return rc;
   const int32_t routes[4][3] = {{0, 16, 32}, {0, 0, 32}, {8, 16, 16}, {0, 16, 16}};
@@ -902,6 +904,16 @@ int grnnd_autotune(const float* points, int64_t n, int32_t d, const int64_t* off
     float ms;
     if ((rc = trial(t, &ms))) return rc;
     if (ms < cur_ms) cur = t, cur_ms = ms;
+  }
+  if (p->precision != GRNND_FP32) {  // quantized rows: one bulk copy per row, or gather4 copies
+    base = cur;
+    for (int r = 1; r <= 2; ++r) {
+      grnnd_tuning t = base;
+      t.row_copies = r;
+      float ms;
+      if ((rc = trial(t, &ms))) return rc;
+      if (ms < cur_ms) cur = t, cur_ms = ms;
+    }
   }
   cur.ms = cur_ms;
   *best = cur;

@@ -62,6 +62,8 @@ struct PointsSet {
   // Join launch shape (grnnd_tuning): lane-group routing by pool size, CTAs per SM caps.
   int group_max[3] = {8, 16, 32};
   int warp_ctas = 0, team_ctas = 0;
+  int row_copies = 0;  // quantized rows of the warp join: 1 one bulk copy per row, 2 gather4 (where
+                       // possible), 0 gather4 for BF16 rows of at most 128 dimensions, else 1
 };
 
 // Where a build's device memory comes from: cudaMalloc / cudaFree (pool == nullptr), or

@@ -15,6 +15,12 @@ constexpr int kMaxRWide = 256;    // largest pool capacity R of the library
 constexpr int kRedChunk = 1024;   // redirect slots a join CTA reserves at a time, at most
 constexpr int64_t kMaxJoinGrid = 2048;  // CTAs of one join kernel at most (sizes the redirect slack)
 
+// A TMA tensor map: the driver's 128-byte, 64-byte aligned descriptor, passed to a kernel by
+// value (as a __grid_constant__ parameter) and named to the copy by its address.
+struct alignas(64) TmaMap {
+  unsigned long long w[16];
+};
+
 struct PointsDev {
   const float* X;
   int ld;
@@ -26,6 +32,10 @@ struct PointsDev {
 };
 
 struct JoinArgs {
+  // the quantized rows as a 2-D tensor (ldb columns x n rows; boxes of one 128-column chunk
+  // plus the first 16 bytes after it, one row high) for the warp join's gather4 copies
+  TmaMap rows_map;
+  int rows_tma;  // 1: the warp join stages quantized rows by gather4 copies through rows_map
   PointsDev P;
   int64_t n;
   int R;

@@ -8,6 +8,7 @@
 //                 (Alg 6) over fixed-capacity pools (Sec 3.5)
 //   reverse       reverse-edge sampling (Sec 3.6) feeding the same merge
 //   quantize      BF16 copy of the points + per-row norm and residual for the BF16 form
+#include <cuda.h>  // CUtensorMap and the types of cuTensorMapEncodeTiled (fetched at run time)
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -1298,23 +1299,39 @@ struct WPrec<0> {
   using T = float;
   static constexpr int RS = WDC + 4;
   static constexpr int VEC = 4;
+  static constexpr int RSB = RS * 4;    // bytes per staged row
+  static constexpr int GB = 4 * RSB;    // bytes per four rows (rows are contiguous: no gather4)
 };
 template <>
 struct WPrec<1> {
   using T = __nv_bfloat16;
   static constexpr int RS = WDC + 8;
   static constexpr int VEC = 16;
+  static constexpr int RSB = RS * 2;                 // 272 bytes: one gather4 box row
+  static constexpr int GB = (4 * RSB + 127) & ~127;  // four rows of one gather4, 128-byte aligned
 };
 template <>
 struct WPrec<2> {
   using T = uint8_t;                  // e4m3 bytes
   static constexpr int RS = WDC + 16; // 144-byte rows, as for BF16 in bytes per 64 columns
   static constexpr int VEC = 32;      // whole k32 steps (32 bytes)
+  static constexpr int RSB = RS;
+  static constexpr int GB = (4 * RSB + 127) & ~127;
 };
 
-template <int PREC>
-struct __align__(16) WarpSlot {
-  typename WPrec<PREC>::T rows[WM][WPrec<PREC>::RS];  // by row: group base + local row
+// The staged rows of a warp: row r (group base + local row) at (r / 4) * GS + (r % 4) * RSB
+// bytes.  With one bulk copy per row GS = 4 * RSB: rows are contiguous, and the 8 rows of an
+// ldmatrix phase (RSB / 16 odd) hit distinct banks.  With gather4 copies (TMA) GS = GB, so
+// that every four rows, the destination of one copy, start on a 128-byte boundary; rows r and
+// r + 4 then share banks (a 2-way conflict in every ldmatrix phase).
+template <int PREC, bool TMA>
+struct WLayout {
+  static constexpr int GS = TMA ? WPrec<PREC>::GB : 4 * WPrec<PREC>::RSB;
+};
+template <int PREC, bool TMA>
+struct __align__(128) WarpSlot {
+  unsigned char rowb[(WM / 4) * WLayout<PREC, TMA>::GS];
+  int32_t rid[WM];              // by row: the point id whose row is staged there
   float pd[WM * (WM - 1) / 2];  // group g's pairs from g * VW (VW - 1) / 2
   int32_t pid[WM];              // by position: group base + local pi position
   uint32_t fire[WM];            // by position; bits: earlier local positions that fired with it
@@ -1322,7 +1339,7 @@ struct __align__(16) WarpSlot {
   float rdq[WM];                // by row: norm of the quantization residual
   int32_t roff[WM];             // by row: local index of the first pair of new row i
   uint8_t rpos[WM], prow[WM];   // local position of a row / local row of a position
-  uint8_t inv[WM];              // by storage slot (group base + slot): local position
+  uint8_t src[WM];              // by position (group base + position): local storage slot
   uint8_t kil[WM];              // by position: the column that absorbed it (chain rounds)
   uint16_t rq[WRQ];             // pairs (row i << 5 | row j) whose decision is re-taken in FP32
   int32_t nrq;                  // queued re-decisions of the item
@@ -1330,6 +1347,26 @@ struct __align__(16) WarpSlot {
   uint64_t bar;
   unsigned long long red_next, red_end;
 };
+
+template <int PREC, bool TMA>
+__device__ __forceinline__ typename WPrec<PREC>::T* wrow(WarpSlot<PREC, TMA>& s, int r) {
+  return reinterpret_cast<typename WPrec<PREC>::T*>(s.rowb + (r >> 2) * WLayout<PREC, TMA>::GS +
+                                                    (r & 3) * WPrec<PREC>::RSB);
+}
+
+// TMA gather of four rows (y0..y3) of a 2-D tensor, columns x .. x + box - 1, into four
+// consecutive box rows at dst (128-byte aligned); completion counted on `bar` (4 x box bytes,
+// out-of-range elements read as zero).  x times the element size is a multiple of 16 bytes.
+__device__ __forceinline__ void tma_gather4(void* dst, const TmaMap* map, int x, int y0, int y1, int y2, int y3,
+                                            uint64_t* bar) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(d),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(b)
+      : "memory");
+}
 
 __device__ __forceinline__ uint32_t lanes_below32(int p) { return p == 0 ? 0u : (0xffffffffu >> (32 - p)); }
 __device__ __forceinline__ uint32_t low_bits32(int w) { return w >= 32 ? 0xffffffffu : ((1u << w) - 1u); }
@@ -1345,10 +1382,10 @@ struct WItem {
 };
 
 // The work record of item w for this lane's group: the vertex word and m (m = 0: the group
-// has no vertex).  cnt: records per class 0..2.
+// has no vertex).  cnt: records per class 0..2.  Class 2 items come first (one vertex of
+// 17..32 entries per warp), then class 1 (two of 9..16), then class 0 (four of at most 8).
 struct WRec {
-  uint64_t r0;
-  int m;
+  ulonglong2 r;
   int cls;
 };
 __device__ __forceinline__ void warp_rec_load(const JoinArgs& a, int64_t w, int64_t n2, int64_t n1, const int cnt[3],
@@ -1368,32 +1405,31 @@ __device__ __forceinline__ void warp_rec_load(const JoinArgs& a, int64_t w, int6
   const int lw = 3 + cls;  // log2 of the group width
   const int64_t rr = it * (32 >> lw) + (lane >> lw);
   x.cls = cls;
-  x.m = 0;
-  x.r0 = 0;
-  if (rr < (int64_t)(cls == 2 ? cnt[2] : cls == 1 ? cnt[1] : cnt[0])) {
-    const uint64_t* r = a.rec[cls] + rr * a.rec_w[cls];
-    x.r0 = r[0];
-    x.m = (int)r[1];
-  }
+  x.r = make_ulonglong2(0ull, 0ull);
+  if (rr < (int64_t)(cls == 2 ? cnt[2] : cls == 1 ? cnt[1] : cnt[0])) x.r = *reinterpret_cast<const ulonglong2*>(a.rec[cls] + rr * a.rec_w[cls]);
 }
 // The item of a loaded record: this lane's pool key (storage slot lane % group width).
 __device__ __forceinline__ void warp_item_of(const JoinArgs& a, const WRec& r, int lane, WItem& x) {
   x.cls = r.cls;
-  x.m = r.m;
-  x.v = r.m > 0 ? (int64_t)(r.r0 & 0xffffffffull) : -1;
-  x.lo = (uint32_t)(r.r0 >> 32);
+  x.m = (int)r.r.y;
+  x.v = x.m > 0 ? (int64_t)(r.r.x & 0xffffffffull) : -1;
+  x.lo = (uint32_t)(r.r.x >> 32);
   x.key = kEmpty;
   const int gl = lane & ((8 << r.cls) - 1);
   if (gl < x.m && in_bounds((uint64_t)x.v < (uint64_t)a.n, a.err)) x.key = a.keys_in[x.v * a.R + gl];
 }
 
-template <int METRIC, int PREC>
-__global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
+// TMA: quantized rows staged by gather4 copies through a.rows_map (else one bulk copy per row)
+template <int METRIC, int PREC, bool TMA>
+__global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_constant__ JoinArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using C = WPrec<PREC>;
   using T = typename C::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  WarpSlot<PREC>& s = reinterpret_cast<WarpSlot<PREC>*>(smem_raw)[wid];
+  // the warp slots start on a 128-byte boundary (the launch adds 128 bytes for this)
+  unsigned char* const sbase = smem_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u);
+  WarpSlot<PREC, TMA>& s = reinterpret_cast<WarpSlot<PREC, TMA>*>(sbase)[wid];
+  static_assert(!TMA || PREC >= 1, "gather4 copies are for quantized rows");
   const int cnt[3] = {a.list_n[0], a.list_n[1], a.list_n[2]};
   const int64_t n2 = cnt[2], n1 = (cnt[1] + 1) / 2, n0 = (cnt[0] + 3) / 4;
   const int64_t items = n2 + n1 + n0;
@@ -1467,8 +1503,28 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
                       in_bounds((uint64_t)id_s < (uint64_t)a.n, a.err);
     const uint32_t needm = __ballot_sync(0xffffffffu, need);
     const int nch = needm ? nchd : 0;
-    auto issue = [&](int c) {  // the bulk copies of chunk c, completing on the warp's mbarrier
+    if (TMA && valid_s) s.rid[gb + row_s] = (int32_t)id_s;
+    auto issue = [&](int c) {  // the copies of chunk c, completing on the warp's mbarrier
       const int c0 = c * WDC;
+      if constexpr (TMA) {
+        // one gather4 per four rows of a group with pairs, issued by the lane of the first of
+        // them (rows gb + gl .. gb + gl + 3 = lane .. lane + 3); a group's last copy repeats
+        // its first row in the places past m.  Each copies whole boxes: the chunk's columns
+        // and, after the last chunk, the first 16 bytes of the row's tail.
+        const bool iss = need && (gl & 3) == 0;
+        const uint32_t im = __ballot_sync(0xffffffffu, iss);
+        if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(im) * 4u * (uint32_t)C::RSB);
+        inflight = true;
+        __syncwarp();
+        if (iss) {
+          int4 q = *reinterpret_cast<const int4*>(&s.rid[lane]);
+          if (gl + 1 >= m) q.y = q.x;
+          if (gl + 2 >= m) q.z = q.x;
+          if (gl + 3 >= m) q.w = q.x;
+          tma_gather4(wrow(s, lane), &a.rows_map, c0, q.x, q.y, q.z, q.w, &s.bar);
+        }
+        return;
+      }
       const int cpy = (min(WDC, d - c0) + C::VEC - 1) / C::VEC * C::VEC;
       // a quantized row's last chunk brings the row's terms (norm^2, residual) along
       const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
@@ -1478,43 +1534,50 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       if (need) {
         const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id_s * a.P.ld + c0)
                                    : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)id_s * a.P.ldb + c0;
-        bulk_g2s(&s.rows[gb + row_s][0], src, bytes, &s.bar);
+        bulk_g2s(wrow(s, gb + row_s), src, bytes, &s.bar);
       }
     };
     if (nch > 0) issue(0);
 
-    // ---- visit order: bitonic sort of (h, id, source lane) within each lane group ---------
+    // ---- visit order: the position of each entry is its rank in (h, id) order in its group --
+    // Ranks count, per entry, the group's entries with a smaller key: over the high 32 bits
+    // of h alone when those are distinct in every group (two of 32 hashes share them with
+    // probability about 1e-7), else over the full (h, id).  (The serial orders put their
+    // index in the high bits.)
     const uint32_t idl = key_id(keyl);
     uint64_t h = ~0ull;
-    uint32_t hid = 0xffffffffu, hs = (uint32_t)lane;
-    if (gl < m) {
-      h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - cur.lo),
-                                          (uint64_t)(idl - cur.lo))
-          : (a.order == 1) ? (uint64_t)gl
-                           : (uint64_t)(m - 1 - gl);
-      hid = idl;
-    }
-#pragma unroll
-    for (int kk = 2; kk <= 32; kk <<= 1) {
-      if (kk > VW) break;
-#pragma unroll
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        const uint64_t oh = __shfl_xor_sync(0xffffffffu, h, jj);
-        const uint32_t oid = __shfl_xor_sync(0xffffffffu, hid, jj);
-        const uint32_t os = __shfl_xor_sync(0xffffffffu, hs, jj);
-        const bool up = (kk == VW) || ((lane & kk) == 0);
-        const bool lower = (lane & jj) == 0;
-        const bool other_less = (oh < h) || (oh == h && oid < hid);
-        const bool take = (lower == up) ? other_less : !other_less;
-        if (take) {
-          h = oh;
-          hid = oid;
-          hs = os;
+    if (valid_s)
+      h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - cur.lo), (uint64_t)(idl - cur.lo))
+          : (a.order == 1) ? (uint64_t)gl << 32
+                           : (uint64_t)(m - 1 - gl) << 32;
+    int pi_s = gl;  // this storage slot's position (slots past m keep positions m .. VW - 1)
+    {
+      const uint32_t k32 = (uint32_t)(h >> 32);
+      const uint64_t mv = valid_s ? (((uint64_t)g << 32) | k32) : (~0ull << 32) | (uint64_t)lane;
+      const bool tie = __any_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, mv)) > 1);
+      int r = 0;
+      if (!tie) {
+#pragma unroll 8
+        for (int j = 0; j < VW; ++j) {
+          const uint32_t kj = __shfl_sync(0xffffffffu, k32, gb + j);
+          r += (j < m && kj < k32) ? 1 : 0;
+        }
+      } else {
+        for (int j = 0; j < VW; ++j) {
+          const uint64_t hj = __shfl_sync(0xffffffffu, h, gb + j);
+          const uint32_t ij = __shfl_sync(0xffffffffu, idl, gb + j);
+          r += (j < m && (hj < h || (hj == h && ij < idl))) ? 1 : 0;
         }
       }
+      if (valid_s) {
+        pi_s = r;
+        s.src[gb + r] = (uint8_t)gl;
+      }
     }
-    // lane gb + p now holds local pi position p: its source lane hs (storage slot hs - gb)
-    const int slot = (int)hs - gb;
+    __syncwarp();
+    // lane gb + p takes local pi position p: its source lane hs (storage slot hs - gb)
+    const int hs = gb + (gl < m ? (int)s.src[lane] : gl);
+    const int slot = hs - gb;
     const uint64_t key = __shfl_sync(0xffffffffu, keyl, (int)hs);
     const bool valid_p = gl < m;
     const uint32_t below = lanes_below32(gl);
@@ -1525,7 +1588,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       s.pid[P] = id;
       s.prow[P] = (uint8_t)row;
       s.rpos[gb + row] = (uint8_t)gl;
-      s.inv[hs] = (uint8_t)gl;  // storage slot -> pi position
       if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
       // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
       s.rnd[gb + row] = make_float2(0.0f, key_dist(key));
@@ -1542,7 +1604,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
     // slots' position bits
     uint32_t closer_p;
     {
-      const uint32_t bit = gl < m ? (1u << s.inv[lane]) : 0u;  // this lane as storage slot
+      const uint32_t bit = valid_s ? (1u << pi_s) : 0u;  // this lane as storage slot
       uint32_t x = bit;
 #pragma unroll
       for (int dd = 1; dd < 32; dd <<= 1) {
@@ -1567,7 +1629,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
         if (need) {
           const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-          const float2 t = *reinterpret_cast<const float2*>(&s.rows[gb + row_s][cpy]);
+          const float2 t = *reinterpret_cast<const float2*>(wrow(s, gb + row_s) + cpy);
           s.rnd[gb + row_s].x = t.x;
           s.rdq[gb + row_s] = t.y;
         }
@@ -1576,7 +1638,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
       if (PREC >= 1) {
         // tiles one at a time; partial dot products wait in pd between chunks (d > 128),
         // and the last chunk takes the fire decisions straight from the accumulators
-        const T* rows = &s.rows[0][0];
         constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
         const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
         const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
@@ -1606,8 +1667,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
           const int ra = I * 16 + (lane & 15);
           const int rb = J * 8 + (lane & 7);
-          const T* pa = rows + ra * C::RS + (lane >> 4) * KB;
-          const T* pb = rows + rb * C::RS + ((lane >> 3) & 1) * KB;
+          const T* pa = wrow(s, ra) + (lane >> 4) * KB;
+          const T* pb = wrow(s, rb) + ((lane >> 3) & 1) * KB;
           for (int ks = 0; ks < ksteps; ++ks) {
             uint32_t fa[4], fb[2];
             ldmatrix_x4(fa, pa + ks * 2 * KB);
@@ -1664,7 +1725,6 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           }
         }
       } else {
-        const float* rows = reinterpret_cast<const float*>(&s.rows[0][0]);
         const int full4 = clen & ~3, rem = clen & 3;
         for (int q = gl; q < np; q += VW) {
           int i = 0;  // the new local row owning pair q
@@ -1672,8 +1732,8 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
           for (int w2 = 16; w2 > 0; w2 >>= 1)
             if (i + w2 < k && s.roff[gb + i + w2] <= q) i += w2;
           const int j = i + 1 + (q - s.roff[gb + i]);
-          const float* ra = rows + (gb + i) * C::RS;
-          const float* rb = rows + (gb + j) * C::RS;
+          const float* ra = reinterpret_cast<const float*>(wrow(s, gb + i));
+          const float* rb = reinterpret_cast<const float*>(wrow(s, gb + j));
           float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           for (int u = 0; u < full4; u += 4)
             dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
@@ -1836,11 +1896,11 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(JoinArgs a) {
   }
 }
 
-template <int METRIC, int PREC>
-cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* name, bool setup_only = false) {
-  const size_t smem = sizeof(WarpSlot<PREC>) * WW;
+template <int METRIC, int PREC, bool TMA>
+cudaError_t launch_join_warp_v(const JoinArgs& a, cudaStream_t st, const char* name, bool setup_only) {
+  const size_t smem = sizeof(WarpSlot<PREC, TMA>) * WW + 128;  // + alignment of the slots
   static KernelSetup ks;
-  auto kern = rnd_join_warp_kernel<METRIC, PREC>;
+  auto kern = rnd_join_warp_kernel<METRIC, PREC, TMA>;
   int per_sm = 0;
   cudaError_t e = setup_kernel(ks, kern, WW * 32, smem, smem, &per_sm);
   if (e != cudaSuccess || setup_only) return e;
@@ -1850,6 +1910,13 @@ cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* n
   ProfScope ps(name, st);
   kern<<<(unsigned)blocks, WW * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int METRIC, int PREC>
+cudaError_t launch_join_warp_t(const JoinArgs& a, cudaStream_t st, const char* name, bool setup_only = false) {
+  if constexpr (PREC >= 1)
+    if (a.rows_tma) return launch_join_warp_v<METRIC, PREC, true>(a, st, name, setup_only);
+  return launch_join_warp_v<METRIC, PREC, false>(a, st, name, setup_only);
 }
 
 }  // namespace
@@ -2892,11 +2959,62 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
   return cudaGetLastError();
 }
 
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+}  // namespace
+
+// The quantized rows (n rows of ldb elements: bfloat16 for BF16, bytes for FP8) as a 2-D
+// tensor map whose box is one staged row of the warp join (its 128-column chunk and the 16
+// bytes after it) and one row high, for gather4 copies.  False (the join then copies row by
+// row) when the rows do not meet the copy's rules: base 16-byte aligned, row pitch a multiple
+// of 16 bytes, at most 2^31 - 1 rows.
+bool encode_rows_map(TmaMap* m, const void* Xb, int64_t n, int ldb, int precision) {
+  static_assert(sizeof(TmaMap) == sizeof(CUtensorMap) && alignof(TmaMap) >= 64, "tensor map layout");
+  if (!Xb || n <= 0 || n > INT32_MAX || ldb <= 0) return false;
+  const bool bf = precision == GRNND_BF16;
+  if (!bf && precision != GRNND_FP8) return false;
+  const int esz = bf ? 2 : 1;
+  const cuuint32_t box = bf ? (cuuint32_t)WPrec<1>::RS : (cuuint32_t)WPrec<2>::RS;
+  if ((reinterpret_cast<uintptr_t>(Xb) & 15u) || ((int64_t)ldb * esz) % 16 != 0) return false;
+  const EncodeTiledFn f = encode_tiled();
+  if (!f) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ldb, (cuuint64_t)n};
+  const cuuint64_t pitch[1] = {(cuuint64_t)ldb * (cuuint64_t)esz};
+  const cuuint32_t boxd[2] = {box, 1u};
+  const cuuint32_t es[2] = {1u, 1u};
+  const CUresult r = f(reinterpret_cast<CUtensorMap*>(m), bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                       2u, const_cast<void*>(Xb), dims, pitch, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 JoinArgs make_join_args(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
                         const int32_t* deg_in, uint64_t seed, int t1, int t2, int order,
                         const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int emit,
                         int64_t* stats) {
   JoinArgs a;
+  // gather4 copies: fewer copy instructions, but 2-way bank conflicts in the tiles; measured
+  // faster for BF16 rows of one 128-column chunk, slower for longer rows and for FP8
+  const bool gather4 = P.row_copies == 2 || (P.row_copies == 0 && P.precision == GRNND_BF16 && P.d <= 128);
+  a.rows_tma = (gather4 && P.Xb && (P.precision == GRNND_BF16 || P.precision == GRNND_FP8) &&
+                encode_rows_map(&a.rows_map, P.Xb, n, P.ldb, P.precision))
+                   ? 1
+                   : 0;
   a.P.X = P.X;
   a.P.ld = P.ld;
   a.P.Xb = P.Xb;

@@ -37,18 +37,18 @@ class GrnndError(RuntimeError):
 class Tuning(ctypes.Structure):
     """grnnd_tuning: lane-group routing by pool size and CTAs-per-SM caps of the join."""
     _fields_ = [("group_max", ctypes.c_int32 * 3), ("warp_ctas_per_sm", ctypes.c_int32),
-                ("team_ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("team_ctas_per_sm", ctypes.c_int32), ("row_copies", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self):
         return {"group_max": list(self.group_max), "warp_ctas_per_sm": self.warp_ctas_per_sm,
-                "team_ctas_per_sm": self.team_ctas_per_sm, "ms": self.ms}
+                "team_ctas_per_sm": self.team_ctas_per_sm, "row_copies": self.row_copies, "ms": self.ms}
 
 
-def tuning(group_max=(8, 16, 32), warp_ctas_per_sm=0, team_ctas_per_sm=0) -> Tuning:
+def tuning(group_max=(8, 16, 32), warp_ctas_per_sm=0, team_ctas_per_sm=0, row_copies=0) -> Tuning:
     t = Tuning()
     for c in range(3):
         t.group_max[c] = group_max[c]
-    t.warp_ctas_per_sm, t.team_ctas_per_sm = warp_ctas_per_sm, team_ctas_per_sm
+    t.warp_ctas_per_sm, t.team_ctas_per_sm, t.row_copies = warp_ctas_per_sm, team_ctas_per_sm, row_copies
     return t
 
 

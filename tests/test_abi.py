@@ -122,6 +122,10 @@ def test_tuning_is_validated(L):
         p = G.params(S=4, R=8, tuning=t)
         assert L.grnnd_build_ex(pts, 100, 4, ctypes.byref(p), ctypes.byref(h)) == G.EINVAL
         assert b"tuning" in L.grnnd_last_error()
+    for rc in (-1, 3):
+        p = G.params(S=4, R=8, tuning=G.tuning(row_copies=rc))
+        assert L.grnnd_build_ex(pts, 100, 4, ctypes.byref(p), ctypes.byref(h)) == G.EINVAL
+        assert b"row_copies" in L.grnnd_last_error()
 
 
 def test_server_validates_before_any_cuda_call(L):

@@ -764,12 +764,30 @@ def test_tunings_give_the_same_graph(G, precision, metric):
             assert (a == b).all(), (gm, w, t)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("d", [40, 128, 200, 300])
+def test_row_copies_give_the_same_graph(G, precision, d):
+    """The warp join stages quantized rows by TMA gather4 copies (four rows per copy, boxes of
+    one 128-column chunk plus 16 bytes; out-of-range columns read as zero) or by one bulk copy
+    per row: the same rows arrive, so the graphs are equal, on integer data (exact tiles) and
+    on Gaussian data (tiles with FP32 re-decisions), with one chunk (d <= 128, the box wider
+    than the row for d = 40) and several (d = 200, 300)."""
+    prec = {"bf16": G.BF16, "fp8": G.FP8}[precision]
+    kw = dict(S=16, R=32, T1=2, T2=4, seed=5, precision=prec)
+    for X in (synth.small_integers(3000, d, -8, 8, seed=d), synth.gaussian_mixture(3000, d, 10, seed=d)):
+        a = G.build(X, tuning=G.tuning(row_copies=2), **kw).to_numpy()
+        b = G.build(X, tuning=G.tuning(row_copies=1), **kw).to_numpy()
+        for u, v in zip(a, b):
+            assert (u == v).all()
+
+
 def test_autotune_picks_a_candidate(G):
     X = synth.small_integers(4000, 32, -8, 8, seed=8)
     t = G.autotune(X, S=16, R=32, T1=2, T2=4, precision=G.BF16)
     assert t.ms > 0
     assert list(t.group_max) in ([8, 16, 32], [0, 16, 32], [0, 0, 32], [8, 16, 16], [0, 16, 16])
     assert 0 <= t.warp_ctas_per_sm <= 3 and t.team_ctas_per_sm in (0, 2, 4, 6)
+    assert t.row_copies in (0, 1, 2)
 
 
 # ---------------------------------------------------------------------------------------
