@@ -1454,31 +1454,36 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
   bool inflight = false;
   int st_vert = 0, st_rows = 0, st_pairs = 0, st_fired = 0, st_check = 0;  // per lane; summed at the end
 
-  // The first item of each warp is gw; the later ones come from a device work queue (items
-  // GW, GW + 1, ... in the order warps ask), which evens out items of uneven cost.  Loads are
-  // pipelined so that no item waits for memory: when item w starts, the pool keys of the next
-  // item w1 (whose record arrived during item w - 1) and the record of the item after, w2
-  // (whose ticket arrived during item w - 1), are requested, and the ticket after w2 is asked.
+  // Items below S go to the warps in turn (warp gw takes gw, gw + GW, ...); the last ones,
+  // S, S + 1, ..., come from a device work queue in the order warps ask, which evens out the
+  // end of the launch without an atomic per item.  Loads are pipelined so that no item waits
+  // for memory: when item w starts, the pool keys of the next item w1 (whose record arrived
+  // during item w - 1) and the record of the item after, w2, are requested; a queue ticket is
+  // asked one item before it is needed.
+  const int64_t S = items > 5 * GW ? items - 4 * GW : (items < GW ? items : GW);
   WItem nx;
   WRec nrec;
   warp_rec_load(a, gw, n2, n1, cnt, lane, nrec);
   warp_item_of(a, nrec, lane, nx);
   unsigned int tq = 0;
-  if (lane == 0) tq = atomicAdd(a.work_q, 1u);
-  int64_t wnext = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
+  int64_t wnext = gw + GW;
+  if (wnext >= S) {
+    if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+    wnext = S + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
+  }
   if (wnext < items) {
     warp_rec_load(a, wnext, n2, n1, cnt, lane, nrec);
-    if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+    if (lane == 0 && wnext + GW >= S) tq = atomicAdd(a.work_q, 1u);
   }
   for (int64_t w = gw; w < items;) {
     const WItem cur = nx;
     int64_t w2 = items;
     if (wnext < items) {
       warp_item_of(a, nrec, lane, nx);
-      w2 = GW + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
+      w2 = wnext + GW < S ? wnext + GW : S + (int64_t)__shfl_sync(0xffffffffu, tq, 0);
       if (w2 < items) {
         warp_rec_load(a, w2, n2, n1, cnt, lane, nrec);
-        if (lane == 0) tq = atomicAdd(a.work_q, 1u);
+        if (lane == 0 && w2 + GW >= S) tq = atomicAdd(a.work_q, 1u);
       }
     }
     const int cls = cur.cls, lw = 3 + cls, VW = 1 << lw, G = 32 >> lw;
@@ -1975,7 +1980,10 @@ struct __align__(16) TeamKey {
 
 struct __align__(16) TeamSmem {
   union {
-    TeamKey hk[TM];                 // order key by storage slot (visit order), until the tiles
+    struct {
+      TeamKey hk[TM];               // order key by storage slot (visit order), until the tiles
+      uint32_t hk32[TM];            // its high 32 hash bits (~0 past m)
+    };
     float pd[TM * (TM - 1) / 2];    // per pair: its distance (partial dot product between chunks)
   };
   uint64_t fire[TM], closer[TM];  // by pi position; bit a < b: pair (a, b) fired / a is closer
@@ -2081,17 +2089,18 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     const uint32_t idl = key_id(keyl);
     const bool has = tid < m;
     uint64_t h = ~0ull;
-    if (has)
+    if (has)  // (the serial orders put their index in the high bits)
       h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - lo),
                                           (uint64_t)(idl - lo))
-          : (a.order == 1) ? (uint64_t)tid
-                           : (uint64_t)(m - 1 - tid);
+          : (a.order == 1) ? (uint64_t)tid << 32
+                           : (uint64_t)(m - 1 - tid) << 32;
     {
       TeamKey hk;
       hk.h = h;
       hk.id = has ? idl : 0xffffffffu;
       hk.pad = 0u;
       s.hk[tid] = hk;
+      s.hk32[tid] = has ? (uint32_t)(h >> 32) : 0xffffffffu;
     }
     {
       const unsigned nw = __ballot_sync(0xffffffffu, has && !key_old(keyl));  // new entries by slot
@@ -2137,17 +2146,21 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
     };
     if (nch > 0) issue(0, stage);
+    // position = rank of the entry's key among the m entries: over the high 32 hash bits
+    // (entries past m hold ~0 there and never count), then checked: equal high bits leave
+    // two entries with one rank, and the ranks are taken again over the full (h, id)
     int pi = 0;
     if (has) {
-#pragma unroll 4
-      for (int f = 0; f < m; ++f) {
-        const TeamKey o = s.hk[f];
-        pi += (o.h < h) || (o.h == h && o.id < idl);
+      const uint32_t k32 = (uint32_t)(h >> 32);
+      for (int f = 0; f < m; f += 4) {
+        const uint4 o = *reinterpret_cast<const uint4*>(&s.hk32[f]);
+        pi += (o.x < k32 ? 1 : 0) + (o.y < k32 ? 1 : 0) + (o.z < k32 ? 1 : 0) + (o.w < k32 ? 1 : 0);
       }
+      s.prow[pi] = (uint8_t)tid;  // this rank's claim
     }
     // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
     // closer mask of a position is the OR of the position bits of the slots before its own
-    const uint64_t pbit = has ? (1ull << pi) : 0ull;
+    uint64_t pbit = has ? (1ull << pi) : 0ull;
     uint64_t pre = pbit;
 #pragma unroll
     for (int dd = 1; dd < 32; dd <<= 1) {
@@ -2156,6 +2169,23 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     }
     if (warp == 0 && lane == 31) s.wtot = pre;
     __syncthreads();
+    if (__syncthreads_or(has && s.prow[pi] != (uint8_t)tid)) {  // a tie in the high bits
+      pi = 0;
+      if (has)
+        for (int f = 0; f < m; ++f) {
+          const TeamKey o = s.hk[f];
+          pi += (o.h < h) || (o.h == h && o.id < idl);
+        }
+      pbit = has ? (1ull << pi) : 0ull;
+      pre = pbit;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
+        if (lane >= dd) pre |= y;
+      }
+      if (warp == 0 && lane == 31) s.wtot = pre;
+      __syncthreads();
+    }
     if (warp == 1) pre |= s.wtot;
     if (has) {
       s.pid[pi] = (int32_t)idl;
