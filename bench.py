@@ -34,11 +34,11 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # ncu DRAM bytes (read + write) per unit of the join -- one round, i.e. its warp and team
 # launches -- for the workload above: DRAM bytes per algorithmic byte of the join, measured by
 # an ncu capture of rounds 1 and 2 of a 600,000-point build of the same generator (BF16 rows
-# of 173 MB, larger than L2; 0.8653 = 8.469 GB / 9.787 GB), times the full workload's
+# of 173 MB, larger than L2; 0.8571 = 8.389 GB / 9.787 GB), times the full workload's
 # algorithmic bytes per round (2.2025e9); reported only while the join kernels' code is
 # unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 0.8653 * 2.2025e9,
-           "source_sha256": "64f411b1c481049c41b70340c104bbea910d55d241f881ab5f418e8977d1a452"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 0.8571 * 2.2025e9,
+           "source_sha256": "e48b8856c7ccf943e8994ed8090c4cde9c89c391b100f4bbd4fa1249384a8fb6"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm

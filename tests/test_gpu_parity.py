@@ -140,6 +140,31 @@ def test_join_round_matches_oracle(G, orc, n, d, S, R, order, metric, hist):
         p = want
 
 
+# ids 26175 and 54119 share the high 32 bits of their visit-order hash at seed 1, round
+# (1, 1), vertex 0 (found by searching the oracle's hash); the kernels rank visit orders
+# over those bits and must fall back to the full (h, id) order for such a pool
+TIE_SEED, TIE_IDS = 1, (26175, 54119)
+
+
+@pytest.mark.parametrize("m", [12, 30, 50])
+def test_join_round_visit_order_tie_in_high_hash_bits(G, orc, m):
+    ha, hb = (orc.counter_hash(TIE_SEED, 1, 1, 0, i) for i in TIE_IDS)
+    assert ha >> 32 == hb >> 32 and ha != hb
+    n, d, R = 60000, 8, 64
+    X = synth.small_integers(n, d, -8, 8, seed=m)
+    rng = np.random.default_rng(m)
+    others = rng.choice(np.setdiff1d(np.arange(1, n), TIE_IDS), m - 2, replace=False)
+    ids = np.concatenate([others, TIE_IDS]).astype(np.int64)
+    dist = np.array([orc.dist(X[0], X[i]) for i in ids])
+    o = np.lexsort((ids, dist))
+    p = orc.Pool.empty(n, R)
+    p.ids[0, :m], p.dist[0, :m], p.deg[0] = ids[o], dist[o], m
+    Xd, _ = G.device_points(X)
+    want, _, _ = orc.round_(X, p, TIE_SEED, 1, 1)
+    keys, deg = G.join_round(Xd, d, to_keys(G, p), torch.from_numpy(p.deg).cuda(), TIE_SEED, 1, 1)
+    assert_pool_equal(G, keys, deg, want)
+
+
 def test_join_round_skips_old_pairs_exactly(G, orc):
     # the device always skips old x old pairs; the oracle evaluates them: same pools
     X = synth.small_integers(1500, 10, -8, 8, seed=5)
