@@ -430,16 +430,22 @@ struct RecSet {
   int cap[kNumClasses];
 };
 
-__global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
+constexpr int kPrepWarps = 8;  // warps per prep block (256 threads)
+__global__ void __launch_bounds__(kPrepWarps * 32) prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
                             int64_t n, int R, uint8_t* __restrict__ active,
                             int32_t* __restrict__ list_n, int warp_ok, int3 gmax, RecSet rs,
                             const int2* __restrict__ vseg,
                             const uint8_t* __restrict__ hint, int64_t* __restrict__ stats) {
-  const int lane = threadIdx.x & 31;
+  // record places: a warp counts its active vertices per class (ballots), the block adds
+  // its warps' counts up and takes one range per class from list_n (one atomic per block and
+  // class, not per warp: the class counters are few addresses that every block hits)
+  __shared__ int s_cnt[kPrepWarps][kNumClasses];  // per warp; then its first place in the block's range
+  __shared__ int s_base[kNumClasses];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long props = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-    const int64_t v = base + lane;
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {  // uniform over the block
+    const int64_t v = b0 + threadIdx.x;
     bool act = false;
     int m = 0;
     if (v < n) {
@@ -453,29 +459,54 @@ __global__ void prep_kernel(const uint64_t* __restrict__ keys, const int32_t* __
     }
     const int cls = m > kTeamMaxM ? 4 : !warp_ok ? 3 : (m <= gmax.x ? 0 : (m <= gmax.y ? 1 : (m <= gmax.z ? 2 : 3)));
     unsigned bc[kNumClasses];
-    int off[kNumClasses];
 #pragma unroll
     for (int c = 0; c < kNumClasses; ++c) {
       bc[c] = __ballot_sync(0xffffffffu, act && cls == c);
-      int o = 0;
-      if (lane == 0 && bc[c]) o = atomicAdd(&list_n[c], __popc(bc[c]));
-      off[c] = __shfl_sync(0xffffffffu, o, 0);
+      if (lane == 0) s_cnt[warp][c] = __popc(bc[c]);
     }
+    __syncthreads();
+    if (threadIdx.x < kNumClasses) {
+      const int c = threadIdx.x;
+      int tot = 0;
+      for (int w = 0; w < kPrepWarps; ++w) {
+        const int x = s_cnt[w][c];
+        s_cnt[w][c] = tot;
+        tot += x;
+      }
+      s_base[c] = tot ? atomicAdd(&list_n[c], tot) : 0;
+    }
+    __syncthreads();
     // each active vertex writes its record: v and its build's first id, and m (the join reads
     // the pool keys from the vertex's own row, which nothing else writes before its join)
     if (act) {
-      uint64_t* r = rs.rec[0] + (int64_t)(off[0] + __popc(bc[0] & lanemask_lt())) * rs.w[0];
+      unsigned mb = bc[0];
+      int o = s_base[0] + s_cnt[warp][0];
+      uint64_t* rg = rs.rec[0];
+      int W = rs.w[0];
 #pragma unroll
-      for (int c = 1; c < kNumClasses; ++c)
-        if (cls == c) r = rs.rec[c] + (int64_t)(off[c] + __popc(bc[c] & lanemask_lt())) * rs.w[c];
+      for (int q = 1; q < kNumClasses; ++q)
+        if (cls == q) {
+          mb = bc[q];
+          o = s_base[q] + s_cnt[warp][q];
+          rg = rs.rec[q];
+          W = rs.w[q];
+        }
+      uint64_t* r = rg + (int64_t)(o + __popc(mb & lanemask_lt())) * W;
       r[0] = (uint64_t)v | ((uint64_t)(vseg ? vseg[v].x : 0) << 32);
       r[1] = (uint64_t)m;
     }
   }
-  if (stats) {
+  if (stats) {  // (every thread of the block gets here: the loop above is uniform over it)
+    __shared__ long long s_props[kPrepWarps];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) props += __shfl_xor_sync(0xffffffffu, props, o);
-    if (lane == 0 && props) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[4]), (unsigned long long)props);
+    if (lane == 0) s_props[warp] = props;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long t = 0;
+      for (int w = 0; w < kPrepWarps; ++w) t += s_props[w];
+      if (t) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[4]), (unsigned long long)t);
+    }
   }
 }
 
@@ -1434,7 +1465,35 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
   const int64_t n2 = cnt[2], n1 = (cnt[1] + 1) / 2, n0 = (cnt[0] + 3) / 4;
   const int64_t items = n2 + n1 + n0;
   const int64_t gw = (int64_t)blockIdx.x * WW + wid, GW = (int64_t)gridDim.x * WW;
-  if (gw >= items || *(volatile int32_t*)a.err) return;  // nothing to do, or the round has failed
+  // The counters (a.stats) of the CTA's warps are added up in shared memory; the last warp
+  // to leave adds them to the global counters: one atomic per CTA and counter, not per warp
+  // (the counters are a few addresses that every CTA hits when the launch ends).
+  __shared__ unsigned long long s_st[5];
+  __shared__ int s_left;
+  if (threadIdx.x < 5) s_st[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) s_left = WW;
+  __syncthreads();
+  auto leave = [&](long long c0, long long c1, long long c2, long long c3, long long c4) {  // lane 0
+    if (!a.stats) return;
+    if (c0) atomicAdd(&s_st[0], (unsigned long long)c0);
+    if (c1) atomicAdd(&s_st[1], (unsigned long long)c1);
+    if (c2) atomicAdd(&s_st[2], (unsigned long long)c2);
+    if (c3) atomicAdd(&s_st[3], (unsigned long long)c3);
+    if (c4) atomicAdd(&s_st[4], (unsigned long long)c4);
+    __threadfence_block();
+    if (atomicSub(&s_left, 1) == 1) {  // the CTA's last warp
+      __threadfence_block();
+      unsigned long long* g = reinterpret_cast<unsigned long long*>(a.stats);
+      const int slot[5] = {0, 1, 2, 3, 7};
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        if (s_st[q]) atomicAdd(&g[slot[q]], s_st[q]);
+    }
+  };
+  if (gw >= items || *(volatile int32_t*)a.err) {  // nothing to do, or the round has failed
+    if (lane == 0) leave(0, 0, 0, 0, 0);
+    return;
+  }
   const int R = a.R, d = a.P.d;
   const int nchd = (d + WDC - 1) / WDC;
   const uint64_t head = hash_head(a.seed, (uint64_t)a.t1, (uint64_t)a.t2);  // visit-order hash, uniform part
@@ -1759,6 +1818,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
       if (inflight) mbar_wait(&s.bar, phb, kWaitLimit);  // let this warp's copies land
       if (a.emit_redirects)
         for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+      if (lane == 0) leave(0, 0, 0, 0, 0);
       return;
     }
     // queued re-decisions, one per lane: the FP32 rows of every pair load at once
@@ -1824,7 +1884,9 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
     const int nkeep = __popc(alive & validm);
     if (m > 0 && in_bounds((uint64_t)v < (uint64_t)a.n, a.err)) {
       if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
-      for (int t = nkeep + gl; t < R; t += VW) a.keys_out[v * R + t] = kEmpty;
+      // in place, the slots past m are empty already (pool rows end in empty slots)
+      const int pend = a.keys_out == a.keys_in ? m : R;
+      for (int t = nkeep + gl; t < pend; t += VW) a.keys_out[v * R + t] = kEmpty;
       if (gl == 0) a.deg_out[v] = nkeep;
     }
     const int ndead = m - nkeep;
@@ -1890,14 +1952,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
       st_fired += __shfl_xor_sync(0xffffffffu, st_fired, o);
       st_check += __shfl_xor_sync(0xffffffffu, st_check, o);
     }
-    if (lane == 0) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)st_vert);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)st_rows);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)st_pairs);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)st_fired);
-      if (PREC >= 1 && st_check)
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[7]), (unsigned long long)st_check);
-    }
+    if (lane == 0) leave(st_vert, st_rows, st_pairs, st_fired, PREC >= 1 ? st_check : 0);
   }
 }
 
@@ -2421,7 +2476,9 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
     const uint64_t smask = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);  // survivors by slot
     const bool vok = in_bounds((uint64_t)v < (uint64_t)a.n, a.err);
     if (surv && vok) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
-    for (int t = nkeep + tid; vok && t < R; t += TM) a.keys_out[v * R + t] = kEmpty;
+    // in place, the slots past m are empty already (pool rows end in empty slots)
+    const int pend = a.keys_out == a.keys_in ? m : R;
+    for (int t = nkeep + tid; vok && t < pend; t += TM) a.keys_out[v * R + t] = kEmpty;
     if (tid == 0 && vok) a.deg_out[v] = nkeep;
     if (a.emit_redirects && has && !surv) {
       const int kp = s.killer[pi];
@@ -2825,7 +2882,28 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   long long n_new = 0, n_in = 0;
   // in place (keys_out == keys_in): every row already holds the target's base pool
   const bool in_place = a.keys_out == a.keys_in;
-  if (*a.err) return;
+  // the new-entry and proposal counts of the block's warps are added up in shared memory and
+  // the last warp to leave adds them to the global counters (one atomic per block, not per
+  // warp: the counters are two addresses that every block hits)
+  __shared__ unsigned long long s_cnt[2];
+  __shared__ int s_left;
+  if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) s_left = blockDim.x >> 5;
+  __syncthreads();
+  auto leave = [&](long long nn, long long ni) {  // lane 0
+    if (nn) atomicAdd(&s_cnt[0], (unsigned long long)nn);
+    if (ni) atomicAdd(&s_cnt[1], (unsigned long long)ni);
+    __threadfence_block();
+    if (atomicSub(&s_left, 1) == 1) {  // the block's last warp
+      __threadfence_block();
+      if (s_cnt[0]) atomicAdd(reinterpret_cast<unsigned long long*>(a.round_new), s_cnt[0]);
+      if (a.stats && s_cnt[1]) atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[6]), s_cnt[1]);
+    }
+  };
+  if (*a.err) {
+    if (lane == 0) leave(0, 0);
+    return;
+  }
   bool old_pass = a.old_pass != 0;
   if (!old_pass && a.qflags) {
     const float mxa = __uint_as_float(a.qflags[1]);
@@ -2940,10 +3018,7 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
     }
     if (a.next_active && ul < a.n && (merged_l || a.next_active_all)) a.next_active[ul] = mynew ? 1 : 0;
   }
-  if (lane == 0) {
-    if (n_new) atomicAdd(reinterpret_cast<unsigned long long*>(a.round_new), (unsigned long long)n_new);
-    if (a.stats && n_in) atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[6]), (unsigned long long)n_in);
-  }
+  if (lane == 0) leave(n_new, n_in);
 }
 
 cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t st) {
@@ -2972,7 +3047,7 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
 
 cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Workspace& ws,
                      const PointsSet& P, const uint8_t* hint, int64_t* stats, cudaStream_t st) {
-  const int64_t blocks = std::min<int64_t>(ceil_div(ws.n, 256), (int64_t)sm_count() * 8);
+  const int64_t blocks = std::min<int64_t>(ceil_div(ws.n, kPrepWarps * 32), (int64_t)sm_count() * 8);
   ProfScope ps("prep", st);
   // the warp kernels take FP32 rows of up to 128 dimensions (BF16 rows of any length)
   const int warp_ok = (P.precision == 0 && P.d > 128) ? 0 : 1;
@@ -2983,8 +3058,7 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
     rs.cap[c] = ws.rec_cap[c];
   }
   const int3 gmax = make_int3(P.group_max[0], P.group_max[1], P.group_max[2]);
-  // (the join kernels read the quantized rows' terms themselves, a vertex ahead of their use)
-  prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
+  prep_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
                                                 gmax, rs, P.vseg, hint, stats);
   return cudaGetLastError();
 }
@@ -3199,44 +3273,56 @@ cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* k
 // floor(rho * deg) entries of its row (the closest ones); every pool is then merged
 // with the proposals it received.
 // =====================================================================================
-__global__ void reverse_propose_kernel(int64_t n, int R, float rho,
-                                       const uint64_t* __restrict__ keys,
-                                       const int32_t* __restrict__ deg,
-                                       int32_t* __restrict__ tgt, uint64_t* __restrict__ pk,
-                                       unsigned long long* __restrict__ red_n,
-                                       int32_t* __restrict__ count, int64_t red_cap,
-                                       int32_t* __restrict__ err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t total = n * R;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    const int64_t i = base + lane;
-    bool emit = false;
-    int32_t t = -1;
-    uint64_t key = 0;
-    if (i < total) {
-      const int64_t v = i / R;
-      const int j = (int)(i - v * R);
-      const int r = (int)floor((double)rho * (double)deg[v]);
-      if (j < r) {
-        const uint64_t k = keys[i];
-        t = (int32_t)key_id(k);
-        key = (k & 0xFFFFFFFF00000000ull) | ((uint64_t)v << 1);
-        emit = true;
+// Reverse sampling (Sec 3.6): row v proposes its first floor(rho * deg) entries u (its nearest)
+// to u, as (d(v, u), v).  A block takes kRevRows rows at a time (each warp kRevRows / 8 of
+// them): the rows' proposal counts are known before any is written, so the block adds them
+// up and reserves its slots with one atomic (the slot counter is one address that every
+// block hits).
+constexpr int kRevWarps = 8, kRevRows = 32;
+__global__ void __launch_bounds__(kRevWarps * 32) reverse_propose_kernel(
+    int64_t n, int R, float rho, const uint64_t* __restrict__ keys, const int32_t* __restrict__ deg,
+    int32_t* __restrict__ tgt, uint64_t* __restrict__ pk, unsigned long long* __restrict__ red_n,
+    int32_t* __restrict__ count, int64_t red_cap, int32_t* __restrict__ err) {
+  __shared__ int s_r[kRevRows];      // proposals of each row of the block's chunk
+  __shared__ int s_pre[kRevRows];    // their first slot, from the chunk's base
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t r0 = (int64_t)blockIdx.x * kRevRows; r0 < n; r0 += (int64_t)gridDim.x * kRevRows) {  // block-uniform
+    if (threadIdx.x < kRevRows) {
+      const int64_t v = r0 + threadIdx.x;
+      s_r[threadIdx.x] = v < n ? (int)floor((double)rho * (double)deg[v]) : 0;
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive prefix over the chunk's rows, one per lane
+      const int x = s_r[lane];
+      int inc = x;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, dd);
+        if (lane >= dd) inc += y;
+      }
+      s_pre[lane] = inc - x;
+      unsigned long long b = 0;
+      if (lane == 31 && inc > 0) b = atomicAdd(red_n, (unsigned long long)inc);
+      if (lane == 31) s_base = b;
+    }
+    __syncthreads();
+    for (int q = warp; q < kRevRows; q += kRevWarps) {
+      const int64_t v = r0 + q;
+      const int r = s_r[q];
+      const unsigned long long sb = s_base + (unsigned long long)s_pre[q];
+      for (int j = lane; j < r; j += 32) {
+        const uint64_t k = keys[v * R + j];
+        const int32_t t = (int32_t)key_id(k);
+        const unsigned long long slot = sb + (unsigned long long)j;
+        if (in_bounds(slot < (unsigned long long)red_cap && (uint64_t)(uint32_t)t < (uint64_t)n, err)) {
+          tgt[slot] = t;
+          pk[slot] = (k & 0xFFFFFFFF00000000ull) | ((uint64_t)v << 1);
+          atomicAdd(&count[t], 1);
+        }
       }
     }
-    const unsigned b = __ballot_sync(0xffffffffu, emit);
-    unsigned long long off = 0;
-    if (lane == 0 && b) off = atomicAdd(red_n, (unsigned long long)__popc(b));
-    off = __shfl_sync(0xffffffffu, off, 0);
-    if (emit) {
-      const unsigned long long slot = off + __popc(b & lanemask_lt());
-      if (in_bounds(slot < (unsigned long long)red_cap && (uint64_t)(uint32_t)t < (uint64_t)n, err)) {
-        tgt[slot] = t;
-        pk[slot] = key;
-        atomicAdd(&count[t], 1);
-      }
-    }
+    __syncthreads();  // (s_r, s_pre and s_base are rewritten for the next chunk)
   }
 }
 
@@ -3248,9 +3334,9 @@ cudaError_t launch_reverse(int64_t n, int R, float rho, const uint64_t* keys_in,
   if ((e = cudaMemsetAsync(ws.list_n, 0, 48, st)) != cudaSuccess) return e;  // list_n, red_n, work queues
   if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
   {
-    const int64_t blocks = std::min<int64_t>(ceil_div(n * R, 256), (int64_t)sm_count() * 32);
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, kRevRows), (int64_t)sm_count() * 16);
     ProfScope ps("reverse_propose", st);
-    reverse_propose_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, R, rho, keys_in, deg_in, ws.red_tgt,
+    reverse_propose_kernel<<<(unsigned)blocks, kRevWarps * 32, 0, st>>>(n, R, rho, keys_in, deg_in, ws.red_tgt,
                                                             ws.red_key, ws.red_n, ws.count, ws.red_cap,
                                                             ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

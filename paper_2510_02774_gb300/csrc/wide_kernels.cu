@@ -333,7 +333,9 @@ __global__ void __launch_bounds__(XW) rnd_join_wide_kernel(JoinArgs a) {
     __syncthreads();
     const bool vok = in_bounds((uint64_t)v < (uint64_t)a.n, a.err);
     if (surv && vok) a.keys_out[v * R + survbefore] = key | 1ull;
-    for (int t = nkeep + tid; vok && t < R; t += XW) a.keys_out[v * R + t] = kEmpty;
+    // in place, the slots past m are empty already (pool rows end in empty slots)
+    const int pend = a.keys_out == a.keys_in ? m : R;
+    for (int t = nkeep + tid; vok && t < pend; t += XW) a.keys_out[v * R + t] = kEmpty;
     if (tid == 0 && vok) a.deg_out[v] = nkeep;
     if (a.emit_redirects && has && !surv) {
       const int kp = s.killer[pi];
