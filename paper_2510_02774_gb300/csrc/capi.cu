@@ -5,6 +5,7 @@
 // reverse-edge sampling (Sec 3.6) after every outer iteration but the last, then the
 // optional final prune, the export to (ids, dists) rows and the search entry.
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -512,11 +513,14 @@ int grnnd_set_memory_cache(uint64_t bytes) {
 namespace {
 // Pinned host slots for the per-round probe of the build driver (one pair per host thread;
 // released at thread exit).
+// A round's status word and new-entry counter as they lie in the workspace (the counter 256
+// bytes after the status word), read back with one copy.
 struct RoundProbe {
-  int64_t fresh;
   int32_t err;
-  int32_t pad;
+  unsigned char pad[252];
+  int64_t fresh;
 };
+static_assert(offsetof(RoundProbe, fresh) == 256, "round probe layout");
 struct ProbeHolder {
   RoundProbe* p = nullptr;
   ~ProbeHolder() {
@@ -744,8 +748,12 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
       const int cur = (int)(rounds & 1);
       ++rounds;
       if (capture) continue;
-      GR_CU(cudaMemcpyAsync(&probe[cur].fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
-      GR_CU(cudaMemcpyAsync(&probe[cur].err, ws.err, 4, cudaMemcpyDeviceToHost, st));
+      if (reinterpret_cast<char*>(ws.round_new) == reinterpret_cast<char*>(ws.err) + 256) {
+        GR_CU(cudaMemcpyAsync(&probe[cur], ws.err, sizeof(RoundProbe), cudaMemcpyDeviceToHost, st));
+      } else {
+        GR_CU(cudaMemcpyAsync(&probe[cur].fresh, ws.round_new, 8, cudaMemcpyDeviceToHost, st));
+        GR_CU(cudaMemcpyAsync(&probe[cur].err, ws.err, 4, cudaMemcpyDeviceToHost, st));
+      }
       GR_CU(cudaEventRecord(rev[cur], st));
       if (prev >= 0) {  // the previous round's outcome, read while this one runs
         GR_CU(cudaEventSynchronize(rev[prev]));

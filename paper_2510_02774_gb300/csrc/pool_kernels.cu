@@ -435,7 +435,11 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prep_kernel(const uint64_t* _
                             int64_t n, int R, uint8_t* __restrict__ active,
                             int32_t* __restrict__ list_n, int warp_ok, int3 gmax, RecSet rs,
                             const int2* __restrict__ vseg,
-                            const uint8_t* __restrict__ hint, int64_t* __restrict__ stats) {
+                            const uint8_t* __restrict__ hint, int64_t* __restrict__ stats,
+                            int32_t* __restrict__ zero_count, int64_t* __restrict__ zero_new) {
+  // (zero_count, zero_new: the round's redirect counts and new-entry counter, cleared here
+  // instead of by separate memsets)
+  if (zero_new && blockIdx.x == 0 && threadIdx.x == 0) *zero_new = 0;
   // record places: a warp counts its active vertices per class (ballots), the block adds
   // its warps' counts up and takes one range per class from list_n (one atomic per block and
   // class, not per warp: the class counters are few addresses that every block hits)
@@ -449,6 +453,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prep_kernel(const uint64_t* _
     bool act = false;
     int m = 0;
     if (v < n) {
+      if (zero_count) zero_count[v] = 0;
       m = deg[v];
       props += m;
       if (hint)  // the last merge of these pools recorded which rows hold a new entry
@@ -2695,6 +2700,25 @@ __device__ __forceinline__ void list_insert(uint64_t& x0, uint64_t& x1, uint64_t
   if (lane + 32 >= R) x1 = kEmpty;
 }
 
+// list_insert when every copy of an id carries one key up to the old bit (a build's canonical
+// distances) and b is new: a copy already listed sits where b would go, and stays as it is.
+__device__ __forceinline__ void list_insert_exact(uint64_t& x0, uint64_t& x1, uint64_t b, int R) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t bk = b >> 1;  // (dist, id)
+  const int pos = __popc(__ballot_sync(0xffffffffu, (x0 >> 1) < bk)) + __popc(__ballot_sync(0xffffffffu, (x1 >> 1) < bk));
+  if (pos >= R) return;
+  const uint64_t at = __shfl_sync(0xffffffffu, pos < 32 ? x0 : x1, pos & 31);
+  if ((at >> 1) == bk) return;  // listed already (an empty slot never matches a finite key)
+  const uint64_t x0last = __shfl_sync(0xffffffffu, x0, 31);
+  uint64_t u0 = __shfl_up_sync(0xffffffffu, x0, 1);
+  uint64_t u1 = __shfl_up_sync(0xffffffffu, x1, 1);
+  if (lane == 0) u1 = x0last;
+  x0 = lane > pos ? u0 : (lane == pos ? b : x0);
+  x1 = lane + 32 > pos ? u1 : (lane + 32 == pos ? b : x1);
+  if (lane >= R) x0 = kEmpty;
+  if (lane + 32 >= R) x1 = kEmpty;
+}
+
 // Per-warp scratch of merge_chunk.
 struct __align__(16) MergeScratch {
   uint64_t row[64];   // the row as it came in (by index), then its kept entries, compacted
@@ -2957,7 +2981,10 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
                             (out1 != kEmpty && (out1 & 1ull) && key_id(out1) == idt);
           if (__any_sync(0xffffffffu, held) && lane == t) bl |= 1ull;
         }
-        for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
+        if (old_pass || !a.keys_canonical)
+          for (int t = 0; t < (int)c; ++t) list_insert(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
+        else
+          for (int t = 0; t < (int)c; ++t) list_insert_exact(out0, out1, __shfl_sync(0xffffffffu, bl, t), R);
       } else {  // chunks of 32 proposals merged into the row
         out0 = lane < na ? base[lane] : kEmpty;
         out1 = lane + 32 < na ? base[32 + lane] : kEmpty;
@@ -3021,7 +3048,7 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   if (lane == 0) leave(n_new, n_in);
 }
 
-cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t st) {
+cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t st, bool new_cleared = false) {
   const int64_t n = ws.n;
   if (sa.bucket) {
     const int64_t nb = ceil_div(n, SCAN_TILE);
@@ -3037,7 +3064,7 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
                                                                  n * ws.R);
     }
   }
-  cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
+  if (!new_cleared) cudaMemsetAsync(ws.round_new, 0, sizeof(int64_t), st);
   if (sa.R > kTeamMaxM) return launch_select_wide(sa, st);  // rows of more than 64 entries
   const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 16);
   ProfScope ps("select", st);
@@ -3046,7 +3073,8 @@ cudaError_t merge_tail(const Workspace& ws, const SelectArgs& sa, cudaStream_t s
 }
 
 cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Workspace& ws,
-                     const PointsSet& P, const uint8_t* hint, int64_t* stats, cudaStream_t st) {
+                     const PointsSet& P, const uint8_t* hint, int64_t* stats, cudaStream_t st,
+                     bool clear_round = false) {
   const int64_t blocks = std::min<int64_t>(ceil_div(ws.n, kPrepWarps * 32), (int64_t)sm_count() * 8);
   ProfScope ps("prep", st);
   // the warp kernels take FP32 rows of up to 128 dimensions (BF16 rows of any length)
@@ -3059,7 +3087,8 @@ cudaError_t run_prep(const uint64_t* keys_in, const int32_t* deg_in, const Works
   }
   const int3 gmax = make_int3(P.group_max[0], P.group_max[1], P.group_max[2]);
   prep_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, st>>>(keys_in, deg_in, ws.n, ws.R, ws.active, ws.list_n, warp_ok,
-                                                gmax, rs, P.vseg, hint, stats);
+                                                gmax, rs, P.vseg, hint, stats, clear_round ? ws.count : nullptr,
+                                                clear_round ? ws.round_new : nullptr);
   return cudaGetLastError();
 }
 
@@ -3204,10 +3233,17 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
                          const Workspace& ws, uint64_t* keys_out, int32_t* deg_out, int64_t* stats,
                          cudaStream_t st, bool use_hint, bool keys_canonical) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.count, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.list_n, 0, 48, st)) != cudaSuccess) return e;  // list_n, red_n, work queues
-  if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;  // this step's status
-  if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, stats, st)) != cudaSuccess)
+  // list_n, red_n, the work queues and this step's status word with one memset where they are
+  // adjacent (the workspace carve puts the status word 256 bytes after list_n); the redirect
+  // counts and the new-entry counter are cleared by prep
+  const bool adjacent = reinterpret_cast<char*>(ws.err) == reinterpret_cast<char*>(ws.list_n) + 256;
+  if (adjacent) {
+    if ((e = cudaMemsetAsync(ws.list_n, 0, 256 + 4, st)) != cudaSuccess) return e;
+  } else {
+    if ((e = cudaMemsetAsync(ws.list_n, 0, 48, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.err, 0, 4, st)) != cudaSuccess) return e;
+  }
+  if ((e = run_prep(keys_in, deg_in, ws, P, use_hint ? ws.next_active : nullptr, stats, st, true)) != cudaSuccess)
     return e;
   const JoinArgs a = make_join_args(P, n, R, keys_in, deg_in, seed, t1, t2, order, ws, keys_out,
                                     deg_out, 1, stats);
@@ -3231,7 +3267,7 @@ cudaError_t launch_round(const PointsSet& P, int64_t n, int R, const uint64_t* k
   sa.qflags = P.precision >= 1 ? P.qflags : nullptr;
   sa.d = P.d;
   sa.keys_canonical = keys_canonical ? 1 : 0;
-  return merge_tail(ws, sa, st);
+  return merge_tail(ws, sa, st, true);
 }
 
 cudaError_t launch_final(const PointsSet& P, int64_t n, int R, const uint64_t* keys_in,
