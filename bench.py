@@ -34,11 +34,11 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # ncu DRAM bytes (read + write) per unit of the join -- one round, i.e. its warp and team
 # launches -- for the workload above: DRAM bytes per algorithmic byte of the join, measured by
 # an ncu capture of rounds 1 and 2 of a 600,000-point build of the same generator (BF16 rows
-# of 173 MB, larger than L2; 0.8571 = 8.389 GB / 9.787 GB), times the full workload's
+# of 173 MB, larger than L2; 0.8135 = 7.962 GB / 9.787 GB), times the full workload's
 # algorithmic bytes per round (2.2025e9); reported only while the join kernels' code is
 # unchanged since that capture.
-TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 0.8571 * 2.2025e9,
-           "source_sha256": "e48b8856c7ccf943e8994ed8090c4cde9c89c391b100f4bbd4fa1249384a8fb6"}
+TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 0.8135 * 2.2025e9,
+           "source_sha256": "ea2de775982267655ca95c010a6b4509d3db053ed50bb3659bc65f5180e09380"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-gist", action="store_true",
+                    help="skip the GIST-shaped 1M x 960 line (BF16 and FP32 build, recall by beam) of a full-size run")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--forms", default="fp32,bf16", help="comma list of fp32, bf16, fp8 (the last one is the headline)")
     ap.add_argument("--report", choices=["precision", "ablation", "batched", "serve", "rounds"], default=None,
@@ -224,6 +226,52 @@ def join_algorithmic_bytes(rows, n, proposals, fired, rechecks, d, elem):
     written) once, each redirect written (target + key) and counted, and the FP32 rows of
     every re-decided pair (three rows: the pair and the row it is decided against)."""
     return rows * d * elem + n * 4 + proposals * 8 + fired * (12 + 4) + rechecks * 3 * d * 4
+
+
+def gist_line(seed):
+    """The same metric on the precision workload at full size: GIST-shaped 1M x 960 (continuous,
+    per-dimension scales spanning 100x), BF16 and FP32 forms, one warm-up and one timed build
+    each (CUDA events around the build call, points resident on the device), and recall@10
+    of 1000 held-out queries against exact k-NN at beams 64, 80, 96 and 128 (the smallest
+    beam reaching 0.95 is reported: at beam 64 this workload stays just below it)."""
+    import numpy as np
+    import torch
+    from paper_2510_02774_gb300 import grnnd, synth
+    n, nq, k = 1_000_000, 1000, 10
+    kw = dict(S=32, R=64, T1=4, T2=15, rho=0.6, seed=seed)
+    X, Q = synth.gist_like(n, nq, seed=seed)
+    d = X.shape[1]
+    Xd = torch.from_numpy(X).cuda()
+    Qt = torch.from_numpy(Q).cuda()
+    Xp, _ = grnnd.device_points(X)
+    Qp, _ = grnnd.device_points(Q)
+    del X
+    gt = grnnd.brute_knn(Xp, d, Qp, k)[0].cpu().numpy()
+    del Xp
+    out = {"workload": f"GIST1M-shaped synthetic: n={n}, d={d}, 500-cluster mixture, per-dimension scales "
+                       f"log-uniform in [0.1, 10]; S 32, R 64, T1 4, T2 15; {nq} held-out queries, k={k}",
+           "forms": {}}
+    for name, prec in (("bf16", grnnd.BF16), ("fp32", grnnd.FP32)):
+        grnnd.build(Xd, precision=prec, **kw)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        g = grnnd.build(Xd, precision=prec, **kw)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        by_beam = {}
+        for bm in (64, 80, 96, 128):
+            found = g.search(Qt, k, bm).cpu().numpy()
+            by_beam[bm] = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(found, gt)]))
+            if by_beam[bm] >= 0.95:
+                break
+        out["forms"][name] = {"build_ms": ms, "points_per_s": n / (ms / 1e3), "recall@10_by_beam": by_beam,
+                              "smallest_beam_recall_0.95": min((b for b, r in by_beam.items() if r >= 0.95),
+                                                               default=None)}
+        del g
+    out["bf16_speedup_vs_fp32"] = out["forms"]["fp32"]["build_ms"] / out["forms"]["bf16"]["build_ms"]
+    return out
 
 
 def run_precision_report(args):
@@ -792,6 +840,15 @@ def main():
                           f"(initialisation single-threaded), {dt:.1f} s"),
                "single_thread": {"value": rate1, "unit": "points/s", "cores": 1, "seconds": dt1}}
 
+    # ---- the same metric on the precision workload (GIST-shaped 1M x 960) ----------------
+    gist = None
+    if rank == 0 and world == 1 and n == WORKLOAD["n"] and not args.no_gist:
+        del Xd
+        try:
+            gist = gist_line(args.seed)
+        except Exception as ex:  # reported in the line; the headline above stands
+            gist = {"error": f"{type(ex).__name__}: {ex}"}
+
     if rank == 0:
         p99 = _pct(step_ms, 0.99)
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -820,7 +877,8 @@ def main():
                         "d2h_bytes_per_step": n * w["R"] * 4 + n * 4},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "kernels_ms": {k: round(v[1], 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])},
-                "build_stats": {k: v / args.steps for k, v in agg.items()}}
+                "build_stats": {k: v / args.steps for k, v in agg.items()},
+                "gist1m": gist}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -7,11 +7,13 @@ import pytest
 def test_report_modes_and_arms_resolve(monkeypatch):
     import bench
     for name in ("run_precision_report", "run_rounds_report", "run_ablation_report", "run_batched_report",
-                 "run_serve_report", "run_reference", "oracle_build_rate", "join_algorithmic_bytes", "main"):
+                 "run_serve_report", "run_reference", "oracle_build_rate", "join_algorithmic_bytes", "gist_line",
+                 "main"):
         assert callable(getattr(bench, name)), name
     for argv in (["bench.py"], ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
                  ["bench.py", "--report", "precision", "--shape", "deep", "--n", "1000"],
-                 ["bench.py", "--report", "rounds", "--rounds", "2"], ["bench.py", "--report", "serve"]):
+                 ["bench.py", "--report", "rounds", "--rounds", "2"], ["bench.py", "--report", "serve"],
+                 ["bench.py", "--no-gist", "--steps", "2"]):
         monkeypatch.setattr(sys, "argv", argv)
         a = bench._args()
         assert a.gpus == 1
