@@ -489,6 +489,16 @@ def run_batched_report(args):
         one = grnnd.build(X[int(off[b]):int(off[b + 1])], **kw)
         same &= bool((gs[b].to_numpy()[0] == one.to_numpy()[0]).all()) and gs[b].entry == one.entry
     bms = sorted(t[1] for t in tb)
+    # the pool-capacity autotuner on the largest build's generator (its rows plus 500 held-out
+    # queries): the fastest R of 16, 24, 32 whose graph reaches recall@10 >= 0.95 at beam 64,
+    # then the batched pass with that capacity
+    bmax = int(np.argmax(sizes))
+    Xs, Qs = synth.deep_like(int(sizes[bmax]), 500, seed=1000 + bmax)
+    kwp = {k2: v for k2, v in kw.items() if k2 != "R"}
+    R_pool, rec_pool, ms_pool = grnnd.autotune_pool(np.concatenate([Xs, Qs]), 500, [16, 24, 32],
+                                                    recall_target=0.95, k=10, beam=64, tuning=tune, **kwp)
+    tp, _ = timed(lambda: grnnd.build_batch(X, off, tuning=tune, **{**kw, "R": R_pool, "S": min(16, R_pool)}),
+                  max(3, args.steps))
     grnnd.profile_begin()
     grnnd.build_batch(X, off, tuning=tune, **kw)  # not captured while profiling
     torch.cuda.synchronize()
@@ -501,6 +511,9 @@ def run_batched_report(args):
             "sequential_ms": ts[0][1], "sequential_points_per_s": total / (ts[0][1] / 1e3),
             "speedup": ts[0][1] / bms[len(bms) // 2], "same_graphs_sampled": same,
             "tuning": tune.as_dict(), "batched_default_tuning_ms_p50": sorted(t[1] for t in tb0)[len(tb0) // 2],
+            "pool_autotune": {"sample_n": int(sizes[bmax]), "queries": 500, "candidates": [16, 24, 32],
+                              "recall_target": 0.95, "R": R_pool, "recall@10": rec_pool, "sample_build_ms": ms_pool,
+                              "batched_ms_p50": sorted(t[1] for t in tp)[len(tp) // 2]},
             "kernels_ms_profiled_pass": kern}
     print(json.dumps(line), flush=True)
 

@@ -131,6 +131,22 @@ GRNND_API void grnnd_params_default(grnnd_params *p);
 GRNND_API int grnnd_autotune(const float *points, int64_t n, int32_t d, const int64_t *offsets,
                              int32_t nbuild, const grnnd_params *p, grnnd_tuning *best);
 
+/* Pool-capacity autotuner (no counterpart in the paper): chooses the pool capacity R of a
+ * build -- the candidate that builds fastest among those whose graph reaches recall@k >=
+ * recall_target, or the one of highest recall when none does.  The last nq rows of `points`
+ * (n rows of d floats, host or device, as for grnnd_build_ex) are held out as queries; each
+ * candidate R builds the first n - nq rows with p's parameters but R and S = min(p->S, R),
+ * once to settle allocations and once timed, and its graph is searched (grnnd_search with
+ * k and beam) against the exact k nearest neighbours of the built rows (grnnd_brute_knn).
+ * The candidates are tried in the order given.  Writes the chosen R, its recall and its
+ * build time (ms) to *R_out, *recall_out and *ms_out (each may be NULL).  Validation:
+ * 1 <= ncand <= 64, every candidate 2 <= R <= 256, 1 <= nq <= n - 3, 1 <= k <= 32,
+ * k <= beam <= 256, 0 < recall_target <= 1.  Synchronous. */
+GRNND_API int grnnd_autotune_pool(const float *points, int64_t n, int32_t d, int64_t nq,
+                                  const grnnd_params *p, const int32_t *R_candidates, int32_t ncand,
+                                  float recall_target, int32_t k, int32_t beam, int32_t *R_out,
+                                  float *recall_out, float *ms_out);
+
 /* Memory cache of whole builds on the current device (no counterpart in the paper).  A build
  * allocates its device memory (points, graph, pools, round workspace: about 4 GB for 1M x 128
  * with R = 64) and frees the scratch part when it returns.  With bytes > 0, grnnd_build_ex and

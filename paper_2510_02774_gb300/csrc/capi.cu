@@ -928,6 +928,80 @@ int grnnd_autotune(const float* points, int64_t n, int32_t d, const int64_t* off
   return GRNND_OK;
 }
 
+int grnnd_autotune_pool(const float* points, int64_t n, int32_t d, int64_t nq, const grnnd_params* p,
+                        const int32_t* R_candidates, int32_t ncand, float recall_target, int32_t k,
+                        int32_t beam, int32_t* R_out, float* recall_out, float* ms_out) {
+  if (!points || !p || !R_candidates) return fail(GRNND_EINVAL, "points, params and candidates must be given");
+  if (ncand < 1 || ncand > 64) return fail(GRNND_EINVAL, "need 1 <= ncand <= 64");
+  for (int c = 0; c < ncand; ++c)
+    if (R_candidates[c] < 2 || R_candidates[c] > 256) return fail(GRNND_EINVAL, "pool candidates need 2 <= R <= 256");
+  if (d < 1) return fail(GRNND_EINVAL, "need d >= 1");
+  if (nq < 1 || nq > n - 3) return fail(GRNND_EINVAL, "need 1 <= nq <= n - 3 held-out query rows");
+  if (k < 1 || k > 32 || beam < k || beam > 256) return fail(GRNND_EINVAL, "need 1 <= k <= 32 and k <= beam <= 256");
+  if (!(recall_target > 0.0f && recall_target <= 1.0f)) return fail(GRNND_EINVAL, "need 0 < recall_target <= 1");
+  const int64_t nb = n - nq;  // the built rows; the rest are the queries
+  if (k > nb) return fail(GRNND_EINVAL, "need k <= n - nq");
+  const cudaStream_t st = p->stream ? static_cast<cudaStream_t>(p->stream) : g_stream;
+  const float* qrows = points + nb * (int64_t)d;
+  // exact k nearest neighbours of the queries among the built rows, on a device copy whose
+  // rows are padded to a multiple of 4 floats (the exact k-NN kernel reads 16-byte vectors)
+  const int32_t ld = (d + 3) & ~3;
+  DevMem mp, mi;
+  GR_CU(mp.alloc((size_t)n * ld * 4));
+  if (ld != d) GR_CU(cudaMemsetAsync(mp.p, 0, (size_t)n * ld * 4, st));
+  GR_CU(cudaMemcpy2DAsync(mp.p, (size_t)ld * 4, points, (size_t)d * 4, (size_t)d * 4, (size_t)n,
+                          is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  const float* dpts = static_cast<const float*>(mp.p);
+  GR_CU(mi.alloc((size_t)nq * k * 4));
+  GR_CU(grnnd::launch_brute_knn(dpts, nb, d, ld, p->metric, dpts + nb * (int64_t)ld, nq, ld, k,
+                                static_cast<int32_t*>(mi.p), nullptr, st));
+  std::vector<int32_t> gt((size_t)nq * k), got((size_t)nq * k);
+  GR_CU(cudaMemcpyAsync(gt.data(), mi.p, gt.size() * 4, cudaMemcpyDeviceToHost, st));
+  GR_CU(cudaStreamSynchronize(st));
+  int best = -1;
+  float best_ms = 0.0f, best_rec = -1.0f;
+  for (int c = 0; c < ncand; ++c) {
+    grnnd_params q = *p;
+    q.R = R_candidates[c];
+    q.S = std::min<int64_t>(std::min(p->S, q.R), nb - 1);
+    grnnd_graph* g = nullptr;
+    int rc = grnnd_build_ex(points, nb, d, &q, &g);  // settles the allocations
+    if (rc != GRNND_OK) return rc;
+    grnnd_free(g);
+    g = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    rc = grnnd_build_ex(points, nb, d, &q, &g);
+    const auto t1 = std::chrono::steady_clock::now();
+    if (rc != GRNND_OK) return rc;
+    const float ms = std::chrono::duration<float, std::milli>(t1 - t0).count();
+    rc = grnnd_search(g, qrows, nq, k, beam, got.data());
+    grnnd_free(g);
+    if (rc != GRNND_OK) return rc;
+    int64_t hit = 0;
+    for (int64_t i = 0; i < nq; ++i)
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b)
+          if (got[i * k + a] == gt[i * k + b] && got[i * k + a] >= 0) {
+            ++hit;
+            break;
+          }
+    const float rec = (float)((double)hit / ((double)nq * k));
+    const bool ok = rec >= recall_target, best_ok = best_rec >= recall_target;
+    // passing candidates by build time; while none passes, by recall (then time)
+    const bool better = best < 0 || (ok && (!best_ok || ms < best_ms)) ||
+                        (!ok && !best_ok && (rec > best_rec || (rec == best_rec && ms < best_ms)));
+    if (better) {
+      best = c;
+      best_ms = ms;
+      best_rec = rec;
+    }
+  }
+  if (R_out) *R_out = R_candidates[best];
+  if (recall_out) *recall_out = best_rec;
+  if (ms_out) *ms_out = best_ms;
+  return GRNND_OK;
+}
+
 int grnnd_build(const float* points, int64_t n, int32_t d, int32_t metric, int32_t S, int32_t R,
                 int32_t T1, int32_t T2, uint64_t seed, grnnd_graph** graph_out) {
   grnnd_params p;

@@ -125,6 +125,10 @@ _SIGS = {
     "grnnd_get_stream": (ctypes.c_void_p, []),
     "grnnd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int32, ctypes.POINTER(Params), ctypes.POINTER(Tuning)]),
+    "grnnd_autotune_pool": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "grnnd_build_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "grnnd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32,
@@ -374,6 +378,28 @@ def autotune(points, S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, preci
                                 None if off is None else off.ctypes.data_as(ctypes.c_void_p),
                                 0 if off is None else len(off) - 1, ctypes.byref(p), ctypes.byref(t)))
     return t
+
+
+def autotune_pool(points, nq: int, candidates, recall_target: float = 0.95, k: int = 10, beam: int = 64,
+                  S=16, R=32, T1=4, T2=8, rho=0.6, seed=0, metric=L2SQ, precision=FP32, order=ORDER_RANDOM,
+                  final_prune=True, stream=None, tuning=None):
+    """grnnd_autotune_pool: the pool capacity R among `candidates` for builds like this one
+    (the last nq rows of `points` are the held-out queries); returns (R, recall, build ms)."""
+    if isinstance(points, np.ndarray):
+        pts = np.ascontiguousarray(points, dtype=np.float32)
+        ptr = pts.ctypes.data_as(ctypes.c_void_p)
+        st = None
+    else:
+        pts = points.contiguous()
+        ptr = ctypes.c_void_p(pts.data_ptr())
+        st = _stream_ptr(stream).value if pts.is_cuda else None
+    p = params(S, R, T1, T2, rho, seed, metric, precision, order, final_prune, st, 0, tuning)
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    r, rec, ms = ctypes.c_int32(), ctypes.c_float(), ctypes.c_float()
+    _check(lib().grnnd_autotune_pool(ptr, pts.shape[0], pts.shape[1], nq, ctypes.byref(p),
+                                     cand.ctypes.data_as(ctypes.c_void_p), len(cand), recall_target, k, beam,
+                                     ctypes.byref(r), ctypes.byref(rec), ctypes.byref(ms)))
+    return r.value, rec.value, ms.value
 
 
 def search(graph: Graph, queries, k: int = 10, beam: int = 64):

@@ -113,6 +113,21 @@ def test_build_batch_validates_before_any_launch(L):
     assert all(h is None for h in hs)
 
 
+def test_autotune_pool_is_validated(L):
+    import ctypes
+    pts = ctypes.c_void_p(1 << 20)
+    p = G.params(S=8, R=16)
+    out = (ctypes.c_int32(), ctypes.c_float(), ctypes.c_float())
+    for cands, nq, tgt, k, beam in [((), 10, 0.9, 10, 64), ((1,), 10, 0.9, 10, 64), ((16, 257), 10, 0.9, 10, 64),
+                                    ((16,), 0, 0.9, 10, 64), ((16,), 98, 0.9, 10, 64), ((16,), 10, 0.0, 10, 64),
+                                    ((16,), 10, 1.5, 10, 64), ((16,), 10, 0.9, 0, 64), ((16,), 10, 0.9, 33, 64),
+                                    ((16,), 10, 0.9, 10, 8), ((16,), 10, 0.9, 10, 257)]:
+        c = (ctypes.c_int32 * max(1, len(cands)))(*cands)
+        rc = L.grnnd_autotune_pool(pts, 100, 4, nq, ctypes.byref(p), c, len(cands), tgt, k, beam,
+                                   *(ctypes.byref(x) for x in out))
+        assert rc == G.EINVAL, (cands, nq, tgt, k, beam)
+
+
 def test_tuning_is_validated(L):
     import ctypes
     pts = ctypes.c_void_p(1 << 20)

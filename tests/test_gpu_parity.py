@@ -806,6 +806,33 @@ def test_row_copies_give_the_same_graph(G, precision, d):
             assert (u == v).all()
 
 
+def test_autotune_pool_picks_a_capacity_that_reaches_the_target(G, orc):
+    """grnnd_autotune_pool measures each candidate R's recall on held-out rows against exact
+    k-NN; its choice must reach the target when a candidate does, and its recall must equal
+    the recall of the same build measured here (builds are deterministic)."""
+    n, nq, d, k, beam = 6000, 200, 32, 10, 32
+    X = synth.gaussian_mixture(n + nq, d, 20, 10.0, 1.0, seed=4)
+    kw = dict(S=16, T1=3, T2=6, seed=3)
+    cands, target = [8, 16, 32], 0.9
+    R, rec, ms = G.autotune_pool(X, nq, cands, recall_target=target, k=k, beam=beam, **kw)
+    assert R in cands and ms > 0
+    Xp, _ = G.device_points(X[:n])
+    Qp, _ = G.device_points(X[n:])
+    gt = G.brute_knn(Xp, d, Qp, k)[0].cpu().numpy()  # the tuner's own ground truth
+    gt64 = orc.brute_knn(X[:n], X[n:], k)[0]
+    recalls = {}
+    for r in cands:
+        g = G.build(X[:n], R=r, **{**kw, "S": min(16, r)})
+        found = np.asarray(G.search(g, X[n:], k, beam))
+        recalls[r] = orc.recall_at_k(found, gt)
+        assert abs(recalls[r] - orc.recall_at_k(found, gt64)) <= 0.005
+    assert abs(recalls[R] - rec) < 1e-6, (R, rec, recalls)
+    if any(v >= target for v in recalls.values()):
+        assert recalls[R] >= target
+    else:
+        assert recalls[R] == max(recalls.values())
+
+
 def test_autotune_picks_a_candidate(G):
     X = synth.small_integers(4000, 32, -8, 8, seed=8)
     t = G.autotune(X, S=16, R=32, T1=2, T2=4, precision=G.BF16)
