@@ -637,7 +637,7 @@ int build_core(const float* points, int64_t n, int32_t d, const grnnd_params* p,
   // points -> padded device rows; the segment of every vertex
   const cudaMemcpyKind kind = is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (ld != d) GR_CU(cudaMemsetAsync(X, 0, (size_t)n * ld * 4, st));
-  GR_CU(cudaMemcpy2DAsync(X, (size_t)ld * 4, points, (size_t)d * 4, (size_t)d * 4, (size_t)n, kind, st));
+  GR_CU(grnnd::copy_rows(X, ld, points, d, n, kind, st));
   GR_CU(cudaMemsetAsync(stats, 0, 256, st));
   std::vector<int2> hseg;
   if (batched) {
@@ -949,8 +949,8 @@ int grnnd_autotune_pool(const float* points, int64_t n, int32_t d, int64_t nq, c
   DevMem mp, mi;
   GR_CU(mp.alloc((size_t)n * ld * 4));
   if (ld != d) GR_CU(cudaMemsetAsync(mp.p, 0, (size_t)n * ld * 4, st));
-  GR_CU(cudaMemcpy2DAsync(mp.p, (size_t)ld * 4, points, (size_t)d * 4, (size_t)d * 4, (size_t)n,
-                          is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  GR_CU(grnnd::copy_rows(static_cast<float*>(mp.p), ld, points, d, n,
+                         is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   const float* dpts = static_cast<const float*>(mp.p);
   GR_CU(mi.alloc((size_t)nq * k * 4));
   GR_CU(grnnd::launch_brute_knn(dpts, nb, d, ld, p->metric, dpts + nb * (int64_t)ld, nq, ld, k,
@@ -1035,7 +1035,7 @@ int grnnd_search(const grnnd_graph* g, const float* queries, int64_t nq, int32_t
   float* dq = static_cast<float*>(mq.p);
   const cudaMemcpyKind kind = is_device_ptr(queries) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (ldq != g->d) GR_CU(cudaMemsetAsync(dq, 0, (size_t)nq * ldq * 4, st));
-  GR_CU(cudaMemcpy2DAsync(dq, (size_t)ldq * 4, queries, (size_t)g->d * 4, (size_t)g->d * 4, (size_t)nq, kind, st));
+  GR_CU(grnnd::copy_rows(dq, ldq, queries, g->d, nq, kind, st));
   GR_CU(grnnd::launch_search(g->points, g->n, g->d, g->ld, g->metric, g->ids, g->deg, g->R, g->entry,
                              dq, nq, ldq, k, beam, dids, nullptr, st));
   if (!out_dev) GR_CU(cudaMemcpyAsync(ids_out, dids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));

@@ -234,8 +234,7 @@ int search_batch(const grnnd_graph* g, const std::vector<Request*>& batch, cudaM
   for (Request* r : batch) {  // the queries of every request, one after the other
     if (e != cudaSuccess) break;
     const cudaMemcpyKind kind = is_device_ptr(r->queries) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    e = cudaMemcpy2DAsync(q + off * ld, (size_t)ld * 4, r->queries, (size_t)d * 4, (size_t)d * 4,
-                          (size_t)r->units, kind, st);
+    e = grnnd::copy_rows(q + off * ld, ld, r->queries, d, r->units, kind, st);
     off += r->units;
   }
   if (e == cudaSuccess)
