@@ -806,6 +806,23 @@ def test_row_copies_give_the_same_graph(G, precision, d):
             assert (u == v).all()
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_build_batch_row_copies_give_the_same_graphs(G, precision):
+    """Batched builds stage every build's quantized rows through one tensor map over all of
+    them: gather4 and per-row staging give the same graphs, build by build."""
+    sizes = [700, 40, 3000, 1200]
+    parts = [synth.gaussian_mixture(m, 128, 10, seed=200 + i) for i, m in enumerate(sizes)]
+    X = torch.from_numpy(np.concatenate(parts)).cuda()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    prec = {"bf16": G.BF16, "fp8": G.FP8}[precision]
+    kw = dict(S=12, R=32, T1=2, T2=4, seed=13, precision=prec)
+    ga = G.build_batch(X, off, tuning=G.tuning(row_copies=2), **kw)
+    gb = G.build_batch(X, off, tuning=G.tuning(row_copies=1), **kw)
+    for a, b in zip(ga, gb):
+        for u, v in zip(a.to_numpy(), b.to_numpy()):
+            assert (u == v).all()
+
+
 def test_autotune_pool_picks_a_capacity_that_reaches_the_target(G, orc):
     """grnnd_autotune_pool measures each candidate R's recall on held-out rows against exact
     k-NN; its choice must reach the target when a candidate does, and its recall must equal
