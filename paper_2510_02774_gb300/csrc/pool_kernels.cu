@@ -18,6 +18,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include <atomic>
+#include <type_traits>
 #include <mutex>
 
 namespace grnnd {
@@ -1550,399 +1551,411 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
         if (lane == 0 && w2 + GW >= S) tq = atomicAdd(a.work_q, 1u);
       }
     }
-    const int cls = cur.cls, lw = 3 + cls, VW = 1 << lw, G = 32 >> lw;
-    const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
-    const uint32_t gmask = low_bits32(VW);
-    const int m = cur.m;
-    const int64_t v = cur.v;
-    const uint64_t keyl = cur.key;
-    // ---- rows, and the first chunk's gather in flight while the visit order is sorted ----
-    // Rows hold the new entries first, then the old ones, each part in storage-slot order
-    // (lane gb + s holds slot s here): the pairs are enumerated over rows (new row i, any
-    // later row j), so the order inside each part does not matter.
-    const uint32_t validm = low_bits32(m);
-    const bool valid_s = gl < m;
-    const uint32_t news = (__ballot_sync(0xffffffffu, valid_s && !key_old(keyl)) >> gb) & gmask;
-    const int k = __popc(news);
-    const int np = k * (m - 1) - k * (k - 1) / 2;
-    const uint32_t below_s = lanes_below32(gl);
-    const int row_s = ((news >> gl) & 1u) ? __popc(news & below_s) : k + __popc(~news & validm & below_s);
-    const uint32_t id_s = key_id(keyl);
-    const bool need = valid_s && np > 0 &&  // rows of groups with pairs only
-                      in_bounds((uint64_t)id_s < (uint64_t)a.n, a.err);
-    const uint32_t needm = __ballot_sync(0xffffffffu, need);
-    const int nch = needm ? nchd : 0;
-    if (TMA && valid_s) s.rid[gb + row_s] = (int32_t)id_s;
-    auto issue = [&](int c) {  // the copies of chunk c, completing on the warp's mbarrier
-      const int c0 = c * WDC;
-      if constexpr (TMA) {
-        // one gather4 per four rows of a group with pairs, issued by the lane of the first of
-        // them (rows gb + gl .. gb + gl + 3 = lane .. lane + 3); a group's last copy repeats
-        // its first row in the places past m.  Each copies whole boxes: the chunk's columns
-        // and, after the last chunk, the first 16 bytes of the row's tail.
-        const bool iss = need && (gl & 3) == 0;
-        const uint32_t im = __ballot_sync(0xffffffffu, iss);
-        if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(im) * 4u * (uint32_t)C::RSB);
+    // the item's work, compiled once per lane-group width (VW = 32, 16 or 8 lanes per pool)
+    bool quit = false;  // a bounded wait gave up: the warp stops
+    auto item = [&](auto vw_tag) {
+      constexpr int VW = decltype(vw_tag)::value, lw = VW == 32 ? 5 : (VW == 16 ? 4 : 3), G = 32 / VW;
+      const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
+      const uint32_t gmask = low_bits32(VW);
+      const int m = cur.m;
+      const int64_t v = cur.v;
+      const uint64_t keyl = cur.key;
+      // ---- rows, and the first chunk's gather in flight while the visit order is sorted ----
+      // Rows hold the new entries first, then the old ones, each part in storage-slot order
+      // (lane gb + s holds slot s here): the pairs are enumerated over rows (new row i, any
+      // later row j), so the order inside each part does not matter.
+      const uint32_t validm = low_bits32(m);
+      const bool valid_s = gl < m;
+      const uint32_t news = (__ballot_sync(0xffffffffu, valid_s && !key_old(keyl)) >> gb) & gmask;
+      const int k = __popc(news);
+      const int np = k * (m - 1) - k * (k - 1) / 2;
+      const uint32_t below_s = lanes_below32(gl);
+      const int row_s = ((news >> gl) & 1u) ? __popc(news & below_s) : k + __popc(~news & validm & below_s);
+      const uint32_t id_s = key_id(keyl);
+      const bool need = valid_s && np > 0 &&  // rows of groups with pairs only
+                        in_bounds((uint64_t)id_s < (uint64_t)a.n, a.err);
+      const uint32_t needm = __ballot_sync(0xffffffffu, need);
+      const int nch = needm ? nchd : 0;
+      if (TMA && valid_s) s.rid[gb + row_s] = (int32_t)id_s;
+      auto issue = [&](int c) {  // the copies of chunk c, completing on the warp's mbarrier
+        const int c0 = c * WDC;
+        if constexpr (TMA) {
+          // one gather4 per four rows of a group with pairs, issued by the lane of the first of
+          // them (rows gb + gl .. gb + gl + 3 = lane .. lane + 3); a group's last copy repeats
+          // its first row in the places past m.  Each copies whole boxes: the chunk's columns
+          // and, after the last chunk, the first 16 bytes of the row's tail.
+          const bool iss = need && (gl & 3) == 0;
+          const uint32_t im = __ballot_sync(0xffffffffu, iss);
+          if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(im) * 4u * (uint32_t)C::RSB);
+          inflight = true;
+          __syncwarp();
+          if (iss) {
+            int4 q = *reinterpret_cast<const int4*>(&s.rid[lane]);
+            if (gl + 1 >= m) q.y = q.x;
+            if (gl + 2 >= m) q.z = q.x;
+            if (gl + 3 >= m) q.w = q.x;
+            tma_gather4(wrow(s, lane), &a.rows_map, c0, q.x, q.y, q.z, q.w, &s.bar);
+          }
+          return;
+        }
+        const int cpy = (min(WDC, d - c0) + C::VEC - 1) / C::VEC * C::VEC;
+        // a quantized row's last chunk brings the row's terms (norm^2, residual) along
+        const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
+        if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
         inflight = true;
         __syncwarp();
-        if (iss) {
-          int4 q = *reinterpret_cast<const int4*>(&s.rid[lane]);
-          if (gl + 1 >= m) q.y = q.x;
-          if (gl + 2 >= m) q.z = q.x;
-          if (gl + 3 >= m) q.w = q.x;
-          tma_gather4(wrow(s, lane), &a.rows_map, c0, q.x, q.y, q.z, q.w, &s.bar);
-        }
-        return;
-      }
-      const int cpy = (min(WDC, d - c0) + C::VEC - 1) / C::VEC * C::VEC;
-      // a quantized row's last chunk brings the row's terms (norm^2, residual) along
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
-      if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
-      inflight = true;
-      __syncwarp();
-      if (need) {
-        const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id_s * a.P.ld + c0)
-                                   : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)id_s * a.P.ldb + c0;
-        bulk_g2s(wrow(s, gb + row_s), src, bytes, &s.bar);
-      }
-    };
-    if (nch > 0) issue(0);
-
-    // ---- visit order: the position of each entry is its rank in (h, id) order in its group --
-    // Ranks count, per entry, the group's entries with a smaller key: over the high 32 bits
-    // of h alone when those are distinct in every group (two of 32 hashes share them with
-    // probability about 1e-7), else over the full (h, id).  (The serial orders put their
-    // index in the high bits.)
-    const uint32_t idl = key_id(keyl);
-    uint64_t h = ~0ull;
-    if (valid_s)
-      h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - cur.lo), (uint64_t)(idl - cur.lo))
-          : (a.order == 1) ? (uint64_t)gl << 32
-                           : (uint64_t)(m - 1 - gl) << 32;
-    int pi_s = gl;  // this storage slot's position (slots past m keep positions m .. VW - 1)
-    {
-      const uint32_t k32 = (uint32_t)(h >> 32);
-      const uint64_t mv = valid_s ? (((uint64_t)g << 32) | k32) : (~0ull << 32) | (uint64_t)lane;
-      const bool tie = __any_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, mv)) > 1);
-      int r = 0;
-      if (!tie) {
-#pragma unroll 8
-        for (int j = 0; j < VW; ++j) {
-          const uint32_t kj = __shfl_sync(0xffffffffu, k32, gb + j);
-          r += (j < m && kj < k32) ? 1 : 0;
-        }
-      } else {
-        for (int j = 0; j < VW; ++j) {
-          const uint64_t hj = __shfl_sync(0xffffffffu, h, gb + j);
-          const uint32_t ij = __shfl_sync(0xffffffffu, idl, gb + j);
-          r += (j < m && (hj < h || (hj == h && ij < idl))) ? 1 : 0;
-        }
-      }
-      if (valid_s) {
-        pi_s = r;
-        s.src[gb + r] = (uint8_t)gl;
-      }
-    }
-    __syncwarp();
-    // lane gb + p takes local pi position p: its source lane hs (storage slot hs - gb)
-    const int hs = gb + (gl < m ? (int)s.src[lane] : gl);
-    const int slot = hs - gb;
-    const uint64_t key = __shfl_sync(0xffffffffu, keyl, (int)hs);
-    const bool valid_p = gl < m;
-    const uint32_t below = lanes_below32(gl);
-    const int row = __shfl_sync(0xffffffffu, row_s, (int)hs);  // the row of this position's entry
-    const int32_t id = (int32_t)key_id(key);
-    const int P = gb + gl;
-    if (valid_p) {
-      s.pid[P] = id;
-      s.prow[P] = (uint8_t)row;
-      s.rpos[gb + row] = (uint8_t)gl;
-      if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
-      // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
-      s.rnd[gb + row] = make_float2(0.0f, key_dist(key));
-    }
-    if (lane == 0) s.nrq = 0;
-    if (gl == 0) {
-      s.gk[g] = k;
-      s.gm[g] = m;
-    }
-    s.fire[lane] = 0u;  // fire bits are set by the pairs that fire (shared atomics)
-    __syncwarp();
-    // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
-    // closer mask of a position is the prefix OR, over the slots before its own, of the
-    // slots' position bits
-    uint32_t closer_p;
-    {
-      const uint32_t bit = valid_s ? (1u << pi_s) : 0u;  // this lane as storage slot
-      uint32_t x = bit;
-#pragma unroll
-      for (int dd = 1; dd < 32; dd <<= 1) {
-        if (dd >= VW) break;
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, dd, VW);
-        if (gl >= dd) x |= y;
-      }
-      closer_p = __shfl_sync(0xffffffffu, x ^ bit, (int)hs);
-    }
-
-    // ---- gather + tile ---------------------------------------------------------------
-    const int pdb = g * ((VW * (VW - 1)) >> 1);
-    bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-      const int c0 = c * WDC;
-      const int clen = min(WDC, d - c0);
-      if (c > 0) issue(c);  // (chunk 0 is in flight since before the visit order)
-      ok = mbar_wait(&s.bar, phb, kWaitLimit);
-      if (!__all_sync(0xffffffffu, ok)) break;
-      phb ^= 1u;
-      inflight = false;
-      if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
         if (need) {
-          const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-          const float2 t = *reinterpret_cast<const float2*>(wrow(s, gb + row_s) + cpy);
-          s.rnd[gb + row_s].x = t.x;
-          s.rdq[gb + row_s] = t.y;
+          const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)id_s * a.P.ld + c0)
+                                     : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)id_s * a.P.ldb + c0;
+          bulk_g2s(wrow(s, gb + row_s), src, bytes, &s.bar);
+        }
+      };
+      if (nch > 0) issue(0);
+
+      // ---- visit order: the position of each entry is its rank in (h, id) order in its group --
+      // Ranks count, per entry, the group's entries with a smaller key: over the high 32 bits
+      // of h alone when those are distinct in every group (two of 32 hashes share them with
+      // probability about 1e-7), else over the full (h, id).  (The serial orders put their
+      // index in the high bits.)
+      const uint32_t idl = key_id(keyl);
+      uint64_t h = ~0ull;
+      if (valid_s)
+        h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - cur.lo), (uint64_t)(idl - cur.lo))
+            : (a.order == 1) ? (uint64_t)gl << 32
+                             : (uint64_t)(m - 1 - gl) << 32;
+      int pi_s = gl;  // this storage slot's position (slots past m keep positions m .. VW - 1)
+      {
+        const uint32_t k32 = (uint32_t)(h >> 32);
+        const uint64_t mv = valid_s ? (((uint64_t)g << 32) | k32) : (~0ull << 32) | (uint64_t)lane;
+        const bool tie = __any_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, mv)) > 1);
+        int r = 0;
+        if (!tie) {
+  #pragma unroll 8
+          for (int j = 0; j < VW; ++j) {
+            const uint32_t kj = __shfl_sync(0xffffffffu, k32, gb + j);
+            r += (j < m && kj < k32) ? 1 : 0;
+          }
+        } else {
+          for (int j = 0; j < VW; ++j) {
+            const uint64_t hj = __shfl_sync(0xffffffffu, h, gb + j);
+            const uint32_t ij = __shfl_sync(0xffffffffu, idl, gb + j);
+            r += (j < m && (hj < h || (hj == h && ij < idl))) ? 1 : 0;
+          }
+        }
+        if (valid_s) {
+          pi_s = r;
+          s.src[gb + r] = (uint8_t)gl;
+        }
+      }
+      __syncwarp();
+      // lane gb + p takes local pi position p: its source lane hs (storage slot hs - gb)
+      const int hs = gb + (gl < m ? (int)s.src[lane] : gl);
+      const int slot = hs - gb;
+      const uint64_t key = __shfl_sync(0xffffffffu, keyl, (int)hs);
+      const bool valid_p = gl < m;
+      const uint32_t below = lanes_below32(gl);
+      const int row = __shfl_sync(0xffffffffu, row_s, (int)hs);  // the row of this position's entry
+      const int32_t id = (int32_t)key_id(key);
+      const int P = gb + gl;
+      if (valid_p) {
+        s.pid[P] = id;
+        s.prow[P] = (uint8_t)row;
+        s.rpos[gb + row] = (uint8_t)gl;
+        if (row < k) s.roff[gb + row] = row * (m - 1) - row * (row - 1) / 2;
+        // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
+        s.rnd[gb + row] = make_float2(0.0f, key_dist(key));
+      }
+      if (lane == 0) s.nrq = 0;
+      if (gl == 0) {
+        s.gk[g] = k;
+        s.gm[g] = m;
+      }
+      s.fire[lane] = 0u;  // fire bits are set by the pairs that fire (shared atomics)
+      __syncwarp();
+      // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
+      // closer mask of a position is the prefix OR, over the slots before its own, of the
+      // slots' position bits
+      uint32_t closer_p;
+      {
+        const uint32_t bit = valid_s ? (1u << pi_s) : 0u;  // this lane as storage slot
+        uint32_t x = bit;
+  #pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          if (dd >= VW) break;
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, dd, VW);
+          if (gl >= dd) x |= y;
+        }
+        closer_p = __shfl_sync(0xffffffffu, x ^ bit, (int)hs);
+      }
+
+      // ---- gather + tile ---------------------------------------------------------------
+      const int pdb = g * ((VW * (VW - 1)) >> 1);
+      bool ok = true;
+      for (int c = 0; c < nch; ++c) {
+        const int c0 = c * WDC;
+        const int clen = min(WDC, d - c0);
+        if (c > 0) issue(c);  // (chunk 0 is in flight since before the visit order)
+        ok = mbar_wait(&s.bar, phb, kWaitLimit);
+        if (!__all_sync(0xffffffffu, ok)) break;
+        phb ^= 1u;
+        inflight = false;
+        if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
+          if (need) {
+            const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+            const float2 t = *reinterpret_cast<const float2*>(wrow(s, gb + row_s) + cpy);
+            s.rnd[gb + row_s].x = t.x;
+            s.rdq[gb + row_s] = t.y;
+          }
+          __syncwarp();
+        }
+        if (PREC >= 1) {
+          // tiles one at a time; partial dot products wait in pd between chunks (d > 128),
+          // and the last chunk takes the fire decisions straight from the accumulators
+          constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
+          const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
+          const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
+          const bool first_c = (c == 0), last_c = (c + 1 == nch);
+          const int g8 = lane >> 2, tg = lane & 3;
+          const int npg = (VW * (VW - 1)) >> 1;  // pairs per lane group
+          for (int t = 0; t < 6; ++t) {
+            // tiles (I, J): (0,0..3), (1,2), (1,3); lane groups use the diagonal ones only
+            const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
+            const bool use = (VW == 32) ? (I < KI && J < NJ) : (t != 2 && t != 3);
+            if (!use) continue;
+            // this lane's elements: rows i0, i0 + 8 of the warp's row space, columns j0, j0 + 1
+            const int i0 = I * 16 + g8, j0 = J * 8 + 2 * tg;
+            int q[4];
+            bool ve[4];
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+              const int ge = i >> lw;  // the lane group both rows must belong to
+              const int eb = ge << lw, li = i - eb, lj = j - eb;
+              const int ke = (VW == 32) ? k : s.gk[ge], me = (VW == 32) ? m : s.gm[ge];
+              ve[e] = ((j >> lw) == ge) && li < ke && lj > li && lj < me;
+              q[e] = ve[e] ? ge * npg + s.roff[i] + (lj - li - 1) : 0;
+            }
+            float acc[4];
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
+            const int ra = I * 16 + (lane & 15);
+            const int rb = J * 8 + (lane & 7);
+            const T* pa = wrow(s, ra) + (lane >> 4) * KB;
+            const T* pb = wrow(s, rb) + ((lane >> 3) & 1) * KB;
+            for (int ks = 0; ks < ksteps; ++ks) {
+              uint32_t fa[4], fb[2];
+              ldmatrix_x4(fa, pa + ks * 2 * KB);
+              ldmatrix_x2(fb, pb + ks * 2 * KB);
+              mma_q<PREC>(acc, fa, fb);
+            }
+            if (!last_c) {
+  #pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (ve[e]) s.pd[q[e]] = acc[e];
+              continue;
+            }
+            const float2 rI[2] = {s.rnd[i0], s.rnd[i0 + 8]};
+            const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
+            const int pI[2] = {s.rpos[i0], s.rpos[i0 + 8]};
+            const int pJ[2] = {s.rpos[j0], s.rpos[j0 + 1]};
+            float scI[2] = {1.0f, 1.0f}, scJ[2] = {1.0f, 1.0f};
+            if (PREC == 2) {  // the rows' power-of-two scales (exact products)
+              scI[0] = q_scale(s.rdq[i0]);
+              scI[1] = q_scale(s.rdq[i0 + 8]);
+              scJ[0] = q_scale(s.rdq[j0]);
+              scJ[1] = q_scale(s.rdq[j0 + 1]);
+            }
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (!ve[e]) continue;
+              const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+              const int ge = i >> lw, eb = ge << lw;
+              const float gij = (PREC == 2) ? acc[e] * scI[e >> 1] * scJ[e & 1] : acc[e];
+              const float2 ri = rI[e >> 1], rj = rJ[e & 1];
+              float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
+                                        : __fsub_rn(1.0f, gij);
+              const float mx = fmaxf(ri.y, rj.y);
+              bool fire = dab < mx;
+              const int pa2 = pI[e >> 1], pb2 = pJ[e & 1];
+              if (!exact) {
+                const float eqi = s.rdq[i], eqj = s.rdq[j];
+                const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
+                if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
+                  ++st_check;
+                  const int slot = atomicAdd(&s.nrq, 1);
+                  if (slot < WRQ) {
+                    s.rq[slot] = (uint16_t)((i << 5) | j);  // taken below, all together
+                    continue;
+                  }
+                  const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
+                  const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
+                  dab = row_dist<METRIC>(xa, xb, d);
+                  fire = dab < mx;
+                }
+              }
+              s.pd[q[e]] = dab;
+              if (fire) atomicOr(&s.fire[eb + max(pa2, pb2)], 1u << min(pa2, pb2));
+            }
+          }
+        } else {
+          const int full4 = clen & ~3, rem = clen & 3;
+          for (int q = gl; q < np; q += VW) {
+            int i = 0;  // the new local row owning pair q
+  #pragma unroll
+            for (int w2 = 16; w2 > 0; w2 >>= 1)
+              if (i + w2 < k && s.roff[gb + i + w2] <= q) i += w2;
+            const int j = i + 1 + (q - s.roff[gb + i]);
+            const float* ra = reinterpret_cast<const float*>(wrow(s, gb + i));
+            const float* rb = reinterpret_cast<const float*>(wrow(s, gb + j));
+            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int u = 0; u < full4; u += 4)
+              dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
+                                 *reinterpret_cast<const float4*>(rb + u));
+            if (rem)
+              dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
+                                 mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
+            const float dab = dist_finish4<METRIC>(acc);
+            s.pd[pdb + q] = dab;
+            const int pa = s.rpos[gb + i], pb = s.rpos[gb + j];
+            if (dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y)) atomicOr(&s.fire[gb + max(pa, pb)], 1u << min(pa, pb));
+          }
         }
         __syncwarp();
       }
-      if (PREC >= 1) {
-        // tiles one at a time; partial dot products wait in pd between chunks (d > 128),
-        // and the last chunk takes the fire decisions straight from the accumulators
-        constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
-        const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
-        const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
-        const bool first_c = (c == 0), last_c = (c + 1 == nch);
-        const int g8 = lane >> 2, tg = lane & 3;
-        const int npg = (VW * (VW - 1)) >> 1;  // pairs per lane group
-        for (int t = 0; t < 6; ++t) {
-          // tiles (I, J): (0,0..3), (1,2), (1,3); lane groups use the diagonal ones only
-          const int I = t < 4 ? 0 : 1, J = t < 4 ? t : t - 2;
-          const bool use = (VW == 32) ? (I < KI && J < NJ) : (t != 2 && t != 3);
-          if (!use) continue;
-          // this lane's elements: rows i0, i0 + 8 of the warp's row space, columns j0, j0 + 1
-          const int i0 = I * 16 + g8, j0 = J * 8 + 2 * tg;
-          int q[4];
-          bool ve[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
-            const int ge = i >> lw;  // the lane group both rows must belong to
-            const int eb = ge << lw, li = i - eb, lj = j - eb;
-            const int ke = (VW == 32) ? k : s.gk[ge], me = (VW == 32) ? m : s.gm[ge];
-            ve[e] = ((j >> lw) == ge) && li < ke && lj > li && lj < me;
-            q[e] = ve[e] ? ge * npg + s.roff[i] + (lj - li - 1) : 0;
-          }
-          float acc[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
-          const int ra = I * 16 + (lane & 15);
-          const int rb = J * 8 + (lane & 7);
-          const T* pa = wrow(s, ra) + (lane >> 4) * KB;
-          const T* pb = wrow(s, rb) + ((lane >> 3) & 1) * KB;
-          for (int ks = 0; ks < ksteps; ++ks) {
-            uint32_t fa[4], fb[2];
-            ldmatrix_x4(fa, pa + ks * 2 * KB);
-            ldmatrix_x2(fb, pb + ks * 2 * KB);
-            mma_q<PREC>(acc, fa, fb);
-          }
-          if (!last_c) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (ve[e]) s.pd[q[e]] = acc[e];
-            continue;
-          }
-          const float2 rI[2] = {s.rnd[i0], s.rnd[i0 + 8]};
-          const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
-          const int pI[2] = {s.rpos[i0], s.rpos[i0 + 8]};
-          const int pJ[2] = {s.rpos[j0], s.rpos[j0 + 1]};
-          float scI[2] = {1.0f, 1.0f}, scJ[2] = {1.0f, 1.0f};
-          if (PREC == 2) {  // the rows' power-of-two scales (exact products)
-            scI[0] = q_scale(s.rdq[i0]);
-            scI[1] = q_scale(s.rdq[i0 + 8]);
-            scJ[0] = q_scale(s.rdq[j0]);
-            scJ[1] = q_scale(s.rdq[j0 + 1]);
-          }
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (!ve[e]) continue;
-            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
-            const int ge = i >> lw, eb = ge << lw;
-            const float gij = (PREC == 2) ? acc[e] * scI[e >> 1] * scJ[e & 1] : acc[e];
-            const float2 ri = rI[e >> 1], rj = rJ[e & 1];
-            float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
-                                      : __fsub_rn(1.0f, gij);
-            const float mx = fmaxf(ri.y, rj.y);
-            bool fire = dab < mx;
-            const int pa2 = pI[e >> 1], pb2 = pJ[e & 1];
-            if (!exact) {
-              const float eqi = s.rdq[i], eqj = s.rdq[j];
-              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
-              if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
-                ++st_check;
-                const int slot = atomicAdd(&s.nrq, 1);
-                if (slot < WRQ) {
-                  s.rq[slot] = (uint16_t)((i << 5) | j);  // taken below, all together
-                  continue;
-                }
-                const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
-                const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
-                dab = row_dist<METRIC>(xa, xb, d);
-                fire = dab < mx;
-              }
-            }
-            s.pd[q[e]] = dab;
-            if (fire) atomicOr(&s.fire[eb + max(pa2, pb2)], 1u << min(pa2, pb2));
-          }
+      if (!__all_sync(0xffffffffu, ok)) {  // a bounded wait gave up: report and stop the warp
+        if (lane == 0) atomicExch(a.err, kErrTimeout);
+        if (inflight) mbar_wait(&s.bar, phb, kWaitLimit);  // let this warp's copies land
+        if (a.emit_redirects)
+          for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
+        if (lane == 0) leave(0, 0, 0, 0, 0);
+        quit = true;
+        return;
+      }
+      // queued re-decisions, one per lane: the FP32 rows of every pair load at once
+      if (PREC >= 1 && nch > 0) {
+        const int nq = min(s.nrq, WRQ);
+        for (int t = lane; t < nq; t += 32) {
+          const int i = s.rq[t] >> 5, j = s.rq[t] & 31;
+          const int ge = i >> lw, eb = ge << lw, li = i - eb, lj = j - eb;
+          const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+          const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
+          const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
+          const float dab = row_dist<METRIC>(xa, xb, d);
+          s.pd[ge * ((VW * (VW - 1)) >> 1) + s.roff[i] + (lj - li - 1)] = dab;
+          if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y)) atomicOr(&s.fire[eb + max(pa2, pb2)], 1u << min(pa2, pb2));
         }
-      } else {
-        const int full4 = clen & ~3, rem = clen & 3;
-        for (int q = gl; q < np; q += VW) {
-          int i = 0;  // the new local row owning pair q
-#pragma unroll
-          for (int w2 = 16; w2 > 0; w2 >>= 1)
-            if (i + w2 < k && s.roff[gb + i + w2] <= q) i += w2;
-          const int j = i + 1 + (q - s.roff[gb + i]);
-          const float* ra = reinterpret_cast<const float*>(wrow(s, gb + i));
-          const float* rb = reinterpret_cast<const float*>(wrow(s, gb + j));
-          float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          for (int u = 0; u < full4; u += 4)
-            dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
-                               *reinterpret_cast<const float4*>(rb + u));
-          if (rem)
-            dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
-                               mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
-          const float dab = dist_finish4<METRIC>(acc);
-          s.pd[pdb + q] = dab;
-          const int pa = s.rpos[gb + i], pb = s.rpos[gb + j];
-          if (dab < fmaxf(s.rnd[gb + i].y, s.rnd[gb + j].y)) atomicOr(&s.fire[gb + max(pa, pb)], 1u << min(pa, pb));
-        }
+        __syncwarp();
       }
       __syncwarp();
-    }
-    if (!__all_sync(0xffffffffu, ok)) {  // a bounded wait gave up: report and stop the warp
-      if (lane == 0) atomicExch(a.err, kErrTimeout);
-      if (inflight) mbar_wait(&s.bar, phb, kWaitLimit);  // let this warp's copies land
-      if (a.emit_redirects)
-        for (unsigned long long i = s.red_next + lane; i < s.red_end; i += 32) a.red_tgt[i] = -1;
-      if (lane == 0) leave(0, 0, 0, 0, 0);
-      return;
-    }
-    // queued re-decisions, one per lane: the FP32 rows of every pair load at once
-    if (PREC >= 1 && nch > 0) {
-      const int nq = min(s.nrq, WRQ);
-      for (int t = lane; t < nq; t += 32) {
-        const int i = s.rq[t] >> 5, j = s.rq[t] & 31;
-        const int ge = i >> lw, eb = ge << lw, li = i - eb, lj = j - eb;
-        const int pa2 = s.rpos[i], pb2 = s.rpos[j];
-        const float* xa = a.P.X + (int64_t)s.pid[eb + pa2] * a.P.ld;
-        const float* xb = a.P.X + (int64_t)s.pid[eb + pb2] * a.P.ld;
-        const float dab = row_dist<METRIC>(xa, xb, d);
-        s.pd[ge * ((VW * (VW - 1)) >> 1) + s.roff[i] + (lj - li - 1)] = dab;
-        if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y)) atomicOr(&s.fire[eb + max(pa2, pb2)], 1u << min(pa2, pb2));
-      }
-      __syncwarp();
-    }
-    __syncwarp();
 
-    // ---- prune: the chain's outcome, one column (pi position) per lane of the group -------
-    // Column b of the sequential pair scan kills K_b: its live firing partners before the
-    // first closer one f, then b itself (absorbed by f); all of them when none is closer.
-    // Its live partners are the valid positions that no column c < b killed, so the scan's
-    // outcome is the fixed point of K_b = rule(fire[b] & valid & ~OR_{c<b} K_c).  Rounds
-    // that apply the rule to every column at once, from K = 0, reach it: after round r the
-    // columns 0..r hold their final value, so it takes at most m rounds; the first round
-    // whose K has the prefix it was computed from (in every group of the warp) is the fixed
-    // point and ends the loop.
-    uint32_t alive = validm;
-    int mykill = -1;
-    {
-      const uint32_t fb = s.fire[P];
-      uint32_t K = 0u, before = 0u, inc = 0u;  // before: the OR of K over the earlier columns
-      int f = -1;
-      for (int r = 0;; ++r) {
-        const uint32_t cand = fb & validm & ~before;
-        const uint32_t x = cand & closer_p;
-        const uint32_t low = x & (0u - x);  // first closer partner (0: none)
-        f = x ? __ffs(x) - 1 : -1;
-        K = x ? ((cand & (low - 1u)) | (1u << gl)) : cand;
-        inc = K;  // inclusive prefix OR over the group's columns
-#pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-          if (dd >= VW) break;
-          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, dd, VW);
-          if (gl >= dd) inc |= y;
+      // ---- prune: the chain's outcome, one column (pi position) per lane of the group -------
+      // Column b of the sequential pair scan kills K_b: its live firing partners before the
+      // first closer one f, then b itself (absorbed by f); all of them when none is closer.
+      // Its live partners are the valid positions that no column c < b killed, so the scan's
+      // outcome is the fixed point of K_b = rule(fire[b] & valid & ~OR_{c<b} K_c).  Rounds
+      // that apply the rule to every column at once, from K = 0, reach it: after round r the
+      // columns 0..r hold their final value, so it takes at most m rounds; the first round
+      // whose K has the prefix it was computed from (in every group of the warp) is the fixed
+      // point and ends the loop.
+      uint32_t alive = validm;
+      int mykill = -1;
+      {
+        const uint32_t fb = s.fire[P];
+        uint32_t K = 0u, before = 0u, inc = 0u;  // before: the OR of K over the earlier columns
+        int f = -1;
+        for (int r = 0;; ++r) {
+          const uint32_t cand = fb & validm & ~before;
+          const uint32_t x = cand & closer_p;
+          const uint32_t low = x & (0u - x);  // first closer partner (0: none)
+          f = x ? __ffs(x) - 1 : -1;
+          K = x ? ((cand & (low - 1u)) | (1u << gl)) : cand;
+          inc = K;  // inclusive prefix OR over the group's columns
+  #pragma unroll
+          for (int dd = 1; dd < 32; dd <<= 1) {
+            if (dd >= VW) break;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, dd, VW);
+            if (gl >= dd) inc |= y;
+          }
+          uint32_t bn = __shfl_up_sync(0xffffffffu, inc, 1, VW);
+          if (gl == 0) bn = 0u;
+          // the new K has the prefix this round used: it is the fixed point
+          if (!__any_sync(0xffffffffu, bn != before) || r >= WM) break;
+          before = bn;
         }
-        uint32_t bn = __shfl_up_sync(0xffffffffu, inc, 1, VW);
-        if (gl == 0) bn = 0u;
-        // the new K has the prefix this round used: it is the fixed point
-        if (!__any_sync(0xffffffffu, bn != before) || r >= WM) break;
-        before = bn;
-      }
-      alive = validm & ~__shfl_sync(0xffffffffu, inc, gb + VW - 1);
-      for (uint32_t ab = K & ~(1u << gl); ab; ab &= ab - 1) s.kil[gb + __ffs(ab) - 1] = (uint8_t)gl;
-      __syncwarp();
-      if (valid_p && !((alive >> gl) & 1u)) mykill = f >= 0 ? f : (int)s.kil[P];
-    }
-    __syncwarp();
-    // ---- emit ----------------------------------------------------------------------------
-    const bool surv = valid_p && ((alive >> gl) & 1u);
-    const uint32_t smask = (__reduce_or_sync(0xffffffffu, surv ? (1u << hs) : 0u) >> gb) & gmask;
-    const int nkeep = __popc(alive & validm);
-    if (m > 0 && in_bounds((uint64_t)v < (uint64_t)a.n, a.err)) {
-      if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
-      // in place, the slots past m are empty already (pool rows end in empty slots)
-      const int pend = a.keys_out == a.keys_in ? m : R;
-      for (int t = nkeep + gl; t < pend; t += VW) a.keys_out[v * R + t] = kEmpty;
-      if (gl == 0) a.deg_out[v] = nkeep;
-    }
-    const int ndead = m - nkeep;
-    // redirects of all groups: one reservation per warp, groups in order
-    int pre = 0, tot = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int nd = __shfl_sync(0xffffffffu, ndead, (q << lw) & 31);
-      if (q < G) {
-        if (q < g) pre += nd;
-        tot += nd;
-      }
-    }
-    if (a.emit_redirects && tot > 0) {
-      // fill the warp's chunk to its end, then continue in a fresh one (tot < WRED)
-      const unsigned long long base = s.red_next, end = s.red_end;
-      unsigned long long b1 = base, next = base + (unsigned long long)tot;
-      int avail = tot;
-      if (next > end) {
-        avail = (int)(end - base);
-        unsigned long long nb2 = 0;
-        if (lane == 0) nb2 = atomicAdd(a.red_n, (unsigned long long)WRED);
-        b1 = __shfl_sync(0xffffffffu, nb2, 0);
-        next = b1 + (unsigned long long)(tot - avail);
-        if (lane == 0) s.red_end = b1 + WRED;
+        alive = validm & ~__shfl_sync(0xffffffffu, inc, gb + VW - 1);
+        for (uint32_t ab = K & ~(1u << gl); ab; ab &= ab - 1) s.kil[gb + __ffs(ab) - 1] = (uint8_t)gl;
+        __syncwarp();
+        if (valid_p && !((alive >> gl) & 1u)) mykill = f >= 0 ? f : (int)s.kil[P];
       }
       __syncwarp();
-      if (lane == 0) s.red_next = next;
-      if (valid_p && !surv) {
-        const int ri = s.prow[gb + mykill], rj = row;
-        const int i = min(ri, rj), j = max(ri, rj);
-        const float dd = s.pd[pdb + s.roff[gb + i] + (j - i - 1)];
-        const int32_t tgt = s.pid[gb + mykill];
-        const int rk = pre + __popc(~alive & validm & below);
-        const unsigned long long sl = rk < avail ? base + (unsigned long long)rk : b1 + (unsigned long long)(rk - avail);
-        if (in_bounds(sl < (unsigned long long)a.red_cap && (uint64_t)(uint32_t)tgt < (uint64_t)a.n, a.err)) {
-          a.red_tgt[sl] = tgt;
-          a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
-          atomicAdd(&a.count[tgt], 1);
+      // ---- emit ----------------------------------------------------------------------------
+      const bool surv = valid_p && ((alive >> gl) & 1u);
+      const uint32_t smask = (__reduce_or_sync(0xffffffffu, surv ? (1u << hs) : 0u) >> gb) & gmask;
+      const int nkeep = __popc(alive & validm);
+      if (m > 0 && in_bounds((uint64_t)v < (uint64_t)a.n, a.err)) {
+        if (surv) a.keys_out[v * R + __popc(smask & lanes_below32(slot))] = key | 1ull;
+        // in place, the slots past m are empty already (pool rows end in empty slots)
+        const int pend = a.keys_out == a.keys_in ? m : R;
+        for (int t = nkeep + gl; t < pend; t += VW) a.keys_out[v * R + t] = kEmpty;
+        if (gl == 0) a.deg_out[v] = nkeep;
+      }
+      const int ndead = m - nkeep;
+      // redirects of all groups: one reservation per warp, groups in order
+      int pre = 0, tot = 0;
+  #pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int nd = __shfl_sync(0xffffffffu, ndead, (q << lw) & 31);
+        if (q < G) {
+          if (q < g) pre += nd;
+          tot += nd;
         }
       }
-    }
-    if (gl == 0 && m > 0) {
-      if (np > 0) {
-        st_vert += 1;
-        st_rows += m;
-        st_pairs += np;
+      if (a.emit_redirects && tot > 0) {
+        // fill the warp's chunk to its end, then continue in a fresh one (tot < WRED)
+        const unsigned long long base = s.red_next, end = s.red_end;
+        unsigned long long b1 = base, next = base + (unsigned long long)tot;
+        int avail = tot;
+        if (next > end) {
+          avail = (int)(end - base);
+          unsigned long long nb2 = 0;
+          if (lane == 0) nb2 = atomicAdd(a.red_n, (unsigned long long)WRED);
+          b1 = __shfl_sync(0xffffffffu, nb2, 0);
+          next = b1 + (unsigned long long)(tot - avail);
+          if (lane == 0) s.red_end = b1 + WRED;
+        }
+        __syncwarp();
+        if (lane == 0) s.red_next = next;
+        if (valid_p && !surv) {
+          const int ri = s.prow[gb + mykill], rj = row;
+          const int i = min(ri, rj), j = max(ri, rj);
+          const float dd = s.pd[pdb + s.roff[gb + i] + (j - i - 1)];
+          const int32_t tgt = s.pid[gb + mykill];
+          const int rk = pre + __popc(~alive & validm & below);
+          const unsigned long long sl = rk < avail ? base + (unsigned long long)rk : b1 + (unsigned long long)(rk - avail);
+          if (in_bounds(sl < (unsigned long long)a.red_cap && (uint64_t)(uint32_t)tgt < (uint64_t)a.n, a.err)) {
+            a.red_tgt[sl] = tgt;
+            a.red_key[sl] = make_key(dd, (uint32_t)id, 0u);
+            atomicAdd(&a.count[tgt], 1);
+          }
+        }
       }
-      st_fired += ndead;
-    }
-    __syncwarp();
+      if (gl == 0 && m > 0) {
+        if (np > 0) {
+          st_vert += 1;
+          st_rows += m;
+          st_pairs += np;
+        }
+        st_fired += ndead;
+      }
+      __syncwarp();
+    };
+    if (cur.cls == 2)
+      item(std::integral_constant<int, 32>{});
+    else if (cur.cls == 1)
+      item(std::integral_constant<int, 16>{});
+    else
+      item(std::integral_constant<int, 8>{});
+    if (quit) return;
     w = wnext;
     wnext = w2;
   }
