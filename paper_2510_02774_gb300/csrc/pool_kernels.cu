@@ -1552,9 +1552,11 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
       }
     }
     // the item's work, compiled once per lane-group width (VW = 32, 16 or 8 lanes per pool)
+    // and, for quantized rows, per mode (EX: the tiles are exact, no decision is re-taken)
     bool quit = false;  // a bounded wait gave up: the warp stops
-    auto item = [&](auto vw_tag) {
+    auto item = [&](auto vw_tag, auto ex_tag) {
       constexpr int VW = decltype(vw_tag)::value, lw = VW == 32 ? 5 : (VW == 16 ? 4 : 3), G = 32 / VW;
+      constexpr bool EX = decltype(ex_tag)::value;
       const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
       const uint32_t gmask = low_bits32(VW);
       const int m = cur.m;
@@ -1777,7 +1779,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
               const float mx = fmaxf(ri.y, rj.y);
               bool fire = dab < mx;
               const int pa2 = pI[e >> 1], pb2 = pJ[e & 1];
-              if (!exact) {
+              if constexpr (!EX) {
                 const float eqi = s.rdq[i], eqj = s.rdq[j];
                 const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
                 if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
@@ -1832,7 +1834,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
         return;
       }
       // queued re-decisions, one per lane: the FP32 rows of every pair load at once
-      if (PREC >= 1 && nch > 0) {
+      if (PREC >= 1 && !EX && nch > 0) {
         const int nq = min(s.nrq, WRQ);
         for (int t = lane; t < nq; t += 32) {
           const int i = s.rq[t] >> 5, j = s.rq[t] & 31;
@@ -1949,12 +1951,22 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
       }
       __syncwarp();
     };
-    if (cur.cls == 2)
-      item(std::integral_constant<int, 32>{});
-    else if (cur.cls == 1)
-      item(std::integral_constant<int, 16>{});
-    else
-      item(std::integral_constant<int, 8>{});
+    auto by_width = [&](auto ex_tag) {
+      if (cur.cls == 2)
+        item(std::integral_constant<int, 32>{}, ex_tag);
+      else if (cur.cls == 1)
+        item(std::integral_constant<int, 16>{}, ex_tag);
+      else
+        item(std::integral_constant<int, 8>{}, ex_tag);
+    };
+    if constexpr (PREC >= 1) {
+      if (exact)
+        by_width(std::true_type{});
+      else
+        by_width(std::false_type{});
+    } else {
+      by_width(std::false_type{});
+    }
     if (quit) return;
     w = wnext;
     wnext = w2;
