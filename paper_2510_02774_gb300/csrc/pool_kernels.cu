@@ -2159,381 +2159,398 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
   }
 
   while (p < cnt) {
-    const int64_t v = nv;
-    const uint32_t lo = nlo;  // first id of the vertex's build
-    const int m = nm;
-    const uint64_t keyl = tid < m ? nkey : kEmpty;
-    if (pnext < cnt) {
-      nv = (int64_t)(qr0 & 0xffffffffull);
-      nlo = (uint32_t)(qr0 >> 32);
-      nm = qm;
-      nkey = (tid < nm && in_bounds((uint64_t)nv < (uint64_t)a.n, a.err)) ? a.keys_in[nv * R + tid] : kEmpty;
-      if (tid == 0) s.next_p = (int64_t)gridDim.x + (int64_t)tq;
-    }
-    // ---- visit order: rank of (h, id) among the m entries --------------------------------
-    const uint32_t idl = key_id(keyl);
-    const bool has = tid < m;
-    uint64_t h = ~0ull;
-    if (has)  // (the serial orders put their index in the high bits)
-      h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - lo),
-                                          (uint64_t)(idl - lo))
-          : (a.order == 1) ? (uint64_t)tid << 32
-                           : (uint64_t)(m - 1 - tid) << 32;
-    {
-      TeamKey hk;
-      hk.h = h;
-      hk.id = has ? idl : 0xffffffffu;
-      hk.pad = 0u;
-      s.hk[tid] = hk;
-      s.hk32[tid] = has ? (uint32_t)(h >> 32) : 0xffffffffu;
-    }
-    {
-      const unsigned nw = __ballot_sync(0xffffffffu, has && !key_old(keyl));  // new entries by slot
-      if (lane == 0) s.sm32[warp] = nw;
-    }
-    if (tid == 0) s.nrq = 0;
-    __syncthreads();
-    const int64_t p2 = pnext < cnt ? s.next_p : cnt;  // the record after pnext
-    if (p2 < cnt) {
-      const uint64_t* rn = a.rec[3] + p2 * W;
-      qr0 = rn[0];
-      qm = (int)rn[1];
-      if (tid == 0) tq = atomicAdd(a.work_q + 1, 1u);
-    }
-    // rows: the new entries first, then the old ones, each part in storage-slot order (the
-    // pairs are enumerated over rows: new row i, any later row j, so the order inside each
-    // part does not matter); the first chunk's copies are in flight while the visit order
-    // is ranked
-    const uint64_t news = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);
-    const int k = __popcll(news);
-    const int np = k * (m - 1) - k * (k - 1) / 2;
-    const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
-    int row = 0;
-    if (has) {
-      const uint64_t bt = bits_below(tid);
-      row = ((news >> tid) & 1ull) ? __popcll(news & bt) : k + __popcll(~news & valid & bt);
-    }
-    const int nch = np > 0 ? nchd : 0;
-    auto issue = [&](int c, int st) {
-      const int c0 = c * TDC;
-      const int clen = min(TDC, d - c0);
-      const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-      // a quantized row's last chunk brings the row's terms (norm^2, residual) along
-      const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
-      if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
-      infl |= 1u << st;
+    // the record's work, compiled per mode for quantized rows (EX: exact tiles, no decision
+    // is re-taken)
+    int64_t p2 = cnt;
+    bool quit = false;  // a bounded wait gave up: the team stops
+    auto record = [&](auto ex_tag) {
+      constexpr bool EX = decltype(ex_tag)::value;
+      const int64_t v = nv;
+      const uint32_t lo = nlo;  // first id of the vertex's build
+      const int m = nm;
+      const uint64_t keyl = tid < m ? nkey : kEmpty;
+      if (pnext < cnt) {
+        nv = (int64_t)(qr0 & 0xffffffffull);
+        nlo = (uint32_t)(qr0 >> 32);
+        nm = qm;
+        nkey = (tid < nm && in_bounds((uint64_t)nv < (uint64_t)a.n, a.err)) ? a.keys_in[nv * R + tid] : kEmpty;
+        if (tid == 0) s.next_p = (int64_t)gridDim.x + (int64_t)tq;
+      }
+      // ---- visit order: rank of (h, id) among the m entries --------------------------------
+      const uint32_t idl = key_id(keyl);
+      const bool has = tid < m;
+      uint64_t h = ~0ull;
+      if (has)  // (the serial orders put their index in the high bits)
+        h = (a.order == 0)   ? hash_tail(head, (uint64_t)(v - lo),
+                                            (uint64_t)(idl - lo))
+            : (a.order == 1) ? (uint64_t)tid << 32
+                             : (uint64_t)(m - 1 - tid) << 32;
+      {
+        TeamKey hk;
+        hk.h = h;
+        hk.id = has ? idl : 0xffffffffu;
+        hk.pad = 0u;
+        s.hk[tid] = hk;
+        s.hk32[tid] = has ? (uint32_t)(h >> 32) : 0xffffffffu;
+      }
+      {
+        const unsigned nw = __ballot_sync(0xffffffffu, has && !key_old(keyl));  // new entries by slot
+        if (lane == 0) s.sm32[warp] = nw;
+      }
+      if (tid == 0) s.nrq = 0;
       __syncthreads();
-      // (checked build: a row id out of range is not copied; the stage's wait then gives up)
-      if (has && in_bounds((uint64_t)idl < (uint64_t)a.n, a.err)) {
-        const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
-                                   : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)idl * a.P.ldb + c0;
-        bulk_g2s(rowbase + ((size_t)st * TM + row) * C::RS, src, bytes, &s.bar[st]);
+      p2 = pnext < cnt ? s.next_p : cnt;  // the record after pnext
+      if (p2 < cnt) {
+        const uint64_t* rn = a.rec[3] + p2 * W;
+        qr0 = rn[0];
+        qm = (int)rn[1];
+        if (tid == 0) tq = atomicAdd(a.work_q + 1, 1u);
       }
-    };
-    if (nch > 0) issue(0, stage);
-    // position = rank of the entry's key among the m entries: over the high 32 hash bits
-    // (entries past m hold ~0 there and never count), then checked: equal high bits leave
-    // two entries with one rank, and the ranks are taken again over the full (h, id)
-    int pi = 0;
-    if (has) {
-      const uint32_t k32 = (uint32_t)(h >> 32);
-      for (int f = 0; f < m; f += 4) {
-        const uint4 o = *reinterpret_cast<const uint4*>(&s.hk32[f]);
-        pi += (o.x < k32 ? 1 : 0) + (o.y < k32 ? 1 : 0) + (o.z < k32 ? 1 : 0) + (o.w < k32 ? 1 : 0);
+      // rows: the new entries first, then the old ones, each part in storage-slot order (the
+      // pairs are enumerated over rows: new row i, any later row j, so the order inside each
+      // part does not matter); the first chunk's copies are in flight while the visit order
+      // is ranked
+      const uint64_t news = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);
+      const int k = __popcll(news);
+      const int np = k * (m - 1) - k * (k - 1) / 2;
+      const uint64_t valid = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+      int row = 0;
+      if (has) {
+        const uint64_t bt = bits_below(tid);
+        row = ((news >> tid) & 1ull) ? __popcll(news & bt) : k + __popcll(~news & valid & bt);
       }
-      s.prow[pi] = (uint8_t)tid;  // this rank's claim
-    }
-    // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
-    // closer mask of a position is the OR of the position bits of the slots before its own
-    uint64_t pbit = has ? (1ull << pi) : 0ull;
-    uint64_t pre = pbit;
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
-      if (lane >= dd) pre |= y;
-    }
-    if (warp == 0 && lane == 31) s.wtot = pre;
-    __syncthreads();
-    if (__syncthreads_or(has && s.prow[pi] != (uint8_t)tid)) {  // a tie in the high bits
-      pi = 0;
-      if (has)
-        for (int f = 0; f < m; ++f) {
-          const TeamKey o = s.hk[f];
-          pi += (o.h < h) || (o.h == h && o.id < idl);
+      const int nch = np > 0 ? nchd : 0;
+      auto issue = [&](int c, int st) {
+        const int c0 = c * TDC;
+        const int clen = min(TDC, d - c0);
+        const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+        // a quantized row's last chunk brings the row's terms (norm^2, residual) along
+        const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
+        if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
+        infl |= 1u << st;
+        __syncthreads();
+        // (checked build: a row id out of range is not copied; the stage's wait then gives up)
+        if (has && in_bounds((uint64_t)idl < (uint64_t)a.n, a.err)) {
+          const T* src = (PREC == 0) ? reinterpret_cast<const T*>(a.P.X + (int64_t)idl * a.P.ld + c0)
+                                     : reinterpret_cast<const T*>(a.P.Xb) + (int64_t)idl * a.P.ldb + c0;
+          bulk_g2s(rowbase + ((size_t)st * TM + row) * C::RS, src, bytes, &s.bar[st]);
         }
-      pbit = has ? (1ull << pi) : 0ull;
-      pre = pbit;
-#pragma unroll
+      };
+      if (nch > 0) issue(0, stage);
+      // position = rank of the entry's key among the m entries: over the high 32 hash bits
+      // (entries past m hold ~0 there and never count), then checked: equal high bits leave
+      // two entries with one rank, and the ranks are taken again over the full (h, id)
+      int pi = 0;
+      if (has) {
+        const uint32_t k32 = (uint32_t)(h >> 32);
+        for (int f = 0; f < m; f += 4) {
+          const uint4 o = *reinterpret_cast<const uint4*>(&s.hk32[f]);
+          pi += (o.x < k32 ? 1 : 0) + (o.y < k32 ? 1 : 0) + (o.z < k32 ? 1 : 0) + (o.w < k32 ? 1 : 0);
+        }
+        s.prow[pi] = (uint8_t)tid;  // this rank's claim
+      }
+      // "closer to v" is storage-slot order (rows hold their keys in ascending order): the
+      // closer mask of a position is the OR of the position bits of the slots before its own
+      uint64_t pbit = has ? (1ull << pi) : 0ull;
+      uint64_t pre = pbit;
+  #pragma unroll
       for (int dd = 1; dd < 32; dd <<= 1) {
         const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
         if (lane >= dd) pre |= y;
       }
       if (warp == 0 && lane == 31) s.wtot = pre;
       __syncthreads();
-    }
-    if (warp == 1) pre |= s.wtot;
-    if (has) {
-      s.pid[pi] = (int32_t)idl;
-      s.prow[pi] = (uint8_t)row;
-      s.rpos[row] = (uint8_t)pi;
-      s.closer[pi] = pre ^ pbit;
-      // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
-      s.rnd[row] = make_float2(0.0f, key_dist(keyl));
-    }
-    if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
-    s.fire[tid] = 0ull;  // fire bits are set by the pairs that fire (shared atomics)
-    __syncthreads();
-
-    // ---- gather + tile (chunk 0 is in flight since before the visit order) --------------
-    bool fail = false;
-    for (int c = 0; c < nch; ++c) {
-      const int st = stage;
-      if (nst > 1 && c + 1 < nch) issue(c + 1, st ^ 1);
-      const bool ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
-      if (__syncthreads_or(!ok)) {  // uniform over the team
-        fail = true;
-        break;
+      if (__syncthreads_or(has && s.prow[pi] != (uint8_t)tid)) {  // a tie in the high bits
+        pi = 0;
+        if (has)
+          for (int f = 0; f < m; ++f) {
+            const TeamKey o = s.hk[f];
+            pi += (o.h < h) || (o.h == h && o.id < idl);
+          }
+        pbit = has ? (1ull << pi) : 0ull;
+        pre = pbit;
+  #pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const uint64_t y = __shfl_up_sync(0xffffffffu, pre, dd);
+          if (lane >= dd) pre |= y;
+        }
+        if (warp == 0 && lane == 31) s.wtot = pre;
+        __syncthreads();
       }
-      phb ^= 1u << st;
-      infl &= ~(1u << st);
-      const int clen = min(TDC, d - c * TDC);
-      const T* rows = rowbase + (size_t)st * TM * C::RS;
-      if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
-        if (has) {
-          const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
-          const float2 t = *reinterpret_cast<const float2*>(rows + (size_t)row * C::RS + cpy);
-          s.rnd[row].x = t.x;
-          s.rdq[row] = t.y;
+      if (warp == 1) pre |= s.wtot;
+      if (has) {
+        s.pid[pi] = (int32_t)idl;
+        s.prow[pi] = (uint8_t)row;
+        s.rpos[row] = (uint8_t)pi;
+        s.closer[pi] = pre ^ pbit;
+        // (BF16 / FP8: the quantized row's norm^2 and residual arrive with its last chunk)
+        s.rnd[row] = make_float2(0.0f, key_dist(keyl));
+      }
+      if (tid <= k) s.roff[tid] = tid * (m - 1) - tid * (tid - 1) / 2;
+      s.fire[tid] = 0ull;  // fire bits are set by the pairs that fire (shared atomics)
+      __syncthreads();
+
+      // ---- gather + tile (chunk 0 is in flight since before the visit order) --------------
+      bool fail = false;
+      for (int c = 0; c < nch; ++c) {
+        const int st = stage;
+        if (nst > 1 && c + 1 < nch) issue(c + 1, st ^ 1);
+        const bool ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
+        if (__syncthreads_or(!ok)) {  // uniform over the team
+          fail = true;
+          break;
+        }
+        phb ^= 1u << st;
+        infl &= ~(1u << st);
+        const int clen = min(TDC, d - c * TDC);
+        const T* rows = rowbase + (size_t)st * TM * C::RS;
+        if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
+          if (has) {
+            const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
+            const float2 t = *reinterpret_cast<const float2*>(rows + (size_t)row * C::RS + cpy);
+            s.rnd[row].x = t.x;
+            s.rdq[row] = t.y;
+          }
+          __syncthreads();
+        }
+        if (PREC >= 1) {
+          constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
+          const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
+          const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
+          const bool first_c = (c == 0), last_c = (c + 1 == nch);
+          const int g = lane >> 2, tg = lane & 3;
+          for (int t = warp; t < kTeamTiles; t += 2) {
+            int I, J;
+            team_tile(t, I, J);
+            if (I >= KI || J >= NJ) continue;
+            // this lane's four elements: rows i0, i0 + 8 and columns j0, j0 + 1
+            const int i0 = I * 16 + g, j0 = J * 8 + 2 * tg;
+            int q[4];
+            bool ve[4];
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+              ve[e] = (i < k) && (j > i) && (j < m);
+              q[e] = ve[e] ? s.roff[i] + (j - i - 1) : 0;
+            }
+            float acc[4];
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
+            const int ra = min(I * 16 + (lane & 15), TM - 1);
+            const int rb = J * 8 + (lane & 7);
+            const T* pa = rows + ra * C::RS + (lane >> 4) * KB;
+            const T* pb = rows + rb * C::RS + ((lane >> 3) & 1) * KB;
+            for (int ks = 0; ks < ksteps; ++ks) {
+              uint32_t fa[4], fb[2];
+              ldmatrix_x4(fa, pa + ks * 2 * KB);
+              ldmatrix_x2(fb, pb + ks * 2 * KB);
+              mma_q<PREC>(acc, fa, fb);
+            }
+            if (!last_c) {
+  #pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (ve[e]) s.pd[q[e]] = acc[e];
+              continue;
+            }
+            // last chunk: distance and fire decision of each element
+            const float2 rI[2] = {s.rnd[min(i0, TM - 1)], s.rnd[min(i0 + 8, TM - 1)]};
+            const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
+            float scI[2] = {1.0f, 1.0f}, scJ[2] = {1.0f, 1.0f};
+            if (PREC == 2) {  // the rows' power-of-two scales (exact products)
+              scI[0] = q_scale(s.rdq[min(i0, TM - 1)]);
+              scI[1] = q_scale(s.rdq[min(i0 + 8, TM - 1)]);
+              scJ[0] = q_scale(s.rdq[j0]);
+              scJ[1] = q_scale(s.rdq[j0 + 1]);
+            }
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (!ve[e]) continue;
+              const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
+              const float2 ri = rI[e >> 1], rj = rJ[e & 1];
+              const float gij = (PREC == 2) ? acc[e] * scI[e >> 1] * scJ[e & 1] : acc[e];
+              float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
+                                        : __fsub_rn(1.0f, gij);
+              const float mx = fmaxf(ri.y, rj.y);
+              bool fire = dab < mx;
+              if constexpr (!EX) {
+                const float eqi = s.rdq[i], eqj = s.rdq[j];
+                const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
+                if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
+                  ++st_check;
+                  const int slot = atomicAdd(&s.nrq, 1);
+                  if (slot < TRQ) {
+                    s.rq[slot] = (uint16_t)((i << 6) | j);  // taken below, all together
+                    continue;
+                  }
+                  const float* xa = a.P.X + (int64_t)s.pid[s.rpos[i]] * a.P.ld;
+                  const float* xb = a.P.X + (int64_t)s.pid[s.rpos[j]] * a.P.ld;
+                  dab = row_dist<METRIC>(xa, xb, d);
+                  fire = dab < mx;
+                }
+              }
+              s.pd[q[e]] = dab;
+              const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+              if (fire)
+                atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa2, pb2)]), 1ull << min(pa2, pb2));
+            }
+          }
+        } else {
+          const float* rf = reinterpret_cast<const float*>(rows);
+          const int full4 = clen & ~3, rem = clen & 3;
+          for (int q = tid; q < np; q += TM) {
+            int i = 0;  // the new row owning pair q
+  #pragma unroll
+            for (int w = 32; w > 0; w >>= 1)
+              if (i + w < k && s.roff[i + w] <= q) i += w;
+            const int j = i + 1 + (q - s.roff[i]);
+            const float* ra = rf + i * C::RS;
+            const float* rb = rf + j * C::RS;
+            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int u = 0; u < full4; u += 4)
+              dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
+                                 *reinterpret_cast<const float4*>(rb + u));
+            if (rem)
+              dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
+                                 mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
+            const float dab = dist_finish4<METRIC>(acc);
+            s.pd[q] = dab;
+            const int pa = s.rpos[i], pb = s.rpos[j];
+            if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y))
+              atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa, pb)]), 1ull << min(pa, pb));
+          }
+        }
+        __syncthreads();
+        if (nst > 1) stage ^= 1;
+      }
+      if (fail) {  // a bounded wait gave up: report, let the copies in flight land, stop
+        if (tid == 0) atomicExch(a.err, kErrTimeout);
+        for (int t = 0; t < 2; ++t)
+          if ((infl >> t) & 1u) mbar_wait(&s.bar[t], (phb >> t) & 1u, kWaitLimit);
+        if (a.emit_redirects)
+          for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
+        quit = true;
+        return;
+      }
+
+      // queued re-decisions, one per thread: the FP32 rows of every pair load at once
+      if (PREC >= 1 && !EX && nch > 0 && s.nrq > 0) {
+        const int nq = min(s.nrq, TRQ);
+        for (int t = tid; t < nq; t += TM) {
+          const int i = s.rq[t] >> 6, j = s.rq[t] & 63;
+          const int pa2 = s.rpos[i], pb2 = s.rpos[j];
+          const float* xa = a.P.X + (int64_t)s.pid[pa2] * a.P.ld;
+          const float* xb = a.P.X + (int64_t)s.pid[pb2] * a.P.ld;
+          const float dab = row_dist<METRIC>(xa, xb, d);
+          s.pd[s.roff[i] + (j - i - 1)] = dab;
+          if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y))
+            atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa2, pb2)]), 1ull << min(pa2, pb2));
         }
         __syncthreads();
       }
-      if (PREC >= 1) {
-        constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
-        const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
-        const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-        const bool first_c = (c == 0), last_c = (c + 1 == nch);
-        const int g = lane >> 2, tg = lane & 3;
-        for (int t = warp; t < kTeamTiles; t += 2) {
-          int I, J;
-          team_tile(t, I, J);
-          if (I >= KI || J >= NJ) continue;
-          // this lane's four elements: rows i0, i0 + 8 and columns j0, j0 + 1
-          const int i0 = I * 16 + g, j0 = J * 8 + 2 * tg;
-          int q[4];
-          bool ve[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
-            ve[e] = (i < k) && (j > i) && (j < m);
-            q[e] = ve[e] ? s.roff[i] + (j - i - 1) : 0;
+      // ---- prune: the chain's outcome, one column (pi position) per thread ------------------
+      // Column b of the sequential pair scan kills K_b: its live firing partners before the
+      // first closer one f, then b itself (absorbed by f); all of them when none is closer.
+      // Its live partners are the valid positions that no column c < b killed, so the scan's
+      // outcome is the fixed point of K_b = rule(fire[b] & valid & ~OR_{c<b} K_c).  Rounds
+      // that apply the rule to every column at once, from K = 0, reach it: after round r the
+      // columns 0..r hold their final value, so it takes at most m rounds; the first round
+      // whose K has the prefix it was computed from is the fixed point and ends the loop.
+      {
+        const uint64_t fb = s.fire[tid], cb = s.closer[tid];
+        // the OR of K over the earlier columns: bw of this warp's, t0 of warp 0's (for warp 1)
+        uint64_t K = 0ull, bw = 0ull, t0 = 0ull;
+        int f = -1, r = 0;
+        for (;; ++r) {
+          const uint64_t cand = fb & valid & ~(bw | (warp == 1 ? t0 : 0ull));
+          const uint64_t x = cand & cb;
+          f = x ? __ffsll((long long)x) - 1 : -1;
+          K = x ? ((cand & bits_below(f)) | (1ull << tid)) : cand;
+          uint64_t inc = K;  // inclusive prefix OR over the warp's columns
+  #pragma unroll
+          for (int dd = 1; dd < 32; dd <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, inc, dd);
+            if (lane >= dd) inc |= y;
           }
-          float acc[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[e] = (!first_c && ve[e]) ? s.pd[q[e]] : 0.0f;
-          const int ra = min(I * 16 + (lane & 15), TM - 1);
-          const int rb = J * 8 + (lane & 7);
-          const T* pa = rows + ra * C::RS + (lane >> 4) * KB;
-          const T* pb = rows + rb * C::RS + ((lane >> 3) & 1) * KB;
-          for (int ks = 0; ks < ksteps; ++ks) {
-            uint32_t fa[4], fb[2];
-            ldmatrix_x4(fa, pa + ks * 2 * KB);
-            ldmatrix_x2(fb, pb + ks * 2 * KB);
-            mma_q<PREC>(acc, fa, fb);
-          }
-          if (!last_c) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (ve[e]) s.pd[q[e]] = acc[e];
-            continue;
-          }
-          // last chunk: distance and fire decision of each element
-          const float2 rI[2] = {s.rnd[min(i0, TM - 1)], s.rnd[min(i0 + 8, TM - 1)]};
-          const float2 rJ[2] = {s.rnd[j0], s.rnd[j0 + 1]};
-          float scI[2] = {1.0f, 1.0f}, scJ[2] = {1.0f, 1.0f};
-          if (PREC == 2) {  // the rows' power-of-two scales (exact products)
-            scI[0] = q_scale(s.rdq[min(i0, TM - 1)]);
-            scI[1] = q_scale(s.rdq[min(i0 + 8, TM - 1)]);
-            scJ[0] = q_scale(s.rdq[j0]);
-            scJ[1] = q_scale(s.rdq[j0 + 1]);
-          }
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (!ve[e]) continue;
-            const int i = i0 + ((e >> 1) << 3), j = j0 + (e & 1);
-            const float2 ri = rI[e >> 1], rj = rJ[e & 1];
-            const float gij = (PREC == 2) ? acc[e] * scI[e >> 1] * scJ[e & 1] : acc[e];
-            float dab = (METRIC == 0) ? __fadd_rn(__fsub_rn(ri.x, gij), __fsub_rn(rj.x, gij))
-                                      : __fsub_rn(1.0f, gij);
-            const float mx = fmaxf(ri.y, rj.y);
-            bool fire = dab < mx;
-            if (!exact) {
-              const float eqi = s.rdq[i], eqj = s.rdq[j];
-              const float tol = bf16_bound<METRIC>(dab, ri.x, rj.x, eqi, eqj, d);
-              if (fabsf(dab - mx) <= tol) {  // re-decide with the canonical FP32 d(a,b)
-                ++st_check;
-                const int slot = atomicAdd(&s.nrq, 1);
-                if (slot < TRQ) {
-                  s.rq[slot] = (uint16_t)((i << 6) | j);  // taken below, all together
-                  continue;
-                }
-                const float* xa = a.P.X + (int64_t)s.pid[s.rpos[i]] * a.P.ld;
-                const float* xb = a.P.X + (int64_t)s.pid[s.rpos[j]] * a.P.ld;
-                dab = row_dist<METRIC>(xa, xb, d);
-                fire = dab < mx;
-              }
-            }
-            s.pd[q[e]] = dab;
-            const int pa2 = s.rpos[i], pb2 = s.rpos[j];
-            if (fire)
-              atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa2, pb2)]), 1ull << min(pa2, pb2));
-          }
+          uint64_t bwn = __shfl_up_sync(0xffffffffu, inc, 1);
+          if (lane == 0) bwn = 0ull;
+          if (lane == 31) s.kor[r & 1][warp] = inc;
+          // the new K has the prefix this round used: it is the fixed point
+          const bool moved = __syncthreads_or(bwn != bw || (warp == 0 && lane == 31 && inc != t0)) != 0;
+          if (!moved || r >= TM) break;
+          bw = bwn;
+          t0 = s.kor[r & 1][0];
         }
-      } else {
-        const float* rf = reinterpret_cast<const float*>(rows);
-        const int full4 = clen & ~3, rem = clen & 3;
-        for (int q = tid; q < np; q += TM) {
-          int i = 0;  // the new row owning pair q
-#pragma unroll
-          for (int w = 32; w > 0; w >>= 1)
-            if (i + w < k && s.roff[i + w] <= q) i += w;
-          const int j = i + 1 + (q - s.roff[i]);
-          const float* ra = rf + i * C::RS;
-          const float* rb = rf + j * C::RS;
-          float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          for (int u = 0; u < full4; u += 4)
-            dist_step4<METRIC>(acc, *reinterpret_cast<const float4*>(ra + u),
-                               *reinterpret_cast<const float4*>(rb + u));
-          if (rem)
-            dist_step4<METRIC>(acc, mask4(*reinterpret_cast<const float4*>(ra + full4), rem),
-                               mask4(*reinterpret_cast<const float4*>(rb + full4), rem));
-          const float dab = dist_finish4<METRIC>(acc);
-          s.pd[q] = dab;
-          const int pa = s.rpos[i], pb = s.rpos[j];
-          if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y))
-            atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa, pb)]), 1ull << min(pa, pb));
-        }
+        // absorbers: b for the partners it kills, f for b itself
+        for (uint64_t ab = K & ~(1ull << tid); ab; ab &= ab - 1) s.killer[__ffsll((long long)ab) - 1] = (uint8_t)tid;
+        if (f >= 0) s.killer[tid] = (uint8_t)f;
+        if (tid == 0) s.alive = valid & ~(s.kor[r & 1][0] | s.kor[r & 1][1]);
       }
       __syncthreads();
-      if (nst > 1) stage ^= 1;
-    }
-    if (fail) {  // a bounded wait gave up: report, let the copies in flight land, stop
-      if (tid == 0) atomicExch(a.err, kErrTimeout);
-      for (int t = 0; t < 2; ++t)
-        if ((infl >> t) & 1u) mbar_wait(&s.bar[t], (phb >> t) & 1u, kWaitLimit);
-      if (a.emit_redirects)
-        for (unsigned long long i = s.red_next + tid; i < s.red_end; i += TM) a.red_tgt[i] = -1;
-      return;
-    }
-
-    // queued re-decisions, one per thread: the FP32 rows of every pair load at once
-    if (PREC >= 1 && nch > 0 && s.nrq > 0) {
-      const int nq = min(s.nrq, TRQ);
-      for (int t = tid; t < nq; t += TM) {
-        const int i = s.rq[t] >> 6, j = s.rq[t] & 63;
-        const int pa2 = s.rpos[i], pb2 = s.rpos[j];
-        const float* xa = a.P.X + (int64_t)s.pid[pa2] * a.P.ld;
-        const float* xb = a.P.X + (int64_t)s.pid[pb2] * a.P.ld;
-        const float dab = row_dist<METRIC>(xa, xb, d);
-        s.pd[s.roff[i] + (j - i - 1)] = dab;
-        if (dab < fmaxf(s.rnd[i].y, s.rnd[j].y))
-          atomicOr(reinterpret_cast<unsigned long long*>(&s.fire[max(pa2, pb2)]), 1ull << min(pa2, pb2));
+      // ---- emit ------------------------------------------------------------------------------
+      const uint64_t alive = s.alive;
+      const bool surv = has && ((alive >> pi) & 1ull);
+      const unsigned sb = __ballot_sync(0xffffffffu, surv);
+      if (lane == 0) s.sm32[warp] = sb;
+      const int nkeep = __popcll(alive & valid);
+      const int ndead = m - nkeep;
+      if (a.emit_redirects && tid == 0 && ndead > 0) {
+        // fill the team's chunk to its end, then continue in a fresh one (ndead < TRED)
+        const unsigned long long base = s.red_next;
+        unsigned long long b1 = base, next = base + (unsigned long long)ndead;
+        int avail = ndead;
+        if (next > s.red_end) {
+          avail = (int)(s.red_end - base);
+          b1 = atomicAdd(a.red_n, (unsigned long long)TRED);
+          next = b1 + (unsigned long long)(ndead - avail);
+          s.red_end = b1 + TRED;
+        }
+        s.red_next = next;
+        s.red_b0 = base;
+        s.red_b1 = b1;
+        s.red_avail = avail;
       }
       __syncthreads();
-    }
-    // ---- prune: the chain's outcome, one column (pi position) per thread ------------------
-    // Column b of the sequential pair scan kills K_b: its live firing partners before the
-    // first closer one f, then b itself (absorbed by f); all of them when none is closer.
-    // Its live partners are the valid positions that no column c < b killed, so the scan's
-    // outcome is the fixed point of K_b = rule(fire[b] & valid & ~OR_{c<b} K_c).  Rounds
-    // that apply the rule to every column at once, from K = 0, reach it: after round r the
-    // columns 0..r hold their final value, so it takes at most m rounds; the first round
-    // whose K has the prefix it was computed from is the fixed point and ends the loop.
-    {
-      const uint64_t fb = s.fire[tid], cb = s.closer[tid];
-      // the OR of K over the earlier columns: bw of this warp's, t0 of warp 0's (for warp 1)
-      uint64_t K = 0ull, bw = 0ull, t0 = 0ull;
-      int f = -1, r = 0;
-      for (;; ++r) {
-        const uint64_t cand = fb & valid & ~(bw | (warp == 1 ? t0 : 0ull));
-        const uint64_t x = cand & cb;
-        f = x ? __ffsll((long long)x) - 1 : -1;
-        K = x ? ((cand & bits_below(f)) | (1ull << tid)) : cand;
-        uint64_t inc = K;  // inclusive prefix OR over the warp's columns
-#pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-          const uint64_t y = __shfl_up_sync(0xffffffffu, inc, dd);
-          if (lane >= dd) inc |= y;
+      const uint64_t smask = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);  // survivors by slot
+      const bool vok = in_bounds((uint64_t)v < (uint64_t)a.n, a.err);
+      if (surv && vok) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
+      // in place, the slots past m are empty already (pool rows end in empty slots)
+      const int pend = a.keys_out == a.keys_in ? m : R;
+      for (int t = nkeep + tid; vok && t < pend; t += TM) a.keys_out[v * R + t] = kEmpty;
+      if (tid == 0 && vok) a.deg_out[v] = nkeep;
+      if (a.emit_redirects && has && !surv) {
+        const int kp = s.killer[pi];
+        const int ri = s.prow[kp], rj = row;
+        const int i = min(ri, rj), j = max(ri, rj);
+        const float dd = s.pd[s.roff[i] + (j - i - 1)];
+        const int32_t tgt = s.pid[kp];
+        const int g = __popcll(~alive & valid & bits_below(pi));
+        const unsigned long long sl =
+            g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
+        if (in_bounds(sl < (unsigned long long)a.red_cap && (uint64_t)(uint32_t)tgt < (uint64_t)a.n, a.err)) {
+          a.red_tgt[sl] = tgt;
+          a.red_key[sl] = make_key(dd, idl, 0u);
+          atomicAdd(&a.count[tgt], 1);
         }
-        uint64_t bwn = __shfl_up_sync(0xffffffffu, inc, 1);
-        if (lane == 0) bwn = 0ull;
-        if (lane == 31) s.kor[r & 1][warp] = inc;
-        // the new K has the prefix this round used: it is the fixed point
-        const bool moved = __syncthreads_or(bwn != bw || (warp == 0 && lane == 31 && inc != t0)) != 0;
-        if (!moved || r >= TM) break;
-        bw = bwn;
-        t0 = s.kor[r & 1][0];
       }
-      // absorbers: b for the partners it kills, f for b itself
-      for (uint64_t ab = K & ~(1ull << tid); ab; ab &= ab - 1) s.killer[__ffsll((long long)ab) - 1] = (uint8_t)tid;
-      if (f >= 0) s.killer[tid] = (uint8_t)f;
-      if (tid == 0) s.alive = valid & ~(s.kor[r & 1][0] | s.kor[r & 1][1]);
-    }
-    __syncthreads();
-    // ---- emit ------------------------------------------------------------------------------
-    const uint64_t alive = s.alive;
-    const bool surv = has && ((alive >> pi) & 1ull);
-    const unsigned sb = __ballot_sync(0xffffffffu, surv);
-    if (lane == 0) s.sm32[warp] = sb;
-    const int nkeep = __popcll(alive & valid);
-    const int ndead = m - nkeep;
-    if (a.emit_redirects && tid == 0 && ndead > 0) {
-      // fill the team's chunk to its end, then continue in a fresh one (ndead < TRED)
-      const unsigned long long base = s.red_next;
-      unsigned long long b1 = base, next = base + (unsigned long long)ndead;
-      int avail = ndead;
-      if (next > s.red_end) {
-        avail = (int)(s.red_end - base);
-        b1 = atomicAdd(a.red_n, (unsigned long long)TRED);
-        next = b1 + (unsigned long long)(ndead - avail);
-        s.red_end = b1 + TRED;
+      if (tid == 0) {
+        if (np > 0) {
+          st_vert += 1;
+          st_rows += m;
+          st_pairs += np;
+        }
+        st_fired += ndead;
       }
-      s.red_next = next;
-      s.red_b0 = base;
-      s.red_b1 = b1;
-      s.red_avail = avail;
+      __syncthreads();
+    };
+    if constexpr (PREC >= 1) {
+      if (exact)
+        record(std::true_type{});
+      else
+        record(std::false_type{});
+    } else {
+      record(std::false_type{});
     }
-    __syncthreads();
-    const uint64_t smask = (uint64_t)s.sm32[0] | ((uint64_t)s.sm32[1] << 32);  // survivors by slot
-    const bool vok = in_bounds((uint64_t)v < (uint64_t)a.n, a.err);
-    if (surv && vok) a.keys_out[v * R + __popcll(smask & bits_below(tid))] = keyl | 1ull;
-    // in place, the slots past m are empty already (pool rows end in empty slots)
-    const int pend = a.keys_out == a.keys_in ? m : R;
-    for (int t = nkeep + tid; vok && t < pend; t += TM) a.keys_out[v * R + t] = kEmpty;
-    if (tid == 0 && vok) a.deg_out[v] = nkeep;
-    if (a.emit_redirects && has && !surv) {
-      const int kp = s.killer[pi];
-      const int ri = s.prow[kp], rj = row;
-      const int i = min(ri, rj), j = max(ri, rj);
-      const float dd = s.pd[s.roff[i] + (j - i - 1)];
-      const int32_t tgt = s.pid[kp];
-      const int g = __popcll(~alive & valid & bits_below(pi));
-      const unsigned long long sl =
-          g < s.red_avail ? s.red_b0 + (unsigned long long)g : s.red_b1 + (unsigned long long)(g - s.red_avail);
-      if (in_bounds(sl < (unsigned long long)a.red_cap && (uint64_t)(uint32_t)tgt < (uint64_t)a.n, a.err)) {
-        a.red_tgt[sl] = tgt;
-        a.red_key[sl] = make_key(dd, idl, 0u);
-        atomicAdd(&a.count[tgt], 1);
-      }
-    }
-    if (tid == 0) {
-      if (np > 0) {
-        st_vert += 1;
-        st_rows += m;
-        st_pairs += np;
-      }
-      st_fired += ndead;
-    }
-    __syncthreads();
+    if (quit) return;
     p = pnext;
     pnext = p2;
   }
