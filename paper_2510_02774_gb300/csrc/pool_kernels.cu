@@ -1551,12 +1551,13 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
         if (lane == 0 && w2 + GW >= S) tq = atomicAdd(a.work_q, 1u);
       }
     }
-    // the item's work, compiled once per lane-group width (VW = 32, 16 or 8 lanes per pool)
-    // and, for quantized rows, per mode (EX: the tiles are exact, no decision is re-taken)
+    // the item's work, compiled once per lane-group width (VW = 32, 16 or 8 lanes per pool),
+    // for quantized rows per mode (EX: the tiles are exact, no decision is re-taken), and for
+    // rows of one chunk (ONE: d <= WDC) apart from longer rows
     bool quit = false;  // a bounded wait gave up: the warp stops
-    auto item = [&](auto vw_tag, auto ex_tag) {
+    auto item = [&](auto vw_tag, auto ex_tag, auto one_tag) {
       constexpr int VW = decltype(vw_tag)::value, lw = VW == 32 ? 5 : (VW == 16 ? 4 : 3), G = 32 / VW;
-      constexpr bool EX = decltype(ex_tag)::value;
+      constexpr bool EX = decltype(ex_tag)::value, ONE = decltype(one_tag)::value;
       const int g = lane >> lw, gl = lane & (VW - 1), gb = g << lw;
       const uint32_t gmask = low_bits32(VW);
       const int m = cur.m;
@@ -1602,7 +1603,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
         }
         const int cpy = (min(WDC, d - c0) + C::VEC - 1) / C::VEC * C::VEC;
         // a quantized row's last chunk brings the row's terms (norm^2, residual) along
-        const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
+        const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && (ONE || c + 1 == nchd)) ? (uint32_t)kTailCopy : 0u);
         if (lane == 0) mbar_expect_tx(&s.bar, (uint32_t)__popc(needm) * bytes);
         inflight = true;
         __syncwarp();
@@ -1696,12 +1697,12 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
       for (int c = 0; c < nch; ++c) {
         const int c0 = c * WDC;
         const int clen = min(WDC, d - c0);
-        if (c > 0) issue(c);  // (chunk 0 is in flight since before the visit order)
+        if (!ONE && c > 0) issue(c);  // (chunk 0 is in flight since before the visit order)
         ok = mbar_wait(&s.bar, phb, kWaitLimit);
         if (!__all_sync(0xffffffffu, ok)) break;
         phb ^= 1u;
         inflight = false;
-        if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
+        if (PREC >= 1 && (ONE || c + 1 == nch)) {  // each row's terms, from its tail
           if (need) {
             const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
             const float2 t = *reinterpret_cast<const float2*>(wrow(s, gb + row_s) + cpy);
@@ -1716,7 +1717,7 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
           constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
           const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
           const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;  // used when one vertex fills the warp
-          const bool first_c = (c == 0), last_c = (c + 1 == nch);
+          const bool first_c = ONE || c == 0, last_c = ONE || c + 1 == nch;
           const int g8 = lane >> 2, tg = lane & 3;
           const int npg = (VW * (VW - 1)) >> 1;  // pairs per lane group
           for (int t = 0; t < 6; ++t) {
@@ -1951,21 +1952,31 @@ __global__ void __launch_bounds__(WW * 32, 4) rnd_join_warp_kernel(const __grid_
       }
       __syncwarp();
     };
-    auto by_width = [&](auto ex_tag) {
+    auto by_width = [&](auto ex_tag, auto one_tag) {
       if (cur.cls == 2)
-        item(std::integral_constant<int, 32>{}, ex_tag);
+        item(std::integral_constant<int, 32>{}, ex_tag, one_tag);
       else if (cur.cls == 1)
-        item(std::integral_constant<int, 16>{}, ex_tag);
+        item(std::integral_constant<int, 16>{}, ex_tag, one_tag);
       else
-        item(std::integral_constant<int, 8>{}, ex_tag);
+        item(std::integral_constant<int, 8>{}, ex_tag, one_tag);
+    };
+    auto by_chunks = [&](auto ex_tag) {
+      if constexpr (PREC == 1) {  // (the one-chunk variant for the BF16 form only: compile time)
+        if (nchd == 1)
+          by_width(ex_tag, std::true_type{});
+        else
+          by_width(ex_tag, std::false_type{});
+      } else {
+        by_width(ex_tag, std::false_type{});
+      }
     };
     if constexpr (PREC >= 1) {
       if (exact)
-        by_width(std::true_type{});
+        by_chunks(std::true_type{});
       else
-        by_width(std::false_type{});
+        by_chunks(std::false_type{});
     } else {
-      by_width(std::false_type{});
+      by_chunks(std::false_type{});
     }
     if (quit) return;
     w = wnext;
@@ -2160,11 +2171,11 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
 
   while (p < cnt) {
     // the record's work, compiled per mode for quantized rows (EX: exact tiles, no decision
-    // is re-taken)
+    // is re-taken) and, for BF16 rows, per length (ONE: one chunk of columns)
     int64_t p2 = cnt;
     bool quit = false;  // a bounded wait gave up: the team stops
-    auto record = [&](auto ex_tag) {
-      constexpr bool EX = decltype(ex_tag)::value;
+    auto record = [&](auto ex_tag, auto one_tag) {
+      constexpr bool EX = decltype(ex_tag)::value, ONE = decltype(one_tag)::value;
       const int64_t v = nv;
       const uint32_t lo = nlo;  // first id of the vertex's build
       const int m = nm;
@@ -2225,7 +2236,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         const int clen = min(TDC, d - c0);
         const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
         // a quantized row's last chunk brings the row's terms (norm^2, residual) along
-        const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && c + 1 == nchd) ? (uint32_t)kTailCopy : 0u);
+        const uint32_t bytes = (uint32_t)(cpy * sizeof(T)) + ((PREC >= 1 && (ONE || c + 1 == nchd)) ? (uint32_t)kTailCopy : 0u);
         if (tid == 0) mbar_expect_tx(&s.bar[st], (uint32_t)m * bytes);
         infl |= 1u << st;
         __syncthreads();
@@ -2294,7 +2305,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       bool fail = false;
       for (int c = 0; c < nch; ++c) {
         const int st = stage;
-        if (nst > 1 && c + 1 < nch) issue(c + 1, st ^ 1);
+        if (!ONE && nst > 1 && c + 1 < nch) issue(c + 1, st ^ 1);
         const bool ok = mbar_wait(&s.bar[st], (phb >> st) & 1u, kWaitLimit);
         if (__syncthreads_or(!ok)) {  // uniform over the team
           fail = true;
@@ -2304,7 +2315,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
         infl &= ~(1u << st);
         const int clen = min(TDC, d - c * TDC);
         const T* rows = rowbase + (size_t)st * TM * C::RS;
-        if (PREC >= 1 && c + 1 == nch) {  // each row's terms, from its tail
+        if (PREC >= 1 && (ONE || c + 1 == nch)) {  // each row's terms, from its tail
           if (has) {
             const int cpy = (clen + C::VEC - 1) / C::VEC * C::VEC;
             const float2 t = *reinterpret_cast<const float2*>(rows + (size_t)row * C::RS + cpy);
@@ -2317,7 +2328,7 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
           constexpr int KB = 16 / (int)sizeof(T);  // elements per 16 bytes
           const int ksteps = (clen + 2 * KB - 1) / (2 * KB);
           const int KI = (k + 15) >> 4, NJ = (m + 7) >> 3;
-          const bool first_c = (c == 0), last_c = (c + 1 == nch);
+          const bool first_c = ONE || c == 0, last_c = ONE || c + 1 == nch;
           const int g = lane >> 2, tg = lane & 3;
           for (int t = warp; t < kTeamTiles; t += 2) {
             int I, J;
@@ -2542,13 +2553,23 @@ __global__ void __launch_bounds__(TM, 8) rnd_join_team_kernel(JoinArgs a) {
       }
       __syncthreads();
     };
+    auto by_chunks = [&](auto ex_tag) {
+      if constexpr (PREC == 1) {  // (the one-chunk variant for the BF16 form only: compile time)
+        if (nchd == 1)
+          record(ex_tag, std::true_type{});
+        else
+          record(ex_tag, std::false_type{});
+      } else {
+        record(ex_tag, std::false_type{});
+      }
+    };
     if constexpr (PREC >= 1) {
       if (exact)
-        record(std::true_type{});
+        by_chunks(std::true_type{});
       else
-        record(std::false_type{});
+        by_chunks(std::false_type{});
     } else {
-      record(std::false_type{});
+      by_chunks(std::false_type{});
     }
     if (quit) return;
     p = pnext;
