@@ -2765,13 +2765,14 @@ __device__ __forceinline__ void list_insert(uint64_t& x0, uint64_t& x1, uint64_t
 
 // list_insert when every copy of an id carries one key up to the old bit (a build's canonical
 // distances) and b is new: a copy already listed sits where b would go, and stays as it is.
+// Keys compare through (key | 1), which orders them as (dist, id) whatever the old bits.
 __device__ __forceinline__ void list_insert_exact(uint64_t& x0, uint64_t& x1, uint64_t b, int R) {
   const int lane = threadIdx.x & 31;
-  const uint64_t bk = b >> 1;  // (dist, id)
-  const int pos = __popc(__ballot_sync(0xffffffffu, (x0 >> 1) < bk)) + __popc(__ballot_sync(0xffffffffu, (x1 >> 1) < bk));
+  const uint64_t bk = b | 1ull;
+  const int pos = __popc(__ballot_sync(0xffffffffu, (x0 | 1ull) < bk)) + __popc(__ballot_sync(0xffffffffu, (x1 | 1ull) < bk));
   if (pos >= R) return;
   const uint64_t at = __shfl_sync(0xffffffffu, pos < 32 ? x0 : x1, pos & 31);
-  if ((at >> 1) == bk) return;  // listed already (an empty slot never matches a finite key)
+  if ((at | 1ull) == bk) return;  // listed already (an empty slot never matches a finite key)
   const uint64_t x0last = __shfl_sync(0xffffffffu, x0, 31);
   uint64_t u0 = __shfl_up_sync(0xffffffffu, x0, 1);
   uint64_t u1 = __shfl_up_sync(0xffffffffu, x1, 1);
@@ -2904,60 +2905,70 @@ __device__ __forceinline__ void merge_chunk(uint64_t& x0, uint64_t& x1, uint64_t
 
 // merge_chunk when every copy of an id proposed to the target carries the same distance (the
 // pools' distances all come from the library's canonical FP32 arithmetic or exact tiles, as
-// in a whole build) and the proposals are new: copies of
-// one id then have equal keys up to the old bit, so duplicates are found by comparing keys --
-// adjacent proposals after the sort, and a proposal against its lower bound in the row (the
-// row's copy, old or not, is the one kept) -- with no id hash.  Then, as in merge_chunk, each
-// kept element's rank in the merged row is its index in its own sorted list plus the number
-// of smaller keys in the other list.
+// in a whole build) and the proposals are new: copies of one id then have equal keys up to the
+// old bit, so duplicates are found by comparing keys, with no id hash and no sort:
+//   gap    each proposal's lower bound lo in the row (the number of row entries with a smaller
+//          key; a fixed six-step search), which is also where a row copy of it would sit (the
+//          row's copy, old or not, is the one kept); proposals with lo >= R fall past the
+//          truncation and take no further part (every kept proposal before them is smaller);
+//   rank   the proposals ordered by gap: six ballots over the bits of lo give each proposal the
+//          set of proposals in lower gaps and the set in its own gap; within a gap (mostly a
+//          single proposal) duplicates keep their lowest lane, and keys are compared directly;
+//   place  a kept proposal's merged position is its rank among the kept proposals plus lo; the
+//          row entries fill the other positions in order, so position p that no proposal
+//          took holds row entry p - (positions below p that proposals took): two ballots
+//          (warp OR reductions) of the taken positions replace a search per row entry.
+// Keys compare through (key | 1): (x | 1) < (y | 1) iff x >> 1 < y >> 1 (order and equality
+// of (dist, id), whatever the old bits).
 __device__ __forceinline__ void merge_chunk_exact(uint64_t& x0, uint64_t& x1, uint64_t b, int R, MergeScratch& ms) {
   const int lane = threadIdx.x & 31;
   const uint32_t below = lane == 0 ? 0u : (0xffffffffu >> (32 - lane));
-  {
-    uint64_t t[1] = {b};
-    warp_sort_u64<1>(t);
-    b = t[0];
-  }
-  const uint64_t bk = b >> 1;  // (dist, id)
-  const uint64_t prev = __shfl_up_sync(0xffffffffu, bk, 1);
-  bool keep = b != kEmpty && (lane == 0 || prev != bk);  // the first of each run of copies
+  const uint64_t bk = b | 1ull;
   ms.row[lane] = x0;
   ms.row[lane + 32] = x1;
   const int nr = __popc(__ballot_sync(0xffffffffu, x0 != kEmpty)) + __popc(__ballot_sync(0xffffffffu, x1 != kEmpty));
   __syncwarp();
-  int lo = 0;  // row entries with a smaller key
-  if (keep) {
-    int hi = nr;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((ms.row[mid] >> 1) < bk) lo = mid + 1; else hi = mid;
-    }
-    if (lo < nr && (ms.row[lo] >> 1) == bk) keep = false;  // the row holds this copy already
-  }
-  const unsigned kb = __ballot_sync(0xffffffffu, keep);
-  const int nb = __popc(kb), ib = __popc(kb & below);
-  if (keep) {
-    ms.prop[ib] = b;
-    ms.out[ib + lo] = b;
-  }
-  __syncwarp();
+  // gap: row entries with a smaller key (empty slots, all ones, never are)
+  int lo = 0;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const uint64_t xk = h ? x1 : x0;
-    if (xk != kEmpty) {
-      const uint64_t xkk = xk >> 1;
-      int l2 = 0, h2 = nb;  // kept proposals with a smaller key
-      while (l2 < h2) {
-        const int mid = (l2 + h2) >> 1;
-        if ((ms.prop[mid] >> 1) < xkk) l2 = mid + 1; else h2 = mid;
-      }
-      ms.out[lane + 32 * h + l2] = xk;
-    }
+  for (int st = 32; st > 0; st >>= 1)
+    if ((ms.row[lo + st - 1] | 1ull) < bk) lo += st;
+  if (lo == 63 && (ms.row[63] | 1ull) < bk) lo = 64;
+  const bool cand = b != kEmpty && lo < R && (ms.row[lo] | 1ull) != bk;  // not listed already
+  // rank: the proposals in lower gaps (lt) and in this one (eq), among the candidates
+  unsigned eq = __ballot_sync(0xffffffffu, cand), lt = 0u;
+#pragma unroll
+  for (int bit = 5; bit >= 0; --bit) {
+    const bool one = (lo >> bit) & 1;
+    const unsigned B = __ballot_sync(0xffffffffu, one);
+    lt |= one ? (eq & ~B) : 0u;
+    eq &= one ? B : ~B;
   }
+  ms.prop[lane] = bk;
   __syncwarp();
-  const int tot = min(nb + nr, R);
-  x0 = lane < tot ? ms.out[lane] : kEmpty;
-  x1 = lane + 32 < tot ? ms.out[lane + 32] : kEmpty;
+  const unsigned others = eq & ~(1u << lane);
+  bool keep = cand;
+  if (cand)
+    for (unsigned g = others & below; g; g &= g - 1)
+      if (ms.prop[__ffs(g) - 1] == bk) {  // a lower lane holds the same key
+        keep = false;
+        break;
+      }
+  const unsigned kb = __ballot_sync(0xffffffffu, keep);
+  int w = 0;  // kept proposals of the same gap with a smaller key
+  if (keep)
+    for (unsigned g = others & kb; g; g &= g - 1) w += ms.prop[__ffs(g) - 1] < bk ? 1 : 0;
+  // place
+  const int pos = __popc(lt & kb) + w + lo;
+  if (keep && pos < 64) ms.out[pos] = b;
+  const unsigned t0 = __reduce_or_sync(0xffffffffu, (keep && pos < 32) ? 1u << pos : 0u);
+  const unsigned t1 = __reduce_or_sync(0xffffffffu, (keep && pos >= 32 && pos < 64) ? 1u << (pos - 32) : 0u);
+  __syncwarp();
+  const int tot = min(__popc(kb) + nr, R);
+  const int f0 = lane - __popc(t0 & below);                        // row entries before position lane
+  const int f1 = 32 - __popc(t0) + lane - __popc(t1 & below);      // ... before position lane + 32
+  x0 = lane < tot ? (((t0 >> lane) & 1u) ? ms.out[lane] : ms.row[f0]) : kEmpty;
+  x1 = lane + 32 < tot ? (((t1 >> lane) & 1u) ? ms.out[lane + 32] : ms.row[f1]) : kEmpty;
   __syncwarp();
 }
 
@@ -3000,18 +3011,20 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
   // other, only those that received proposals or still need their base pool copied
   for (int64_t u0 = ((int64_t)blockIdx.x * 8 + warp) * 32; u0 < a.n; u0 += (int64_t)gridDim.x * 8 * 32) {
     const int64_t ul = u0 + lane;
-    int64_t b0l = 0, cl = 0;
+    int64_t b0l = 0;
+    int cl = 0;  // a target's proposal count (its bucket count is an int32_t)
     bool keptl = true;
     if (ul < a.n) {
       if (a.bucket) {
         b0l = a.off[ul];
-        cl = a.off[ul + 1] - b0l;
+        cl = (int)(a.off[ul + 1] - b0l);
       }
       keptl = in_place || (a.active && a.active[ul]);
     }
     // a target with nothing proposed whose pool is in place is final already (and holds no
     // new entry: the join rewrote every row it pruned as old)
     unsigned work = __ballot_sync(0xffffffffu, ul < a.n && (cl != 0 || !keptl));
+    const unsigned keptm = __ballot_sync(0xffffffffu, keptl);
     const bool merged_l = (work >> lane) & 1u;
     // the base pool sizes of the targets to merge, in one load
     const int nal = merged_l ? (keptl ? a.deg_out[ul] : a.deg_in[ul]) : 0;
@@ -3020,8 +3033,9 @@ __global__ void __launch_bounds__(256, 5) select_kernel(SelectArgs a) {
       const int tl = __ffs(work) - 1;
       work &= work - 1;
       const int64_t u = u0 + tl;
-      const int64_t b0 = __shfl_sync(0xffffffffu, b0l, tl), c = __shfl_sync(0xffffffffu, cl, tl);
-      const bool kept = __shfl_sync(0xffffffffu, keptl ? 1 : 0, tl) != 0;
+      const int64_t b0 = __shfl_sync(0xffffffffu, b0l, tl);
+      const int c = __shfl_sync(0xffffffffu, cl, tl);
+      const bool kept = (keptm >> tl) & 1u;
       if (!in_bounds(b0 >= 0 && c >= 0 && b0 + c <= a.n * R, a.err)) continue;
       const uint64_t* base = kept ? a.keys_out + u * R : a.keys_in + u * R;
       const int na = __shfl_sync(0xffffffffu, nal, tl);
