@@ -82,6 +82,15 @@ int sm_count() {
   return v;
 }
 
+// 16-byte asynchronous copy global -> shared (the L1-bypassing form): nbytes (0..16) are read
+// from g, the rest of the 16 bytes are written as zeros; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* sm, const void* g, int nbytes) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(g), "r"(nbytes) : "memory");
+}
+// waits for every cp_async16 this thread issued (a hardware wait: the copies always complete)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // =====================================================================================
 // rnd_init: one warp per vertex.
 //   Sampling follows the sequential definition exactly: candidate j = 0, 1, 2, ... is
@@ -155,28 +164,26 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
     const int CH = use_b ? 2 * IC : IC;  // dimensions per chunk
     for (int c0 = 0; c0 < d; c0 += CH) {
       const int clen = min(CH, d - c0);
+      // every 16-byte granule of the chunk is copied asynchronously (all of them in flight at
+      // once, no registers held); the bytes past d are filled with zeros by the copy itself
       if (use_b) {
-        // row t / GB, granule t % GB of 8 BF16 values (those past d are zero)
+        // row t / GB, granule t % GB of 8 BF16 values
         for (int t = lane; t < (S + 1) * GB; t += 32) {
           const int r = t / GB, q = t % GB;  // (GB is a power of two)
           const int64_t src = r < S ? (int64_t)acc[r] : v;
-          uint4 u = make_uint4(0u, 0u, 0u, 0u);
-          if (8 * q < clen) u = *reinterpret_cast<const uint4*>(Xbs + src * ldb + c0 + 8 * q);
-          *reinterpret_cast<uint4*>(rows_b + r * RSB + 8 * q) = u;
+          const int nbytes = 2 * max(0, min(8, clen - 8 * q));
+          cp_async16(rows_b + r * RSB + 8 * q, Xbs + src * ldb + c0 + (nbytes ? 8 * q : 0), nbytes);
         }
       } else {
-        // row t / GF, granule t % GF of 4 FP32 values (those past d are zero)
+        // row t / GF, granule t % GF of 4 FP32 values (past d: zero, as row_dist's tail)
         for (int t = lane; t < (S + 1) * GF; t += 32) {
           const int r = t / GF, q = t % GF;  // (GF is a power of two)
           const int64_t src = r < S ? (int64_t)acc[r] : v;
-          float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          if (4 * q < clen) {
-            val = *reinterpret_cast<const float4*>(X + src * ld + c0 + 4 * q);
-            if (4 * q + 4 > clen) val = mask4(val, clen - 4 * q);  // past d: zero, as row_dist's tail
-          }
-          *reinterpret_cast<float4*>(&rows[r][4 * q]) = val;
+          const int nbytes = 4 * max(0, min(4, clen - 4 * q));
+          cp_async16(&rows[r][4 * q], X + src * ld + c0 + (nbytes ? 4 * q : 0), nbytes);
         }
       }
+      cp_async_wait_all();
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < E; ++j) {
