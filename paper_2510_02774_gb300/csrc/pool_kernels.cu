@@ -100,13 +100,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // =====================================================================================
 // E: pool entries per lane (32 E >= R); IW: warps per CTA (E = 2, pools of up to 64 entries:
 // 4 warps; E = 8, up to 256 entries: 2 warps, so that the staged rows stay within the static
-// shared memory); IC: FP32 dimensions per staged chunk (64 bytes of each row per round trip).
-// A BF16 source is staged in the same bytes as bfloat16 values, 2 IC dimensions per chunk.
-// (Larger chunks cut round trips but the bigger buffer halves the resident warps: 32-dimension
-// FP32 chunks made the 1M-point init 1.9x slower.)
+// shared memory); IC: FP32 dimensions per staged chunk (4 IC bytes of each row per round
+// trip); SR: staged rows per warp (S + 1 at most: the drawn rows and v's own).  A BF16 source
+// is staged in the same bytes as bfloat16 values, 2 IC dimensions per chunk.  Samples of up to
+// 32 entries stage 33 rows of 128-byte chunks; larger ones 32 E + 1 rows of 64-byte chunks (a
+// bigger buffer would cost resident warps).
 // Xb (may be null): a BF16 copy of the rows (ldb elements per row); when qflags say that every
 // value is exact in BF16, the drawn rows are read from it -- the same values in half the bytes.
-template <int METRIC, int E, int IW, int IC>
+template <int METRIC, int E, int IW, int IC, int SR>
 __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restrict__ X, int64_t n,
                                                            int d, int ld, int S, int R, uint64_t seed,
                                                            uint64_t* __restrict__ keys,
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(IW * 32) rnd_init_kernel(const float* __restri
   constexpr int GB = IC / 4;        // BF16 granules (8 dimensions) per staged row chunk
   __shared__ int32_t acc_ids[IW][32 * E];
   // the chunk of each drawn row (rows 0..S-1) and of v itself (row S), 16-byte granules
-  __shared__ __align__(16) float stage[IW][32 * E + 1][RSF];
+  __shared__ __align__(16) float stage[IW][SR][RSF];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* acc = acc_ids[warp];
   float(*rows)[RSF] = stage[warp];
@@ -255,20 +256,27 @@ cudaError_t launch_pool_init(const float* X, int64_t n, int d, int ld, int metri
   const __nv_bfloat16* Xb = (Xb16 && qflags) ? static_cast<const __nv_bfloat16*>(Xb16) : nullptr;
   const uint64_t magic = ~0ull / (uint64_t)(n - 1);  // the draws' modulus of a single build (n >= 2)
   ProfScope ps("rnd_init", st);
-  if (R <= kTeamMaxM) {
+  if (R <= kTeamMaxM && S <= 32) {
     constexpr int IW = 4;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
     if (metric == 0)
-      rnd_init_kernel<0, 2, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<0, 2, IW, 32, 33><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
     else
-      rnd_init_kernel<1, 2, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<1, 2, IW, 32, 33><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+  } else if (R <= kTeamMaxM) {
+    constexpr int IW = 4;
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 16);
+    if (metric == 0)
+      rnd_init_kernel<0, 2, IW, 16, 65><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+    else
+      rnd_init_kernel<1, 2, IW, 16, 65><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
   } else {  // pools of up to 256 entries
     constexpr int IW = 2;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, IW), (int64_t)sm_count() * 32);
     if (metric == 0)
-      rnd_init_kernel<0, 8, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<0, 8, IW, 16, 257><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
     else
-      rnd_init_kernel<1, 8, IW, 16><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
+      rnd_init_kernel<1, 8, IW, 16, 257><<<(unsigned)blocks, IW * 32, 0, st>>>(X, n, d, ld, S, R, seed, keys, deg, vseg, Xb, ldb, qflags, magic);
   }
   return cudaGetLastError();
 }
