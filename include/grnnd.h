@@ -242,6 +242,10 @@ typedef struct grnnd_kernel_time {
     double ms;
 } grnnd_kernel_time;
 GRNND_API int grnnd_profile_begin(void);
+/* grnnd_profile_begin that times only the kernels named in `names` (host string, a
+ * comma-separated list such as "rnd_join_warp,rnd_join_team"; NULL or "" times every
+ * kernel): the other launches get no events, so the timing perturbs them not at all. */
+GRNND_API int grnnd_profile_begin_only(const char *names);
 GRNND_API int grnnd_profile_end(grnnd_kernel_time *out, int32_t max_entries, int32_t *n_entries);
 
 /* ------------------------------------------------------------------------- */

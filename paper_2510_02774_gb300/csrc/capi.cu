@@ -153,6 +153,7 @@ struct ProfRec {
 };
 struct Profiler {
   bool on = false;
+  std::vector<std::string> only;  // kernel names to time (empty: every kernel)
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   const char* open_name = nullptr;
@@ -178,6 +179,11 @@ bool prof_on() { return g_prof.on; }
 
 void prof_start(const char* name, cudaStream_t st) {
   if (!g_prof.on) return;
+  if (!g_prof.only.empty()) {
+    bool hit = false;
+    for (const auto& o : g_prof.only) hit = hit || o == name;
+    if (!hit) return;  // not timed: no events around this launch
+  }
   g_prof.open_name = name;
   g_prof.open_ev = g_prof.get();
   cudaEventRecord(g_prof.open_ev, st);
@@ -204,7 +210,23 @@ int grnnd_profile_begin(void) {
     g_prof.pool.push_back(r.b);
   }
   g_prof.recs.clear();
+  g_prof.only.clear();
   g_prof.on = true;
+  return GRNND_OK;
+}
+
+int grnnd_profile_begin_only(const char* names) {
+  grnnd_profile_begin();
+  if (names) {
+    const std::string all(names);
+    size_t a = 0;
+    while (a <= all.size()) {
+      size_t b = all.find(',', a);
+      if (b == std::string::npos) b = all.size();
+      if (b > a) g_prof.only.push_back(all.substr(a, b - a));
+      a = b + 1;
+    }
+  }
   return GRNND_OK;
 }
 

@@ -82,6 +82,7 @@ class RequestInfo(ctypes.Structure):
 
 _SIGS = {
     "grnnd_profile_begin": (ctypes.c_int, []),
+    "grnnd_profile_begin_only": (ctypes.c_int, [ctypes.c_char_p]),
     "grnnd_profile_end": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     # name: (restype, argtypes)
     "grnnd_params_default": (None, [ctypes.POINTER(Params)]),
@@ -204,9 +205,13 @@ def _check(rc: int):
 # torch helpers (device memory and streams only)
 # ---------------------------------------------------------------------------------------
 
-def profile_begin():
-    """Starts per-kernel CUDA-event timing of this thread's library launches."""
-    _check(lib().grnnd_profile_begin())
+def profile_begin(only=None):
+    """Starts per-kernel CUDA-event timing of this thread's library launches; `only` (a list
+    of kernel names) limits the timing to those kernels."""
+    if only:
+        _check(lib().grnnd_profile_begin_only(",".join(only).encode()))
+    else:
+        _check(lib().grnnd_profile_begin())
 
 
 def profile_end() -> dict:

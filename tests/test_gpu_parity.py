@@ -823,6 +823,25 @@ def test_build_batch_row_copies_give_the_same_graphs(G, precision):
             assert (u == v).all()
 
 
+def test_profile_times_only_the_named_kernels(G):
+    """grnnd_profile_begin_only brackets only the named kernels with events; the plain form
+    brackets every launch.  The build's result does not depend on either."""
+    X = synth.small_integers(2000, 16, -8, 8, seed=4)
+    kw = dict(S=8, R=16, T1=2, T2=3, seed=1)
+    want = G.build(X, **kw).to_numpy()
+    G.profile_begin(only=["select", "rnd_init"])
+    got = G.build(X, **kw).to_numpy()
+    k = G.profile_end()
+    assert set(k) == {"select", "rnd_init"}, k
+    assert k["rnd_init"][0] == 1 and k["select"][0] >= 1 and k["select"][1] > 0
+    G.profile_begin()
+    G.build(X, **kw)
+    k = G.profile_end()
+    assert {"select", "rnd_init", "prep", "scatter"} <= set(k), k
+    for a, b in zip(want, got):
+        assert (a == b).all()
+
+
 def test_autotune_pool_picks_a_capacity_that_reaches_the_target(G, orc):
     """grnnd_autotune_pool measures each candidate R's recall on held-out rows against exact
     k-NN; its choice must reach the target when a candidate does, and its recall must equal
