@@ -796,9 +796,12 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    e2e_ms = []
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        e2e_step()
+        t1 = time.perf_counter()
+        e2e_step()  # returns after the graph's read-back has completed
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t
     t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
@@ -899,7 +902,8 @@ def main():
                 "bf16_speedup_vs_fp32": (forms["fp32"]["total_ms"] / forms["bf16"]["total_ms"]
                                          if "fp32" in forms and "bf16" in forms else None),
                 "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n * d * 4,
-                        "d2h_bytes_per_step": n * w["R"] * 4 + n * 4},
+                        "d2h_bytes_per_step": n * w["R"] * 4 + n * 4,
+                        "p50_ms": statistics.median(e2e_ms), "p99_ms": _pct(e2e_ms, 0.99)},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "kernels_ms": {k: round(v[1], 3) for k, v in sorted(kern_all.items(), key=lambda kv: -kv[1][1])},
                 "kernels_ms_source": (f"{args.steps} further builds with events around every launch "
