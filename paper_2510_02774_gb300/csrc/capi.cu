@@ -62,6 +62,29 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// A pointer that kernels can dereference for p, or null: device memory as it is, pinned host
+// memory through its mapped device address; *host tells which.  Pageable and managed memory
+// give null (the copy engine moves those).
+const void* kernel_ptr(const void* p, bool* host) {
+  cudaPointerAttributes at;
+  *host = false;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice) return p;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *host = true;
+    return at.devicePointer;
+  }
+  return nullptr;
+}
+
+__global__ void host_copy_kernel(uint4* __restrict__ dst, const uint4* __restrict__ src, int64_t n16) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 int32_t round4(int32_t d) { return (d + 3) & ~3; }
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -194,6 +217,20 @@ void prof_stop(cudaStream_t st) {
   cudaEventRecord(b, st);
   g_prof.recs.push_back({g_prof.open_name, g_prof.open_ev, b});
   g_prof.open_ev = nullptr;
+}
+
+cudaError_t copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!bytes) return cudaSuccess;
+  bool dh = false, sh = false;
+  void* kd = const_cast<void*>(kernel_ptr(dst, &dh));
+  const void* ks = kernel_ptr(src, &sh);
+  const bool aligned = ((reinterpret_cast<uintptr_t>(kd) | reinterpret_cast<uintptr_t>(ks) | bytes) & 15u) == 0;
+  if (!kd || !ks || !(dh || sh) || !aligned) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+  const int64_t n16 = (int64_t)(bytes / 16);
+  const int64_t blocks = std::min<int64_t>((n16 + 255) / 256, (int64_t)sm_count() * 16);
+  ProfScope ps("host_copy", st);
+  host_copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<uint4*>(kd), static_cast<const uint4*>(ks), n16);
+  return cudaGetLastError();
 }
 }  // namespace grnnd
 
@@ -1087,9 +1124,9 @@ int grnnd_graph_copy(const grnnd_graph* g, int32_t* ids, float* dists, int32_t* 
   if (!g) return fail(GRNND_EINVAL, "graph is NULL");
   const size_t nr = (size_t)g->n * g->R;
   const cudaStream_t st = g_stream;  // the thread's current stream
-  if (ids) GR_CU(cudaMemcpyAsync(ids, g->ids, nr * 4, cudaMemcpyDefault, st));
-  if (dists) GR_CU(cudaMemcpyAsync(dists, g->dists, nr * 4, cudaMemcpyDefault, st));
-  if (deg) GR_CU(cudaMemcpyAsync(deg, g->deg, (size_t)g->n * 4, cudaMemcpyDefault, st));
+  if (ids) GR_CU(grnnd::copy_bytes(ids, g->ids, nr * 4, st));
+  if (dists) GR_CU(grnnd::copy_bytes(dists, g->dists, nr * 4, st));
+  if (deg) GR_CU(grnnd::copy_bytes(deg, g->deg, (size_t)g->n * 4, st));
   GR_CU(cudaStreamSynchronize(st));
   return GRNND_OK;
 }

@@ -48,11 +48,19 @@ constexpr int kTailCopy = 16;
 // BF16 copy (row stride ldb = d rounded up to 16, plus the tail), per-row (norm^2, residual)
 // and dataset flags; 2: an FP8-e4m3 copy (ldb = d rounded up to 32, plus the tail) with the
 // same per-row terms, the row's scale exponent in the low byte of the residual.
+// bytes from src to dst on stream st, either side device or host memory.  When one side is
+// pinned (page-locked, mapped) host memory, both are 16-byte aligned and bytes is a multiple
+// of 16, a kernel moves them with 16-byte loads and stores over the host link instead of the
+// copy engine: the same rate (about 210 GB/s up, 190 GB/s down), without the copy engine's
+// periodic stalls between builds (copies of 10-25 ms instead of 1.3-2.4 ms, about every
+// 0.5 s).  Otherwise cudaMemcpyAsync.
+cudaError_t copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 // n rows of d floats into rows of ld >= d floats.  Rows that need no padding go as one
-// contiguous copy (about 210 GB/s from pinned host memory for 512 MB), not as a pitched copy.
+// contiguous copy (copy_bytes), not as a pitched copy.
 inline cudaError_t copy_rows(float* dst, int ld, const float* src, int d, int64_t n, cudaMemcpyKind kind,
                              cudaStream_t st) {
-  if (ld == d) return cudaMemcpyAsync(dst, src, (size_t)n * d * 4, kind, st);
+  if (ld == d) return copy_bytes(dst, src, (size_t)n * d * 4, st);
   return cudaMemcpy2DAsync(dst, (size_t)ld * 4, src, (size_t)d * 4, (size_t)d * 4, (size_t)n, kind, st);
 }
 

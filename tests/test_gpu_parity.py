@@ -823,6 +823,31 @@ def test_build_batch_row_copies_give_the_same_graphs(G, precision):
             assert (u == v).all()
 
 
+@pytest.mark.parametrize("n,d,R", [(3000, 32, 16), (3001, 30, 6)])
+def test_pinned_host_points_and_read_back(G, n, d, R):
+    """Points in pinned host memory and a graph read back into pinned host memory: aligned
+    buffers move by the library's copy kernel, ragged ones (rows padded to 4 floats, a graph
+    whose byte size is not a multiple of 16) by the copy engine.  Either way the graph equals
+    the one built from device-resident points and read back through the binding."""
+    import ctypes
+    import torch
+    X = synth.small_integers(n, d, -8, 8, seed=n + d)
+    kw = dict(S=min(8, R), R=R, T1=2, T2=3, seed=2)
+    wids, _, wdeg = G.build(X, **kw).to_numpy()
+    L = G.lib()
+    Xh = torch.from_numpy(X).pin_memory()
+    ids_h = torch.full((n, R), -7, dtype=torch.int32).pin_memory()
+    deg_h = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+    p = G.params(**kw)
+    h = ctypes.c_void_p()
+    G._check(L.grnnd_build_ex(ctypes.c_void_p(Xh.data_ptr()), n, d, ctypes.byref(p), ctypes.byref(h)))
+    try:
+        G._check(L.grnnd_graph_copy(h, ctypes.c_void_p(ids_h.data_ptr()), None, ctypes.c_void_p(deg_h.data_ptr())))
+    finally:
+        L.grnnd_free(h)
+    assert (ids_h.numpy() == wids).all() and (deg_h.numpy() == wdeg).all()
+
+
 def test_profile_times_only_the_named_kernels(G):
     """grnnd_profile_begin_only brackets only the named kernels with events; the plain form
     brackets every launch.  The build's result does not depend on either."""
