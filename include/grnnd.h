@@ -14,7 +14,11 @@
  *     output handles are set to NULL.
  *   - "device" pointers are CUDA device (or managed) memory on the current
  *     device; "host or device" pointers are classified with
- *     cudaPointerGetAttributes and copied as needed.
+ *     cudaPointerGetAttributes and copied as needed.  Pinned (page-locked)
+ *     host buffers that are 16-byte aligned, with a byte size that is a
+ *     multiple of 16, are moved by the library's own copy kernel (16-byte loads
+ *     and stores over the host link); pageable, misaligned or ragged buffers by
+ *     cudaMemcpyAsync.  The bytes are the same either way.
  *   - Point matrices are row-major float32, one row per point.  Step-level
  *     calls take a leading dimension `ld` (floats per row): ld >= d, ld % 4 == 0,
  *     and the base address 16-byte aligned (rows are moved with bulk copies).
