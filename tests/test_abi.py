@@ -188,3 +188,15 @@ def test_quantized_step_calls_validate(L):
                               ctypes.c_void_p(256), 1, 1, 1, 0, ctypes.c_void_p(256), ctypes.c_void_p(256),
                               ctypes.c_void_p(256), 1 << 30, None, None)
     assert rc == G.EINVAL and b"quantized" in L.grnnd_last_error()
+
+
+def test_profile_filter_is_host_state(L):
+    """grnnd_profile_begin_only parses its name list on the host; with no launch in between,
+    grnnd_profile_end reports no kernel, and neither call touches the GPU."""
+    G.profile_begin(only=["rnd_join_warp", "rnd_join_team"])
+    assert G.profile_end() == {}
+    G.profile_begin()
+    assert G.profile_end() == {}
+    for names in (None, b"", b",,select,"):
+        assert L.grnnd_profile_begin_only(names) == 0
+        assert G.profile_end() == {}
